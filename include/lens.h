@@ -1,0 +1,221 @@
+/*
+ * lens.h -- C ABI of liblens.so: GB300 (sm_103a) FMM-IPM microlensing hot path.
+ *
+ * Method: Jimenez-Vicente & Mediavilla (2022), "Fast Multipole Method for
+ * Gravitational Lensing. Application to High Magnification Quasar
+ * Microlensing".  The library evaluates the lens equation (Eq. 1)
+ *
+ *     y = diag(1 - kappa_s - gamma, 1 - kappa_s + gamma) x
+ *         - sum_i m_i (x - x_i) / |x - x_i|^2
+ *
+ * (point lenses in Einstein units; smooth convergence kappa_s and shear
+ * gamma as allowed by the footnote to Eq. 1, shear along x1) at many rays
+ * with a Fast Multipole Method (Sec. 2.1 and Appendix A: quadtree, P2M, M2M,
+ * M2L, L2L, L2P, P2P), and turns a grid of deflected cells into a
+ * magnification map by first-order Inverse Polygon Mapping (Sec. 2.3 and the
+ * five-step FMM-IPM algorithm of Sec. 2.4, including its ray chunking).
+ *
+ * Conventions shared by every call
+ *   - Every pointer marked "dev" is CUDA device memory on the current device;
+ *     "host" pointers are ordinary host memory.  All floating-point arrays are
+ *     float64, C-contiguous.  Positions are interleaved pairs (x1, x2).
+ *   - The caller owns every buffer it passes.  A plan owns its internal
+ *     arrays, which it obtains from the caller's lens_allocator (or from
+ *     cudaMallocAsync when the allocator pointer is NULL) and frees in
+ *     lens_plan_destroy.
+ *   - Every call returns a lens_status; on error the outputs are undefined
+ *     and lens_last_error() gives a message (thread-local).  No call aborts
+ *     or throws across the ABI.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on it unless noted.
+ *   - A star exactly at a ray contributes nothing to that ray.
+ *   - Environment LENS_FAULT=alloc@K or launch@K makes the K-th internal
+ *     allocation or kernel launch of the process fail with
+ *     LENS_EFAULT_INJECTED (host-side fault injection for tests).
+ */
+#ifndef LENS_H
+#define LENS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lens_plan lens_plan; /* opaque: star tree + expansions */
+
+typedef enum {
+  LENS_OK = 0,
+  LENS_EINVAL = 1,          /* bad argument (size, order, non-finite input) */
+  LENS_ENOMEM = 2,          /* an allocation failed */
+  LENS_ECUDA = 3,           /* a CUDA runtime call or launch failed */
+  LENS_EDEPTH = 4,          /* tree needs more levels than max_depth allows */
+  LENS_EDOMAIN = 5,         /* a ray lies outside the plan's target region */
+  LENS_ETIMEOUT = 6,        /* a bounded device wait expired */
+  LENS_EFAULT_INJECTED = 7  /* LENS_FAULT fault injection fired */
+} lens_status;
+
+/* Device-memory provider for plan internals.  alloc returns a device pointer
+ * (NULL on failure) usable on `stream`; free releases it. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} lens_allocator;
+
+typedef enum {
+  LENS_FP64 = 0,      /* every step in float64 */
+  LENS_FP32_BULK = 1  /* P2P / L2P / M2P in float32 with compensated sums;
+                         P2M, M2M, M2L, L2L, P2L and y = x - alpha in float64 */
+} lens_precision;
+
+typedef struct {
+  int p;               /* expansion order (Appendix A: error ~ (ratio)^p), 1..64 */
+  int leaf_size;       /* a box is split while it holds more stars, 1..1024 */
+  int prec;            /* lens_precision */
+  int max_depth;       /* quadtree depth cap, 0 = default (28), at most 28 */
+  int has_target_box;  /* 1: target_box below is valid */
+  double target_box[4];/* [x1_min, x1_max, x2_min, x2_max]: region of the rays
+                          (local expansions are formed only for boxes that meet
+                          it); 0 = the whole root box */
+} lens_build_opts;
+
+/* Image-plane cell grid (Sec. 2.4, step 2): cell (i, j) is
+ * [x0 + i h, x0 + (i+1) h) x [y0 + j h, y0 + (j+1) h), i < nx, j < ny.
+ * Its corner rays are x = x0 + i h, y = y0 + j h for i <= nx, j <= ny. */
+typedef struct {
+  double x0, y0, h;
+  int64_t nx, ny;
+} lens_grid;
+
+/* Source-plane map window: [u0, u1) x [v0, v1) covered by npx x npy pixels;
+ * pixel (px, py) is map[py * npx + px]. */
+typedef struct {
+  double u0, u1, v0, v1;
+} lens_box;
+
+/* Flux ledger of one map (areas in image-plane units, Einstein radius^2):
+ * area_in_map + area_outside + area_dropped + area_degenerate = area_total. */
+typedef struct {
+  double cells, area_total, area_in_map, area_outside, area_dropped,
+      area_degenerate, cells_dropped, cells_degenerate;
+  int64_t chunks;      /* grid chunks processed (Sec. 2.4, step 2) */
+  double ms_deflect;   /* device time in deflection kernels */
+  double ms_ipm;       /* device time in IPM kernels */
+} lens_ipm_stats;
+
+typedef struct {
+  int64_t n_stars, n_boxes, n_leaves, n_active_boxes, n_active_leaves;
+  int64_t n_v, n_x, n_u, n_w;  /* interaction-list entries (active boxes) */
+  int64_t u_stars;             /* sum over active leaves of stars in U lists */
+  int levels, p, leaf_size, prec;
+  double root_lo[2], root_size;
+  int64_t device_bytes;        /* plan-owned device memory */
+  double ms_build;             /* device time of the last build */
+} lens_plan_info;
+
+/* ---- FMM plan ------------------------------------------------------------
+ * Builds the quadtree over the stars (Appendix A, step 1: Morton keys, radix
+ * sort, adaptive split of boxes holding more than leaf_size stars; empty
+ * quadrants stay as leaves so leaves tile the root), the upward pass (P2M,
+ * M2M: Appendix A steps 2-3) and the downward pass (M2L over interaction
+ * lists, L2L, plus the adaptive P2L lists: Appendix A steps 4-5) for every
+ * box that meets the target region.
+ *   stars_xy: dev, n x 2; masses: dev, n (any real values); n >= 1.
+ *   kappa_s, gamma: smooth field (footnote to Eq. 1).
+ *   opts: host; allocator: host or NULL (cudaMallocAsync on stream).
+ *   *out receives the plan.  Synchronises `stream` once (tree size).
+ * Errors: EINVAL (n < 1, p outside 1..64, leaf_size outside 1..1024,
+ * non-finite star or mass, bad target box), ENOMEM, ECUDA, EDEPTH. */
+lens_status lens_fmm_build(const double* stars_xy, const double* masses,
+                           int64_t n, double kappa_s, double gamma,
+                           const lens_build_opts* opts,
+                           const lens_allocator* allocator, void* stream,
+                           lens_plan** out);
+
+/* Eq. 1 at m arbitrary rays (Sec. 2.1, item 3: targets need not lie on a
+ * grid): L2P + P2P (+ M2P for the adaptive W lists), then y.
+ *   rays_xy: dev m x 2; y_out: dev m x 2; jac_out: dev m x 4 (row-major
+ *   dy/dx) or NULL.  Rays must lie in the plan's target region (EDOMAIN
+ *   otherwise; reported after a stream synchronisation).  m = 0 is a no-op. */
+lens_status lens_deflect(lens_plan* plan, const double* rays_xy, int64_t m,
+                         double* y_out, double* jac_out, void* stream);
+
+/* Eq. 1 at the corner rays of grid rows row0 .. row0+nrows-1 (corner rows,
+ * 0 <= row0, row0 + nrows <= ny + 1), all columns 0..nx.
+ *   y_out: dev nrows x (nx+1) x 2 (row-major); jac_out: dev
+ *   nrows x (nx+1) x 4 or NULL.  No ray array is materialised. */
+lens_status lens_deflect_grid(lens_plan* plan, const lens_grid* grid,
+                              int64_t row0, int64_t nrows, double* y_out,
+                              double* jac_out, void* stream);
+
+/* FMM-IPM magnification map (Sec. 2.4 steps 2-4): the grid is split into row
+ * chunks of at most max_cells_per_chunk cells (0 = sized from free device
+ * memory); each chunk's corner rays are deflected and each cell's mapped
+ * quadrilateral is apportioned over the pixels it overlaps (signed-area
+ * fraction, Sec. 2.3), accumulating
+ *     map[pix] = sum_cells h^2 * a_pix / A_P / S*     (S* = pixel area).
+ * Cells whose pixel bounding box spans more than bbox_cap_px pixels on a side
+ * are dropped and booked in the ledger (bbox_cap_px = 0: no cap).
+ *   map_out: dev npy x npx (overwritten); stats: host or NULL.
+ * Synchronises `stream` at the end. */
+lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid,
+                         const lens_box* box, int npx, int npy,
+                         int64_t max_cells_per_chunk, int bbox_cap_px,
+                         double* map_out, lens_ipm_stats* stats, void* stream);
+
+/* Adjoint of lens_deflect (not in the paper): given grad_y = dL/dy at the m
+ * rays, the transposed FMM (L2P^T, L2L^T, M2L^T, M2M^T, P2M^T, P2P^T, M2P^T,
+ * P2L^T on the same tree) gives
+ *   grad_xy: dev n x 2 = dL/dx_i (caller's star order),
+ *   grad_m:  dev n     = dL/dm_i,
+ *   grad_kg: dev 2     = dL/dkappa_s, dL/dgamma.
+ * Any output pointer may be NULL. */
+lens_status lens_deflect_adjoint(lens_plan* plan, const double* rays_xy,
+                                 int64_t m, const double* grad_y,
+                                 double* grad_xy, double* grad_m,
+                                 double* grad_kg, void* stream);
+
+/* Tree and list statistics of a plan (host struct). */
+lens_status lens_plan_info_get(const lens_plan* plan, lens_plan_info* info);
+
+void lens_plan_destroy(lens_plan* plan);
+
+/* ---- Direct sum ----------------------------------------------------------
+ * Eq. 1 by O(N* x N_x) direct summation on the GPU (Sec. 2.1): the baseline
+ * the FMM is measured against.  prec = LENS_FP64 or LENS_FP32_BULK
+ * (float32 pair terms on split hi/lo coordinates with compensated partial
+ * sums).  Buffers as in lens_deflect; scratch from allocator (may be NULL). */
+lens_status lens_direct_deflect(const double* stars_xy, const double* masses,
+                                int64_t n, double kappa_s, double gamma,
+                                const double* rays_xy, int64_t m, int prec,
+                                double* y_out, double* jac_out,
+                                const lens_allocator* allocator, void* stream);
+
+/* ---- Gaussian-source light curve (differentiable loss) --------------------
+ * F_k = sum_r w_ray exp(-|y_r - s_k|^2 / (2 sigma^2)) / (2 pi sigma^2) for
+ * |y_r - s_k| <= trunc sigma: the magnification of a Gaussian source (Sec.
+ * 2.5) at the ns samples of a track (light curves: Sec. 3.3).
+ *   y: dev m x 2 mapped rays; samples: dev ns x 2; F_out: dev ns. */
+lens_status lens_light_curve(const double* y, int64_t m, double w_ray,
+                             const double* samples, int64_t ns, double sigma,
+                             double trunc, double* F_out, void* stream);
+
+/* dL/dy for L = sum_k (F_k - T_k)^2: F, T dev ns; grad_y_out dev m x 2. */
+lens_status lens_light_curve_grad(const double* y, int64_t m, double w_ray,
+                                  const double* samples, int64_t ns,
+                                  double sigma, double trunc, const double* F,
+                                  const double* T, double* grad_y_out,
+                                  void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* lens_last_error(void);
+
+/* Library version string. */
+const char* lens_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LENS_H */

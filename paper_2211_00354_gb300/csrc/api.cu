@@ -1,0 +1,414 @@
+// api.cu -- the extern "C" boundary of liblens.so (declared in include/lens.h)
+// plus the host plumbing: status codes, thread-local error text, device
+// allocation through the caller's allocator, host-side fault injection
+// (LENS_FAULT=alloc@K | launch@K), and the chunk driver of lens_ipm_map
+// (Sec. 2.4: split the image plane into chunks, deflect each chunk with the
+// FMM, apportion its cells with IPM, accumulate one map).
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lens_internal.h"
+
+namespace lens {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<long long> g_alloc_count{0}, g_launch_count{0};
+
+struct FaultSpec {
+  long long alloc_at = -1, launch_at = -1;
+  FaultSpec() {
+    const char* e = std::getenv("LENS_FAULT");
+    if (!e) return;
+    long long k = 0;
+    if (std::sscanf(e, "alloc@%lld", &k) == 1) alloc_at = k;
+    else if (std::sscanf(e, "launch@%lld", &k) == 1) launch_at = k;
+  }
+};
+const FaultSpec& fault_spec() {
+  static FaultSpec f;
+  return f;
+}
+}  // namespace
+
+void fail(lens_status st, const std::string& msg) { throw Error{st, msg}; }
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      fail(LENS_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    fail(LENS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+void after_launch(const char* name) {
+  const long long k = ++g_launch_count;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) fail(LENS_ECUDA, std::string("launch ") + name + ": " + cudaGetErrorString(e));
+  if (fault_spec().launch_at == k) fail(LENS_EFAULT_INJECTED, std::string("injected launch fault at ") + name);
+}
+
+void fault_point_alloc() {
+  const long long k = ++g_alloc_count;
+  if (fault_spec().alloc_at == k) fail(LENS_EFAULT_INJECTED, "injected allocation fault");
+}
+
+void* DeviceAlloc::alloc(size_t bytes) {
+  fault_point_alloc();
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (custom) {
+    p = a.alloc(bytes, (void*)stream, a.ctx);
+    if (!p) fail(LENS_ENOMEM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(LENS_ENOMEM, "cudaMallocAsync(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+  }
+  return p;
+}
+
+void DeviceAlloc::release(void* p) {
+  if (!p) return;
+  if (custom) a.free(p, (void*)stream, a.ctx);
+  else cudaFreeAsync(p, stream);
+}
+
+}  // namespace lens
+
+using namespace lens;
+
+struct lens_plan {
+  Plan P;
+};
+
+#define LENS_API_BEGIN try {
+#define LENS_API_END                                   \
+  }                                                    \
+  catch (const Error& e) {                             \
+    set_last_error(e.msg);                             \
+    return e.status;                                   \
+  }                                                    \
+  catch (const std::exception& e) {                    \
+    set_last_error(std::string("internal: ") + e.what()); \
+    return LENS_ECUDA;                                 \
+  }                                                    \
+  set_last_error("");                                  \
+  return LENS_OK;
+
+namespace {
+void need(bool ok, const char* msg) {
+  if (!ok) fail(LENS_EINVAL, msg);
+}
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void check_grid(const Plan& P, const lens_grid* g) {
+  need(g != nullptr, "grid is NULL");
+  need(std::isfinite(g->x0) && std::isfinite(g->y0) && std::isfinite(g->h) && g->h > 0,
+       "grid x0, y0 must be finite and h > 0");
+  need(g->nx >= 1 && g->ny >= 1, "grid needs nx >= 1 and ny >= 1");
+  const double x1 = g->x0 + (double)g->nx * g->h, y1 = g->y0 + (double)g->ny * g->h;
+  double lo0, hi0, lo1, hi1;
+  if (P.has_target) {
+    lo0 = P.target[0]; hi0 = P.target[1]; lo1 = P.target[2]; hi1 = P.target[3];
+    if (!(g->x0 >= lo0 && x1 <= hi0 && g->y0 >= lo1 && y1 <= hi1))
+      fail(LENS_EDOMAIN, "grid extends beyond the plan's target box");
+  } else {
+    lo0 = P.root_lo[0]; hi0 = P.root_lo[0] + P.root_size;
+    lo1 = P.root_lo[1]; hi1 = P.root_lo[1] + P.root_size;
+    if (!(g->x0 >= lo0 && x1 < hi0 && g->y0 >= lo1 && y1 < hi1))
+      fail(LENS_EDOMAIN, "grid extends beyond the plan's root box");
+  }
+}
+}  // namespace
+
+extern "C" {
+
+const char* lens_last_error(void) { return g_last_error.c_str(); }
+
+const char* lens_version(void) { return "lens-fmm-gb300 0.1 (sm_103a)"; }
+
+lens_status lens_fmm_build(const double* stars_xy, const double* masses, int64_t n,
+                           double kappa_s, double gamma, const lens_build_opts* opts,
+                           const lens_allocator* allocator, void* stream, lens_plan** out) {
+  lens_plan* plan = nullptr;
+  LENS_API_BEGIN
+  need(out != nullptr, "out is NULL");
+  *out = nullptr;
+  need(opts != nullptr, "opts is NULL");
+  need(stars_xy != nullptr && masses != nullptr, "stars or masses is NULL");
+  need(n >= 1, "need at least one star");
+  need(n < (int64_t)INT32_MAX, "too many stars");
+  need(opts->p >= 1 && opts->p <= kMaxOrder, "p must be in 1..64");
+  need(opts->leaf_size >= 1 && opts->leaf_size <= 1024, "leaf_size must be in 1..1024");
+  need(opts->prec == LENS_FP64 || opts->prec == LENS_FP32_BULK, "prec must be LENS_FP64 or LENS_FP32_BULK");
+  need(opts->max_depth >= 0 && opts->max_depth <= kMaxDepth, "max_depth must be in 0..28");
+  need(std::isfinite(kappa_s) && std::isfinite(gamma), "kappa_s, gamma must be finite");
+  if (opts->has_target_box) {
+    const double* t = opts->target_box;
+    need(std::isfinite(t[0]) && std::isfinite(t[1]) && std::isfinite(t[2]) && std::isfinite(t[3]) &&
+             t[0] <= t[1] && t[2] <= t[3],
+         "target_box must be finite with min <= max");
+  }
+  plan = new lens_plan();
+  Plan& P = plan->P;
+  cudaGetDevice(&P.device);
+  P.da.stream = S(stream);
+  if (allocator && allocator->alloc && allocator->free) {
+    P.da.a = *allocator;
+    P.da.custom = true;
+  }
+  P.n = n;
+  P.p = opts->p;
+  P.leaf = opts->leaf_size;
+  P.prec = opts->prec;
+  P.depth = opts->max_depth ? opts->max_depth : kMaxDepth;
+  P.kappa_s = kappa_s;
+  P.gamma = gamma;
+  P.has_target = opts->has_target_box != 0;
+  if (P.has_target) std::memcpy(P.target, opts->target_box, sizeof(P.target));
+  cudaEvent_t e0, e1;
+  LENS_CUDA(cudaEventCreate(&e0));
+  LENS_CUDA(cudaEventCreate(&e1));
+  LENS_CUDA(cudaEventRecord(e0, S(stream)));
+  tree_build(P, stars_xy, masses, S(stream));
+  fmm_tables(P, S(stream));
+  fmm_p2m(P, S(stream));
+  fmm_m2m(P, S(stream));
+  fmm_downward(P, S(stream));
+  LENS_CUDA(cudaEventRecord(e1, S(stream)));
+  LENS_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  P.ms_build = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *out = plan;
+  plan = nullptr;
+  }
+  catch (const Error& e) {
+    set_last_error(e.msg);
+    if (plan) lens_plan_destroy(plan);
+    return e.status;
+  }
+  catch (const std::exception& e) {
+    set_last_error(std::string("internal: ") + e.what());
+    if (plan) lens_plan_destroy(plan);
+    return LENS_ECUDA;
+  }
+  set_last_error("");
+  return LENS_OK;
+}
+
+void lens_plan_destroy(lens_plan* plan) {
+  if (!plan) return;
+  Plan& P = plan->P;
+  cudaStreamSynchronize(P.da.stream);
+  for (void* p : P.owned) P.da.release(p);
+  cudaStreamSynchronize(P.da.stream);
+  delete plan;
+}
+
+lens_status lens_plan_info_get(const lens_plan* plan, lens_plan_info* info) {
+  LENS_API_BEGIN
+  need(plan && info, "NULL argument");
+  const Plan& P = plan->P;
+  std::memset(info, 0, sizeof(*info));
+  info->n_stars = P.n;
+  info->n_boxes = P.nb;
+  info->n_active_boxes = P.n_active;
+  info->n_active_leaves = P.n_active_leaves;
+  info->n_v = P.nV; info->n_x = P.nX; info->n_u = P.nU; info->n_w = P.nW;
+  info->u_stars = P.u_stars;
+  info->levels = P.nlevels;
+  info->p = P.p; info->leaf_size = P.leaf; info->prec = P.prec;
+  info->root_lo[0] = P.root_lo[0]; info->root_lo[1] = P.root_lo[1];
+  info->root_size = P.root_size;
+  info->device_bytes = P.device_bytes;
+  info->ms_build = P.ms_build;
+  info->n_leaves = -1;  // not tracked separately (n_active_leaves is)
+  LENS_API_END
+}
+
+lens_status lens_deflect(lens_plan* plan, const double* rays_xy, int64_t m, double* y_out,
+                         double* jac_out, void* stream) {
+  LENS_API_BEGIN
+  need(plan != nullptr, "plan is NULL");
+  need(m >= 0, "m must be >= 0");
+  if (m == 0) return LENS_OK;
+  need(rays_xy && y_out, "rays or y_out is NULL");
+  need(m < (int64_t)INT32_MAX, "too many rays in one call");
+  Plan& P = plan->P;
+  P.da.stream = S(stream);
+  evaluate_rays(P, rays_xy, m, y_out, jac_out, S(stream));
+  LENS_API_END
+}
+
+lens_status lens_deflect_grid(lens_plan* plan, const lens_grid* grid, int64_t row0, int64_t nrows,
+                              double* y_out, double* jac_out, void* stream) {
+  LENS_API_BEGIN
+  need(plan != nullptr, "plan is NULL");
+  Plan& P = plan->P;
+  check_grid(P, grid);
+  need(row0 >= 0 && nrows >= 0 && row0 + nrows <= grid->ny + 1, "row range outside the grid");
+  if (nrows == 0) return LENS_OK;
+  need(y_out != nullptr, "y_out is NULL");
+  P.da.stream = S(stream);
+  GridRows g{grid->x0, grid->y0, grid->h, grid->nx, grid->ny, row0, nrows};
+  evaluate_grid(P, g, y_out, jac_out, S(stream));
+  LENS_API_END
+}
+
+lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box* box, int npx,
+                         int npy, int64_t max_cells_per_chunk, int bbox_cap_px, double* map_out,
+                         lens_ipm_stats* stats, void* stream) {
+  LENS_API_BEGIN
+  need(plan != nullptr, "plan is NULL");
+  Plan& P = plan->P;
+  check_grid(P, grid);
+  need(box != nullptr && map_out != nullptr, "box or map_out is NULL");
+  need(npx >= 1 && npy >= 1, "npx, npy must be >= 1");
+  need(std::isfinite(box->u0) && std::isfinite(box->u1) && std::isfinite(box->v0) &&
+           std::isfinite(box->v1) && box->u1 > box->u0 && box->v1 > box->v0,
+       "map window must be finite with u1 > u0, v1 > v0");
+  need(max_cells_per_chunk >= 0 && bbox_cap_px >= 0, "chunk size and cap must be >= 0");
+  cudaStream_t s = S(stream);
+  P.da.stream = s;
+  const int64_t nx = grid->nx, ny = grid->ny;
+  int64_t max_cells = max_cells_per_chunk;
+  if (max_cells == 0) {
+    size_t fr = 0, tot = 0;
+    LENS_CUDA(cudaMemGetInfo(&fr, &tot));
+    // 16 B per corner + 4 B queue slot per cell, within a quarter of free memory
+    max_cells = (int64_t)std::min<double>((double)fr / 4.0 / 20.0, (double)(1ll << 30));
+  }
+  max_cells = std::min<int64_t>(max_cells, 1ll << 30);
+  int64_t rows = std::max<int64_t>(1, max_cells / nx);
+  rows = std::min<int64_t>(rows, ny);
+  need(rows * nx <= (1ll << 30) || rows == 1, "grid rows too wide for one chunk");
+
+  IpmParams ip{};
+  const double du = (box->u1 - box->u0) / npx, dv = (box->v1 - box->v0) / npy;
+  ip.u0 = box->u0; ip.v0 = box->v0;
+  ip.inv_du = 1.0 / du; ip.inv_dv = 1.0 / dv;
+  ip.a_cell = grid->h * grid->h;
+  ip.s_star = du * dv;
+  ip.scale = ip.a_cell / ip.s_star;
+  ip.npx = npx; ip.npy = npy; ip.cap = bbox_cap_px;
+
+  Scratch corners(&P.da, sizeof(PixCorner) * (size_t)(rows + 1) * (size_t)(nx + 1));
+  Scratch queue(&P.da, sizeof(int) * (size_t)rows * (size_t)nx + sizeof(int) * 4);
+  Scratch sdev(&P.da, sizeof(double) * 8);
+  int* qcount = queue.as<int>() + (size_t)rows * (size_t)nx;
+  LENS_CUDA(cudaMemsetAsync(map_out, 0, sizeof(double) * (size_t)npx * (size_t)npy, s));
+  LENS_CUDA(cudaMemsetAsync(sdev.p, 0, sdev.bytes, s));
+  std::vector<cudaEvent_t> ev;
+  auto mark = [&]() {
+    cudaEvent_t e;
+    LENS_CUDA(cudaEventCreate(&e));
+    LENS_CUDA(cudaEventRecord(e, s));
+    ev.push_back(e);
+  };
+  int64_t chunks = 0;
+  for (int64_t r0 = 0; r0 < ny; r0 += rows) {
+    const int64_t nr = std::min<int64_t>(rows, ny - r0);
+    GridRows g{grid->x0, grid->y0, grid->h, nx, ny, r0, nr + 1};
+    mark();
+    evaluate_grid_pix(P, g, corners.as<PixCorner>(), ip, s);
+    mark();
+    ipm_accumulate(corners.as<PixCorner>(), nx, nr, ip, map_out, sdev.as<double>(),
+                   queue.as<int>(), qcount, s);
+    ++chunks;
+  }
+  mark();
+  double hs[8];
+  LENS_CUDA(cudaMemcpyAsync(hs, sdev.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaStreamSynchronize(s));
+  double msd = 0, msi = 0;
+  for (size_t k = 0; k + 1 < ev.size(); ++k) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+    if (k % 2 == 0) msd += ms; else msi += ms;
+  }
+  for (auto e : ev) cudaEventDestroy(e);
+  if (stats) {
+    stats->cells = (double)nx * (double)ny;
+    stats->area_total = stats->cells * ip.a_cell;
+    stats->area_in_map = hs[2];
+    stats->area_outside = hs[3];
+    stats->area_dropped = hs[4];
+    stats->area_degenerate = hs[5];
+    stats->cells_dropped = hs[6];
+    stats->cells_degenerate = hs[7];
+    stats->chunks = chunks;
+    stats->ms_deflect = msd;
+    stats->ms_ipm = msi;
+  }
+  LENS_API_END
+}
+
+lens_status lens_deflect_adjoint(lens_plan* plan, const double* rays_xy, int64_t m,
+                                 const double* grad_y, double* grad_xy, double* grad_m,
+                                 double* grad_kg, void* stream) {
+  LENS_API_BEGIN
+  need(plan != nullptr, "plan is NULL");
+  need(m >= 0, "m must be >= 0");
+  need(m == 0 || (rays_xy && grad_y), "rays or grad_y is NULL");
+  need(m < (int64_t)INT32_MAX, "too many rays in one call");
+  Plan& P = plan->P;
+  P.da.stream = S(stream);
+  adjoint(P, rays_xy, m, grad_y, grad_xy, grad_m, grad_kg, S(stream));
+  LENS_API_END
+}
+
+lens_status lens_direct_deflect(const double* stars_xy, const double* masses, int64_t n,
+                                double kappa_s, double gamma, const double* rays_xy, int64_t m,
+                                int prec, double* y_out, double* jac_out,
+                                const lens_allocator* allocator, void* stream) {
+  LENS_API_BEGIN
+  need(n >= 0 && m >= 0, "sizes must be >= 0");
+  need(prec == LENS_FP64 || prec == LENS_FP32_BULK, "prec must be LENS_FP64 or LENS_FP32_BULK");
+  if (m == 0) return LENS_OK;
+  need(rays_xy && y_out && (n == 0 || (stars_xy && masses)), "NULL buffer");
+  DeviceAlloc da;
+  da.stream = S(stream);
+  if (allocator && allocator->alloc && allocator->free) { da.a = *allocator; da.custom = true; }
+  direct_deflect(stars_xy, masses, n, kappa_s, gamma, rays_xy, m, prec, y_out, jac_out, da,
+                 S(stream));
+  LENS_API_END
+}
+
+lens_status lens_light_curve(const double* y, int64_t m, double w_ray, const double* samples,
+                             int64_t ns, double sigma, double trunc, double* F_out, void* stream) {
+  LENS_API_BEGIN
+  need(m >= 0 && ns >= 0, "sizes must be >= 0");
+  need(sigma > 0 && trunc > 0 && std::isfinite(sigma) && std::isfinite(trunc), "sigma, trunc must be > 0");
+  if (ns == 0) return LENS_OK;
+  need(F_out && samples && (m == 0 || y), "NULL buffer");
+  light_curve(y, m, w_ray, samples, ns, sigma, trunc, F_out, S(stream));
+  LENS_API_END
+}
+
+lens_status lens_light_curve_grad(const double* y, int64_t m, double w_ray, const double* samples,
+                                  int64_t ns, double sigma, double trunc, const double* F,
+                                  const double* T, double* grad_y_out, void* stream) {
+  LENS_API_BEGIN
+  need(m >= 0 && ns >= 0, "sizes must be >= 0");
+  need(sigma > 0 && trunc > 0 && std::isfinite(sigma) && std::isfinite(trunc), "sigma, trunc must be > 0");
+  if (m == 0) return LENS_OK;
+  need(grad_y_out && y && (ns == 0 || (samples && F && T)), "NULL buffer");
+  light_curve_grad(y, m, w_ray, samples, ns, sigma, trunc, F, T, grad_y_out, S(stream));
+  LENS_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// cx.cuh -- device helpers: complex arithmetic on double2/float2, compensated
+// sums, Morton interleave, binomials.  Complex numbers z = x1 + i x2 are the
+// image-plane positions (Appendix A: expansions in complex form).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lens {
+
+template <typename R> struct cx_t;
+template <> struct cx_t<double> { using type = double2; };
+template <> struct cx_t<float> { using type = float2; };
+
+template <typename R> __host__ __device__ __forceinline__ typename cx_t<R>::type mk(R a, R b) {
+  typename cx_t<R>::type z; z.x = a; z.y = b; return z;
+}
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  C z; z.x = a.x * b.x - a.y * b.y; z.y = a.x * b.y + a.y * b.x; return z;
+}
+// a*b + c
+template <typename C> __host__ __device__ __forceinline__ C cfma(C a, C b, C c) {
+  C z;
+  z.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
+  z.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
+  return z;
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  float2 z;
+  z.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x));
+  z.y = fmaf(a.x, b.y, fmaf(a.y, b.x, c.y));
+  return z;
+}
+template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) {
+  C z; z.x = a.x * s; z.y = a.y * s; return z;
+}
+// 1/z
+__host__ __device__ __forceinline__ double2 cinv(double2 z) {
+  double d = 1.0 / (z.x * z.x + z.y * z.y);
+  return make_double2(z.x * d, -z.y * d);
+}
+__device__ __forceinline__ float frcp_fast(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float2 cinv(float2 z) {
+  float d = frcp_fast(z.x * z.x + z.y * z.y);
+  return make_float2(z.x * d, -z.y * d);
+}
+
+// Error-free sum of two floats (Knuth two-sum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// Compensated accumulator (hi, lo) += x
+struct fcomp {
+  float hi, lo;
+  __device__ __forceinline__ void add(float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo += e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Spread the low 32 bits of x to the even bit positions of a 64-bit word.
+__host__ __device__ __forceinline__ uint64_t spread2(uint64_t x) {
+  x &= 0xffffffffull;
+  x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+  x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+__host__ __device__ __forceinline__ uint32_t compact2(uint64_t x) {
+  x &= 0x5555555555555555ull;
+  x = (x | (x >> 1)) & 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0f0f0f0f0f0f0f0full;
+  x = (x | (x >> 4)) & 0x00ff00ff00ff00ffull;
+  x = (x | (x >> 8)) & 0x0000ffff0000ffffull;
+  x = (x | (x >> 16)) & 0x00000000ffffffffull;
+  return (uint32_t)x;
+}
+// Morton code: x bits at even, y bits at odd positions.
+__host__ __device__ __forceinline__ uint64_t morton(uint32_t ix, uint32_t iy) {
+  return spread2(ix) | (spread2(iy) << 1);
+}
+
+}  // namespace lens
+
+namespace lens {
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+}  // namespace lens

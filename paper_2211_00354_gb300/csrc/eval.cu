@@ -1,0 +1,519 @@
+// eval.cu -- the per-ray FMM evaluation, fused: L2P (Appendix A, step 6),
+// P2P with the adjacent leaves (step 7), M2P for the adaptive W lists, and
+// the lens equation y = diag(1-kappa_s-gamma, 1-kappa_s+gamma) x - alpha
+// (Eq. 1 with the smooth field) with an optional Jacobian dy/dx.
+//
+// One CTA works on one tile of rays that lie in one active leaf B.  The stars
+// of B's U list are staged in shared memory as offsets from B's centre (formed
+// in float64 once per CTA, then rounded), so in the float32 form a near-field
+// difference d = (x - c) - (x_j - c) keeps float32 relative accuracy even
+// far from the origin.  Each U leaf's contribution is summed in plain float32
+// and added to a two-sum (hi, lo) accumulator (compensated per source leaf).
+// The local expansion is evaluated by Horner in w = (x - c)/r with b_0 kept
+// in float64.  y is formed in float64.
+//
+// Grid path: the rays of a leaf are an index rectangle of the image-plane
+// grid (x = x0 + i h), so no ray array exists; a ray belongs to the leaf whose
+// half-open box [lo, hi) holds it.  Ray path: rays are bucketed by leaf first.
+#include <algorithm>
+#include <vector>
+
+#include "cx.cuh"
+#include "lens_internal.h"
+
+namespace lens {
+namespace {
+
+constexpr int kEvalThreads = 128;
+constexpr int kSeg = 64;    // U entries staged per round
+constexpr int kChunk = 1024; // stars staged per sub-round
+constexpr int kWChunk = 8;  // W entries staged per round
+
+struct EvalArgs {
+  const double2* spos; const double* smass;
+  const int* start; const int* count; const int* level; const int* ix; const int* iy;
+  const int* aidx;
+  const int64_t* U_off; const int* U_list; const int64_t* W_off; const int* W_list;
+  const double2* M; const double2* L;
+  const int* leaves;
+  const int64_t* tile_off;
+  int64_t nleaf;
+  double lo_x, lo_y, root_size;
+  int p;
+  double a, b;
+  // grid source
+  const int64_t* rect;  // per leaf: i0, ni, j0, nj
+  double gx0, gy0, gh;
+  int64_t gnx1, grow0;
+  // ray source
+  const double* rays; const int64_t* ray_off; const int* perm;
+  double* y; double* jac;
+  // pixel-coordinate output (IPM path): u = y1 * pinv_du + pu_off, etc.
+  PixCorner* pix;
+  double pinv_du, pu_off, pinv_dv, pv_off;
+};
+
+__device__ __forceinline__ double grid_coord(double x0, int64_t i, double h) {
+  return __dadd_rn(x0, __dmul_rn((double)i, h));
+}
+
+template <typename R> struct Acc;
+template <> struct Acc<float> {
+  fcomp v;
+  __device__ __forceinline__ void zero() { v.hi = 0.f; v.lo = 0.f; }
+  __device__ __forceinline__ void add(float x) { v.add(x); }
+  __device__ __forceinline__ double value() const { return v.value(); }
+};
+template <> struct Acc<double> {
+  double v;
+  __device__ __forceinline__ void zero() { v = 0.0; }
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
+template <typename R> __device__ __forceinline__ R rcp_r(R x);
+template <> __device__ __forceinline__ float rcp_r<float>(float x) { return frcp_fast(x); }
+template <> __device__ __forceinline__ double rcp_r<double>(double x) { return 1.0 / x; }
+
+template <typename R, bool JAC, bool GRID, bool PIX, int RPT>
+__global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
+  using C = typename cx_t<R>::type;
+  __shared__ R s_x[kChunk], s_y[kChunk], s_m[kChunk];
+  __shared__ int s_pre[kSeg + 1];
+  __shared__ int s_box[kSeg];
+  __shared__ C s_L[kMaxOrder + 1];
+  __shared__ C s_W[kWChunk][kMaxOrder + 1];
+  __shared__ R s_wx[kWChunk], s_wy[kWChunk], s_wr[kWChunk];
+  __shared__ int64_t s_leaf;
+  const int tid = threadIdx.x;
+  const int p = A.p;
+  if (tid == 0) {
+    int64_t lo = 0, hi = A.nleaf;  // largest k with tile_off[k] <= blockIdx.x
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (A.tile_off[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid;
+    }
+    s_leaf = lo;
+  }
+  __syncthreads();
+  const int64_t k = s_leaf;
+  const int B = A.leaves[k];
+  const int a = A.aidx[B];
+  const int64_t tile = (int64_t)blockIdx.x - A.tile_off[k];
+  const int lv = A.level[B];
+  const double r = A.root_size / (double)(2ull << lv);
+  const double cx = A.lo_x + (2.0 * A.ix[B] + 1.0) * r;
+  const double cy = A.lo_y + (2.0 * A.iy[B] + 1.0) * r;
+  const double2* Lb = A.L + (int64_t)B * (p + 1);
+  for (int l = tid; l <= p; l += kEvalThreads) {
+    const double2 v = Lb[l];
+    s_L[l] = mk<R>((R)v.x, (R)v.y);
+  }
+  // rays of this tile
+  int64_t nr_leaf, i0 = 0, ni = 1, j0 = 0;
+  if (GRID) {
+    i0 = A.rect[4 * k]; ni = A.rect[4 * k + 1]; j0 = A.rect[4 * k + 2];
+    nr_leaf = ni * A.rect[4 * k + 3];
+  } else {
+    nr_leaf = A.ray_off[k + 1] - A.ray_off[k];
+  }
+  R dx[RPT], dy[RPT];
+  double x1[RPT], x2[RPT];
+  int64_t oidx[RPT];
+  bool ok[RPT];
+  Acc<R> n1[RPT], n2[RPT], nj1[RPT], nj2[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int64_t loc = tile * (kEvalThreads * RPT) + (int64_t)q * kEvalThreads + tid;
+    ok[q] = loc < nr_leaf;
+    x1[q] = cx; x2[q] = cy; oidx[q] = 0;
+    if (ok[q]) {
+      if (GRID) {
+        const int64_t i = i0 + loc % ni, j = j0 + loc / ni;
+        x1[q] = grid_coord(A.gx0, i, A.gh);
+        x2[q] = grid_coord(A.gy0, j, A.gh);
+        oidx[q] = (j - A.grow0) * A.gnx1 + i;
+      } else {
+        const int64_t ridx = A.perm[A.ray_off[k] + loc];
+        x1[q] = A.rays[2 * ridx];
+        x2[q] = A.rays[2 * ridx + 1];
+        oidx[q] = ridx;
+      }
+    }
+    dx[q] = (R)(x1[q] - cx);
+    dy[q] = (R)(x2[q] - cy);
+    n1[q].zero(); n2[q].zero(); nj1[q].zero(); nj2[q].zero();
+  }
+  // ---- P2P over the U list ----------------------------------------------
+  const int64_t u_beg = A.U_off[a], u_end = A.U_off[a + 1];
+  for (int64_t e0 = u_beg; e0 < u_end; e0 += kSeg) {
+    const int ne = (int)min64(kSeg, u_end - e0);
+    __syncthreads();
+    if (tid < 32) {
+      int base = 0;
+      for (int half = 0; half < kSeg / 32; ++half) {
+        const int e = half * 32 + tid;
+        int box = -1, c = 0;
+        if (e < ne) { box = A.U_list[e0 + e]; c = A.count[box]; }
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (tid >= o) incl += v;
+        }
+        if (e < kSeg) { s_box[e] = box; s_pre[e + 1] = base + incl; }
+        base += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (tid == 0) s_pre[0] = 0;
+    }
+    __syncthreads();
+    const int tot = s_pre[ne];
+    for (int f0 = 0; f0 < tot; f0 += kChunk) {
+      const int nf = min(kChunk, tot - f0);
+      if (f0 > 0) __syncthreads();
+      for (int f = tid; f < nf; f += kEvalThreads) {
+        const int ff = f0 + f;
+        int lo = 0, hi = ne;  // entry e with s_pre[e] <= ff < s_pre[e+1]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_pre[mid] <= ff) lo = mid; else hi = mid;
+        }
+        const int st = A.start[s_box[lo]] + (ff - s_pre[lo]);
+        const double2 z = A.spos[st];
+        s_x[f] = (R)(z.x - cx);
+        s_y[f] = (R)(z.y - cy);
+        s_m[f] = (R)A.smass[st];
+      }
+      __syncthreads();
+      for (int e = 0; e < ne; ++e) {
+        const int lo = max(s_pre[e], f0) - f0;
+        const int hi = min(s_pre[e + 1], f0 + nf) - f0;
+        if (hi <= lo) continue;
+        R p1[RPT], p2[RPT], pj1[RPT], pj2[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) { p1[q] = 0; p2[q] = 0; pj1[q] = 0; pj2[q] = 0; }
+        for (int j = lo; j < hi; ++j) {
+          const R sx = s_x[j], sy = s_y[j], sm = s_m[j];
+#pragma unroll
+          for (int q = 0; q < RPT; ++q) {
+            const R d1 = dx[q] - sx, d2 = dy[q] - sy;
+            const R r2 = d1 * d1 + d2 * d2;
+            const R inv = r2 > (R)0 ? rcp_r<R>(r2) : (R)0;
+            const R w = sm * inv;
+            p1[q] += w * d1;
+            p2[q] += w * d2;
+            if (JAC) {
+              const R w2 = w * inv;
+              pj1[q] += w2 * (d2 - d1) * (d2 + d1);  // Re f'
+              pj2[q] += w2 * ((R)2 * d1 * d2);       // Im f'
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          n1[q].add(p1[q]); n2[q].add(p2[q]);
+          if (JAC) { nj1[q].add(pj1[q]); nj2[q].add(pj2[q]); }
+        }
+      }
+    }
+  }
+  // ---- M2P over the W list ----------------------------------------------
+  C fw[RPT], dfw[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) { fw[q] = mk<R>(0, 0); dfw[q] = mk<R>(0, 0); }
+  const int64_t w_beg = A.W_off[a], w_end = A.W_off[a + 1];
+  for (int64_t e0 = w_beg; e0 < w_end; e0 += kWChunk) {
+    const int nw = (int)min64(kWChunk, w_end - e0);
+    __syncthreads();
+    for (int t = tid; t < nw * (p + 1); t += kEvalThreads) {
+      const int w = t / (p + 1), kk = t - w * (p + 1);
+      const double2 v = A.M[(int64_t)A.W_list[e0 + w] * (p + 1) + kk];
+      s_W[w][kk] = mk<R>((R)v.x, (R)v.y);
+    }
+    if (tid < nw) {
+      const int Wb = A.W_list[e0 + tid];
+      const double rw = A.root_size / (double)(2ull << A.level[Wb]);
+      const double wcx = A.lo_x + (2.0 * A.ix[Wb] + 1.0) * rw;
+      const double wcy = A.lo_y + (2.0 * A.iy[Wb] + 1.0) * rw;
+      s_wx[tid] = (R)(wcx - cx);
+      s_wy[tid] = (R)(wcy - cy);
+      s_wr[tid] = (R)rw;
+    }
+    __syncthreads();
+    for (int w = 0; w < nw; ++w) {
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const C z = mk<R>(dx[q] - s_wx[w], dy[q] - s_wy[w]);
+        const C inv = cinv(z);
+        const C qq = mk<R>(inv.x * s_wr[w], inv.y * s_wr[w]);
+        C s = s_W[w][p];
+        for (int kk = p - 1; kk >= 0; --kk) s = cfma(s, qq, s_W[w][kk]);
+        fw[q] = cfma(s, inv, fw[q]);
+        if (JAC) {
+          C t = mk<R>((R)(p + 1) * s_W[w][p].x, (R)(p + 1) * s_W[w][p].y);
+          for (int kk = p - 1; kk >= 0; --kk)
+            t = cfma(t, qq, mk<R>((R)(kk + 1) * s_W[w][kk].x, (R)(kk + 1) * s_W[w][kk].y));
+          const C inv2 = cmul(inv, inv);
+          const C d = cmul(t, inv2);
+          dfw[q] = mk<R>(dfw[q].x - d.x, dfw[q].y - d.y);
+        }
+      }
+    }
+  }
+  // ---- L2P + epilogue ----------------------------------------------------
+  __syncthreads();
+  const R ir = (R)(1.0 / r);
+  const double2 b0 = Lb[0];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    if (!ok[q]) continue;
+    const C w = mk<R>(dx[q] * ir, dy[q] * ir);
+    C f = mk<R>(0, 0);
+    C df = mk<R>(0, 0);
+    if (p >= 1) {
+      C s = s_L[p];
+      for (int l = p - 1; l >= 1; --l) s = cfma(s, w, s_L[l]);
+      f = cmul(s, w);
+      if (JAC) {
+        C t = mk<R>((R)p * s_L[p].x, (R)p * s_L[p].y);
+        for (int l = p - 1; l >= 1; --l) t = cfma(t, w, mk<R>((R)l * s_L[l].x, (R)l * s_L[l].y));
+        df = mk<R>(t.x * ir, t.y * ir);
+      }
+    }
+    f = f + fw[q];
+    const double fre = b0.x + (double)f.x;
+    const double fim = b0.y + (double)f.y;
+    const double al1 = fre + n1[q].value();
+    const double al2 = -fim + n2[q].value();
+    const double y1 = fma(A.a, x1[q], -al1);
+    const double y2 = fma(A.b, x2[q], -al2);
+    if (PIX) {
+      const double u = fma(y1, A.pinv_du, A.pu_off), v = fma(y2, A.pinv_dv, A.pv_off);
+      PixCorner pc;
+      if (fabs(u) < 1073741824.0 && fabs(v) < 1073741824.0) {
+        const double fu = floor(u), fv = floor(v);
+        pc.iu = (int)fu; pc.fu = (float)(u - fu);
+        pc.iv = (int)fv; pc.fv = (float)(v - fv);
+      } else {
+        pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
+      }
+      A.pix[oidx[q]] = pc;
+      continue;
+    }
+    A.y[2 * oidx[q]] = y1;
+    A.y[2 * oidx[q] + 1] = y2;
+    if (JAC) {
+      const double dre = (double)df.x + (double)dfw[q].x + nj1[q].value();
+      const double dim = (double)df.y + (double)dfw[q].y + nj2[q].value();
+      A.jac[4 * oidx[q] + 0] = A.a - dre;
+      A.jac[4 * oidx[q] + 1] = dim;
+      A.jac[4 * oidx[q] + 2] = dim;
+      A.jac[4 * oidx[q] + 3] = A.b + dre;
+    }
+  }
+}
+
+constexpr int kRptF = 4, kRptD = 2;
+
+__device__ __forceinline__ int64_t first_at_or_above(double x0, double h, int64_t lo, int64_t hi,
+                                                     double bound) {
+  // smallest i in [lo, hi] with x0 + i h >= bound (hi if none)
+  double g = ceil((bound - x0) / h);
+  int64_t i = g < (double)lo ? lo : (g > (double)hi ? hi : (int64_t)g);
+  while (i > lo && grid_coord(x0, i - 1, h) >= bound) --i;
+  while (i < hi && grid_coord(x0, i, h) < bound) ++i;
+  return i;
+}
+
+__global__ void k_grid_rects(const int* __restrict__ leaves, int64_t nleaf,
+                             const int* __restrict__ level, const int* __restrict__ ix,
+                             const int* __restrict__ iy, double lo_x, double lo_y, double size,
+                             double x0, double y0, double h, int64_t nx, int64_t row0,
+                             int64_t nrows, int tile, int64_t* __restrict__ rect,
+                             int64_t* __restrict__ tiles) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nleaf) return;
+  const int B = leaves[k];
+  const double side = size / (double)(1ull << level[B]);
+  const double bx0 = lo_x + ix[B] * side, bx1 = lo_x + (ix[B] + 1) * side;
+  const double by0 = lo_y + iy[B] * side, by1 = lo_y + (iy[B] + 1) * side;
+  const int64_t i0 = first_at_or_above(x0, h, 0, nx + 1, bx0);
+  const int64_t i1 = first_at_or_above(x0, h, 0, nx + 1, bx1);
+  const int64_t j0 = first_at_or_above(y0, h, row0, row0 + nrows, by0);
+  const int64_t j1 = first_at_or_above(y0, h, row0, row0 + nrows, by1);
+  const int64_t ni = i1 > i0 ? i1 - i0 : 0, nj = j1 > j0 ? j1 - j0 : 0;
+  rect[4 * k] = i0; rect[4 * k + 1] = ni; rect[4 * k + 2] = j0; rect[4 * k + 3] = nj;
+  tiles[k] = (ni * nj + tile - 1) / tile;
+}
+
+__global__ void k_ray_leaf(const double* __restrict__ rays, int64_t m, const int* __restrict__ child,
+                           const int* __restrict__ lidx, double lo_x, double lo_y, double scale,
+                           int depth, int* __restrict__ slot, int64_t* __restrict__ counts,
+                           int* __restrict__ err) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  const double x = rays[2 * r], y = rays[2 * r + 1];
+  const double qmax = (double)((1u << depth) - 1u);
+  const double fx = floor((x - lo_x) * scale), fy = floor((y - lo_y) * scale);
+  if (!(fx >= 0.0 && fx <= qmax && fy >= 0.0 && fy <= qmax)) {  // also catches NaN
+    atomicExch(err, 1);
+    slot[r] = -1;
+    return;
+  }
+  const uint32_t qx = (uint32_t)fx, qy = (uint32_t)fy;
+  int b = 0;
+  for (int l = 0; l < depth; ++l) {
+    const int c = child[b];
+    if (c < 0) break;
+    const int sh = depth - l - 1;
+    b = c + (int)(((qx >> sh) & 1u) | (((qy >> sh) & 1u) << 1));
+  }
+  const int li = lidx[b];
+  if (li < 0) {
+    atomicExch(err, 1);
+    slot[r] = -1;
+    return;
+  }
+  slot[r] = li;
+  atomicAdd((unsigned long long*)&counts[li], 1ull);
+}
+
+__global__ void k_ray_scatter(const int* __restrict__ slot, int64_t m, const int64_t* __restrict__ off,
+                              int64_t* __restrict__ cursor, int* __restrict__ perm) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  const int li = slot[r];
+  if (li < 0) return;
+  const int64_t pos = off[li] + (int64_t)atomicAdd((unsigned long long*)&cursor[li], 1ull);
+  perm[pos] = (int)r;
+}
+
+__global__ void k_tiles_from_counts(const int64_t* __restrict__ counts, int64_t n, int tile,
+                                    int64_t* __restrict__ tiles) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  tiles[k] = (counts[k] + tile - 1) / tile;
+}
+
+template <bool GRID, bool PIX>
+void launch_eval(Plan& P, EvalArgs& A, int64_t total_tiles, bool jac, cudaStream_t s) {
+  if (total_tiles <= 0) return;
+  if (total_tiles > (int64_t)INT32_MAX) fail(LENS_EINVAL, "too many ray tiles in one call");
+  const unsigned g = (unsigned)total_tiles;
+  if (P.prec == LENS_FP64) {
+    if (jac) k_eval<double, true, GRID, PIX, kRptD><<<g, kEvalThreads, 0, s>>>(A);
+    else k_eval<double, false, GRID, PIX, kRptD><<<g, kEvalThreads, 0, s>>>(A);
+  } else {
+    if (jac) k_eval<float, true, GRID, PIX, kRptF><<<g, kEvalThreads, 0, s>>>(A);
+    else k_eval<float, false, GRID, PIX, kRptF><<<g, kEvalThreads, 0, s>>>(A);
+  }
+  LENS_LAUNCHED("k_eval");
+}
+
+EvalArgs base_args(Plan& P) {
+  EvalArgs A{};
+  A.spos = P.spos; A.smass = P.smass;
+  A.start = P.box_start; A.count = P.box_count; A.level = P.box_level;
+  A.ix = P.box_ix; A.iy = P.box_iy; A.aidx = P.box_aidx;
+  A.U_off = P.U_off; A.U_list = P.U_list; A.W_off = P.W_off; A.W_list = P.W_list;
+  A.M = P.M; A.L = P.L;
+  A.leaves = P.active_leaves;
+  A.nleaf = P.n_active_leaves;
+  A.lo_x = P.root_lo[0]; A.lo_y = P.root_lo[1]; A.root_size = P.root_size;
+  A.p = P.p;
+  A.a = 1.0 - P.kappa_s - P.gamma;
+  A.b = 1.0 - P.kappa_s + P.gamma;
+  return A;
+}
+
+int tile_rays(const Plan& P) { return kEvalThreads * (P.prec == LENS_FP64 ? kRptD : kRptF); }
+
+}  // namespace
+
+namespace {
+template <bool PIX>
+void grid_impl(Plan& P, const GridRows& g, double* y, double* jac, PixCorner* pix,
+               const IpmParams* ip, cudaStream_t s) {
+  const int64_t nl = P.n_active_leaves;
+  if (nl == 0 || g.nrows <= 0) return;
+  const int tile = tile_rays(P);
+  Scratch rect(&P.da, sizeof(int64_t) * 4 * nl);
+  Scratch tiles(&P.da, sizeof(int64_t) * (nl + 1));
+  Scratch toff(&P.da, sizeof(int64_t) * (nl + 1));
+  k_grid_rects<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_level, P.box_ix,
+                                                 P.box_iy, P.root_lo[0], P.root_lo[1],
+                                                 P.root_size, g.x0, g.y0, g.h, g.nx, g.row0,
+                                                 g.nrows, tile, rect.as<int64_t>(),
+                                                 tiles.as<int64_t>());
+  LENS_LAUNCHED("k_grid_rects");
+  LENS_CUDA(cudaMemsetAsync(tiles.as<int64_t>() + nl, 0, sizeof(int64_t), s));
+  exclusive_scan_i64(tiles.as<int64_t>(), toff.as<int64_t>(), nl + 1, P.da, s);
+  int64_t total = 0;
+  LENS_CUDA(cudaMemcpyAsync(&total, toff.as<int64_t>() + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaStreamSynchronize(s));
+  EvalArgs A = base_args(P);
+  A.tile_off = toff.as<int64_t>();
+  A.rect = rect.as<int64_t>();
+  A.gx0 = g.x0; A.gy0 = g.y0; A.gh = g.h;
+  A.gnx1 = g.nx + 1; A.grow0 = g.row0;
+  A.y = y; A.jac = jac; A.pix = pix;
+  if (PIX) {
+    A.pinv_du = ip->inv_du; A.pu_off = -ip->u0 * ip->inv_du;
+    A.pinv_dv = ip->inv_dv; A.pv_off = -ip->v0 * ip->inv_dv;
+  }
+  launch_eval<true, PIX>(P, A, total, jac != nullptr, s);
+}
+}  // namespace
+
+void evaluate_grid(Plan& P, const GridRows& g, double* y, double* jac, cudaStream_t s) {
+  grid_impl<false>(P, g, y, jac, nullptr, nullptr, s);
+}
+
+void evaluate_grid_pix(Plan& P, const GridRows& g, PixCorner* out, const IpmParams& ip,
+                       cudaStream_t s) {
+  grid_impl<true>(P, g, nullptr, nullptr, out, &ip, s);
+}
+
+void evaluate_rays(Plan& P, const double* rays, int64_t m, double* y, double* jac, cudaStream_t s) {
+  const int64_t nl = P.n_active_leaves;
+  if (m == 0) return;
+  if (nl == 0) fail(LENS_EDOMAIN, "plan has no active leaves");
+  const int tile = tile_rays(P);
+  Scratch slot(&P.da, sizeof(int) * m);
+  Scratch cnt(&P.da, sizeof(int64_t) * (nl + 1));
+  Scratch off(&P.da, sizeof(int64_t) * (nl + 1));
+  Scratch cur(&P.da, sizeof(int64_t) * (nl + 1));
+  Scratch perm(&P.da, sizeof(int) * m);
+  Scratch tiles(&P.da, sizeof(int64_t) * (nl + 1));
+  Scratch toff(&P.da, sizeof(int64_t) * (nl + 1));
+  Scratch err(&P.da, sizeof(int) * 4);
+  LENS_CUDA(cudaMemsetAsync(cnt.p, 0, cnt.bytes, s));
+  LENS_CUDA(cudaMemsetAsync(cur.p, 0, cur.bytes, s));
+  LENS_CUDA(cudaMemsetAsync(err.p, 0, err.bytes, s));
+  const double scale = (double)(1ull << P.depth) / P.root_size;
+  k_ray_leaf<<<grid_for(m, 256), 256, 0, s>>>(rays, m, P.box_child, P.box_lidx, P.root_lo[0],
+                                              P.root_lo[1], scale, P.depth, slot.as<int>(),
+                                              cnt.as<int64_t>(), err.as<int>());
+  LENS_LAUNCHED("k_ray_leaf");
+  exclusive_scan_i64(cnt.as<int64_t>(), off.as<int64_t>(), nl + 1, P.da, s);
+  k_ray_scatter<<<grid_for(m, 256), 256, 0, s>>>(slot.as<int>(), m, off.as<int64_t>(),
+                                                 cur.as<int64_t>(), perm.as<int>());
+  LENS_LAUNCHED("k_ray_scatter");
+  k_tiles_from_counts<<<grid_for(nl + 1, 256), 256, 0, s>>>(cnt.as<int64_t>(), nl + 1, tile,
+                                                            tiles.as<int64_t>());
+  LENS_LAUNCHED("k_tiles_from_counts");
+  exclusive_scan_i64(tiles.as<int64_t>(), toff.as<int64_t>(), nl + 1, P.da, s);
+  int64_t total = 0;
+  int herr[4] = {0, 0, 0, 0};
+  LENS_CUDA(cudaMemcpyAsync(&total, toff.as<int64_t>() + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaMemcpyAsync(herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaStreamSynchronize(s));
+  if (herr[0]) fail(LENS_EDOMAIN, "a ray lies outside the plan's target region (or is not finite)");
+  EvalArgs A = base_args(P);
+  A.tile_off = toff.as<int64_t>();
+  A.rays = rays; A.ray_off = off.as<int64_t>(); A.perm = perm.as<int>();
+  A.y = y; A.jac = jac;
+  launch_eval<false, false>(P, A, total, jac != nullptr, s);
+}
+
+}  // namespace lens

@@ -1,0 +1,336 @@
+// fmm.cu -- upward and downward passes of the FMM in complex form
+// (Appendix A: multipole "S" and local "R" expansions, the S2S/M2M, S2R/M2L
+// and R2R/L2L translation theorems; Greengard & Rokhlin 1987).
+//
+// The Cauchy sum f(z) = sum_j m_j / (z - z_j) gives the deflection of Eq. 1
+// as alpha = conj(f).  For a box of centre c and half-side r:
+//   multipole  f(z) = sum_k a_k / (z-c)^(k+1),  a_k = sum_j m_j (z_j - c)^k,
+//              stored scaled: A_k = a_k / r^k;
+//   local      f(z) = sum_l b_l (z-c)^l,        stored scaled: B_l = b_l r^l.
+// Scaled, the child->parent M2M and parent->child L2L matrices do not depend
+// on the level (child offset = (+-1 +-i) r_parent / 2), and the M2L matrix of
+// two same-level boxes depends only on their integer offset:
+//   M2M  A^P_l = sum_{k<=l} C(l,k) 2^-k d^(l-k) A^C_k,       d = (+-1 +-i)/2
+//   L2L  B^C_j = sum_{l>=j} C(l,j) 2^-j d^(l-j) B^P_l
+//   M2L  B_l  += (-1)^l u^(l+1) / r * sum_k C(k+l,k) u^k A_k,  u = r/(c_B - c_C)
+// The M2L is split into a diagonal pre-scaling (u^k), one REAL binomial
+// matrix applied to the complex vector, and a diagonal post-scaling, which
+// halves the float64 multiply-adds of a dense complex matrix.
+//   P2L  B_l  += -(m / (z-c)) (r / (z-c))^l        (X lists)
+// Every step here is float64 (the precision split keeps translations in
+// float64).  On GB300 the float64 pipe is ~60x slower than float32, so these
+// kernels are written to issue as few DFMAs as the series allow.
+#include <cmath>
+#include <vector>
+
+#include "cx.cuh"
+#include "lens_internal.h"
+
+namespace lens {
+
+namespace {
+
+constexpr int kWarpsPerBlock = 4;
+
+__device__ __forceinline__ double2 ld2(const double2* p) { return __ldg(p); }
+
+// ---- P2M: one thread per leaf, accumulators in shared memory -----------------
+__global__ void k_p2m(const double2* __restrict__ spos, const double* __restrict__ smass,
+                      const int* __restrict__ start, const int* __restrict__ count,
+                      const int* __restrict__ child, const int* __restrict__ level,
+                      const int* __restrict__ ix, const int* __restrict__ iy, int64_t b0,
+                      int64_t b1, double lo_x, double lo_y, double root_size, int p,
+                      double2* __restrict__ M) {
+  extern __shared__ double2 acc[];  // [(p+1)][blockDim.x]
+  const int64_t b = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= b1) return;
+  const int nst = count[b];
+  double2* out = M + b * (int64_t)(p + 1);
+  if (child[b] >= 0) return;  // internal: M2M fills it
+  if (nst == 0) {
+    for (int k = 0; k <= p; ++k) out[k] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double r = root_size / (double)(2ull << level[b]);
+  const double cx = lo_x + (2.0 * ix[b] + 1.0) * r, cy = lo_y + (2.0 * iy[b] + 1.0) * r;
+  const double ir = 1.0 / r;
+  double2* a = acc + threadIdx.x;
+  const int st = blockDim.x;
+  for (int k = 0; k <= p; ++k) a[k * st] = make_double2(0.0, 0.0);
+  const int s0 = start[b];
+  for (int j = 0; j < nst; ++j) {
+    const double2 z = spos[s0 + j];
+    const double m = smass[s0 + j];
+    const double2 w = make_double2((z.x - cx) * ir, (z.y - cy) * ir);
+    double2 pw = make_double2(m, 0.0);
+    for (int k = 0; k <= p; ++k) {
+      a[k * st] = a[k * st] + pw;
+      pw = cmul(pw, w);
+    }
+  }
+  for (int k = 0; k <= p; ++k) out[k] = a[k * st];
+}
+
+// ---- M2M: one warp per internal box of a level -------------------------------
+__global__ void k_m2m(const int* __restrict__ child, const int* __restrict__ count, int64_t b0,
+                      int64_t b1, int p, const double2* __restrict__ T, double2* __restrict__ M) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = b0 + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  if (b >= b1) return;
+  const int c0 = child[b];
+  if (c0 < 0) return;
+  const int P1 = p + 1;
+  double2 acc[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) acc[s] = make_double2(0.0, 0.0);
+  for (int q = 0; q < 4; ++q) {
+    if (count[c0 + q] == 0) continue;
+    const double2* A = M + (int64_t)(c0 + q) * P1;
+    const double2* Tq = T + (int64_t)q * P1 * P1;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int l = lane + 32 * s;
+      if (l > p) break;
+      double2 v = acc[s];
+      for (int k = 0; k <= l; ++k) v = cfma(ld2(Tq + l * P1 + k), ld2(A + k), v);
+      acc[s] = v;
+    }
+  }
+  double2* out = M + b * (int64_t)P1;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int l = lane + 32 * s;
+    if (l <= p) out[l] = acc[s];
+  }
+}
+
+// ---- downward: L2L + M2L (V) + P2L (X), one warp per active box -----------
+struct DownArgs {
+  const int* active;
+  int64_t a0, a1;
+  const int* parent; const int* child; const int* level; const int* ix; const int* iy;
+  const int* start; const int* count;
+  const int64_t* V_off; const int* V_list;
+  const int64_t* X_off; const int* X_list;
+  const double2* spos; const double* smass;
+  const double2* M;
+  double2* L;
+  FmmTables tab;
+  double lo_x, lo_y, root_size;
+  int p;
+};
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_downward(DownArgs A) {
+  __shared__ double2 sbuf[kWarpsPerBlock][kMaxOrder + 1];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t a = A.a0 + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  if (a >= A.a1) return;
+  const int p = A.p, P1 = p + 1;
+  const int B = A.active[a];
+  const int lv = A.level[B];
+  const double r = A.root_size / (double)(2ull << lv);
+  const double ir = 1.0 / r;
+  double2 acc[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) acc[s] = make_double2(0.0, 0.0);
+  // L2L from the parent (levels >= 2; the parent's local expansion is 0 above)
+  const int par = A.parent[B];
+  if (lv >= 2) {
+    const int q = B - A.child[par];
+    const double2* Lp = A.L + (int64_t)par * P1;
+    const double2* S = A.tab.l2l + (int64_t)q * P1 * P1;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int j = lane + 32 * s;
+      if (j > p) break;
+      double2 v = make_double2(0.0, 0.0);
+      for (int l = j; l <= p; ++l) v = cfma(ld2(S + j * P1 + l), ld2(Lp + l), v);
+      acc[s] = v;
+    }
+  }
+  // M2L from V
+  double2* buf = sbuf[wib];
+  const int bx = A.ix[B], by = A.iy[B];
+  for (int64_t e = A.V_off[a]; e < A.V_off[a + 1]; ++e) {
+    const int C = A.V_list[e];
+    const int dx = A.ix[C] - bx, dy = A.iy[C] - by;
+    const double2* up = A.tab.upow + (int64_t)((dy + 3) * 7 + (dx + 3)) * (p + 2);
+    const double2* Ac = A.M + (int64_t)C * P1;
+    for (int k = lane; k <= p; k += 32) buf[k] = cmul(ld2(Ac + k), ld2(up + k));
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int l = lane + 32 * s;
+      if (l > p) break;
+      double sx = 0.0, sy = 0.0;
+      for (int k = 0; k <= p; ++k) {
+        // C(k+l, k) = binom[(k+l)*ldb + k]
+        const double c = __ldg(A.tab.binom + (int64_t)(k + l) * A.tab.ldb + k);
+        const double2 v = buf[k];
+        sx = fma(c, v.x, sx);
+        sy = fma(c, v.y, sy);
+      }
+      double2 post = ld2(up + l + 1);
+      if (l & 1) post = make_double2(-post.x, -post.y);
+      acc[s] = cfma(post, make_double2(sx * ir, sy * ir), acc[s]);
+    }
+    __syncwarp();
+  }
+  // P2L from X (each star expanded about the box centre)
+  const double cx = A.lo_x + (2.0 * bx + 1.0) * r, cy = A.lo_y + (2.0 * by + 1.0) * r;
+  for (int64_t e = A.X_off[a]; e < A.X_off[a + 1]; ++e) {
+    const int C = A.X_list[e];
+    const int s0 = A.start[C], ns = A.count[C];
+    for (int j = 0; j < ns; ++j) {
+      const double2 z = A.spos[s0 + j];
+      const double m = A.smass[s0 + j];
+      const double2 inv = cinv(make_double2(z.x - cx, z.y - cy));  // 1/(z-c)
+      const double2 q = make_double2(inv.x * r, inv.y * r);        // r/(z-c)
+      const double2 lead = make_double2(-m * inv.x, -m * inv.y);   // -m/(z-c)
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const int l = lane + 32 * s;
+        if (l > p) break;
+        // q^l by binary powering
+        double2 pw = make_double2(1.0, 0.0), bse = q;
+        for (int e2 = l; e2 > 0; e2 >>= 1) {
+          if (e2 & 1) pw = cmul(pw, bse);
+          bse = cmul(bse, bse);
+        }
+        acc[s] = cfma(lead, pw, acc[s]);
+      }
+    }
+  }
+  double2* out = A.L + (int64_t)B * P1;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int l = lane + 32 * s;
+    if (l <= p) out[l] = acc[s];
+  }
+}
+
+}  // namespace
+
+// ---- host: tables ----------------------------------------------------------
+void fmm_tables(Plan& P, cudaStream_t s) {
+  const int p = P.p;
+  const int P1 = p + 1;
+  FmmTables& t = P.tab;
+  t.p = p;
+  t.ldb = p + 2;
+  const int nb = 2 * p + 2;
+  std::vector<double> bin((size_t)nb * t.ldb, 0.0);
+  std::vector<std::vector<double>> full(nb, std::vector<double>(nb, 0.0));
+  for (int n = 0; n < nb; ++n) {
+    full[n][0] = 1.0;
+    for (int k = 1; k <= n; ++k) full[n][k] = full[n - 1][k - 1] + (k <= n - 1 ? full[n - 1][k] : 0.0);
+  }
+  for (int n = 0; n < nb; ++n)
+    for (int k = 0; k < t.ldb && k <= n; ++k) bin[(size_t)n * t.ldb + k] = full[n][k];
+  auto cpow = [](double re, double im, int e) {
+    double pr = 1.0, pi = 0.0;
+    for (int i = 0; i < e; ++i) {
+      double nr = pr * re - pi * im, ni = pr * im + pi * re;
+      pr = nr; pi = ni;
+    }
+    return std::pair<double, double>(pr, pi);
+  };
+  std::vector<double2> m2m((size_t)4 * P1 * P1), l2l((size_t)4 * P1 * P1);
+  for (int q = 0; q < 4; ++q) {
+    const double dre = ((q & 1) ? 0.5 : -0.5), dim = ((q >> 1) ? 0.5 : -0.5);
+    for (int l = 0; l <= p; ++l)
+      for (int k = 0; k <= p; ++k) {
+        double2 v = make_double2(0.0, 0.0);
+        if (k <= l) {
+          auto d = cpow(dre, dim, l - k);
+          const double c = full[l][k] * std::ldexp(1.0, -k);
+          v = make_double2(c * d.first, c * d.second);
+        }
+        m2m[((size_t)q * P1 + l) * P1 + k] = v;
+      }
+    for (int j = 0; j <= p; ++j)
+      for (int l = 0; l <= p; ++l) {
+        double2 v = make_double2(0.0, 0.0);
+        if (l >= j) {
+          auto d = cpow(dre, dim, l - j);
+          const double c = full[l][j] * std::ldexp(1.0, -j);
+          v = make_double2(c * d.first, c * d.second);
+        }
+        l2l[((size_t)q * P1 + j) * P1 + l] = v;
+      }
+  }
+  std::vector<double2> up((size_t)49 * (p + 2));
+  for (int dy = -3; dy <= 3; ++dy)
+    for (int dx = -3; dx <= 3; ++dx) {
+      const int o = (dy + 3) * 7 + (dx + 3);
+      // u = r / (c_B - c_C) = -1 / (2 (dx + i dy))
+      double ure = 0, uim = 0;
+      if (dx != 0 || dy != 0) {
+        const double den = 2.0 * (dx * (double)dx + dy * (double)dy);
+        ure = -dx / den;
+        uim = dy / den;
+      }
+      double pr = 1.0, pi = 0.0;
+      for (int k = 0; k <= p + 1; ++k) {
+        up[(size_t)o * (p + 2) + k] = make_double2(pr, pi);
+        const double nr = pr * ure - pi * uim, ni = pr * uim + pi * ure;
+        pr = nr; pi = ni;
+      }
+    }
+  t.binom = P.dalloc_n<double>(bin.size());
+  t.m2m = P.dalloc_n<double2>(m2m.size());
+  t.l2l = P.dalloc_n<double2>(l2l.size());
+  t.upow = P.dalloc_n<double2>(up.size());
+  LENS_CUDA(cudaMemcpyAsync(t.binom, bin.data(), bin.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  LENS_CUDA(cudaMemcpyAsync(t.m2m, m2m.data(), m2m.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  LENS_CUDA(cudaMemcpyAsync(t.l2l, l2l.data(), l2l.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  LENS_CUDA(cudaMemcpyAsync(t.upow, up.data(), up.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  // host vectors must stay alive until the copies have run
+  LENS_CUDA(cudaStreamSynchronize(s));
+}
+
+void fmm_p2m(Plan& P, cudaStream_t s) {
+  const int p = P.p, P1 = p + 1;
+  P.M = P.dalloc_n<double2>((size_t)P.nb * P1);
+  // P2M on every leaf (thread per box), all levels at once
+  const int tpb = 32;
+  const size_t smem = sizeof(double2) * (size_t)P1 * tpb;
+  if (smem > 48 * 1024)
+    LENS_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_p2m<<<grid_for(P.nb, tpb), tpb, smem, s>>>(P.spos, P.smass, P.box_start, P.box_count,
+                                                P.box_child, P.box_level, P.box_ix, P.box_iy, 0,
+                                                P.nb, P.root_lo[0], P.root_lo[1], P.root_size, p,
+                                                P.M);
+  LENS_LAUNCHED("k_p2m");
+}
+
+void fmm_m2m(Plan& P, cudaStream_t s) {
+  const FmmTables& t = P.tab;
+  for (int l = P.nlevels - 2; l >= 0; --l) {
+    const int64_t b0 = P.level_off[l], b1 = P.level_off[l + 1];
+    k_m2m<<<grid_for((b1 - b0) * 32, 128), 128, 0, s>>>(P.box_child, P.box_count, b0, b1, P.p,
+                                                        t.m2m, P.M);
+    LENS_LAUNCHED("k_m2m");
+  }
+}
+
+void fmm_downward(Plan& P, cudaStream_t s) {
+  const FmmTables& t = P.tab;
+  P.L = P.dalloc_n<double2>((size_t)P.nb * (P.p + 1));
+  DownArgs A{};
+  A.active = P.active;
+  A.parent = P.box_parent; A.child = P.box_child; A.level = P.box_level;
+  A.ix = P.box_ix; A.iy = P.box_iy; A.start = P.box_start; A.count = P.box_count;
+  A.V_off = P.V_off; A.V_list = P.V_list; A.X_off = P.X_off; A.X_list = P.X_list;
+  A.spos = P.spos; A.smass = P.smass; A.M = P.M; A.L = P.L; A.tab = t;
+  A.lo_x = P.root_lo[0]; A.lo_y = P.root_lo[1]; A.root_size = P.root_size; A.p = P.p;
+  for (int l = 0; l < P.nlevels; ++l) {
+    A.a0 = P.active_level_off[l];
+    A.a1 = P.active_level_off[l + 1];
+    if (A.a1 <= A.a0) continue;
+    k_downward<<<grid_for((A.a1 - A.a0) * 32, 32 * kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(A);
+    LENS_LAUNCHED("k_downward");
+  }
+}
+
+}  // namespace lens

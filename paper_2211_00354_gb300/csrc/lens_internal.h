@@ -1,0 +1,204 @@
+// lens_internal.h -- host-side plumbing shared by the liblens translation units:
+// the plan object, status/exception handling, device allocation through the
+// caller's allocator, host-side fault injection and launch checking.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lens.h"
+
+namespace lens {
+
+// Internal failures are C++ exceptions that every extern "C" entry point
+// converts to a lens_status (nothing crosses the ABI).
+struct Error {
+  lens_status status;
+  std::string msg;
+};
+
+[[noreturn]] void fail(lens_status st, const std::string& msg);
+void set_last_error(const std::string& msg);
+
+void check_cuda(cudaError_t e, const char* what);
+// Called after every kernel launch: counts launches (LENS_FAULT=launch@K)
+// and turns a launch error into LENS_ECUDA.
+void after_launch(const char* name);
+// Counts allocations (LENS_FAULT=alloc@K); throws LENS_EFAULT_INJECTED when due.
+void fault_point_alloc();
+
+#define LENS_CUDA(call) ::lens::check_cuda((call), #call)
+#define LENS_LAUNCHED(name) ::lens::after_launch(name)
+
+// Device memory provider: the caller's lens_allocator, or cudaMallocAsync.
+struct DeviceAlloc {
+  lens_allocator a{};
+  bool custom = false;
+  cudaStream_t stream = nullptr;
+  void* alloc(size_t bytes);
+  void release(void* p);
+};
+
+// Scoped scratch buffer (freed, stream-ordered, when it leaves scope).
+struct Scratch {
+  DeviceAlloc* da = nullptr;
+  void* p = nullptr;
+  size_t bytes = 0;
+  Scratch() = default;
+  Scratch(DeviceAlloc* d, size_t b) : da(d), bytes(b) { p = b ? d->alloc(b) : nullptr; }
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  Scratch(Scratch&& o) noexcept : da(o.da), p(o.p), bytes(o.bytes) { o.p = nullptr; }
+  Scratch& operator=(Scratch&& o) noexcept {
+    if (this != &o) { reset(); da = o.da; p = o.p; bytes = o.bytes; o.p = nullptr; }
+    return *this;
+  }
+  ~Scratch() { reset(); }
+  void reset() { if (p && da) da->release(p); p = nullptr; }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+constexpr int kMaxDepth = 28;   // quadtree levels below the root (56-bit keys)
+constexpr int kMaxOrder = 64;   // expansion order cap
+
+// Host-built float64 tables for one order p (device copies owned by the plan).
+struct FmmTables {
+  int p = 0, ldb = 0;
+  double* binom = nullptr;   // C(n, k), n < 2p+2, k < p+2: binom[n*ldb + k]
+  double2* m2m = nullptr;    // [4][p+1][p+1]: row l, col k (k <= l)
+  double2* l2l = nullptr;    // [4][p+1][p+1]: row j, col l (l >= j)
+  double2* upow = nullptr;   // [49][p+2]: u^k for offset (dx,dy) in [-3,3]^2
+};
+
+struct Plan {
+  int device = 0;
+  DeviceAlloc da;
+  std::vector<void*> owned;  // plan-lifetime device allocations
+  int64_t device_bytes = 0;
+
+  int64_t n = 0;
+  int p = 0, leaf = 0, prec = 0, depth = kMaxDepth;
+  double kappa_s = 0, gamma = 0;
+  double root_lo[2] = {0, 0}, root_size = 1;
+  bool has_target = false;
+  double target[4] = {0, 0, 0, 0};
+
+  int nlevels = 0;                     // levels 0 .. nlevels-1 hold boxes
+  std::vector<int64_t> level_off;      // box ids of level l: [level_off[l], level_off[l+1])
+  int64_t nb = 0;
+
+  // sorted stars (Morton order)
+  double2* spos = nullptr;
+  double* smass = nullptr;
+  uint32_t* sidx = nullptr;            // sorted slot -> caller index
+  uint64_t* skey = nullptr;
+
+  // boxes (structure of arrays, level-major, Morton order within a level)
+  int* box_start = nullptr;
+  int* box_count = nullptr;
+  int* box_child = nullptr;            // first of 4 children, -1 for a leaf
+  int* box_parent = nullptr;
+  int* box_level = nullptr;
+  int* box_ix = nullptr;
+  int* box_iy = nullptr;
+  uint64_t* box_code = nullptr;        // Morton code of (ix, iy) at its level
+  uint8_t* box_active = nullptr;
+
+  // active boxes (meet the target region), level-major
+  int64_t n_active = 0, n_active_leaves = 0;
+  int* active = nullptr;               // active box ids
+  std::vector<int64_t> active_level_off;
+  int* active_leaves = nullptr;        // active leaf ids
+  int* box_aidx = nullptr;             // box id -> active index, -1 if inactive
+  int* box_lidx = nullptr;             // box id -> active-leaf index, -1 otherwise
+
+  // interaction lists, CSR over the active list index
+  int64_t nV = 0, nX = 0, nU = 0, nW = 0, u_stars = 0;
+  // (all four lists are indexed by the active index; U and W are empty for
+  //  internal boxes)
+  int64_t* V_off = nullptr; int* V_list = nullptr;
+  int64_t* X_off = nullptr; int* X_list = nullptr;
+  int64_t* U_off = nullptr; int* U_list = nullptr;
+  int64_t* W_off = nullptr; int* W_list = nullptr;
+
+  // expansions: (p+1) complex coefficients per box, scaled (see fmm.cu)
+  double2* M = nullptr;
+  double2* L = nullptr;
+  FmmTables tab;
+
+  double ms_build = 0;
+
+  void* dalloc(size_t bytes) {
+    void* p = da.alloc(bytes);
+    owned.push_back(p);
+    device_bytes += (int64_t)bytes;
+    return p;
+  }
+  template <class T> T* dalloc_n(size_t count) {
+    return static_cast<T*>(dalloc(count * sizeof(T) + (count == 0 ? 16 : 0)));
+  }
+  double half_side(int level) const { return root_size / (double)(2ull << level); }
+};
+
+// ---- launchers (defined in the .cu files) --------------------------------
+void direct_deflect(const double* stars, const double* masses, int64_t n,
+                    double ks, double g, const double* rays, int64_t m, int prec,
+                    double* y, double* jac, DeviceAlloc& da, cudaStream_t s);
+
+void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits,
+                    DeviceAlloc& da, cudaStream_t s);
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, DeviceAlloc& da,
+                        cudaStream_t s);
+
+void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t s);
+void fmm_tables(Plan& P, cudaStream_t s);
+void fmm_p2m(Plan& P, cudaStream_t s);
+void fmm_m2m(Plan& P, cudaStream_t s);
+void fmm_downward(Plan& P, cudaStream_t s);
+
+struct GridRows {  // a band of corner rows of a grid
+  double x0, y0, h;
+  int64_t nx, ny;   // cells (corners nx+1 by ny+1)
+  int64_t row0, nrows;
+};
+void evaluate_grid(Plan& P, const GridRows& g, double* y, double* jac, cudaStream_t s);
+void evaluate_rays(Plan& P, const double* rays, int64_t m, double* y, double* jac,
+                   cudaStream_t s);
+
+struct IpmParams {
+  double u0, v0, inv_du, inv_dv;  // source-plane window origin, inverse pixel size
+  double scale;                   // A_cell / S* (map increment per unit fraction)
+  double a_cell, s_star;          // cell area h^2, pixel area S*
+  int npx, npy, cap;
+};
+// A deflected corner in map-pixel coordinates: u = iu + fu, fu in [0, 1];
+// iu == iv == INT32_MAX marks a corner farther than 2^30 pixels.
+struct __align__(16) PixCorner {
+  int iu; float fu; int iv; float fv;
+};
+void evaluate_grid_pix(Plan& P, const GridRows& g, PixCorner* out, const IpmParams& ip,
+                       cudaStream_t s);
+void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const IpmParams& ip,
+                    double* map, double* stats_dev, int* queue, int* qcount, cudaStream_t s);
+
+void adjoint(Plan& P, const double* rays, int64_t m, const double* gy,
+             double* gxy, double* gm, double* gkg, cudaStream_t s);
+
+void light_curve(const double* y, int64_t m, double w, const double* smp, int64_t ns,
+                 double sigma, double trunc, double* F, cudaStream_t s);
+void light_curve_grad(const double* y, int64_t m, double w, const double* smp,
+                      int64_t ns, double sigma, double trunc, const double* F,
+                      const double* T, double* gy, cudaStream_t s);
+
+// grid size helper: blocks of `threads` covering n, capped
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = (1ll << 31) - 1) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+}  // namespace lens

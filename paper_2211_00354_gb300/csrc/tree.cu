@@ -1,0 +1,544 @@
+// tree.cu -- GPU quadtree over the stars and the adaptive FMM interaction
+// lists (Appendix A, step 1: hierarchical four-fold partition of the plane).
+//
+// Build:
+//  1. root square = bounding box of the stars united with the target region;
+//  2. 56-bit Morton keys (28 levels) and an LSD radix sort of (key, index);
+//  3. split-node enumeration: in Morton order, star i begins a node at every
+//     level deeper than the common prefix it shares with star i-1; a node at
+//     level l < depth splits iff it holds more than leaf_size stars (its end
+//     comes from a binary search on the sorted keys).  One host sync reads the
+//     per-level split counts, which fix every array size;
+//  4. boxes are numbered level by level, Morton order within a level: the 4
+//     children of the split node of rank k at level l are boxes
+//     level_off[l+1] + 4k + q.  Empty quadrants stay as leaves, so the leaves
+//     tile the root and any point has a leaf;
+//  5. boxes that meet the target region are "active" (they get local
+//     expansions); lists are built for active boxes only.
+//
+// Interaction lists of an active box B at level l (adaptive FMM, Carrier-
+// Greengard-Rokhlin): V(B) = non-adjacent children of the parent's colleagues
+// (M2L); X(B) = leaves coarser than B adjacent to the parent but not to B
+// (P2L); for a leaf B also U(B) = adjacent leaves (P2P) and W(B) =
+// non-adjacent children of adjacent boxes finer than B (M2P).  Empty boxes
+// are skipped in every list.
+#include <algorithm>
+#include <vector>
+
+#include "cx.cuh"
+#include "lens_internal.h"
+
+namespace lens {
+
+namespace {
+
+struct LevelOffsets {
+  int64_t off[kMaxDepth + 2];
+  int nlevels;
+};
+
+__global__ void k_bounds(const double* __restrict__ stars, const double* __restrict__ m,
+                         int64_t n, double* __restrict__ part) {
+  __shared__ double sh[5][256];
+  double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY, bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = stars[2 * i], y = stars[2 * i + 1], w = m[i];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(w)) { bad += 1; continue; }
+    xmin = fmin(xmin, x); xmax = fmax(xmax, x);
+    ymin = fmin(ymin, y); ymax = fmax(ymax, y);
+  }
+  sh[0][threadIdx.x] = xmin; sh[1][threadIdx.x] = xmax;
+  sh[2][threadIdx.x] = ymin; sh[3][threadIdx.x] = ymax; sh[4][threadIdx.x] = bad;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] = fmin(sh[0][threadIdx.x], sh[0][threadIdx.x + o]);
+      sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + o]);
+      sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + o]);
+      sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + o]);
+      sh[4][threadIdx.x] += sh[4][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) part[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_keys(const double* __restrict__ stars, int64_t n, double lo_x, double lo_y,
+                       double scale, int depth, uint64_t* __restrict__ keys,
+                       uint32_t* __restrict__ idx) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double qmax = (double)((1u << depth) - 1u);
+  double fx = floor((stars[2 * i] - lo_x) * scale);
+  double fy = floor((stars[2 * i + 1] - lo_y) * scale);
+  fx = fmin(fmax(fx, 0.0), qmax);
+  fy = fmin(fmax(fy, 0.0), qmax);
+  keys[i] = morton((uint32_t)fx, (uint32_t)fy);
+  idx[i] = (uint32_t)i;
+}
+
+__global__ void k_gather(const double* __restrict__ stars, const double* __restrict__ m,
+                         const uint32_t* __restrict__ idx, int64_t n, double2* __restrict__ spos,
+                         double* __restrict__ smass) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t j = idx[i];
+  spos[i] = make_double2(stars[2 * (int64_t)j], stars[2 * (int64_t)j + 1]);
+  smass[i] = m[j];
+}
+
+// first index in [lo, hi) whose key is > v  (keys sorted ascending)
+__device__ __forceinline__ int64_t upper_bound(const uint64_t* k, int64_t lo, int64_t hi, uint64_t v) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (k[mid] <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int64_t lower_bound(const uint64_t* k, int64_t lo, int64_t hi, uint64_t v) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (k[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int first_level(const uint64_t* k, int64_t i, int depth) {
+  if (i == 0) return 0;
+  const uint64_t x = k[i - 1] ^ k[i];
+  if (x == 0) return depth + 1;
+  const int lcp = (__clzll((long long)x) - (64 - 2 * depth)) >> 1;
+  return lcp + 1;
+}
+
+// Pass 1 (write == false): per-level split counts.  Pass 2: write entries
+// (level << 32 | first star) at per-level cursors.
+template <bool WRITE>
+__global__ void k_splits(const uint64_t* __restrict__ k, int64_t n, int depth, int leaf,
+                         unsigned long long* __restrict__ counts, int* __restrict__ deep_flag,
+                         unsigned long long* __restrict__ cursor, uint64_t* __restrict__ out) {
+  __shared__ unsigned int sc[kMaxDepth + 1];
+  if (!WRITE) {
+    for (int q = threadIdx.x; q <= kMaxDepth; q += blockDim.x) sc[q] = 0;
+    __syncthreads();
+  }
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    for (int l = first_level(k, i, depth); l <= depth; ++l) {
+      const uint64_t mask = (l == 0) ? ~0ull : ((1ull << (2 * (depth - l))) - 1ull);
+      const int64_t end = (l == 0) ? n : upper_bound(k, i + 1, n, k[i] | mask);
+      if (end - i <= leaf) break;
+      if (l == depth) { if (!WRITE) atomicExch(deep_flag, 1); break; }
+      if (WRITE) {
+        unsigned long long pos = atomicAdd(&cursor[l], 1ull);
+        out[pos] = ((uint64_t)l << 32) | (uint64_t)i;
+      } else {
+        atomicAdd(&sc[l], 1u);
+      }
+    }
+  }
+  if (!WRITE) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < kMaxDepth; q += blockDim.x)
+      if (sc[q]) atomicAdd(&counts[q], (unsigned long long)sc[q]);
+  }
+}
+
+__global__ void k_root(int64_t n, int* start, int* count, int* parent, int* level, int* ix,
+                       int* iy, uint64_t* code) {
+  start[0] = 0; count[0] = (int)n; parent[0] = -1; level[0] = 0; ix[0] = 0; iy[0] = 0; code[0] = 0;
+}
+
+__global__ void k_fill_boxes(const uint64_t* __restrict__ splits, int64_t nsplit,
+                             LevelOffsets split_off, LevelOffsets box_off,
+                             const uint64_t* __restrict__ k, int64_t n, int depth,
+                             int* box_start, int* box_count, int* box_child, int* box_parent,
+                             int* box_level, int* box_ix, int* box_iy, uint64_t* box_code) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= nsplit) return;
+  const uint64_t e = splits[g];
+  const int l = (int)(e >> 32);
+  const int64_t i = (int64_t)(e & 0xffffffffull);
+  const int64_t rank = g - split_off.off[l];
+  int64_t own = 0;
+  if (l > 0) {
+    // parent split node: the last entry of level l-1 starting at or before i
+    int64_t lo = split_off.off[l - 1], hi = split_off.off[l];
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)(splits[mid] & 0xffffffffull) <= i) lo = mid + 1; else hi = mid;
+    }
+    const int64_t prank = (lo - 1) - split_off.off[l - 1];
+    const int dig = (int)((k[i] >> (2 * (depth - l))) & 3ull);
+    own = box_off.off[l] + 4 * prank + dig;
+  }
+  const uint64_t mask = (l == 0) ? ~0ull : ((1ull << (2 * (depth - l))) - 1ull);
+  const int64_t end = (l == 0) ? n : upper_bound(k, i + 1, n, k[i] | mask);
+  const uint64_t P = (l == 0) ? 0ull : (k[i] >> (2 * (depth - l)));
+  const int pix = (int)compact2(P), piy = (int)compact2(P >> 1);
+  const int64_t c0 = box_off.off[l + 1] + 4 * rank;
+  box_child[own] = (int)c0;
+  const int sh = 2 * (depth - l - 1);
+  int64_t b[5];
+  b[0] = i;
+  b[4] = end;
+  for (int q = 1; q < 4; ++q) b[q] = lower_bound(k, i, end, ((P << 2) | (uint64_t)q) << sh);
+  for (int q = 0; q < 4; ++q) {
+    const int64_t c = c0 + q;
+    box_start[c] = (int)b[q];
+    box_count[c] = (int)(b[q + 1] - b[q]);
+    box_parent[c] = (int)own;
+    box_level[c] = l + 1;
+    box_ix[c] = 2 * pix + (q & 1);
+    box_iy[c] = 2 * piy + (q >> 1);
+    box_code[c] = (P << 2) | (uint64_t)q;
+  }
+}
+
+struct TreeView {
+  const int* start; const int* count; const int* child; const int* level;
+  const int* ix; const int* iy; const uint64_t* code;
+  LevelOffsets lo;
+};
+
+__global__ void k_active_flags(TreeView T, int64_t nb, double root_lo_x, double root_lo_y,
+                               double root_size, int has_target, double t0, double t1,
+                               double t2, double t3, uint8_t* __restrict__ active,
+                               int64_t* __restrict__ fa, int64_t* __restrict__ fl) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  bool act = true;
+  if (has_target) {
+    const double side = root_size / (double)(1ull << T.level[b]);
+    const double x0 = root_lo_x + T.ix[b] * side, y0 = root_lo_y + T.iy[b] * side;
+    act = (x0 <= t1) && (x0 + side >= t0) && (y0 <= t3) && (y0 + side >= t2);
+  }
+  active[b] = act ? 1 : 0;
+  fa[b] = act ? 1 : 0;
+  fl[b] = (act && T.child[b] < 0) ? 1 : 0;
+}
+
+__global__ void k_compact(const int64_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                          int64_t n, int* __restrict__ out, int* __restrict__ inv) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  if (flag[b]) out[pos[b]] = (int)b;
+  if (inv) inv[b] = flag[b] ? (int)pos[b] : -1;
+}
+
+// box containing cell (level, ix, iy): the box at that level if it exists,
+// else the coarser leaf that covers it; -1 outside the root.
+__device__ int find_box(const TreeView& T, int level, long long ix, long long iy) {
+  const long long lim = 1ll << level;
+  if (ix < 0 || iy < 0 || ix >= lim || iy >= lim) return -1;
+  for (int l = level; l >= 0; --l) {
+    const uint64_t c = morton((uint32_t)ix, (uint32_t)iy);
+    int64_t lo = T.lo.off[l], hi = T.lo.off[l + 1];
+    const int64_t end = hi;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if (T.code[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    if (lo < end && T.code[lo] == c) return (int)lo;
+    ix >>= 1; iy >>= 1;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ bool adjacent(const TreeView& T, int a, int b) {
+  const int la = T.level[a], lb = T.level[b];
+  const int L = la > lb ? la : lb;
+  const long long ax0 = (long long)T.ix[a] << (L - la), ax1 = (long long)(T.ix[a] + 1) << (L - la);
+  const long long ay0 = (long long)T.iy[a] << (L - la), ay1 = (long long)(T.iy[a] + 1) << (L - la);
+  const long long bx0 = (long long)T.ix[b] << (L - lb), bx1 = (long long)(T.ix[b] + 1) << (L - lb);
+  const long long by0 = (long long)T.iy[b] << (L - lb), by1 = (long long)(T.iy[b] + 1) << (L - lb);
+  return ax0 <= bx1 && bx0 <= ax1 && ay0 <= by1 && by0 <= ay1;
+}
+
+struct ListOut {
+  int64_t* cV; int64_t* cX; int64_t* cU; int64_t* cW;        // counts (pass 1)
+  const int64_t* oV; const int64_t* oX; const int64_t* oU; const int64_t* oW;  // offsets (pass 2)
+  int* V; int* X; int* U; int* W;
+  int64_t* ustars;  // per active index: stars in U (pass 1)
+};
+
+template <bool WRITE>
+__global__ void k_lists(TreeView T, const int* __restrict__ active, int64_t nact, ListOut o) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= nact) return;
+  const int B = active[a];
+  const int l = T.level[B];
+  const long long bx = T.ix[B], by = T.iy[B];
+  int64_t nV = 0, nX = 0, nU = 0, nW = 0, us = 0;
+  int64_t pV = WRITE ? o.oV[a] : 0, pX = WRITE ? o.oX[a] : 0;
+  int64_t pU = WRITE ? o.oU[a] : 0, pW = WRITE ? o.oW[a] : 0;
+  if (l >= 2) {
+    int seen[9];
+    int nseen = 0;
+    const long long px = bx >> 1, py = by >> 1;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int Q = find_box(T, l - 1, px + dx, py + dy);
+        if (Q < 0) continue;
+        if (T.level[Q] == l - 1 && T.child[Q] >= 0) {
+          for (int q = 0; q < 4; ++q) {
+            const int C = T.child[Q] + q;
+            if (T.count[C] == 0 || adjacent(T, C, B)) continue;
+            if (WRITE) o.V[pV++] = C;
+            ++nV;
+          }
+        } else {
+          bool dup = false;
+          for (int s = 0; s < nseen; ++s) dup |= (seen[s] == Q);
+          if (dup) continue;
+          seen[nseen++] = Q;
+          if (T.count[Q] == 0 || adjacent(T, Q, B)) continue;
+          if (WRITE) o.X[pX++] = Q;
+          ++nX;
+        }
+      }
+  }
+  if (T.child[B] < 0) {
+    int seen[9];
+    int nseen = 0;
+    int stack[128];
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int C = find_box(T, l, bx + dx, by + dy);
+        if (C < 0) continue;
+        if (T.level[C] < l) {
+          bool dup = false;
+          for (int s = 0; s < nseen; ++s) dup |= (seen[s] == C);
+          if (dup) continue;
+          seen[nseen++] = C;
+          if (T.count[C] > 0) { if (WRITE) o.U[pU++] = C; ++nU; us += T.count[C]; }
+          continue;
+        }
+        if (T.count[C] == 0) continue;
+        if (T.child[C] < 0) { if (WRITE) o.U[pU++] = C; ++nU; us += T.count[C]; continue; }
+        int sp = 0;
+        for (int q = 3; q >= 0; --q) stack[sp++] = T.child[C] + q;
+        while (sp > 0) {
+          const int Dn = stack[--sp];
+          if (T.count[Dn] == 0) continue;
+          if (adjacent(T, Dn, B)) {
+            if (T.child[Dn] < 0) { if (WRITE) o.U[pU++] = Dn; ++nU; us += T.count[Dn]; }
+            else if (sp + 4 <= 128) { for (int q = 3; q >= 0; --q) stack[sp++] = T.child[Dn] + q; }
+          } else {
+            if (WRITE) o.W[pW++] = Dn;
+            ++nW;
+          }
+        }
+      }
+  }
+  if (!WRITE) {
+    o.cV[a] = nV; o.cX[a] = nX; o.cU[a] = nU; o.cW[a] = nW; o.ustars[a] = us;
+  }
+}
+
+}  // namespace
+
+void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t s) {
+  const int64_t n = P.n;
+  const int depth = P.depth;
+  // ---- 1. bounds + finiteness -------------------------------------------
+  const int nbb = (int)std::min<int64_t>(1024, (n + 255) / 256);
+  std::vector<double> part(5 * (size_t)nbb);
+  {
+    Scratch dpart(&P.da, sizeof(double) * 5 * nbb);
+    k_bounds<<<nbb, 256, 0, s>>>(stars, masses, n, dpart.as<double>());
+    LENS_LAUNCHED("k_bounds");
+    LENS_CUDA(cudaMemcpyAsync(part.data(), dpart.p, sizeof(double) * 5 * nbb,
+                              cudaMemcpyDeviceToHost, s));
+    LENS_CUDA(cudaStreamSynchronize(s));
+  }
+  double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY, bad = 0;
+  for (int b = 0; b < nbb; ++b) {
+    xmin = std::min(xmin, part[5 * b]); xmax = std::max(xmax, part[5 * b + 1]);
+    ymin = std::min(ymin, part[5 * b + 2]); ymax = std::max(ymax, part[5 * b + 3]);
+    bad += part[5 * b + 4];
+  }
+  if (bad > 0) fail(LENS_EINVAL, "non-finite star position or mass");
+  if (P.has_target) {
+    xmin = std::min(xmin, P.target[0]); xmax = std::max(xmax, P.target[1]);
+    ymin = std::min(ymin, P.target[2]); ymax = std::max(ymax, P.target[3]);
+  }
+  double size = std::max(xmax - xmin, ymax - ymin);
+  const double mag = std::max({std::fabs(xmin), std::fabs(xmax), std::fabs(ymin), std::fabs(ymax), 1e-300});
+  if (!(size > 1e-12 * mag)) size = std::max(1.0, 1e-6 * mag);
+  size *= 1.0 + 1e-6;
+  P.root_size = size;
+  P.root_lo[0] = 0.5 * (xmin + xmax) - 0.5 * size;
+  P.root_lo[1] = 0.5 * (ymin + ymax) - 0.5 * size;
+
+  // ---- 2. keys + sort + gather ------------------------------------------
+  P.skey = P.dalloc_n<uint64_t>(n);
+  P.sidx = P.dalloc_n<uint32_t>(n);
+  P.spos = P.dalloc_n<double2>(n);
+  P.smass = P.dalloc_n<double>(n);
+  const double scale = (double)(1ull << depth) / size;
+  k_keys<<<grid_for(n, 256), 256, 0, s>>>(stars, n, P.root_lo[0], P.root_lo[1], scale, depth,
+                                           P.skey, P.sidx);
+  LENS_LAUNCHED("k_keys");
+  radix_sort_u64(P.skey, P.sidx, n, 2 * depth, P.da, s);
+  k_gather<<<grid_for(n, 256), 256, 0, s>>>(stars, masses, P.sidx, n, P.spos, P.smass);
+  LENS_LAUNCHED("k_gather");
+
+  // ---- 3. split nodes ---------------------------------------------------
+  Scratch dcnt(&P.da, sizeof(unsigned long long) * (kMaxDepth + 2) + sizeof(int) * 4);
+  unsigned long long* counts = dcnt.as<unsigned long long>();
+  int* deep = reinterpret_cast<int*>(counts + kMaxDepth + 2);
+  LENS_CUDA(cudaMemsetAsync(dcnt.p, 0, dcnt.bytes, s));
+  k_splits<false><<<grid_for(n, 256), 256, 0, s>>>(P.skey, n, depth, P.leaf, counts, deep,
+                                                   nullptr, nullptr);
+  LENS_LAUNCHED("k_splits<count>");
+  unsigned long long hc[kMaxDepth + 2];
+  int hdeep[4];
+  LENS_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaMemcpyAsync(hdeep, deep, sizeof(hdeep), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaStreamSynchronize(s));
+  if (hdeep[0]) fail(LENS_EDEPTH, "a box at the depth cap still holds more than leaf_size stars "
+                                  "(coincident stars?): raise leaf_size or max_depth");
+  LevelOffsets soff{}, boff{};
+  int64_t nsplit = 0;
+  int maxl = -1;
+  for (int l = 0; l < depth; ++l) {
+    soff.off[l] = nsplit;
+    nsplit += (int64_t)hc[l];
+    if (hc[l]) maxl = l;
+  }
+  for (int l = depth; l <= kMaxDepth + 1; ++l) soff.off[l] = nsplit;
+  P.nlevels = maxl + 2;  // levels 0 .. maxl+1
+  P.level_off.assign(P.nlevels + 1, 0);
+  P.level_off[0] = 0;
+  P.level_off[1] = 1;
+  for (int l = 1; l < P.nlevels; ++l) P.level_off[l + 1] = P.level_off[l] + 4 * (int64_t)hc[l - 1];
+  P.nb = P.level_off[P.nlevels];
+  if (P.nb > (int64_t)INT32_MAX) fail(LENS_ENOMEM, "tree too large");
+  for (int l = 0; l <= kMaxDepth + 1; ++l)
+    boff.off[l] = l <= P.nlevels ? P.level_off[l] : P.nb;
+  boff.nlevels = P.nlevels;
+
+  const int64_t nb = P.nb;
+  P.box_start = P.dalloc_n<int>(nb);
+  P.box_count = P.dalloc_n<int>(nb);
+  P.box_child = P.dalloc_n<int>(nb);
+  P.box_parent = P.dalloc_n<int>(nb);
+  P.box_level = P.dalloc_n<int>(nb);
+  P.box_ix = P.dalloc_n<int>(nb);
+  P.box_iy = P.dalloc_n<int>(nb);
+  P.box_code = P.dalloc_n<uint64_t>(nb);
+  P.box_active = P.dalloc_n<uint8_t>(nb);
+  LENS_CUDA(cudaMemsetAsync(P.box_child, 0xff, sizeof(int) * nb, s));
+  k_root<<<1, 1, 0, s>>>(n, P.box_start, P.box_count, P.box_parent, P.box_level, P.box_ix,
+                          P.box_iy, P.box_code);
+  LENS_LAUNCHED("k_root");
+  if (nsplit > 0) {
+    Scratch dspl(&P.da, sizeof(uint64_t) * nsplit);
+    Scratch dcur(&P.da, sizeof(unsigned long long) * (kMaxDepth + 2));
+    std::vector<unsigned long long> hcur(kMaxDepth + 2);
+    for (int l = 0; l < kMaxDepth + 2; ++l) hcur[l] = (unsigned long long)soff.off[l];
+    LENS_CUDA(cudaMemcpyAsync(dcur.p, hcur.data(), sizeof(unsigned long long) * hcur.size(),
+                              cudaMemcpyHostToDevice, s));
+    k_splits<true><<<grid_for(n, 256), 256, 0, s>>>(P.skey, n, depth, P.leaf, nullptr, nullptr,
+                                                    dcur.as<unsigned long long>(),
+                                                    dspl.as<uint64_t>());
+    LENS_LAUNCHED("k_splits<write>");
+    int bits = 32;
+    while ((1ll << (bits - 32)) <= depth) ++bits;
+    radix_sort_u64(dspl.as<uint64_t>(), nullptr, nsplit, bits, P.da, s);
+    k_fill_boxes<<<grid_for(nsplit, 256), 256, 0, s>>>(
+        dspl.as<uint64_t>(), nsplit, soff, boff, P.skey, n, depth, P.box_start, P.box_count,
+        P.box_child, P.box_parent, P.box_level, P.box_ix, P.box_iy, P.box_code);
+    LENS_LAUNCHED("k_fill_boxes");
+  }
+
+  // ---- 4. active boxes -------------------------------------------------
+  TreeView T{P.box_start, P.box_count, P.box_child, P.box_level, P.box_ix, P.box_iy,
+             P.box_code, boff};
+  Scratch fa(&P.da, sizeof(int64_t) * nb), fl(&P.da, sizeof(int64_t) * nb);
+  Scratch pa(&P.da, sizeof(int64_t) * nb), pl(&P.da, sizeof(int64_t) * nb);
+  k_active_flags<<<grid_for(nb, 256), 256, 0, s>>>(
+      T, nb, P.root_lo[0], P.root_lo[1], P.root_size, P.has_target ? 1 : 0, P.target[0],
+      P.target[1], P.target[2], P.target[3], P.box_active, fa.as<int64_t>(), fl.as<int64_t>());
+  LENS_LAUNCHED("k_active_flags");
+  exclusive_scan_i64(fa.as<int64_t>(), pa.as<int64_t>(), nb, P.da, s);
+  exclusive_scan_i64(fl.as<int64_t>(), pl.as<int64_t>(), nb, P.da, s);
+  std::vector<int64_t> hpos(P.nlevels + 1);
+  int64_t lastf[2], lastp[2];
+  for (int l = 0; l < P.nlevels; ++l)
+    LENS_CUDA(cudaMemcpyAsync(&hpos[l], pa.as<int64_t>() + P.level_off[l], sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaMemcpyAsync(&lastf[0], fa.as<int64_t>() + nb - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaMemcpyAsync(&lastp[0], pa.as<int64_t>() + nb - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaMemcpyAsync(&lastf[1], fl.as<int64_t>() + nb - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaMemcpyAsync(&lastp[1], pl.as<int64_t>() + nb - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaStreamSynchronize(s));
+  P.n_active = lastf[0] + lastp[0];
+  P.n_active_leaves = lastf[1] + lastp[1];
+  hpos[P.nlevels] = P.n_active;
+  P.active_level_off = hpos;
+  P.active = P.dalloc_n<int>(P.n_active);
+  P.active_leaves = P.dalloc_n<int>(P.n_active_leaves);
+  P.box_aidx = P.dalloc_n<int>(nb);
+  k_compact<<<grid_for(nb, 256), 256, 0, s>>>(fa.as<int64_t>(), pa.as<int64_t>(), nb, P.active,
+                                               P.box_aidx);
+  LENS_LAUNCHED("k_compact");
+  P.box_lidx = P.dalloc_n<int>(nb);
+  k_compact<<<grid_for(nb, 256), 256, 0, s>>>(fl.as<int64_t>(), pl.as<int64_t>(), nb,
+                                               P.active_leaves, P.box_lidx);
+  LENS_LAUNCHED("k_compact");
+
+  // ---- 5. interaction lists ------------------------------------------
+  const int64_t na = P.n_active;
+  Scratch cnt(&P.da, sizeof(int64_t) * 5 * (na + 1));
+  int64_t* c = cnt.as<int64_t>();
+  ListOut o{};
+  o.cV = c; o.cX = c + na; o.cU = c + 2 * na; o.cW = c + 3 * na; o.ustars = c + 4 * na;
+  k_lists<false><<<grid_for(na, 128), 128, 0, s>>>(T, P.active, na, o);
+  LENS_LAUNCHED("k_lists<count>");
+  int64_t* offs[4];
+  int64_t tot[4];
+  for (int q = 0; q < 4; ++q) {
+    offs[q] = reinterpret_cast<int64_t*>(P.dalloc(sizeof(int64_t) * (na + 1)));
+    exclusive_scan_i64(c + q * na, offs[q], na, P.da, s);
+  }
+  // totals: last offset + last count; also total U stars
+  std::vector<int64_t> hl(10, 0);
+  for (int q = 0; q < 4; ++q) {
+    if (na > 0) {
+      LENS_CUDA(cudaMemcpyAsync(&hl[2 * q], offs[q] + na - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      LENS_CUDA(cudaMemcpyAsync(&hl[2 * q + 1], c + q * na + na - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    }
+  }
+  Scratch usum(&P.da, sizeof(int64_t) * (na + 1));
+  if (na > 0) {
+    exclusive_scan_i64(c + 4 * na, usum.as<int64_t>(), na, P.da, s);
+    LENS_CUDA(cudaMemcpyAsync(&hl[8], usum.as<int64_t>() + na - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LENS_CUDA(cudaMemcpyAsync(&hl[9], c + 4 * na + na - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  }
+  LENS_CUDA(cudaStreamSynchronize(s));
+  for (int q = 0; q < 4; ++q) tot[q] = hl[2 * q] + hl[2 * q + 1];
+  P.u_stars = hl[8] + hl[9];
+  // write the totals as the sentinel offsets[na]
+  for (int q = 0; q < 4; ++q)
+    LENS_CUDA(cudaMemcpyAsync(offs[q] + na, &tot[q], sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  P.nV = tot[0]; P.nX = tot[1]; P.nU = tot[2]; P.nW = tot[3];
+  P.V_list = P.dalloc_n<int>(tot[0]);
+  P.X_list = P.dalloc_n<int>(tot[1]);
+  P.U_list = P.dalloc_n<int>(tot[2]);
+  P.W_list = P.dalloc_n<int>(tot[3]);
+  o.oV = offs[0]; o.oX = offs[1]; o.oU = offs[2]; o.oW = offs[3];
+  o.V = P.V_list; o.X = P.X_list; o.U = P.U_list; o.W = P.W_list;
+  k_lists<true><<<grid_for(na, 128), 128, 0, s>>>(T, P.active, na, o);
+  LENS_LAUNCHED("k_lists<write>");
+  P.V_off = offs[0];
+  P.X_off = offs[1];
+  P.U_off = offs[2];
+  P.W_off = offs[3];
+  // the host copies of the totals must outlive the async H2D copies above
+  LENS_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace lens

@@ -1,0 +1,340 @@
+"""Thin ctypes binding of liblens.so (include/lens.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Tensors are torch float64 CUDA tensors; the binding passes
+their data pointers and the current CUDA stream.  Plan-owned device memory
+comes from torch's caching allocator through the C ABI's allocator hook.
+There is no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import torch
+
+from . import _build
+
+LENS_OK = 0
+LENS_EINVAL = 1
+LENS_ENOMEM = 2
+LENS_ECUDA = 3
+LENS_EDEPTH = 4
+LENS_EDOMAIN = 5
+LENS_ETIMEOUT = 6
+LENS_EFAULT_INJECTED = 7
+STATUS_NAMES = {0: "LENS_OK", 1: "LENS_EINVAL", 2: "LENS_ENOMEM", 3: "LENS_ECUDA",
+                4: "LENS_EDEPTH", 5: "LENS_EDOMAIN", 6: "LENS_ETIMEOUT",
+                7: "LENS_EFAULT_INJECTED"}
+
+FP64 = 0
+FP32_BULK = 1
+
+# Every symbol include/lens.h declares (checked by the ABI tests).
+EXPORTED = ("lens_fmm_build", "lens_deflect", "lens_deflect_grid", "lens_ipm_map",
+            "lens_deflect_adjoint", "lens_plan_info_get", "lens_plan_destroy",
+            "lens_direct_deflect", "lens_light_curve", "lens_light_curve_grad",
+            "lens_last_error", "lens_version")
+
+
+class LensError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+class lens_build_opts(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("leaf_size", ctypes.c_int), ("prec", ctypes.c_int),
+                ("max_depth", ctypes.c_int), ("has_target_box", ctypes.c_int),
+                ("target_box", ctypes.c_double * 4)]
+
+
+class lens_grid(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("h", ctypes.c_double),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64)]
+
+
+class lens_box(ctypes.Structure):
+    _fields_ = [("u0", ctypes.c_double), ("u1", ctypes.c_double), ("v0", ctypes.c_double),
+                ("v1", ctypes.c_double)]
+
+
+class lens_ipm_stats(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_double), ("area_total", ctypes.c_double),
+                ("area_in_map", ctypes.c_double), ("area_outside", ctypes.c_double),
+                ("area_dropped", ctypes.c_double), ("area_degenerate", ctypes.c_double),
+                ("cells_dropped", ctypes.c_double), ("cells_degenerate", ctypes.c_double),
+                ("chunks", ctypes.c_int64), ("ms_deflect", ctypes.c_double),
+                ("ms_ipm", ctypes.c_double)]
+
+
+class lens_plan_info(ctypes.Structure):
+    _fields_ = [("n_stars", ctypes.c_int64), ("n_boxes", ctypes.c_int64),
+                ("n_leaves", ctypes.c_int64), ("n_active_boxes", ctypes.c_int64),
+                ("n_active_leaves", ctypes.c_int64), ("n_v", ctypes.c_int64),
+                ("n_x", ctypes.c_int64), ("n_u", ctypes.c_int64), ("n_w", ctypes.c_int64),
+                ("u_stars", ctypes.c_int64), ("levels", ctypes.c_int), ("p", ctypes.c_int),
+                ("leaf_size", ctypes.c_int), ("prec", ctypes.c_int),
+                ("root_lo", ctypes.c_double * 2), ("root_size", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64), ("ms_build", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class lens_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load liblens.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("liblens.so is missing: run paper_2211_00354_gb300._build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i64, d, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    st = ctypes.c_int
+    lib.lens_fmm_build.argtypes = [vp, vp, i64, d, d, ctypes.POINTER(lens_build_opts),
+                                   ctypes.POINTER(lens_allocator), vp, ctypes.POINTER(vp)]
+    lib.lens_fmm_build.restype = st
+    lib.lens_deflect.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.lens_deflect.restype = st
+    lib.lens_deflect_grid.argtypes = [vp, ctypes.POINTER(lens_grid), i64, i64, vp, vp, vp]
+    lib.lens_deflect_grid.restype = st
+    lib.lens_ipm_map.argtypes = [vp, ctypes.POINTER(lens_grid), ctypes.POINTER(lens_box), i, i,
+                                 i64, i, vp, ctypes.POINTER(lens_ipm_stats), vp]
+    lib.lens_ipm_map.restype = st
+    lib.lens_deflect_adjoint.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
+    lib.lens_deflect_adjoint.restype = st
+    lib.lens_plan_info_get.argtypes = [vp, ctypes.POINTER(lens_plan_info)]
+    lib.lens_plan_info_get.restype = st
+    lib.lens_plan_destroy.argtypes = [vp]
+    lib.lens_plan_destroy.restype = None
+    lib.lens_direct_deflect.argtypes = [vp, vp, i64, d, d, vp, i64, i, vp, vp,
+                                        ctypes.POINTER(lens_allocator), vp]
+    lib.lens_direct_deflect.restype = st
+    lib.lens_light_curve.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp]
+    lib.lens_light_curve.restype = st
+    lib.lens_light_curve_grad.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp, vp, vp]
+    lib.lens_light_curve_grad.restype = st
+    lib.lens_last_error.argtypes = []
+    lib.lens_last_error.restype = ctypes.c_char_p
+    lib.lens_version.argtypes = []
+    lib.lens_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != LENS_OK:
+        msg = _lib.lens_last_error().decode(errors="replace")
+        raise LensError(status, msg)
+
+
+def _dev(t: torch.Tensor, name: str, shape_last: Optional[int] = None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor (the library has no CPU path)" % name)
+    if t.dtype != torch.float64:
+        raise TypeError("%s must be float64" % name)
+    t = t.contiguous()
+    if shape_last is not None and (t.dim() != 2 or t.shape[1] != shape_last):
+        raise ValueError("%s must have shape (n, %d)" % (name, shape_last))
+    return t
+
+
+def _stream_ptr(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+# Torch caching-allocator hooks (kept alive at module level).
+_live = {}
+
+
+def _torch_alloc(size, stream, ctx):
+    try:
+        ptr = torch.cuda.caching_allocator_alloc(int(size), torch.cuda.current_device(),
+                                                 int(stream or 0))
+        return ptr
+    except Exception:  # allocation failure -> NULL -> LENS_ENOMEM
+        return None
+
+
+def _torch_free(ptr, stream, ctx):
+    try:
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:
+        pass
+
+
+_ALLOC_CB = ALLOC_FN(_torch_alloc)
+_FREE_CB = FREE_FN(_torch_free)
+TORCH_ALLOCATOR = lens_allocator(_ALLOC_CB, _FREE_CB, None)
+
+
+def grid_struct(grid) -> lens_grid:
+    return lens_grid(float(grid.x0), float(grid.y0), float(grid.h), int(grid.nx), int(grid.ny))
+
+
+class LensFMM:
+    """An FMM plan over a star field (lens_fmm_build) and its evaluations."""
+
+    def __init__(self, stars: torch.Tensor, masses: torch.Tensor, kappa_s: float = 0.0,
+                 gamma: float = 0.0, p: int = 16, leaf_size: int = 16, prec: int = FP32_BULK,
+                 target_box=None, max_depth: int = 0, use_torch_allocator: bool = True,
+                 stream=None):
+        lib = load()
+        stars = _dev(stars, "stars", 2)
+        masses = _dev(masses, "masses").reshape(-1)
+        if masses.shape[0] != stars.shape[0]:
+            raise ValueError("stars and masses disagree in length")
+        opts = lens_build_opts()
+        opts.p, opts.leaf_size, opts.prec, opts.max_depth = int(p), int(leaf_size), int(prec), int(max_depth)
+        if target_box is not None:
+            opts.has_target_box = 1
+            for k in range(4):
+                opts.target_box[k] = float(target_box[k])
+        self._handle = ctypes.c_void_p()
+        self.kappa_s, self.gamma, self.p, self.leaf_size, self.prec = (
+            float(kappa_s), float(gamma), int(p), int(leaf_size), int(prec))
+        self.n = int(stars.shape[0])
+        alloc = ctypes.byref(TORCH_ALLOCATOR) if use_torch_allocator else None
+        self._stars, self._masses = stars, masses  # kept alive until the build syncs
+        _check(lib.lens_fmm_build(stars.data_ptr(), masses.data_ptr(), self.n, self.kappa_s,
+                                  self.gamma, ctypes.byref(opts), alloc, _stream_ptr(stream),
+                                  ctypes.byref(self._handle)))
+        self._stars = self._masses = None
+
+    def close(self):
+        if getattr(self, "_handle", None) is not None and self._handle.value:
+            _lib.lens_plan_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self) -> dict:
+        inf = lens_plan_info()
+        _check(_lib.lens_plan_info_get(self._handle, ctypes.byref(inf)))
+        out = {}
+        for name, _ in lens_plan_info._fields_:
+            v = getattr(inf, name)
+            out[name] = list(v) if name == "root_lo" else v
+        return out
+
+    def deflect(self, rays: torch.Tensor, jacobian: bool = False, stream=None):
+        rays = _dev(rays, "rays", 2)
+        m = rays.shape[0]
+        y = torch.empty_like(rays)
+        jac = torch.empty((m, 2, 2), dtype=torch.float64, device=rays.device) if jacobian else None
+        _check(_lib.lens_deflect(self._handle, rays.data_ptr(), m, y.data_ptr(),
+                                 jac.data_ptr() if jacobian else None, _stream_ptr(stream)))
+        return (y, jac) if jacobian else y
+
+    def deflect_grid(self, grid, row0: int = 0, nrows: Optional[int] = None,
+                     jacobian: bool = False, stream=None):
+        g = grid_struct(grid)
+        if nrows is None:
+            nrows = g.ny + 1 - row0
+        dev = torch.device("cuda", torch.cuda.current_device())
+        y = torch.empty((nrows, g.nx + 1, 2), dtype=torch.float64, device=dev)
+        jac = (torch.empty((nrows, g.nx + 1, 2, 2), dtype=torch.float64, device=dev)
+               if jacobian else None)
+        _check(_lib.lens_deflect_grid(self._handle, ctypes.byref(g), int(row0), int(nrows),
+                                      y.data_ptr(), jac.data_ptr() if jacobian else None,
+                                      _stream_ptr(stream)))
+        return (y, jac) if jacobian else y
+
+    def ipm_map(self, grid, box, npx: int, npy: int, max_cells_per_chunk: int = 0,
+                bbox_cap: int = 0, out: Optional[torch.Tensor] = None, stream=None):
+        g = grid_struct(grid)
+        b = lens_box(*(float(v) for v in box))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        mp = out if out is not None else torch.empty((npy, npx), dtype=torch.float64, device=dev)
+        st = lens_ipm_stats()
+        _check(_lib.lens_ipm_map(self._handle, ctypes.byref(g), ctypes.byref(b), int(npx),
+                                 int(npy), int(max_cells_per_chunk), int(bbox_cap),
+                                 mp.data_ptr(), ctypes.byref(st), _stream_ptr(stream)))
+        stats = {name: getattr(st, name) for name, _ in lens_ipm_stats._fields_}
+        return mp, stats
+
+    def adjoint(self, rays: torch.Tensor, grad_y: torch.Tensor, stream=None):
+        rays = _dev(rays, "rays", 2)
+        grad_y = _dev(grad_y, "grad_y", 2)
+        dev = rays.device
+        gxy = torch.empty((self.n, 2), dtype=torch.float64, device=dev)
+        gm = torch.empty((self.n,), dtype=torch.float64, device=dev)
+        gkg = torch.empty((2,), dtype=torch.float64, device=dev)
+        _check(_lib.lens_deflect_adjoint(self._handle, rays.data_ptr(), rays.shape[0],
+                                         grad_y.data_ptr(), gxy.data_ptr(), gm.data_ptr(),
+                                         gkg.data_ptr(), _stream_ptr(stream)))
+        return gxy, gm, gkg
+
+
+def direct_deflect(stars, masses, kappa_s, gamma, rays, prec=FP64, jacobian=False, stream=None):
+    """Eq. 1 by GPU direct summation (lens_direct_deflect)."""
+    lib = load()
+    stars = _dev(stars, "stars", 2)
+    masses = _dev(masses, "masses").reshape(-1)
+    rays = _dev(rays, "rays", 2)
+    y = torch.empty_like(rays)
+    jac = torch.empty((rays.shape[0], 2, 2), dtype=torch.float64, device=rays.device) if jacobian else None
+    _check(lib.lens_direct_deflect(stars.data_ptr(), masses.data_ptr(), stars.shape[0],
+                                   float(kappa_s), float(gamma), rays.data_ptr(), rays.shape[0],
+                                   int(prec), y.data_ptr(), jac.data_ptr() if jacobian else None,
+                                   ctypes.byref(TORCH_ALLOCATOR), _stream_ptr(stream)))
+    return (y, jac) if jacobian else y
+
+
+def light_curve(y, w_ray, samples, sigma, trunc=6.0, stream=None):
+    lib = load()
+    y = _dev(y.reshape(-1, 2), "y", 2)
+    samples = _dev(samples, "samples", 2)
+    F = torch.empty((samples.shape[0],), dtype=torch.float64, device=y.device)
+    _check(lib.lens_light_curve(y.data_ptr(), y.shape[0], float(w_ray), samples.data_ptr(),
+                                samples.shape[0], float(sigma), float(trunc), F.data_ptr(),
+                                _stream_ptr(stream)))
+    return F
+
+
+def light_curve_grad(y, w_ray, samples, sigma, F, T, trunc=6.0, stream=None):
+    lib = load()
+    y = _dev(y.reshape(-1, 2), "y", 2)
+    samples = _dev(samples, "samples", 2)
+    F = _dev(F, "F")
+    T = _dev(T, "T")
+    g = torch.empty_like(y)
+    _check(lib.lens_light_curve_grad(y.data_ptr(), y.shape[0], float(w_ray), samples.data_ptr(),
+                                     samples.shape[0], float(sigma), float(trunc), F.data_ptr(),
+                                     T.data_ptr(), g.data_ptr(), _stream_ptr(stream)))
+    return g
+
+
+def version() -> str:
+    return load().lens_version().decode()

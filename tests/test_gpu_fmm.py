@@ -1,0 +1,154 @@
+"""FMM deflection (lens_fmm_build + lens_deflect / lens_deflect_grid) against
+the FP64 oracle: error falls geometrically with p, meets 1e-10 (FP64 form) and
+2e-5 (FP32-bulk form), on uniform and clustered (adaptive) fields, full grids
+with ragged leaf tiles, Jacobians, and the error paths."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_00354_gb300 import lens, synth
+from helpers import alpha_rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def plan_for(f, p, leaf, prec, box=None):
+    return lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=p, leaf_size=leaf,
+                        prec=prec, target_box=box)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    f = synth.c1_plain(seed=0)
+    x = synth.random_rays(7, 4000, (-10, -10), (10, 10))
+    y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x)
+    return f, x, y_ref
+
+
+def test_error_falls_geometrically_with_p(c1):
+    f, x, y_ref = c1
+    errs = []
+    for p in (4, 8, 12, 16, 24, 32):
+        with plan_for(f, p, 16, lens.FP64, (-10, 10, -10, 10)) as P:
+            y = P.deflect(T(x)).cpu().numpy()
+        errs.append(alpha_rel_err(y, y_ref, x, f.kappa_s, f.gamma).max())
+    print("max rel err vs p:", dict(zip((4, 8, 12, 16, 24, 32), errs)))
+    for a, b in zip(errs, errs[1:]):
+        assert b < 0.6 * a
+    # p = 12 (the plain-method configuration): 0.55^13 a-priori ratio
+    assert errs[2] < 1e-3
+
+
+@pytest.mark.parametrize("prec,p,tol", [(lens.FP64, 48, 1e-10), (lens.FP32_BULK, 24, 2e-5)])
+def test_stated_tolerances(c1, prec, p, tol):
+    f, x, y_ref = c1
+    with plan_for(f, p, 16, prec, (-10, 10, -10, 10)) as P:
+        y = P.deflect(T(x)).cpu().numpy()
+    err = alpha_rel_err(y, y_ref, x, f.kappa_s, f.gamma)
+    print("prec", prec, "p", p, "max", err.max(), "p99.9", np.quantile(err, 0.999))
+    assert err.max() < tol
+
+
+def test_full_grid_matches_oracle_and_ray_path():
+    # every corner of a grid that spans many leaves, with a ragged last tile
+    f = synth.config_uniform(seed=9, n=3000, kappa_star=0.4, kappa_s=0.05, gamma=0.3)
+    grid = synth.Grid(x0=-6.0, y0=-5.0, h=0.037, nx=301, ny=257)
+    xc = grid.corners().reshape(-1, 2)
+    y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, xc)
+    with plan_for(f, 40, 8, lens.FP64, (-6.0, 6.0, -5.0, 5.0)) as P:
+        yg = P.deflect_grid(grid).cpu().numpy().reshape(-1, 2)
+        yr = P.deflect(T(xc)).cpu().numpy()
+        band = P.deflect_grid(grid, row0=100, nrows=33).cpu().numpy()
+        info = P.info()
+    assert info["n_active_leaves"] > 50
+    assert alpha_rel_err(yg, y_ref, xc, f.kappa_s, f.gamma).max() < 1e-10
+    assert alpha_rel_err(yr, y_ref, xc, f.kappa_s, f.gamma).max() < 1e-10
+    np.testing.assert_array_equal(band, yg.reshape(grid.ny + 1, grid.nx + 1, 2)[100:133])
+
+
+def clustered(seed=0, nc=30, per=80):
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(-8, 8, (nc, 2))
+    u = rng.random((nc, per)) * (400.0 / 401.0)
+    r = 0.3 * np.sqrt(u / (1 - u))
+    t = rng.uniform(0, 2 * np.pi, (nc, per))
+    stars = (centres[:, None, :] + np.stack([r * np.cos(t), r * np.sin(t)], -1)).reshape(-1, 2)
+    m = rng.lognormal(0, 1, nc * per)
+    return synth.Field(stars=stars, masses=m, kappa_s=0.3, gamma=0.3, kappa_star=0.2)
+
+
+def test_adaptive_tree_on_clustered_field():
+    # deep, unbalanced tree: U, V, W and X lists all populated
+    f = clustered()
+    x = np.concatenate([synth.random_rays(1, 2000, (-9, -9), (9, 9)),
+                        f.stars[::7] + 1e-3])  # rays inside the clusters too
+    y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x)
+    with plan_for(f, 48, 4, lens.FP64, (-9.5, 9.5, -9.5, 9.5)) as P:
+        y = P.deflect(T(x)).cpu().numpy()
+        info = P.info()
+    print(info)
+    assert info["n_w"] > 0 and info["n_x"] > 0 and info["levels"] > 8
+    err = alpha_rel_err(y, y_ref, x, f.kappa_s, f.gamma)
+    assert err.max() < 1e-10, err.max()
+    with plan_for(f, 24, 16, lens.FP32_BULK, (-9.5, 9.5, -9.5, 9.5)) as P:
+        y32 = P.deflect(T(x)).cpu().numpy()
+    assert alpha_rel_err(y32, y_ref, x, f.kappa_s, f.gamma).max() < 2e-5
+
+
+@pytest.mark.parametrize("prec,tol", [(lens.FP64, 1e-8), (lens.FP32_BULK, 2e-4)])
+def test_jacobian(prec, tol):
+    f = synth.config_uniform(seed=1, n=800, kappa_star=0.3, kappa_s=0.2, gamma=0.4)
+    x = synth.random_rays(2, 1500, (-5, -5), (5, 5))
+    _, jac_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x, jacobian=True)
+    with plan_for(f, 40, 8, prec, (-5, 5, -5, 5)) as P:
+        _, jac = P.deflect(T(x), jacobian=True)
+    d = np.abs(jac.cpu().numpy() - jac_ref).reshape(-1, 4).max(1)
+    sc = np.maximum(np.abs(jac_ref).reshape(-1, 4).max(1), 1.0)
+    assert (d / sc).max() < tol
+
+
+def test_tiny_fields():
+    for n, leaf in ((1, 16), (5, 16), (40, 1), (17, 16)):
+        f = synth.config_uniform(seed=n, n=n, kappa_star=0.3, kappa_s=0.0, gamma=0.1)
+        L = max(1.0, np.abs(f.stars).max())
+        x = synth.random_rays(5, 300, (-L, -L), (L, L))
+        y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x)
+        with plan_for(f, 40, leaf, lens.FP64, (-L, L, -L, L)) as P:
+            y = P.deflect(T(x)).cpu().numpy()
+        assert alpha_rel_err(y, y_ref, x, f.kappa_s, f.gamma).max() < 1e-10, (n, leaf)
+
+
+def test_no_target_box_means_whole_root():
+    f = synth.config_uniform(seed=3, n=500, kappa_star=0.3, kappa_s=0.0, gamma=0.1)
+    lo, hi = f.stars.min(0), f.stars.max(0)
+    x = synth.random_rays(6, 500, lo, hi)
+    y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x)
+    with plan_for(f, 40, 8, lens.FP64, None) as P:
+        y = P.deflect(T(x)).cpu().numpy()
+        assert P.info()["n_active_boxes"] == P.info()["n_boxes"]
+    assert alpha_rel_err(y, y_ref, x, f.kappa_s, f.gamma).max() < 1e-10
+
+
+def test_error_paths():
+    f = synth.config_uniform(seed=0, n=100, kappa_star=0.3, kappa_s=0, gamma=0)
+    with plan_for(f, 8, 8, lens.FP32_BULK, (-1, 1, -1, 1)) as P:
+        with pytest.raises(lens.LensError) as e:
+            P.deflect(T([[5.0, 5.0]]))
+        assert e.value.status == lens.LENS_EDOMAIN
+        with pytest.raises(lens.LensError) as e:
+            P.deflect_grid(synth.Grid(-2, -2, 0.1, 40, 40))
+        assert e.value.status == lens.LENS_EDOMAIN
+        assert P.deflect(T(np.zeros((0, 2)))).shape == (0, 2)
+    # coincident stars beyond leaf_size: depth cap
+    stars = np.zeros((20, 2))
+    with pytest.raises(lens.LensError) as e:
+        lens.LensFMM(T(stars), T(np.ones(20)), p=8, leaf_size=4)
+    assert e.value.status == lens.LENS_EDEPTH
+    with pytest.raises(lens.LensError) as e:
+        lens.LensFMM(T(np.full((4, 2), np.nan)), T(np.ones(4)), p=8, leaf_size=4)
+    assert e.value.status == lens.LENS_EINVAL
