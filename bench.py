@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""FMM-IPM hot-path benchmark (one JSON line on rank 0).
+
+A step is one pass of the whole hot path over the high-magnification map
+workload (kappa_* = 0.45, gamma = 0.45, mean mu = 10; N* = 1.5e6 equal-mass
+stars uniform in a disk; 2000^2-pixel map over 200 Einstein radii; ~1.1e8
+image-plane cells): quadtree build + upward/downward FMM passes
+(lens_fmm_build) and the chunked deflection + IPM map (lens_ipm_map).
+``value`` is corner rays deflected per second (whole job), inputs resident
+in HBM; ``e2e`` is the same metric through the C ABI with host buffers
+(star upload and map download inside the timed region).
+
+--impl reference times the CPU oracle (plain FP64 direct sum of Eq. 1) on the
+host cores on a bounded sample of the same rays, in the same unit.
+Under torchrun every rank computes its own independent map (seed = rank):
+weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "FMM rays deflected/s at stated error vs GPU direct sum; IPM map time (1xGB300)"
+UNIT = "rays/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+FP64_PEAK_TFLOPS = 1.18                           # measured DFMA probe
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--p", type=int, default=16)
+    ap.add_argument("--leaf", type=int, default=8)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--n-stars", type=int, default=1_500_000)
+    ap.add_argument("--npix", type=int, default=2000)
+    ap.add_argument("--half-map", type=float, default=100.0)
+    ap.add_argument("--h", type=float, default=0.063)
+    ap.add_argument("--cap", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(args, seed):
+    from paper_2211_00354_gb300 import synth
+    return synth.c2_high_mag(seed=seed, n=args.n_stars, npix=args.npix, half_map=args.half_map,
+                             h=args.h)
+
+
+def workload_name(args):
+    return ("high-magnification map: N*=%d equal-mass stars uniform in a disk, kappa*=0.45, "
+            "kappa_s=0, gamma=0.45 (mu=10), %d^2 map over %g ER, h=%g ER, p=%d, leaf=%d, %s"
+            % (args.n_stars, args.npix, 2 * args.half_map, args.h, args.p, args.leaf,
+               "FP32-bulk" if args.prec == "fp32" else "FP64"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join(HERE, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_oracle_rays_per_s(f, budget_s, seed):
+    """Time the FP64 CPU oracle (direct sum, OpenMP over all host cores) on a
+    bounded random sample of the workload's corner rays."""
+    import oracle
+    from paper_2211_00354_gb300 import synth
+    oracle.build()
+    _, x = synth.subsample_grid_rays(seed + 100, f.grid, 64)
+    t0 = time.perf_counter()
+    oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x)
+    dt = time.perf_counter() - t0
+    m = int(max(64, min(1 << 17, 64 * budget_s / max(dt, 1e-6))))
+    _, x = synth.subsample_grid_rays(seed + 101, f.grid, m)
+    t0 = time.perf_counter()
+    oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return m / dt, m, dt, cores
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    f = workload(args, args.seed)
+    vals = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state
+    m_used = 0
+    cores = None
+    for _ in range(args.steps):
+        v, m, dt, cores = cpu_oracle_rays_per_s(f, args.cpu_seconds / max(1, args.steps), args.seed)
+        vals.append(v)
+        m_used = m
+    value = statistics.median(vals)
+    sample = ("%d random corner rays of the workload grid per step, FP64 direct sum over all "
+              "%d stars (OpenMP)" % (m_used, f.n))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * m_used / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2211_00354_gb300 import lens
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    f = workload(args, args.seed + rank)
+    g = f.grid
+    prec = lens.FP32_BULK if args.prec == "fp32" else lens.FP64
+    target = (g.x0, g.x0 + g.nx * g.h, g.y0, g.y0 + g.ny * g.h)
+    stars = torch.tensor(f.stars, device=dev)
+    masses = torch.tensor(f.masses, device=dev)
+    mp = torch.empty((f.npy, f.npx), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        P = lens.LensFMM(stars, masses, f.kappa_s, f.gamma, p=args.p, leaf_size=args.leaf,
+                         prec=prec, target_box=target)
+        _, st = P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp)
+        info = P.info()
+        return P, st, info
+
+    for _ in range(args.warmup):
+        P, _, _ = step()
+        P.close()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    tot_ms, stats, infos = 0.0, [], []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        if not args.no_flush:
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P, st, info = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot_ms += e0.elapsed_time(e1)
+        stats.append(st)
+        infos.append(info)
+        P.close()
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ms = tot_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    rays_step = stats[-1]["rays"]
+    total_rays = rays_step * world
+    value = total_rays / (ms / 1e3)
+
+    # ---- kernel-level roofline (live CUDA events inside the library) -----
+    K = args.steps
+    ms_eval = sum(s["ms_eval_kernel"] for s in stats) / K
+    ms_ipm = sum(s["ms_ipm_kernel"] for s in stats) / K
+    pairs = stats[-1]["p2p_pairs"]
+    m2p = stats[-1]["m2p_evals"]
+    eval_flops = 10.0 * pairs + 8.0 * (args.p + 1) * (rays_step + m2p)
+    launches = stats[-1]["chunks"]
+    eval_tflops = eval_flops / (ms_eval / 1e3) / 1e12
+    ipm_bytes = 16.0 * rays_step + 16.0 * stats[-1]["ipm_updates"]
+    ipm_gbs = ipm_bytes / (ms_ipm / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(HERE, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    if ms_eval >= ms_ipm:
+        roof = {"bound": "alu", "kernel": "k_eval (fused L2P+P2P+M2P)",
+                "achieved": eval_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": eval_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "ms_per_launch": ms_eval / launches}
+    else:
+        roof = {"bound": "hbm", "kernel": "k_ipm_fast+k_ipm_slow", "achieved": ipm_gbs,
+                "peak": hbm_peak, "unit": "GB/s", "frac": ipm_gbs / hbm_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "ms_per_launch": ms_ipm / launches}
+
+    # ---- accuracy of this configuration vs the GPU FP64 direct sum ------
+    extra = {}
+    if not args.no_accuracy and rank == 0:
+        from paper_2211_00354_gb300 import synth
+        _, xs = synth.subsample_grid_rays(args.seed + 7, g, 4096)
+        xs_t = torch.tensor(xs, device=dev)
+        P = lens.LensFMM(stars, masses, f.kappa_s, f.gamma, p=args.p, leaf_size=args.leaf,
+                         prec=prec, target_box=target)
+        y = P.deflect(xs_t)
+        P.close()
+        y_ref = lens.direct_deflect(stars, masses, f.kappa_s, f.gamma, xs_t, prec=lens.FP64)
+        a = torch.tensor([1 - f.kappa_s - f.gamma, 1 - f.kappa_s + f.gamma], device=dev,
+                         dtype=torch.float64)
+        al = a * xs_t - y_ref
+        mag = al.norm(dim=1)
+        err = (y - y_ref).norm(dim=1) / torch.clamp(mag, min=1e-3 * mag.pow(2).mean().sqrt())
+        extra["error_vs_gpu_direct_fp64"] = {"max": float(err.max()),
+                                             "p99.9": float(torch.quantile(err, 0.999)),
+                                             "rays": 4096}
+        # GPU direct-sum throughput on the same workload (FP32 and FP64 forms)
+        _, xd = synth.subsample_grid_rays(args.seed + 8, g, 1 << 19)
+        xd_t = torch.tensor(xd, device=dev)
+        for name, pr, nr in (("direct_f32", lens.FP32_BULK, 1 << 19), ("direct_f64", lens.FP64, 1 << 15)):
+            xx = xd_t[:nr].contiguous()
+            lens.direct_deflect(stars, masses, f.kappa_s, f.gamma, xx[:256].contiguous(), prec=pr)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lens.direct_deflect(stars, masses, f.kappa_s, f.gamma, xx, prec=pr)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            extra[name + "_rays_per_s"] = nr / (e0.elapsed_time(e1) / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ---------------
+    e2e = None
+    if not args.no_e2e:
+        h_stars = torch.tensor(f.stars).pin_memory()
+        h_masses = torch.tensor(f.masses).pin_memory()
+        h_map = torch.empty((f.npy, f.npx), dtype=torch.float64).pin_memory()
+        d_stars = torch.empty_like(stars)
+        d_masses = torch.empty_like(masses)
+        e_ms = 0.0
+        for it in range(1 + args.steps):
+            if not args.no_flush:
+                flush.fill_(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d_stars.copy_(h_stars, non_blocking=True)
+            d_masses.copy_(h_masses, non_blocking=True)
+            P = lens.LensFMM(d_stars, d_masses, f.kappa_s, f.gamma, p=args.p, leaf_size=args.leaf,
+                             prec=prec, target_box=target)
+            P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp)
+            h_map.copy_(mp, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            P.close()
+            if it > 0:
+                e_ms += e0.elapsed_time(e1)
+        e_ms /= args.steps
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": total_rays / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h_stars.numel() * 8 + h_masses.numel() * 8),
+               "d2h_bytes_per_step": int(h_map.numel() * 8), "ms_per_step": e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, m, dt, cores = cpu_oracle_rays_per_s(f, args.cpu_seconds, args.seed)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d random corner rays of the workload grid, FP64 direct sum over all %d "
+                         "stars, %.1f s" % (m, f.n, dt)}
+
+    if rank == 0:
+        info = infos[-1]
+        st = stats[-1]
+        mu_mean = float(mp[int(0.05 * f.npy):int(0.95 * f.npy), int(0.05 * f.npx):int(0.95 * f.npx)].mean())
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": workload_name(args), "n_stars": f.n, "cells": g.n_cells,
+                       "grid": [g.nx, g.ny], "npix": [f.npx, f.npy], "p": args.p,
+                       "leaf_size": args.leaf, "bbox_cap_px": args.cap,
+                       "l2": "flushed between steps (256 MiB write)" if not args.no_flush else "not flushed",
+                       "parallelism": "independent map per GPU" if world > 1 else "1 GPU"},
+            "map_ms": ms, "maps_per_s": world / (ms / 1e3),
+            "omega_per_s": 10.0 * f.npx * f.npy * f.n * world / (ms / 1e3),
+            "phase_ms": {"build": info["ms_build"], "deflect": st["ms_deflect"],
+                         "ipm": st["ms_ipm"], "eval_kernel": ms_eval, "ipm_kernels": ms_ipm},
+            "work": {"rays": rays_step, "p2p_pairs": pairs, "m2p_evals": m2p,
+                     "ipm_updates": st["ipm_updates"], "pairs_per_ray": pairs / rays_step},
+            "tree": {k: info[k] for k in ("n_boxes", "n_active_boxes", "n_active_leaves", "n_v",
+                                          "n_x", "n_u", "n_w", "levels")},
+            "ledger": {k: st[k] for k in ("area_total", "area_in_map", "area_outside",
+                                           "area_dropped", "area_degenerate", "cells_dropped")},
+            "mean_mu_interior": mu_mean,
+            "roofline": roof,
+            "ipm_roofline": {"bound": "hbm", "achieved": ipm_gbs, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": ipm_gbs / hbm_peak},
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": int(sum(s_["launches"] for s_ in stats) / K
+                                + sum(i_["build_launches"] for i_ in infos) / K),
+            "wall_s": wall,
+        }
+        line.update(extra)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -101,8 +101,17 @@ typedef struct {
   double cells, area_total, area_in_map, area_outside, area_dropped,
       area_degenerate, cells_dropped, cells_degenerate;
   int64_t chunks;      /* grid chunks processed (Sec. 2.4, step 2) */
-  double ms_deflect;   /* device time in deflection kernels */
-  double ms_ipm;       /* device time in IPM kernels */
+  double ms_deflect;   /* stream time of the deflection phase (all chunks) */
+  double ms_ipm;       /* stream time of the IPM phase (all chunks) */
+  /* algorithmic work and kernel-only device time (CUDA events around the
+   * launches of the fused L2P+P2P+M2P kernel and of the IPM kernels) */
+  double rays;         /* corner rays deflected (chunk seams counted twice) */
+  double p2p_pairs;    /* ray-star pairs summed directly (U lists) */
+  double m2p_evals;    /* ray-box multipole evaluations (W lists) */
+  double ipm_updates;  /* (cell, pixel) map increments */
+  double ms_eval_kernel;
+  double ms_ipm_kernel;
+  int64_t launches;    /* kernels this call launched */
 } lens_ipm_stats;
 
 typedef struct {
@@ -113,6 +122,7 @@ typedef struct {
   double root_lo[2], root_size;
   int64_t device_bytes;        /* plan-owned device memory */
   double ms_build;             /* device time of the last build */
+  int64_t build_launches;      /* kernels the build launched */
 } lens_plan_info;
 
 /* ---- FMM plan ------------------------------------------------------------

@@ -4,6 +4,7 @@
 // (LENS_FAULT=alloc@K | launch@K), and the chunk driver of lens_ipm_map
 // (Sec. 2.4: split the image plane into chunks, deflect each chunk with the
 // FMM, apportion its cells with IPM, accumulate one map).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -55,6 +56,8 @@ void after_launch(const char* name) {
   if (e != cudaSuccess) fail(LENS_ECUDA, std::string("launch ") + name + ": " + cudaGetErrorString(e));
   if (fault_spec().launch_at == k) fail(LENS_EFAULT_INJECTED, std::string("injected launch fault at ") + name);
 }
+
+long long launch_count() { return g_launch_count.load(); }
 
 void fault_point_alloc() {
   const long long k = ++g_alloc_count;
@@ -181,6 +184,7 @@ lens_status lens_fmm_build(const double* stars_xy, const double* masses, int64_t
   LENS_CUDA(cudaEventCreate(&e0));
   LENS_CUDA(cudaEventCreate(&e1));
   LENS_CUDA(cudaEventRecord(e0, S(stream)));
+  const long long l0 = launch_count();
   tree_build(P, stars_xy, masses, S(stream));
   fmm_tables(P, S(stream));
   fmm_p2m(P, S(stream));
@@ -191,6 +195,7 @@ lens_status lens_fmm_build(const double* stars_xy, const double* masses, int64_t
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
   P.ms_build = ms;
+  P.build_launches = launch_count() - l0;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *out = plan;
@@ -213,9 +218,11 @@ lens_status lens_fmm_build(const double* stars_xy, const double* masses, int64_t
 void lens_plan_destroy(lens_plan* plan) {
   if (!plan) return;
   Plan& P = plan->P;
-  cudaStreamSynchronize(P.da.stream);
+  // the plan's arrays may be in use on any stream the caller evaluated on
+  cudaDeviceSynchronize();
   for (void* p : P.owned) P.da.release(p);
   cudaStreamSynchronize(P.da.stream);
+  P.ev_clear();
   delete plan;
 }
 
@@ -236,6 +243,7 @@ lens_status lens_plan_info_get(const lens_plan* plan, lens_plan_info* info) {
   info->root_size = P.root_size;
   info->device_bytes = P.device_bytes;
   info->ms_build = P.ms_build;
+  info->build_launches = P.build_launches;
   info->n_leaves = -1;  // not tracked separately (n_active_leaves is)
   LENS_API_END
 }
@@ -308,10 +316,17 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
 
   Scratch corners(&P.da, sizeof(PixCorner) * (size_t)(rows + 1) * (size_t)(nx + 1));
   Scratch queue(&P.da, sizeof(int) * (size_t)rows * (size_t)nx + sizeof(int) * 4);
-  Scratch sdev(&P.da, sizeof(double) * 8);
+  Scratch sdev(&P.da, sizeof(double) * 16);
   int* qcount = queue.as<int>() + (size_t)rows * (size_t)nx;
   LENS_CUDA(cudaMemsetAsync(map_out, 0, sizeof(double) * (size_t)npx * (size_t)npy, s));
   LENS_CUDA(cudaMemsetAsync(sdev.p, 0, sdev.bytes, s));
+  P.ev_clear();
+  P.timing = true;
+  P.work = sdev.as<double>() + 12;
+  struct Reset {
+    Plan& P;
+    ~Reset() { P.timing = false; P.work = nullptr; P.ev_clear(); }
+  } reset{P};
   std::vector<cudaEvent_t> ev;
   auto mark = [&]() {
     cudaEvent_t e;
@@ -320,6 +335,7 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     ev.push_back(e);
   };
   int64_t chunks = 0;
+  const long long l0 = launch_count();
   for (int64_t r0 = 0; r0 < ny; r0 += rows) {
     const int64_t nr = std::min<int64_t>(rows, ny - r0);
     GridRows g{grid->x0, grid->y0, grid->h, nx, ny, r0, nr + 1};
@@ -327,11 +343,11 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     evaluate_grid_pix(P, g, corners.as<PixCorner>(), ip, s);
     mark();
     ipm_accumulate(corners.as<PixCorner>(), nx, nr, ip, map_out, sdev.as<double>(),
-                   queue.as<int>(), qcount, s);
+                   queue.as<int>(), qcount, s, &P.ev_ipm);
     ++chunks;
   }
   mark();
-  double hs[8];
+  double hs[16];
   LENS_CUDA(cudaMemcpyAsync(hs, sdev.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
   LENS_CUDA(cudaStreamSynchronize(s));
   double msd = 0, msi = 0;
@@ -341,6 +357,16 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     if (k % 2 == 0) msd += ms; else msi += ms;
   }
   for (auto e : ev) cudaEventDestroy(e);
+  // every corner of every chunk must have been owned by exactly one leaf
+  double expect_rays = 0;
+  for (int64_t r0 = 0; r0 < ny; r0 += rows)
+    expect_rays += (double)(std::min<int64_t>(rows, ny - r0) + 1) * (double)(nx + 1);
+  if (hs[12] != expect_rays)
+    fail(LENS_ECUDA, "internal: leaves covered " + std::to_string(hs[12]) + " of " +
+                         std::to_string(expect_rays) + " grid rays");
+  double mse = 0, msk = 0;
+  for (auto& e : P.ev_eval) { float ms = 0; cudaEventElapsedTime(&ms, e.first, e.second); mse += ms; }
+  for (auto& e : P.ev_ipm) { float ms = 0; cudaEventElapsedTime(&ms, e.first, e.second); msk += ms; }
   if (stats) {
     stats->cells = (double)nx * (double)ny;
     stats->area_total = stats->cells * ip.a_cell;
@@ -353,6 +379,13 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     stats->chunks = chunks;
     stats->ms_deflect = msd;
     stats->ms_ipm = msi;
+    stats->rays = hs[12];
+    stats->p2p_pairs = hs[13];
+    stats->m2p_evals = hs[14];
+    stats->ipm_updates = hs[8];
+    stats->ms_eval_kernel = mse;
+    stats->ms_ipm_kernel = msk;
+    stats->launches = launch_count() - l0;
   }
   LENS_API_END
 }

@@ -78,7 +78,13 @@ template <> __device__ __forceinline__ double rcp_r<double>(double x) { return 1
 template <typename R, bool JAC, bool GRID, bool PIX, int RPT>
 __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
   using C = typename cx_t<R>::type;
+  // In the float32 form a near-field difference is taken on split offsets,
+  // d = (x_hi - s_hi) + (x_lo - s_lo): the hi difference is exact when the
+  // star is close to the ray, so d keeps float32 relative accuracy even when
+  // |d| is far below the leaf size.
+  constexpr bool SPLIT = sizeof(R) == 4;
   __shared__ R s_x[kChunk], s_y[kChunk], s_m[kChunk];
+  __shared__ R s_xl[SPLIT ? kChunk : 1], s_yl[SPLIT ? kChunk : 1];
   __shared__ int s_pre[kSeg + 1];
   __shared__ int s_box[kSeg];
   __shared__ C s_L[kMaxOrder + 1];
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
   } else {
     nr_leaf = A.ray_off[k + 1] - A.ray_off[k];
   }
-  R dx[RPT], dy[RPT];
+  R dx[RPT], dy[RPT], dxl[RPT], dyl[RPT];
   double x1[RPT], x2[RPT];
   int64_t oidx[RPT];
   bool ok[RPT];
@@ -140,8 +146,11 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
         oidx[q] = ridx;
       }
     }
-    dx[q] = (R)(x1[q] - cx);
-    dy[q] = (R)(x2[q] - cy);
+    const double ox = x1[q] - cx, oy = x2[q] - cy;
+    dx[q] = (R)ox;
+    dy[q] = (R)oy;
+    dxl[q] = SPLIT ? (R)(ox - (double)dx[q]) : (R)0;
+    dyl[q] = SPLIT ? (R)(oy - (double)dy[q]) : (R)0;
     n1[q].zero(); n2[q].zero(); nj1[q].zero(); nj2[q].zero();
   }
   // ---- P2P over the U list ----------------------------------------------
@@ -180,8 +189,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
         }
         const int st = A.start[s_box[lo]] + (ff - s_pre[lo]);
         const double2 z = A.spos[st];
-        s_x[f] = (R)(z.x - cx);
-        s_y[f] = (R)(z.y - cy);
+        const double ox = z.x - cx, oy = z.y - cy;
+        s_x[f] = (R)ox;
+        s_y[f] = (R)oy;
+        if (SPLIT) {
+          s_xl[f] = (R)(ox - (double)s_x[f]);
+          s_yl[f] = (R)(oy - (double)s_y[f]);
+        }
         s_m[f] = (R)A.smass[st];
       }
       __syncthreads();
@@ -194,9 +208,11 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
         for (int q = 0; q < RPT; ++q) { p1[q] = 0; p2[q] = 0; pj1[q] = 0; pj2[q] = 0; }
         for (int j = lo; j < hi; ++j) {
           const R sx = s_x[j], sy = s_y[j], sm = s_m[j];
+          const R sxl = SPLIT ? s_xl[j] : (R)0, syl = SPLIT ? s_yl[j] : (R)0;
 #pragma unroll
           for (int q = 0; q < RPT; ++q) {
-            const R d1 = dx[q] - sx, d2 = dy[q] - sy;
+            const R d1 = SPLIT ? (dx[q] - sx) + (dxl[q] - sxl) : dx[q] - sx;
+            const R d2 = SPLIT ? (dy[q] - sy) + (dyl[q] - syl) : dy[q] - sy;
             const R r2 = d1 * d1 + d2 * d2;
             const R inv = r2 > (R)0 ? rcp_r<R>(r2) : (R)0;
             const R w = sm * inv;
@@ -346,6 +362,31 @@ __global__ void k_grid_rects(const int* __restrict__ leaves, int64_t nleaf,
   tiles[k] = (ni * nj + tile - 1) / tile;
 }
 
+// algorithmic work of one grid band: rays, ray-star pairs, ray-box M2P evals
+__global__ void k_work_count(const int* __restrict__ leaves, int64_t nleaf,
+                             const int* __restrict__ aidx, const int64_t* __restrict__ rect,
+                             const int64_t* __restrict__ ustar, const int64_t* __restrict__ W_off,
+                             double* __restrict__ work) {
+  __shared__ double sh[3][128];
+  double r = 0, pp = 0, mw = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nleaf;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int a = aidx[leaves[k]];
+    const double nr = (double)rect[4 * k + 1] * (double)rect[4 * k + 3];
+    r += nr;
+    pp += nr * (double)ustar[a];
+    mw += nr * (double)(W_off[a + 1] - W_off[a]);
+  }
+  sh[0][threadIdx.x] = r; sh[1][threadIdx.x] = pp; sh[2][threadIdx.x] = mw;
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) atomicAdd(&work[threadIdx.x], sh[threadIdx.x][0]);
+}
+
 __global__ void k_ray_leaf(const double* __restrict__ rays, int64_t m, const int* __restrict__ child,
                            const int* __restrict__ lidx, double lo_x, double lo_y, double scale,
                            int depth, int* __restrict__ slot, int64_t* __restrict__ counts,
@@ -461,7 +502,20 @@ void grid_impl(Plan& P, const GridRows& g, double* y, double* jac, PixCorner* pi
     A.pinv_du = ip->inv_du; A.pu_off = -ip->u0 * ip->inv_du;
     A.pinv_dv = ip->inv_dv; A.pv_off = -ip->v0 * ip->inv_dv;
   }
-  launch_eval<true, PIX>(P, A, total, jac != nullptr, s);
+  if (P.work) {
+    k_work_count<<<grid_for(nl, 128, 1024), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx,
+                                                        rect.as<int64_t>(), P.ustar_cnt,
+                                                        P.W_off, P.work);
+    LENS_LAUNCHED("k_work_count");
+  }
+  if (P.timing) {
+    auto e = event_pair_begin(s);
+    launch_eval<true, PIX>(P, A, total, jac != nullptr, s);
+    event_pair_end(e, s);
+    P.ev_eval.push_back(e);
+  } else {
+    launch_eval<true, PIX>(P, A, total, jac != nullptr, s);
+  }
 }
 }  // namespace
 

@@ -12,8 +12,10 @@
 //   fast path (one thread per cell): pixel bounding box at most 2 x 2 and a
 //     well-conditioned polygon -> float32 clipping in coordinates local to
 //     the box (a single-pixel box needs no clipping: the fraction is 1);
-//   slow path (one warp per queued cell): any larger or ill-conditioned cell
-//     is redone in float64, the warp's lanes striding over its pixels.
+//   queued path (one warp per cell, lanes striding over the cell's pixels):
+//     larger cells in float32, where pixels that no edge meets take the
+//     polygon's winding number and only boundary pixels are clipped;
+//     ill-conditioned cells (|A_P| small against the box) in float64.
 // Overlaps come from a streaming Sutherland-Hodgman chain against the four
 // sides of the pixel with a running shoelace sum; clipping against a convex
 // window keeps the winding-weighted area, so inverted and self-intersecting
@@ -120,19 +122,19 @@ struct IpmArgs {
 
 __device__ __forceinline__ void block_add_stats(double* stats, double in_map, double outside,
                                                 double dropped, double degen, double ndrop,
-                                                double ndeg) {
-  __shared__ double sh[6][kIpmThreads / 32];
-  double v[6] = {in_map, outside, dropped, degen, ndrop, ndeg};
+                                                double ndeg, double nupd) {
+  __shared__ double sh[7][kIpmThreads / 32];
+  double v[7] = {in_map, outside, dropped, degen, ndrop, ndeg, nupd};
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 7; ++k) {
     double x = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) sh[k][w] = x;
   }
   __syncthreads();
-  if (threadIdx.x < 6) {
+  if (threadIdx.x < 7) {
     double x = 0;
     for (int q = 0; q < kIpmThreads / 32; ++q) x += sh[threadIdx.x][q];
     if (x != 0.0) atomicAdd(&stats[threadIdx.x + 2], x);
@@ -141,7 +143,7 @@ __device__ __forceinline__ void block_add_stats(double* stats, double in_map, do
 
 __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
   const int64_t c = blockIdx.x * (int64_t)kIpmThreads + threadIdx.x;
-  double in_map = 0, outside = 0, dropped = 0, degen = 0, ndrop = 0, ndeg = 0;
+  double in_map = 0, outside = 0, dropped = 0, degen = 0, ndrop = 0, ndeg = 0, nupd = 0;
   const double ac = A.ip.a_cell;
   if (c < A.ncells) {
     const int64_t j = c / A.nx, i = c - j * A.nx;
@@ -184,6 +186,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
         if (ix0 == ix1 && iy0 == iy1) {
           atomicAdd(&A.map[(int64_t)iy0 * A.ip.npx + ix0], A.ip.scale);
           in_map = ac;
+          nupd = 1;
         } else {
           const float inv = 1.0f / A_loc;
           double fin = 0.0;
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
               const float fr = a * inv;
               atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], A.ip.scale * (double)fr);
               fin += (double)fr;
+              nupd += 1;
             }
           }
           in_map = ac * fin;
@@ -207,17 +211,49 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
       }
     }
   }
-  block_add_stats(A.stats, in_map, outside, dropped, degen, ndrop, ndeg);
+  block_add_stats(A.stats, in_map, outside, dropped, degen, ndrop, ndeg, nupd);
 }
 
-// one warp per queued cell, float64
-__global__ void __launch_bounds__(kIpmThreads) k_ipm_slow(IpmArgs A) {
+// Does the segment P->Q meet the closed unit square at (ox, oy)?
+__device__ __forceinline__ bool seg_meets_pixel(float px, float py, float qx, float qy, float ox,
+                                                float oy) {
+  if (fmaxf(px, qx) < ox || fminf(px, qx) > ox + 1.f || fmaxf(py, qy) < oy ||
+      fminf(py, qy) > oy + 1.f)
+    return false;
+  const float dx = qx - px, dy = qy - py;
+  const float c00 = dx * (oy - py) - dy * (ox - px);
+  const float c10 = c00 - dy, c01 = c00 + dx, c11 = c00 + dx - dy;
+  const float lo = fminf(fminf(c00, c10), fminf(c01, c11));
+  const float hi = fmaxf(fmaxf(c00, c10), fmaxf(c01, c11));
+  return !(lo > 0.f || hi < 0.f);
+}
+
+// winding number of the closed polygon q around (x, y)
+__device__ __forceinline__ int winding4(const float* qx, const float* qy, float x, float y) {
+  int w = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float ax = qx[e], ay = qy[e], bx = qx[(e + 1) & 3], by = qy[(e + 1) & 3];
+    const float cr = (bx - ax) * (y - ay) - (x - ax) * (by - ay);
+    if (ay <= y && by > y && cr > 0.f) ++w;
+    else if (by <= y && ay > y && cr < 0.f) --w;
+  }
+  return w;
+}
+
+// One warp per queued cell (bounding box larger than 2 x 2 pixels, or an
+// ill-conditioned polygon).  Well-conditioned cells run in float32 in
+// coordinates local to their box: a pixel that no edge meets is covered by
+// the polygon's winding number exactly, so only pixels on the boundary are
+// clipped.  Ill-conditioned cells (|A_P| small against the box) run the full
+// clip in float64.
+__global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
   const int lane = threadIdx.x & 31;
   const int64_t wg = (blockIdx.x * (int64_t)kIpmThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kIpmThreads) >> 5;
   const int nq = *A.qcount;
   const double ac = A.ip.a_cell;
-  double in_map = 0, outside = 0, degen = 0, ndeg = 0;
+  double in_map = 0, outside = 0, degen = 0, ndeg = 0, nupd = 0;
   for (int64_t t = wg; t < nq; t += nwarps) {
     const int64_t c = A.queue[t];
     const int64_t j = c / A.nx, i = c - j * A.nx;
@@ -227,48 +263,95 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_slow(IpmArgs A) {
     q4[1] = A.yc[j * W + i + 1];
     q4[2] = A.yc[(j + 1) * W + i + 1];
     q4[3] = A.yc[(j + 1) * W + i];
-    double u[4], v[4];
     int ix0 = kFar, ix1 = -kFar, iy0 = kFar, iy1 = -kFar;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      u[k] = (double)q4[k].iu + (double)q4[k].fu;
-      v[k] = (double)q4[k].iv + (double)q4[k].fv;
       ix0 = min(ix0, q4[k].iu); ix1 = max(ix1, q4[k].iu);
       iy0 = min(iy0, q4[k].iv); iy1 = max(iy1, q4[k].iv);
-    }
-    const double A_P = 0.5 * ((u[1] - u[0]) * (v[2] - v[0]) - (u[2] - u[0]) * (v[1] - v[0]) +
-                              (u[2] - u[0]) * (v[3] - v[0]) - (u[3] - u[0]) * (v[2] - v[0]));
-    if (!(fabs(A_P) * A.ip.s_star > 1e-14 * ac)) {
-      if (lane == 0) { degen += ac; ndeg += 1; }
-      continue;
     }
     const int cx0 = max(ix0, 0), cx1 = min(ix1, A.ip.npx - 1);
     const int cy0 = max(iy0, 0), cy1 = min(iy1, A.ip.npy - 1);
     const int64_t w = (int64_t)cx1 - cx0 + 1, npix = w * ((int64_t)cy1 - cy0 + 1);
-    const double inv = 1.0 / A_P;
-    double fin = 0.0;
-    for (int64_t t2 = lane; t2 < npix; t2 += 32) {
-      const int64_t py = cy0 + t2 / w, px = cx0 + t2 % w;
-      double qx[4], qy[4];
+    float fx[4], fy[4];
+    float xmn = 1e30f, xmx = -1e30f, ymn = 1e30f, ymx = -1e30f;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) { qx[k] = u[k] - (double)px; qy[k] = v[k] - (double)py; }
-      const double a = overlap<double>(qx, qy, 0.0, 0.0);
-      if (a == 0.0) continue;
-      const double fr = a * inv;
-      atomicAdd(&A.map[py * A.ip.npx + px], A.ip.scale * fr);
-      fin += fr;
+    for (int k = 0; k < 4; ++k) {
+      fx[k] = (float)(q4[k].iu - ix0) + q4[k].fu;
+      fy[k] = (float)(q4[k].iv - iy0) + q4[k].fv;
+      xmn = fminf(xmn, fx[k]); xmx = fmaxf(xmx, fx[k]);
+      ymn = fminf(ymn, fy[k]); ymx = fmaxf(ymx, fy[k]);
+    }
+    const float A_loc = 0.5f * ((fx[1] - fx[0]) * (fy[2] - fy[0]) - (fx[2] - fx[0]) * (fy[1] - fy[0]) +
+                                (fx[2] - fx[0]) * (fy[3] - fy[0]) - (fx[3] - fx[0]) * (fy[2] - fy[0]));
+    const bool fp32 = fabsf(A_loc) > 2e-2f * (xmx - xmn) * (ymx - ymn) && fabsf(A_loc) > A.thr_area;
+    double fin = 0.0;
+    if (fp32) {
+      const float inv = 1.0f / A_loc;
+      for (int64_t t2 = lane; t2 < npix; t2 += 32) {
+        const int py = cy0 + (int)(t2 / w), px = cx0 + (int)(t2 % w);
+        const float ox = (float)(px - ix0), oy = (float)(py - iy0);
+        bool cut = false;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          cut |= seg_meets_pixel(fx[e], fy[e], fx[(e + 1) & 3], fy[(e + 1) & 3], ox, oy);
+        const float a = cut ? overlap<float>(fx, fy, ox, oy)
+                            : (float)winding4(fx, fy, ox + 0.5f, oy + 0.5f);
+        if (a == 0.0f) continue;
+        const float fr = a * inv;
+        atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], A.ip.scale * (double)fr);
+        fin += (double)fr;
+        nupd += 1;
+      }
+    } else {
+      double u[4], v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        u[k] = (double)q4[k].iu + (double)q4[k].fu;
+        v[k] = (double)q4[k].iv + (double)q4[k].fv;
+      }
+      const double A_P = 0.5 * ((u[1] - u[0]) * (v[2] - v[0]) - (u[2] - u[0]) * (v[1] - v[0]) +
+                                (u[2] - u[0]) * (v[3] - v[0]) - (u[3] - u[0]) * (v[2] - v[0]));
+      if (!(fabs(A_P) * A.ip.s_star > 1e-14 * ac)) {
+        if (lane == 0) { degen += ac; ndeg += 1; }
+        continue;
+      }
+      const double inv = 1.0 / A_P;
+      for (int64_t t2 = lane; t2 < npix; t2 += 32) {
+        const int64_t py = cy0 + t2 / w, px = cx0 + t2 % w;
+        double qx[4], qy[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { qx[k] = u[k] - (double)px; qy[k] = v[k] - (double)py; }
+        const double a = overlap<double>(qx, qy, 0.0, 0.0);
+        if (a == 0.0) continue;
+        const double fr = a * inv;
+        atomicAdd(&A.map[py * A.ip.npx + px], A.ip.scale * fr);
+        fin += fr;
+        nupd += 1;
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fin += __shfl_xor_sync(0xffffffffu, fin, o);
     if (lane == 0) { in_map += ac * fin; outside += ac * (1.0 - fin); }
   }
-  block_add_stats(A.stats, in_map, outside, 0.0, degen, 0.0, ndeg);
+  block_add_stats(A.stats, in_map, outside, 0.0, degen, 0.0, ndeg, nupd);
 }
 
 }  // namespace
 
+std::pair<cudaEvent_t, cudaEvent_t> event_pair_begin(cudaStream_t s) {
+  std::pair<cudaEvent_t, cudaEvent_t> e;
+  LENS_CUDA(cudaEventCreate(&e.first));
+  LENS_CUDA(cudaEventCreate(&e.second));
+  LENS_CUDA(cudaEventRecord(e.first, s));
+  return e;
+}
+void event_pair_end(std::pair<cudaEvent_t, cudaEvent_t>& e, cudaStream_t s) {
+  LENS_CUDA(cudaEventRecord(e.second, s));
+}
+
 void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const IpmParams& ip,
-                    double* map, double* stats_dev, int* queue, int* qcount, cudaStream_t s) {
+                    double* map, double* stats_dev, int* queue, int* qcount, cudaStream_t s,
+                    std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev) {
   const int64_t ncells = nx * nrows_cells;
   if (ncells <= 0) return;
   IpmArgs A{};
@@ -276,12 +359,18 @@ void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const 
   A.queue = queue; A.qcount = qcount; A.ip = ip;
   A.thr_area = (float)(1e-13 * ip.a_cell / ip.s_star);
   LENS_CUDA(cudaMemsetAsync(qcount, 0, sizeof(int), s));
+  std::pair<cudaEvent_t, cudaEvent_t> e;
+  if (ev) e = event_pair_begin(s);
   k_ipm_fast<<<grid_for(ncells, kIpmThreads), kIpmThreads, 0, s>>>(A);
   LENS_LAUNCHED("k_ipm_fast");
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  k_ipm_slow<<<sms * 4, kIpmThreads, 0, s>>>(A);
-  LENS_LAUNCHED("k_ipm_slow");
+  k_ipm_queue<<<sms * 8, kIpmThreads, 0, s>>>(A);
+  LENS_LAUNCHED("k_ipm_queue");
+  if (ev) {
+    event_pair_end(e, s);
+    ev->push_back(e);
+  }
 }
 
 }  // namespace lens

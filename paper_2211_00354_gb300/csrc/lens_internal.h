@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/lens.h"
@@ -29,6 +30,8 @@ void check_cuda(cudaError_t e, const char* what);
 void after_launch(const char* name);
 // Counts allocations (LENS_FAULT=alloc@K); throws LENS_EFAULT_INJECTED when due.
 void fault_point_alloc();
+// kernels launched so far by this process (through LENS_LAUNCHED)
+long long launch_count();
 
 #define LENS_CUDA(call) ::lens::check_cuda((call), #call)
 #define LENS_LAUNCHED(name) ::lens::after_launch(name)
@@ -130,6 +133,20 @@ struct Plan {
   FmmTables tab;
 
   double ms_build = 0;
+  int64_t build_launches = 0;
+
+  // per-active-index count of stars in the U list (work accounting)
+  int64_t* ustar_cnt = nullptr;
+  // optional kernel timing and work counters (lens_ipm_map turns them on)
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_eval, ev_ipm;
+  double* work = nullptr;  // device [4]: rays, p2p pairs, m2p evals, spare
+  void ev_clear() {
+    for (auto& e : ev_eval) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    for (auto& e : ev_ipm) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    ev_eval.clear();
+    ev_ipm.clear();
+  }
 
   void* dalloc(size_t bytes) {
     void* p = da.alloc(bytes);
@@ -182,7 +199,11 @@ struct __align__(16) PixCorner {
 void evaluate_grid_pix(Plan& P, const GridRows& g, PixCorner* out, const IpmParams& ip,
                        cudaStream_t s);
 void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const IpmParams& ip,
-                    double* map, double* stats_dev, int* queue, int* qcount, cudaStream_t s);
+                    double* map, double* stats_dev, int* queue, int* qcount, cudaStream_t s,
+                    std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev);
+// a pair of recorded events bracketing work on a stream
+std::pair<cudaEvent_t, cudaEvent_t> event_pair_begin(cudaStream_t s);
+void event_pair_end(std::pair<cudaEvent_t, cudaEvent_t>& e, cudaStream_t s);
 
 void adjoint(Plan& P, const double* rays, int64_t m, const double* gy,
              double* gxy, double* gm, double* gkg, cudaStream_t s);

@@ -212,7 +212,10 @@ __global__ void k_active_flags(TreeView T, int64_t nb, double root_lo_x, double 
   if (has_target) {
     const double side = root_size / (double)(1ull << T.level[b]);
     const double x0 = root_lo_x + T.ix[b] * side, y0 = root_lo_y + T.iy[b] * side;
-    act = (x0 <= t1) && (x0 + side >= t0) && (y0 <= t3) && (y0 + side >= t2);
+    // a sliver of slack so that rays on the target's edge, whatever rounding
+    // produced them, always fall in an active leaf
+    const double eps = 1e-9 * root_size;
+    act = (x0 <= t1 + eps) && (x0 + side >= t0 - eps) && (y0 <= t3 + eps) && (y0 + side >= t2 - eps);
   }
   active[b] = act ? 1 : 0;
   fa[b] = act ? 1 : 0;
@@ -512,6 +515,10 @@ void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t
       LENS_CUDA(cudaMemcpyAsync(&hl[2 * q + 1], c + q * na + na - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     }
   }
+  P.ustar_cnt = P.dalloc_n<int64_t>(na + 1);
+  if (na > 0)
+    LENS_CUDA(cudaMemcpyAsync(P.ustar_cnt, c + 4 * na, sizeof(int64_t) * na,
+                              cudaMemcpyDeviceToDevice, s));
   Scratch usum(&P.da, sizeof(int64_t) * (na + 1));
   if (na > 0) {
     exclusive_scan_i64(c + 4 * na, usum.as<int64_t>(), na, P.da, s);

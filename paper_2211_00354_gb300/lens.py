@@ -66,7 +66,10 @@ class lens_ipm_stats(ctypes.Structure):
                 ("area_dropped", ctypes.c_double), ("area_degenerate", ctypes.c_double),
                 ("cells_dropped", ctypes.c_double), ("cells_degenerate", ctypes.c_double),
                 ("chunks", ctypes.c_int64), ("ms_deflect", ctypes.c_double),
-                ("ms_ipm", ctypes.c_double)]
+                ("ms_ipm", ctypes.c_double), ("rays", ctypes.c_double),
+                ("p2p_pairs", ctypes.c_double), ("m2p_evals", ctypes.c_double),
+                ("ipm_updates", ctypes.c_double), ("ms_eval_kernel", ctypes.c_double),
+                ("ms_ipm_kernel", ctypes.c_double), ("launches", ctypes.c_int64)]
 
 
 class lens_plan_info(ctypes.Structure):
@@ -77,7 +80,8 @@ class lens_plan_info(ctypes.Structure):
                 ("u_stars", ctypes.c_int64), ("levels", ctypes.c_int), ("p", ctypes.c_int),
                 ("leaf_size", ctypes.c_int), ("prec", ctypes.c_int),
                 ("root_lo", ctypes.c_double * 2), ("root_size", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64), ("ms_build", ctypes.c_double)]
+                ("device_bytes", ctypes.c_int64), ("ms_build", ctypes.c_double),
+                ("build_launches", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

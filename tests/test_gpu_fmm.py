@@ -56,7 +56,8 @@ def test_stated_tolerances(c1, prec, p, tol):
 
 def test_full_grid_matches_oracle_and_ray_path():
     # every corner of a grid that spans many leaves, with a ragged last tile
-    f = synth.config_uniform(seed=9, n=3000, kappa_star=0.4, kappa_s=0.05, gamma=0.3)
+    f = synth.config_uniform(seed=9, n=3000, kappa_star=0.4, kappa_s=0.05, gamma=0.3,
+                             radius=15.0)
     grid = synth.Grid(x0=-6.0, y0=-5.0, h=0.037, nx=301, ny=257)
     xc = grid.corners().reshape(-1, 2)
     y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, xc)
@@ -138,7 +139,10 @@ def test_error_paths():
     f = synth.config_uniform(seed=0, n=100, kappa_star=0.3, kappa_s=0, gamma=0)
     with plan_for(f, 8, 8, lens.FP32_BULK, (-1, 1, -1, 1)) as P:
         with pytest.raises(lens.LensError) as e:
-            P.deflect(T([[5.0, 5.0]]))
+            P.deflect(T([[0.0, 0.0], [1e6, 5.0]]))   # second ray outside the root
+        assert e.value.status == lens.LENS_EDOMAIN
+        with pytest.raises(lens.LensError) as e:
+            P.deflect(T([[float("nan"), 0.0]]))
         assert e.value.status == lens.LENS_EDOMAIN
         with pytest.raises(lens.LensError) as e:
             P.deflect_grid(synth.Grid(-2, -2, 0.1, 40, 40))

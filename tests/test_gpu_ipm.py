@@ -71,7 +71,7 @@ def test_point_lens_magnification():
     h = 0.0125
     grid = synth.Grid(x0=-3.5 + 0.5 * h, y0=-3.5 + 0.5 * h, h=h, nx=560, ny=560)
     with lens.LensFMM(T([[0.0, 0.0]]), T([1.0]), 0.0, 0.0, p=16, leaf_size=4,
-                      prec=lens.FP32_BULK, target_box=(-3.5, 3.5, -3.5, 3.5)) as P:
+                      prec=lens.FP32_BULK, target_box=(-3.6, 3.6, -3.6, 3.6)) as P:
         mp, st = P.ipm_map(grid, box, 40, 40, bbox_cap=64)
     mp = mp.cpu().numpy()
     c = -2.0 + (np.arange(40) + 0.5) * 0.1
