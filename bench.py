@@ -373,7 +373,8 @@ def main():
             "phase_ms": {"build": info["ms_build"], "deflect": st["ms_deflect"],
                          "ipm": st["ms_ipm"], "eval_kernel": ms_eval, "ipm_kernels": ms_ipm},
             "work": {"rays": rays_step, "p2p_pairs": pairs, "m2p_evals": m2p,
-                     "ipm_updates": st["ipm_updates"], "pairs_per_ray": pairs / rays_step},
+                     "ipm_updates": st["ipm_updates"], "cells_queued": st["cells_queued"],
+                     "pairs_per_ray": pairs / rays_step},
             "tree": {k: info[k] for k in ("n_boxes", "n_active_boxes", "n_active_leaves", "n_v",
                                           "n_x", "n_u", "n_w", "levels")},
             "ledger": {k: st[k] for k in ("area_total", "area_in_map", "area_outside",

@@ -109,6 +109,7 @@ typedef struct {
   double p2p_pairs;    /* ray-star pairs summed directly (U lists) */
   double m2p_evals;    /* ray-box multipole evaluations (W lists) */
   double ipm_updates;  /* (cell, pixel) map increments */
+  double cells_queued; /* cells sent to the warp-per-cell path */
   double ms_eval_kernel;
   double ms_ipm_kernel;
   int64_t launches;    /* kernels this call launched */

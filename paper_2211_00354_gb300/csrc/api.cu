@@ -383,6 +383,7 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     stats->p2p_pairs = hs[13];
     stats->m2p_evals = hs[14];
     stats->ipm_updates = hs[8];
+    stats->cells_queued = hs[9];
     stats->ms_eval_kernel = mse;
     stats->ms_ipm_kernel = msk;
     stats->launches = launch_count() - l0;

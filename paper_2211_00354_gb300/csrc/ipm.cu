@@ -9,17 +9,16 @@
 // Corners arrive in pixel coordinates u = (y1 - u0)/du, v = (y2 - v0)/dv,
 // split as (floor, float fraction) by the deflection epilogue, so the common
 // case needs no float64 at all:
-//   fast path (one thread per cell): pixel bounding box at most 2 x 2 and a
-//     well-conditioned polygon -> float32 clipping in coordinates local to
-//     the box (a single-pixel box needs no clipping: the fraction is 1);
+//   fast path (one thread per cell): pixel bounding box at most 4 x 4 and a
+//     well-conditioned polygon -> float32 in coordinates local to the box
+//     (a single-pixel box needs no overlap at all: the fraction is 1);
 //   queued path (one warp per cell, lanes striding over the cell's pixels):
-//     larger cells in float32, where pixels that no edge meets take the
-//     polygon's winding number and only boundary pixels are clipped;
-//     ill-conditioned cells (|A_P| small against the box) in float64.
-// Overlaps come from a streaming Sutherland-Hodgman chain against the four
-// sides of the pixel with a running shoelace sum; clipping against a convex
-// window keeps the winding-weighted area, so inverted and self-intersecting
-// (critical) cells are handled "naively", as the first-order IPM does.
+//     larger cells in float32, ill-conditioned cells (|A_P| small against
+//     the box) in float64.
+// Overlaps come from Green's theorem, edge by edge (the apportioning rule of
+// Sec. 2.3): the result is the winding-number-weighted area, so inverted and
+// self-intersecting (critical) cells are handled "naively", as the
+// first-order IPM does.
 // Ledger per chunk: area_in_map, area_outside, area_dropped (bbox larger
 // than the cap, or a corner beyond 2^30 pixels), area_degenerate
 // (|A_P| <= 1e-14 h^2).
@@ -32,82 +31,39 @@ namespace {
 constexpr int kIpmThreads = 256;
 constexpr int kFar = 0x7fffffff;
 
-// Streaming Sutherland-Hodgman against 4 half-planes (x >= x0, x <= x0+1,
-// y >= y0, y <= y0+1) feeding a shoelace accumulator.
+// Mean of clamp(g, 0, 1) for g running linearly from a to b, written so that
+// no branch cancels digits: equal-region cases are exact, and a kink inside
+// [a, b] contributes each region's piece separately.
 template <typename T>
-struct ClipChain {
-  T bx0, bx1, by0, by1;
-  T fx[4], fy[4], px[4], py[4];
-  bool pin[4], started[4];
-  T ox, oy, lx, ly, area2;
-  int nsink;
+__device__ __forceinline__ T mean_clamp01(T a, T b) {
+  if (a > b) { const T t = a; a = b; b = t; }
+  if (b <= (T)0) return (T)0;
+  if (a >= (T)1) return (T)1;
+  if (a >= (T)0 && b <= (T)1) return (T)0.5 * (a + b);
+  const T lo = a > (T)0 ? a : (T)0, hi = b < (T)1 ? b : (T)1;
+  const T I = (T)0.5 * (hi - lo) * (hi + lo) + (b > (T)1 ? b - (T)1 : (T)0);
+  return I / (b - a);
+}
 
-  __device__ __forceinline__ void init(T x0, T y0) {
-    bx0 = x0; bx1 = x0 + (T)1; by0 = y0; by1 = y0 + (T)1;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) started[k] = false;
-    nsink = 0;
-    area2 = (T)0;
-  }
-  __device__ __forceinline__ T val(int K, T x, T y) const {
-    switch (K) {
-      case 0: return x - bx0;
-      case 1: return bx1 - x;
-      case 2: return y - by0;
-      default: return by1 - y;
-    }
-  }
-  __device__ __forceinline__ void sink(T x, T y) {
-    if (nsink == 0) { ox = x; oy = y; }
-    else if (nsink >= 2) area2 += (lx - ox) * (y - oy) - (x - ox) * (ly - oy);
-    lx = x; ly = y;
-    ++nsink;
-  }
-  template <int K>
-  __device__ __forceinline__ void cross_point(T ax, T ay, T va, T cx, T cy, T vc) {
-    const T t = va / (va - vc);
-    T ix = ax + t * (cx - ax), iy = ay + t * (cy - ay);
-    if (K == 0) ix = bx0; else if (K == 1) ix = bx1; else if (K == 2) iy = by0; else iy = by1;
-    put<K + 1>(ix, iy);
-  }
-  template <int K>
-  __device__ __forceinline__ void put(T x, T y) {
-    if constexpr (K == 4) {
-      sink(x, y);
-    } else {
-      const T v = val(K, x, y);
-      const bool in = v >= (T)0;
-      if (!started[K]) {
-        started[K] = true; fx[K] = x; fy[K] = y;
-      } else if (in != pin[K]) {
-        cross_point<K>(px[K], py[K], val(K, px[K], py[K]), x, y, v);
-      }
-      if (in) put<K + 1>(x, y);
-      px[K] = x; py[K] = y; pin[K] = in;
-    }
-  }
-  template <int K>
-  __device__ __forceinline__ void close() {
-    if constexpr (K < 4) {
-      if (started[K]) {
-        const T vf = val(K, fx[K], fy[K]);
-        const bool fin = vf >= (T)0;
-        if (fin != pin[K]) cross_point<K>(px[K], py[K], val(K, px[K], py[K]), fx[K], fy[K], vf);
-      }
-      close<K + 1>();
-    }
-  }
-  __device__ __forceinline__ T area() const { return (T)0.5 * area2; }
-};
-
+// Signed (winding-weighted) area of the quadrilateral q inside the unit pixel
+// [X, X+1] x [Y, Y+1] by Green's theorem: with g(x) = clamp(x - X, 0, 1) on
+// the row band Y <= y <= Y+1, dg/dx is the pixel's indicator, so the area is
+// the contour integral of g dy; on each straight edge g is piecewise linear,
+// giving (y_b - y_a) * mean(g) over the edge's part inside the band.
 template <typename T>
-__device__ __forceinline__ T overlap(const T* qx, const T* qy, T x0, T y0) {
-  ClipChain<T> c;
-  c.init(x0, y0);
+__device__ __forceinline__ T pixel_area(const T* qx, const T* qy, T X, T Y) {
+  T s = (T)0;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) c.template put<0>(qx[k], qy[k]);
-  c.template close<0>();
-  return c.area();
+  for (int e = 0; e < 4; ++e) {
+    const T x0 = qx[e], y0 = qy[e], x1 = qx[(e + 1) & 3], y1 = qy[(e + 1) & 3];
+    if (y1 == y0) continue;
+    const T ya = fmin(fmax(y0, Y), Y + (T)1), yb = fmin(fmax(y1, Y), Y + (T)1);
+    if (ya == yb) continue;
+    const T sl = (x1 - x0) / (y1 - y0);
+    const T xa = x0 + (ya - y0) * sl, xb = x0 + (yb - y0) * sl;
+    s += (yb - ya) * mean_clamp01<T>(xa - X, xb - X);
+  }
+  return s;
 }
 
 struct IpmArgs {
@@ -140,6 +96,8 @@ __device__ __forceinline__ void block_add_stats(double* stats, double in_map, do
     if (x != 0.0) atomicAdd(&stats[threadIdx.x + 2], x);
   }
 }
+
+constexpr int kSmallBox = 4;  // cells whose pixel box is at most 4 x 4 stay per-thread
 
 __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
   const int64_t c = blockIdx.x * (int64_t)kIpmThreads + threadIdx.x;
@@ -180,8 +138,8 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
       const float A_loc = 0.5f * ((qx[1] - qx[0]) * (qy[2] - qy[0]) - (qx[2] - qx[0]) * (qy[1] - qy[0]) +
                                   (qx[2] - qx[0]) * (qy[3] - qy[0]) - (qx[3] - qx[0]) * (qy[2] - qy[0]));
       const float ext = (xmx - xmn) * (ymx - ymn);
-      const bool small = (ix1 - ix0 <= 1) && (iy1 - iy0 <= 1);
-      const bool good = fabsf(A_loc) > 1e-3f * ext && fabsf(A_loc) > A.thr_area;
+      const bool small = (ix1 - ix0 < kSmallBox) && (iy1 - iy0 < kSmallBox);
+      const bool good = fabsf(A_loc) > 2e-2f * ext && fabsf(A_loc) > A.thr_area;
       if (small && good) {
         if (ix0 == ix1 && iy0 == iy1) {
           atomicAdd(&A.map[(int64_t)iy0 * A.ip.npx + ix0], A.ip.scale);
@@ -190,11 +148,11 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
         } else {
           const float inv = 1.0f / A_loc;
           double fin = 0.0;
-          for (int py = iy0; py <= iy1; ++py) {
-            if (py < 0 || py >= A.ip.npy) continue;
-            for (int px = ix0; px <= ix1; ++px) {
-              if (px < 0 || px >= A.ip.npx) continue;
-              const float a = overlap<float>(qx, qy, (float)(px - ix0), (float)(py - iy0));
+          const int py0 = max(iy0, 0), py1 = min(iy1, A.ip.npy - 1);
+          const int px0 = max(ix0, 0), px1 = min(ix1, A.ip.npx - 1);
+          for (int py = py0; py <= py1; ++py) {
+            for (int px = px0; px <= px1; ++px) {
+              const float a = pixel_area<float>(qx, qy, (float)(px - ix0), (float)(py - iy0));
               if (a == 0.0f) continue;
               const float fr = a * inv;
               atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], A.ip.scale * (double)fr);
@@ -214,39 +172,10 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
   block_add_stats(A.stats, in_map, outside, dropped, degen, ndrop, ndeg, nupd);
 }
 
-// Does the segment P->Q meet the closed unit square at (ox, oy)?
-__device__ __forceinline__ bool seg_meets_pixel(float px, float py, float qx, float qy, float ox,
-                                                float oy) {
-  if (fmaxf(px, qx) < ox || fminf(px, qx) > ox + 1.f || fmaxf(py, qy) < oy ||
-      fminf(py, qy) > oy + 1.f)
-    return false;
-  const float dx = qx - px, dy = qy - py;
-  const float c00 = dx * (oy - py) - dy * (ox - px);
-  const float c10 = c00 - dy, c01 = c00 + dx, c11 = c00 + dx - dy;
-  const float lo = fminf(fminf(c00, c10), fminf(c01, c11));
-  const float hi = fmaxf(fmaxf(c00, c10), fmaxf(c01, c11));
-  return !(lo > 0.f || hi < 0.f);
-}
-
-// winding number of the closed polygon q around (x, y)
-__device__ __forceinline__ int winding4(const float* qx, const float* qy, float x, float y) {
-  int w = 0;
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const float ax = qx[e], ay = qy[e], bx = qx[(e + 1) & 3], by = qy[(e + 1) & 3];
-    const float cr = (bx - ax) * (y - ay) - (x - ax) * (by - ay);
-    if (ay <= y && by > y && cr > 0.f) ++w;
-    else if (by <= y && ay > y && cr < 0.f) --w;
-  }
-  return w;
-}
-
-// One warp per queued cell (bounding box larger than 2 x 2 pixels, or an
-// ill-conditioned polygon).  Well-conditioned cells run in float32 in
-// coordinates local to their box: a pixel that no edge meets is covered by
-// the polygon's winding number exactly, so only pixels on the boundary are
-// clipped.  Ill-conditioned cells (|A_P| small against the box) run the full
-// clip in float64.
+// One warp per queued cell (pixel box larger than 4 x 4, or an
+// ill-conditioned polygon), lanes striding over the cell's pixels.
+// Well-conditioned cells run in float32 in coordinates local to their box;
+// ill-conditioned ones (|A_P| small against the box) run the clip in float64.
 __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
   const int lane = threadIdx.x & 31;
   const int64_t wg = (blockIdx.x * (int64_t)kIpmThreads + threadIdx.x) >> 5;
@@ -254,6 +183,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
   const int nq = *A.qcount;
   const double ac = A.ip.a_cell;
   double in_map = 0, outside = 0, degen = 0, ndeg = 0, nupd = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&A.stats[9], (double)nq);
   for (int64_t t = wg; t < nq; t += nwarps) {
     const int64_t c = A.queue[t];
     const int64_t j = c / A.nx, i = c - j * A.nx;
@@ -289,13 +219,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
       const float inv = 1.0f / A_loc;
       for (int64_t t2 = lane; t2 < npix; t2 += 32) {
         const int py = cy0 + (int)(t2 / w), px = cx0 + (int)(t2 % w);
-        const float ox = (float)(px - ix0), oy = (float)(py - iy0);
-        bool cut = false;
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          cut |= seg_meets_pixel(fx[e], fy[e], fx[(e + 1) & 3], fy[(e + 1) & 3], ox, oy);
-        const float a = cut ? overlap<float>(fx, fy, ox, oy)
-                            : (float)winding4(fx, fy, ox + 0.5f, oy + 0.5f);
+        const float a = pixel_area<float>(fx, fy, (float)(px - ix0), (float)(py - iy0));
         if (a == 0.0f) continue;
         const float fr = a * inv;
         atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], A.ip.scale * (double)fr);
@@ -321,7 +245,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
         double qx[4], qy[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) { qx[k] = u[k] - (double)px; qy[k] = v[k] - (double)py; }
-        const double a = overlap<double>(qx, qy, 0.0, 0.0);
+        const double a = pixel_area<double>(qx, qy, 0.0, 0.0);
         if (a == 0.0) continue;
         const double fr = a * inv;
         atomicAdd(&A.map[py * A.ip.npx + px], A.ip.scale * fr);
