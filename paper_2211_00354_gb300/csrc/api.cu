@@ -370,12 +370,12 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
   if (stats) {
     stats->cells = (double)nx * (double)ny;
     stats->area_total = stats->cells * ip.a_cell;
-    stats->area_in_map = hs[2];
-    stats->area_outside = hs[3];
-    stats->area_dropped = hs[4];
-    stats->area_degenerate = hs[5];
-    stats->cells_dropped = hs[6];
-    stats->cells_degenerate = hs[7];
+    stats->area_in_map = ip.a_cell * hs[2];
+    stats->area_outside = ip.a_cell * hs[3];
+    stats->area_dropped = ip.a_cell * hs[4];
+    stats->area_degenerate = ip.a_cell * hs[5];
+    stats->cells_dropped = hs[4];
+    stats->cells_degenerate = hs[5];
     stats->chunks = chunks;
     stats->ms_deflect = msd;
     stats->ms_ipm = msi;

@@ -101,3 +101,50 @@ namespace lens {
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
 }  // namespace lens
+
+namespace lens {
+// ---- float-float ("double-single") arithmetic on the float32 pipe --------
+// A value is hi + lo with |lo| <= ulp(hi)/2 (about 48 significant bits).  On
+// GB300 the float64 pipe is ~60x slower than float32, so per-ray offsets and
+// the lens-equation epilogue run in this form; float64 is used once per CTA.
+struct ff {
+  float hi, lo;
+};
+__host__ __device__ __forceinline__ ff ff_of(double x) {
+  ff r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ ff ff_norm(float s, float e) {  // |s| >= |e|
+  ff r;
+  r.hi = s + e;
+  r.lo = e - (r.hi - s);
+  return r;
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  return ff_norm(s, e);
+}
+__device__ __forceinline__ ff ff_add(ff a, float b) {
+  float s, e;
+  two_sum(a.hi, b, s, e);
+  e += a.lo;
+  return ff_norm(s, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return ff_norm(p, e);
+}
+__device__ __forceinline__ ff ff_mul(ff a, float b) {
+  const float p = a.hi * b;
+  const float e = fmaf(a.hi, b, -p) + a.lo * b;
+  return ff_norm(p, e);
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+}  // namespace lens

@@ -124,33 +124,53 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
     nr_leaf = A.ray_off[k + 1] - A.ray_off[k];
   }
   R dx[RPT], dy[RPT], dxl[RPT], dyl[RPT];
-  double x1[RPT], x2[RPT];
+  double x1[RPT], x2[RPT];  // float64 ray positions (float64 form, and the ray path)
   int64_t oidx[RPT];
   bool ok[RPT];
   Acc<R> n1[RPT], n2[RPT], nj1[RPT], nj2[RPT];
+  // float32 form on the grid: a ray's offset from the leaf centre is
+  // (x(i0) - c) + (i - i0) h, formed in float-float from per-CTA float64
+  // constants, so no float64 instruction runs per ray.
+  ff bx{0.f, 0.f}, by{0.f, 0.f}, hf{0.f, 0.f};
+  if (SPLIT && GRID) {
+    bx = ff_of(grid_coord(A.gx0, i0, A.gh) - cx);
+    by = ff_of(grid_coord(A.gy0, j0, A.gh) - cy);
+    hf = ff_of(A.gh);
+  }
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int64_t loc = tile * (kEvalThreads * RPT) + (int64_t)q * kEvalThreads + tid;
     ok[q] = loc < nr_leaf;
     x1[q] = cx; x2[q] = cy; oidx[q] = 0;
+    dx[q] = 0; dy[q] = 0; dxl[q] = 0; dyl[q] = 0;
     if (ok[q]) {
       if (GRID) {
-        const int64_t i = i0 + loc % ni, j = j0 + loc / ni;
-        x1[q] = grid_coord(A.gx0, i, A.gh);
-        x2[q] = grid_coord(A.gy0, j, A.gh);
+        const int64_t di = loc % ni, dj = loc / ni;
+        const int64_t i = i0 + di, j = j0 + dj;
         oidx[q] = (j - A.grow0) * A.gnx1 + i;
+        if (SPLIT) {
+          const ff ox = ff_add(bx, ff_mul(hf, (float)di));
+          const ff oy = ff_add(by, ff_mul(hf, (float)dj));
+          dx[q] = (R)ox.hi; dxl[q] = (R)ox.lo;
+          dy[q] = (R)oy.hi; dyl[q] = (R)oy.lo;
+        } else {
+          x1[q] = grid_coord(A.gx0, i, A.gh);
+          x2[q] = grid_coord(A.gy0, j, A.gh);
+        }
       } else {
         const int64_t ridx = A.perm[A.ray_off[k] + loc];
         x1[q] = A.rays[2 * ridx];
         x2[q] = A.rays[2 * ridx + 1];
         oidx[q] = ridx;
       }
+      if (!(SPLIT && GRID)) {
+        const double ox = x1[q] - cx, oy = x2[q] - cy;
+        dx[q] = (R)ox;
+        dy[q] = (R)oy;
+        dxl[q] = SPLIT ? (R)(ox - (double)dx[q]) : (R)0;
+        dyl[q] = SPLIT ? (R)(oy - (double)dy[q]) : (R)0;
+      }
     }
-    const double ox = x1[q] - cx, oy = x2[q] - cy;
-    dx[q] = (R)ox;
-    dy[q] = (R)oy;
-    dxl[q] = SPLIT ? (R)(ox - (double)dx[q]) : (R)0;
-    dyl[q] = SPLIT ? (R)(oy - (double)dy[q]) : (R)0;
     n1[q].zero(); n2[q].zero(); nj1[q].zero(); nj2[q].zero();
   }
   // ---- P2P over the U list ----------------------------------------------
@@ -277,9 +297,29 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
     }
   }
   // ---- L2P + epilogue ----------------------------------------------------
+  // y1 = a x1 - alpha1 = (a c1 - b0_1) + (a dx - f_1 - near_1)
+  // y2 = b x2 - alpha2 = (b c2 + b0_2) + (b dy + f_2 - near_2)
+  // (alpha = conj(f_total), f_total = b0 + f + near).  The bracketed leaf
+  // constants are float64 once per CTA; the per-ray parts are float-float in
+  // the float32 form.
   __syncthreads();
   const R ir = (R)(1.0 / r);
   const double2 b0 = Lb[0];
+  const double K1 = A.a * cx - b0.x, K2 = A.b * cy + b0.y;
+  const ff af = ff_of(A.a), bf = ff_of(A.b);
+  ff U1f{0.f, 0.f}, V1f{0.f, 0.f}, iduf{0.f, 0.f}, idvf{0.f, 0.f};
+  int64_t U1i = 0, V1i = 0;
+  bool far_leaf = false;
+  if (PIX) {
+    const double U1 = fma(K1, A.pinv_du, A.pu_off), V1 = fma(K2, A.pinv_dv, A.pv_off);
+    far_leaf = !(fabs(U1) < 1073741824.0 && fabs(V1) < 1073741824.0);
+    if (!far_leaf) {
+      const double fu = floor(U1), fv = floor(V1);
+      U1i = (int64_t)fu; V1i = (int64_t)fv;
+      U1f = ff_of(U1 - fu); V1f = ff_of(V1 - fv);
+    }
+    iduf = ff_of(A.pinv_du); idvf = ff_of(A.pinv_dv);
+  }
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     if (!ok[q]) continue;
@@ -297,24 +337,56 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
       }
     }
     f = f + fw[q];
-    const double fre = b0.x + (double)f.x;
-    const double fim = b0.y + (double)f.y;
-    const double al1 = fre + n1[q].value();
-    const double al2 = -fim + n2[q].value();
-    const double y1 = fma(A.a, x1[q], -al1);
-    const double y2 = fma(A.b, x2[q], -al2);
-    if (PIX) {
-      const double u = fma(y1, A.pinv_du, A.pu_off), v = fma(y2, A.pinv_dv, A.pv_off);
-      PixCorner pc;
-      if (fabs(u) < 1073741824.0 && fabs(v) < 1073741824.0) {
-        const double fu = floor(u), fv = floor(v);
-        pc.iu = (int)fu; pc.fu = (float)(u - fu);
-        pc.iv = (int)fv; pc.fv = (float)(v - fv);
-      } else {
-        pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
+    double y1, y2;
+    if constexpr (SPLIT) {
+      ff T1 = ff_mul(af, ff{(float)dx[q], (float)dxl[q]});
+      T1 = ff_add(T1, -(float)f.x);
+      T1 = ff_add(T1, ff{-n1[q].v.hi, -n1[q].v.lo});
+      ff T2 = ff_mul(bf, ff{(float)dy[q], (float)dyl[q]});
+      T2 = ff_add(T2, (float)f.y);
+      T2 = ff_add(T2, ff{-n2[q].v.hi, -n2[q].v.lo});
+      if (PIX) {
+        PixCorner pc;
+        const ff U = ff_add(U1f, ff_mul(iduf, T1));
+        const ff V = ff_add(V1f, ff_mul(idvf, T2));
+        bool far = far_leaf || !(fabsf(U.hi) < 5.0e8f) || !(fabsf(V.hi) < 5.0e8f);
+        float ku = floorf(U.hi), kv = floorf(V.hi);
+        float fu = (U.hi - ku) + U.lo, fv = (V.hi - kv) + V.lo;
+        if (fu < 0.f) { ku -= 1.f; fu += 1.f; } else if (fu >= 1.f) { ku += 1.f; fu -= 1.f; }
+        if (fv < 0.f) { kv -= 1.f; fv += 1.f; } else if (fv >= 1.f) { kv += 1.f; fv -= 1.f; }
+        const int64_t iu = U1i + (int64_t)ku, iv = V1i + (int64_t)kv;
+        far = far || !(iu > -1073741824ll && iu < 1073741824ll && iv > -1073741824ll &&
+                       iv < 1073741824ll);
+        if (!far) {
+          pc.iu = (int)iu; pc.fu = fu; pc.iv = (int)iv; pc.fv = fv;
+        } else {
+          pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
+        }
+        A.pix[oidx[q]] = pc;
+        continue;
       }
-      A.pix[oidx[q]] = pc;
-      continue;
+      y1 = K1 + ff_to_double(T1);
+      y2 = K2 + ff_to_double(T2);
+    } else {
+      const double fre = b0.x + (double)f.x;
+      const double fim = b0.y + (double)f.y;
+      const double al1 = fre + n1[q].value();
+      const double al2 = -fim + n2[q].value();
+      y1 = fma(A.a, x1[q], -al1);
+      y2 = fma(A.b, x2[q], -al2);
+      if (PIX) {
+        const double u = fma(y1, A.pinv_du, A.pu_off), v = fma(y2, A.pinv_dv, A.pv_off);
+        PixCorner pc;
+        if (fabs(u) < 1073741824.0 && fabs(v) < 1073741824.0) {
+          const double fu = floor(u), fv = floor(v);
+          pc.iu = (int)fu; pc.fu = (float)(u - fu);
+          pc.iv = (int)fv; pc.fv = (float)(v - fv);
+        } else {
+          pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
+        }
+        A.pix[oidx[q]] = pc;
+        continue;
+      }
     }
     A.y[2 * oidx[q]] = y1;
     A.y[2 * oidx[q] + 1] = y2;

@@ -74,26 +74,43 @@ struct IpmArgs {
   int* queue; int* qcount;
   IpmParams ip;
   float thr_area;       // fast-path lower bound on |A_P| in pixel units
+  float scale_f;        // ip.scale in float32
 };
 
-__device__ __forceinline__ void block_add_stats(double* stats, double in_map, double outside,
-                                                double dropped, double degen, double ndrop,
-                                                double ndeg, double nupd) {
-  __shared__ double sh[7][kIpmThreads / 32];
-  double v[7] = {in_map, outside, dropped, degen, ndrop, ndeg, nupd};
+// Ledger of one thread: fractions in float32, counts in integers (no
+// float64 per cell).  Device stats slots: [2] sum of in-map fractions,
+// [3] sum of outside fractions (cells wholly outside count 1), [4] dropped
+// cells, [5] degenerate cells, [8] map increments, [9] queued cells; the
+// host multiplies by the cell area.
+struct Ledger {
+  float fin = 0.f, fout = 0.f;
+  unsigned ndrop = 0, ndeg = 0, nupd = 0;
+};
+
+__device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L) {
+  __shared__ float shf[2][kIpmThreads / 32];
+  __shared__ unsigned shu[3][kIpmThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float f0 = L.fin, f1 = L.fout;
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    double x = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) sh[k][w] = x;
+  for (int o = 16; o > 0; o >>= 1) {
+    f0 += __shfl_xor_sync(0xffffffffu, f0, o);
+    f1 += __shfl_xor_sync(0xffffffffu, f1, o);
+  }
+  const unsigned u0 = __reduce_add_sync(0xffffffffu, L.ndrop);
+  const unsigned u1 = __reduce_add_sync(0xffffffffu, L.ndeg);
+  const unsigned u2 = __reduce_add_sync(0xffffffffu, L.nupd);
+  if (lane == 0) {
+    shf[0][w] = f0; shf[1][w] = f1;
+    shu[0][w] = u0; shu[1][w] = u1; shu[2][w] = u2;
   }
   __syncthreads();
-  if (threadIdx.x < 7) {
+  if (threadIdx.x < 5) {
     double x = 0;
-    for (int q = 0; q < kIpmThreads / 32; ++q) x += sh[threadIdx.x][q];
-    if (x != 0.0) atomicAdd(&stats[threadIdx.x + 2], x);
+    for (int q = 0; q < kIpmThreads / 32; ++q)
+      x += threadIdx.x < 2 ? (double)shf[threadIdx.x][q] : (double)shu[threadIdx.x - 2][q];
+    const int slot = threadIdx.x < 4 ? 2 + threadIdx.x : 8;
+    if (x != 0.0) atomicAdd(&stats[slot], x);
   }
 }
 
@@ -101,8 +118,7 @@ constexpr int kSmallBox = 4;  // cells whose pixel box is at most 4 x 4 stay per
 
 __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
   const int64_t c = blockIdx.x * (int64_t)kIpmThreads + threadIdx.x;
-  double in_map = 0, outside = 0, dropped = 0, degen = 0, ndrop = 0, ndeg = 0, nupd = 0;
-  const double ac = A.ip.a_cell;
+  Ledger led;
   if (c < A.ncells) {
     const int64_t j = c / A.nx, i = c - j * A.nx;
     const int64_t W = A.nx + 1;
@@ -120,11 +136,11 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
       iy0 = min(iy0, q4[k].iv); iy1 = max(iy1, q4[k].iv);
     }
     if (far) {
-      dropped = ac; ndrop = 1;
+      led.ndrop = 1;
     } else if (ix1 < 0 || iy1 < 0 || ix0 > A.ip.npx - 1 || iy0 > A.ip.npy - 1) {
-      outside = ac;
+      led.fout = 1.f;
     } else if (A.ip.cap > 0 && ((int64_t)ix1 - ix0 + 1 > A.ip.cap || (int64_t)iy1 - iy0 + 1 > A.ip.cap)) {
-      dropped = ac; ndrop = 1;
+      led.ndrop = 1;
     } else {
       float qx[4], qy[4];
       float xmn = 1e30f, xmx = -1e30f, ymn = 1e30f, ymx = -1e30f;
@@ -143,11 +159,11 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
       if (small && good) {
         if (ix0 == ix1 && iy0 == iy1) {
           atomicAdd(&A.map[(int64_t)iy0 * A.ip.npx + ix0], A.ip.scale);
-          in_map = ac;
-          nupd = 1;
+          led.fin = 1.f;
+          led.nupd = 1;
         } else {
           const float inv = 1.0f / A_loc;
-          double fin = 0.0;
+          float fin = 0.f;
           const int py0 = max(iy0, 0), py1 = min(iy1, A.ip.npy - 1);
           const int px0 = max(ix0, 0), px1 = min(ix1, A.ip.npx - 1);
           for (int py = py0; py <= py1; ++py) {
@@ -155,13 +171,13 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
               const float a = pixel_area<float>(qx, qy, (float)(px - ix0), (float)(py - iy0));
               if (a == 0.0f) continue;
               const float fr = a * inv;
-              atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], A.ip.scale * (double)fr);
-              fin += (double)fr;
-              nupd += 1;
+              atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], (double)(A.scale_f * fr));
+              fin += fr;
+              led.nupd += 1;
             }
           }
-          in_map = ac * fin;
-          outside = ac * (1.0 - fin);
+          led.fin = fin;
+          led.fout = 1.f - fin;
         }
       } else {
         const int slot = atomicAdd(A.qcount, 1);
@@ -169,7 +185,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
       }
     }
   }
-  block_add_stats(A.stats, in_map, outside, dropped, degen, ndrop, ndeg, nupd);
+  block_add_stats(A.stats, led);
 }
 
 // One warp per queued cell (pixel box larger than 4 x 4, or an
@@ -182,7 +198,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
   const int64_t nwarps = ((int64_t)gridDim.x * kIpmThreads) >> 5;
   const int nq = *A.qcount;
   const double ac = A.ip.a_cell;
-  double in_map = 0, outside = 0, degen = 0, ndeg = 0, nupd = 0;
+  Ledger led;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&A.stats[9], (double)nq);
   for (int64_t t = wg; t < nq; t += nwarps) {
     const int64_t c = A.queue[t];
@@ -214,7 +230,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
     const float A_loc = 0.5f * ((fx[1] - fx[0]) * (fy[2] - fy[0]) - (fx[2] - fx[0]) * (fy[1] - fy[0]) +
                                 (fx[2] - fx[0]) * (fy[3] - fy[0]) - (fx[3] - fx[0]) * (fy[2] - fy[0]));
     const bool fp32 = fabsf(A_loc) > 2e-2f * (xmx - xmn) * (ymx - ymn) && fabsf(A_loc) > A.thr_area;
-    double fin = 0.0;
+    float fin = 0.f;
     if (fp32) {
       const float inv = 1.0f / A_loc;
       for (int64_t t2 = lane; t2 < npix; t2 += 32) {
@@ -222,9 +238,9 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
         const float a = pixel_area<float>(fx, fy, (float)(px - ix0), (float)(py - iy0));
         if (a == 0.0f) continue;
         const float fr = a * inv;
-        atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], A.ip.scale * (double)fr);
-        fin += (double)fr;
-        nupd += 1;
+        atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], (double)(A.scale_f * fr));
+        fin += fr;
+        led.nupd += 1;
       }
     } else {
       double u[4], v[4];
@@ -236,7 +252,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
       const double A_P = 0.5 * ((u[1] - u[0]) * (v[2] - v[0]) - (u[2] - u[0]) * (v[1] - v[0]) +
                                 (u[2] - u[0]) * (v[3] - v[0]) - (u[3] - u[0]) * (v[2] - v[0]));
       if (!(fabs(A_P) * A.ip.s_star > 1e-14 * ac)) {
-        if (lane == 0) { degen += ac; ndeg += 1; }
+        if (lane == 0) led.ndeg += 1;
         continue;
       }
       const double inv = 1.0 / A_P;
@@ -249,15 +265,15 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
         if (a == 0.0) continue;
         const double fr = a * inv;
         atomicAdd(&A.map[py * A.ip.npx + px], A.ip.scale * fr);
-        fin += fr;
-        nupd += 1;
+        fin += (float)fr;
+        led.nupd += 1;
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fin += __shfl_xor_sync(0xffffffffu, fin, o);
-    if (lane == 0) { in_map += ac * fin; outside += ac * (1.0 - fin); }
+    if (lane == 0) { led.fin += fin; led.fout += 1.f - fin; }
   }
-  block_add_stats(A.stats, in_map, outside, 0.0, degen, 0.0, ndeg, nupd);
+  block_add_stats(A.stats, led);
 }
 
 }  // namespace
@@ -282,6 +298,7 @@ void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const 
   A.yc = yc; A.nx = nx; A.ncells = ncells; A.map = map; A.stats = stats_dev;
   A.queue = queue; A.qcount = qcount; A.ip = ip;
   A.thr_area = (float)(1e-13 * ip.a_cell / ip.s_star);
+  A.scale_f = (float)ip.scale;
   LENS_CUDA(cudaMemsetAsync(qcount, 0, sizeof(int), s));
   std::pair<cudaEvent_t, cudaEvent_t> e;
   if (ev) e = event_pair_begin(s);
