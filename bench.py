@@ -374,6 +374,7 @@ def main():
                          "ipm": st["ms_ipm"], "eval_kernel": ms_eval, "ipm_kernels": ms_ipm},
             "work": {"rays": rays_step, "p2p_pairs": pairs, "m2p_evals": m2p,
                      "ipm_updates": st["ipm_updates"], "cells_queued": st["cells_queued"],
+                     "cells_fp64": st["cells_fp64"],
                      "pairs_per_ray": pairs / rays_step},
             "tree": {k: info[k] for k in ("n_boxes", "n_active_boxes", "n_active_leaves", "n_v",
                                           "n_x", "n_u", "n_w", "levels")},

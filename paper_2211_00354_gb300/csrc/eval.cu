@@ -145,12 +145,16 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
     dx[q] = 0; dy[q] = 0; dxl[q] = 0; dyl[q] = 0;
     if (ok[q]) {
       if (GRID) {
-        const int64_t di = loc % ni, dj = loc / ni;
+        // 32-bit division: a 64-bit one is emulated with float64 instructions
+        const uint32_t l32 = (uint32_t)loc, n32 = (uint32_t)ni;
+        const uint32_t dj32 = l32 / n32;
+        const int64_t dj = dj32, di = (int64_t)(l32 - dj32 * n32);
         const int64_t i = i0 + di, j = j0 + dj;
         oidx[q] = (j - A.grow0) * A.gnx1 + i;
         if (SPLIT) {
-          const ff ox = ff_add(bx, ff_mul(hf, (float)di));
-          const ff oy = ff_add(by, ff_mul(hf, (float)dj));
+          // int32 -> float: an int64 conversion runs on the float64 pipe
+          const ff ox = ff_add(bx, ff_mul(hf, (float)(int)di));
+          const ff oy = ff_add(by, ff_mul(hf, (float)(int)dj));
           dx[q] = (R)ox.hi; dxl[q] = (R)ox.lo;
           dy[q] = (R)oy.hi; dyl[q] = (R)oy.lo;
         } else {
@@ -354,7 +358,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
         float fu = (U.hi - ku) + U.lo, fv = (V.hi - kv) + V.lo;
         if (fu < 0.f) { ku -= 1.f; fu += 1.f; } else if (fu >= 1.f) { ku += 1.f; fu -= 1.f; }
         if (fv < 0.f) { kv -= 1.f; fv += 1.f; } else if (fv >= 1.f) { kv += 1.f; fv -= 1.f; }
-        const int64_t iu = U1i + (int64_t)ku, iv = V1i + (int64_t)kv;
+        // float -> int32 (|k| < 5e8); a float -> int64 conversion would run
+        // on the float64 pipe
+        const int64_t iu = U1i + (int)ku, iv = V1i + (int)kv;
         far = far || !(iu > -1073741824ll && iu < 1073741824ll && iv > -1073741824ll &&
                        iv < 1073741824ll);
         if (!far) {
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
   }
 }
 
-constexpr int kRptF = 4, kRptD = 2;
+constexpr int kRptD = 2;
 
 __device__ __forceinline__ int64_t first_at_or_above(double x0, double h, int64_t lo, int64_t hi,
                                                      double bound) {
@@ -513,13 +519,9 @@ void launch_eval(Plan& P, EvalArgs& A, int64_t total_tiles, bool jac, cudaStream
   if (total_tiles <= 0) return;
   if (total_tiles > (int64_t)INT32_MAX) fail(LENS_EINVAL, "too many ray tiles in one call");
   const unsigned g = (unsigned)total_tiles;
-  if (P.prec == LENS_FP64) {
-    if (jac) k_eval<double, true, GRID, PIX, kRptD><<<g, kEvalThreads, 0, s>>>(A);
-    else k_eval<double, false, GRID, PIX, kRptD><<<g, kEvalThreads, 0, s>>>(A);
-  } else {
-    if (jac) k_eval<float, true, GRID, PIX, kRptF><<<g, kEvalThreads, 0, s>>>(A);
-    else k_eval<float, false, GRID, PIX, kRptF><<<g, kEvalThreads, 0, s>>>(A);
-  }
+  // float64 form only; the float32-bulk form runs k_eval32 (eval32.cu)
+  if (jac) k_eval<double, true, GRID, PIX, kRptD><<<g, kEvalThreads, 0, s>>>(A);
+  else k_eval<double, false, GRID, PIX, kRptD><<<g, kEvalThreads, 0, s>>>(A);
   LENS_LAUNCHED("k_eval");
 }
 
@@ -539,7 +541,9 @@ EvalArgs base_args(Plan& P) {
   return A;
 }
 
-int tile_rays(const Plan& P) { return kEvalThreads * (P.prec == LENS_FP64 ? kRptD : kRptF); }
+int tile_rays(const Plan& P) {
+  return P.prec == LENS_FP64 ? kEvalThreads * kRptD : kEval32Threads * kEval32Rpt;
+}
 
 }  // namespace
 
@@ -564,6 +568,16 @@ void grid_impl(Plan& P, const GridRows& g, double* y, double* jac, PixCorner* pi
   int64_t total = 0;
   LENS_CUDA(cudaMemcpyAsync(&total, toff.as<int64_t>() + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   LENS_CUDA(cudaStreamSynchronize(s));
+  if (P.work) {
+    k_work_count<<<grid_for(nl, 128, 1024), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx,
+                                                        rect.as<int64_t>(), P.ustar_cnt,
+                                                        P.W_off, P.work);
+    LENS_LAUNCHED("k_work_count");
+  }
+  if (P.prec == LENS_FP32_BULK) {
+    eval32_grid(P, g, rect.as<int64_t>(), toff.as<int64_t>(), total, y, jac, pix, ip, s);
+    return;
+  }
   EvalArgs A = base_args(P);
   A.tile_off = toff.as<int64_t>();
   A.rect = rect.as<int64_t>();
@@ -573,12 +587,6 @@ void grid_impl(Plan& P, const GridRows& g, double* y, double* jac, PixCorner* pi
   if (PIX) {
     A.pinv_du = ip->inv_du; A.pu_off = -ip->u0 * ip->inv_du;
     A.pinv_dv = ip->inv_dv; A.pv_off = -ip->v0 * ip->inv_dv;
-  }
-  if (P.work) {
-    k_work_count<<<grid_for(nl, 128, 1024), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx,
-                                                        rect.as<int64_t>(), P.ustar_cnt,
-                                                        P.W_off, P.work);
-    LENS_LAUNCHED("k_work_count");
   }
   if (P.timing) {
     auto e = event_pair_begin(s);
@@ -635,6 +643,10 @@ void evaluate_rays(Plan& P, const double* rays, int64_t m, double* y, double* ja
   LENS_CUDA(cudaMemcpyAsync(herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, s));
   LENS_CUDA(cudaStreamSynchronize(s));
   if (herr[0]) fail(LENS_EDOMAIN, "a ray lies outside the plan's target region (or is not finite)");
+  if (P.prec == LENS_FP32_BULK) {
+    eval32_rays(P, rays, off.as<int64_t>(), perm.as<int>(), toff.as<int64_t>(), total, y, jac, s);
+    return;
+  }
   EvalArgs A = base_args(P);
   A.tile_off = toff.as<int64_t>();
   A.rays = rays; A.ray_off = off.as<int64_t>(); A.perm = perm.as<int>();

@@ -1,0 +1,487 @@
+// eval32.cu -- the float32-bulk form of the fused per-ray FMM evaluation
+// (L2P, Appendix A step 6; P2P with the adjacent leaves, step 7; M2P for
+// the adaptive W lists; the lens equation, Eq. 1 with kappa_s and gamma).
+//
+// GB300's float64 pipe issues ~2 lanes per clock per SM, so a warp-wide
+// float64 instruction costs ~16 issue cycles: even per-CTA float64 set-up
+// (leaf centre, offsets of staged stars) executed by every thread rivals the
+// float32 pair work.  This kernel therefore runs no float64 instruction at
+// all on the grid path.  Everything float64 is done once:
+//   per plan  -- float32 copies of the local (L) and multipole (M)
+//                coefficients; every active leaf's U-list stars as
+//                float-float offsets from the leaf centre plus float32
+//                masses; W-box centre offsets and radii in float32; per-leaf
+//                constants K1 = a c1 - b0_1, K2 = b c2 + b0_2 (the lens
+//                equation evaluated at the centre with the constant term b0
+//                of the local expansion), 1/r;
+//   per call  -- per leaf, the float-float offset of its first grid ray from
+//                the centre and (map path) the leaf's pixel reference point.
+// Per ray: offset dx = (x(i0) - c) + (i - i0) h in float-float; near field
+// d = (x_hi - s_hi) + (x_lo - s_lo) summed per source leaf in float32 and
+// accumulated by two-sum; L2P/M2P by Horner in float32; then
+//   y1 = K1 + (a dx - f1 - near1),  y2 = K2 + (b dy + f2 - near2)
+// with the bracket in float-float (alpha = conj(b0 + f + near)).  On the map
+// path the corner goes straight to pixel coordinates u = U1 + (y1 - K1)/du,
+// split into an integer pixel and a float32 fraction for the IPM kernels.
+#include <vector>
+
+#include "cx.cuh"
+#include "lens_internal.h"
+
+namespace lens {
+
+namespace {
+
+constexpr int kT = kEval32Threads;
+constexpr int kRpt = kEval32Rpt;
+constexpr int kSeg = 64;
+constexpr int kChunk = 1024;
+constexpr int kWChunk = 8;
+
+struct E32Args {
+  const LeafPlan* leaf;
+  const int* leaves;
+  const int64_t* tile_off;
+  int64_t nleaf;
+  const int* aidx;
+  const int* count;
+  const int64_t* U_off; const int* U_list; const int64_t* W_off; const int* W_list;
+  const float2* fL; const float2* fM;
+  const float4* ust; const float* um; const int64_t* uoff; const float4* wgeo;
+  int p;
+  ff af, bf;
+  double a, b;
+  // grid source
+  const int64_t* rect; const LeafGrid* lgrid; ff hf; int64_t gnx1, grow0;
+  // ray source
+  const double* rays; const int64_t* ray_off; const int* perm;
+  double* y; double* jac;
+  PixCorner* pix; ff iduf, idvf;
+};
+
+template <bool JAC, bool GRID, bool PIX>
+__global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
+  __shared__ float s_x[kChunk], s_y[kChunk], s_xl[kChunk], s_yl[kChunk], s_m[kChunk];
+  __shared__ int s_pre[kSeg + 1];
+  __shared__ float2 s_L[kMaxOrder + 1];
+  __shared__ float2 s_W[kWChunk][kMaxOrder + 1];
+  __shared__ float4 s_wg[kWChunk];
+  __shared__ int64_t s_leaf;
+  const int tid = threadIdx.x;
+  const int p = A.p;
+  if (tid == 0) {
+    int64_t lo = 0, hi = A.nleaf;  // largest k with tile_off[k] <= blockIdx.x
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (A.tile_off[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid;
+    }
+    s_leaf = lo;
+  }
+  __syncthreads();
+  const int64_t k = s_leaf;
+  const int B = A.leaves[k];
+  const int a = A.aidx[B];
+  const int64_t tile = (int64_t)blockIdx.x - A.tile_off[k];
+  const LeafPlan lp = A.leaf[k];
+  for (int l = tid; l <= p; l += kT) s_L[l] = A.fL[k * (int64_t)(p + 1) + l];
+
+  // ---- rays of this tile -------------------------------------------------
+  int64_t nr_leaf, i0 = 0, ni = 1, j0 = 0;
+  LeafGrid lg{};
+  if (GRID) {
+    i0 = A.rect[4 * k]; ni = A.rect[4 * k + 1]; j0 = A.rect[4 * k + 2];
+    nr_leaf = ni * A.rect[4 * k + 3];
+    lg = A.lgrid[k];
+  } else {
+    nr_leaf = A.ray_off[k + 1] - A.ray_off[k];
+  }
+  float dx[kRpt], dy[kRpt], dxl[kRpt], dyl[kRpt];
+  int64_t oidx[kRpt];
+  bool ok[kRpt];
+  fcomp n1[kRpt], n2[kRpt], nj1[kRpt], nj2[kRpt];
+#pragma unroll
+  for (int q = 0; q < kRpt; ++q) {
+    const int64_t loc = tile * (kT * kRpt) + (int64_t)q * kT + tid;
+    ok[q] = loc < nr_leaf;
+    dx[q] = dy[q] = dxl[q] = dyl[q] = 0.f;
+    oidx[q] = 0;
+    n1[q] = {0.f, 0.f}; n2[q] = {0.f, 0.f}; nj1[q] = {0.f, 0.f}; nj2[q] = {0.f, 0.f};
+    if (!ok[q]) continue;
+    if (GRID) {
+      // 32-bit division and int32 -> float (64-bit forms run on the float64 pipe)
+      const uint32_t l32 = (uint32_t)loc, n32 = (uint32_t)ni;
+      const uint32_t dj = l32 / n32, di = l32 - dj * n32;
+      oidx[q] = (j0 + (int64_t)dj - A.grow0) * A.gnx1 + i0 + (int64_t)di;
+      const ff ox = ff_add(lg.bx, ff_mul(A.hf, (float)(int)di));
+      const ff oy = ff_add(lg.by, ff_mul(A.hf, (float)(int)dj));
+      dx[q] = ox.hi; dxl[q] = ox.lo;
+      dy[q] = oy.hi; dyl[q] = oy.lo;
+    } else {
+      const int64_t ridx = A.perm[A.ray_off[k] + loc];
+      oidx[q] = ridx;
+      const double ox = A.rays[2 * ridx] - lp.cx, oy = A.rays[2 * ridx + 1] - lp.cy;
+      dx[q] = (float)ox; dxl[q] = (float)(ox - (double)dx[q]);
+      dy[q] = (float)oy; dyl[q] = (float)(oy - (double)dy[q]);
+    }
+  }
+
+  // ---- P2P over the U list (stars pre-staged per leaf in float-float) -----
+  const int64_t u_beg = A.U_off[a], u_end = A.U_off[a + 1];
+  const int64_t star0 = A.uoff[k];
+  int64_t star_done = 0;  // stars of earlier U-entry rounds
+  for (int64_t e0 = u_beg; e0 < u_end; e0 += kSeg) {
+    const int ne = (int)min64(kSeg, u_end - e0);
+    __syncthreads();
+    if (tid < 32) {
+      int base = 0;
+      for (int half = 0; half < kSeg / 32; ++half) {
+        const int e = half * 32 + tid;
+        const int c = (e < ne) ? A.count[A.U_list[e0 + e]] : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (tid >= o) incl += v;
+        }
+        s_pre[e + 1] = base + incl;
+        base += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (tid == 0) s_pre[0] = 0;
+    }
+    __syncthreads();
+    const int tot = s_pre[ne];
+    for (int f0 = 0; f0 < tot; f0 += kChunk) {
+      const int nf = min(kChunk, tot - f0);
+      if (f0 > 0) __syncthreads();
+      for (int f = tid; f < nf; f += kT) {
+        const int64_t g = star0 + star_done + f0 + f;
+        const float4 v = A.ust[g];
+        s_x[f] = v.x; s_y[f] = v.y; s_xl[f] = v.z; s_yl[f] = v.w;
+        s_m[f] = A.um[g];
+      }
+      __syncthreads();
+      for (int e = 0; e < ne; ++e) {
+        const int lo = max(s_pre[e], f0) - f0;
+        const int hi = min(s_pre[e + 1], f0 + nf) - f0;
+        if (hi <= lo) continue;
+        float p1[kRpt], p2[kRpt], pj1[kRpt], pj2[kRpt];
+#pragma unroll
+        for (int q = 0; q < kRpt; ++q) { p1[q] = 0.f; p2[q] = 0.f; pj1[q] = 0.f; pj2[q] = 0.f; }
+        for (int j = lo; j < hi; ++j) {
+          const float sx = s_x[j], sy = s_y[j], sxl = s_xl[j], syl = s_yl[j], sm = s_m[j];
+#pragma unroll
+          for (int q = 0; q < kRpt; ++q) {
+            const float d1 = (dx[q] - sx) + (dxl[q] - sxl);
+            const float d2 = (dy[q] - sy) + (dyl[q] - syl);
+            const float r2 = fmaf(d1, d1, d2 * d2);
+            const float inv = r2 > 0.f ? frcp_fast(r2) : 0.f;
+            const float w = sm * inv;
+            p1[q] = fmaf(w, d1, p1[q]);
+            p2[q] = fmaf(w, d2, p2[q]);
+            if (JAC) {
+              const float w2 = w * inv;
+              pj1[q] = fmaf(w2, (d2 - d1) * (d2 + d1), pj1[q]);
+              pj2[q] = fmaf(w2, 2.f * d1 * d2, pj2[q]);
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kRpt; ++q) {
+          n1[q].add(p1[q]); n2[q].add(p2[q]);
+          if (JAC) { nj1[q].add(pj1[q]); nj2[q].add(pj2[q]); }
+        }
+      }
+    }
+    star_done += tot;
+  }
+
+  // ---- M2P over the W list --------------------------------------------------
+  float2 fw[kRpt], dfw[kRpt];
+#pragma unroll
+  for (int q = 0; q < kRpt; ++q) { fw[q] = make_float2(0.f, 0.f); dfw[q] = make_float2(0.f, 0.f); }
+  const int64_t w_beg = A.W_off[a], w_end = A.W_off[a + 1];
+  for (int64_t e0 = w_beg; e0 < w_end; e0 += kWChunk) {
+    const int nw = (int)min64(kWChunk, w_end - e0);
+    __syncthreads();
+    for (int t = tid; t < nw * (p + 1); t += kT) {
+      const int w = t / (p + 1), kk = t - w * (p + 1);
+      s_W[w][kk] = A.fM[(int64_t)A.W_list[e0 + w] * (p + 1) + kk];
+    }
+    if (tid < nw) s_wg[tid] = A.wgeo[e0 + tid];
+    __syncthreads();
+    for (int w = 0; w < nw; ++w) {
+      const float4 gw = s_wg[w];
+#pragma unroll
+      for (int q = 0; q < kRpt; ++q) {
+        const float2 z = make_float2(dx[q] - gw.x, dy[q] - gw.y);
+        const float2 inv = cinv(z);
+        const float2 qq = make_float2(inv.x * gw.z, inv.y * gw.z);
+        float2 s = s_W[w][p];
+        for (int kk = p - 1; kk >= 0; --kk) s = cfma(s, qq, s_W[w][kk]);
+        fw[q] = cfma(s, inv, fw[q]);
+        if (JAC) {
+          float2 t = make_float2((float)(p + 1) * s_W[w][p].x, (float)(p + 1) * s_W[w][p].y);
+          for (int kk = p - 1; kk >= 0; --kk)
+            t = cfma(t, qq, make_float2((float)(kk + 1) * s_W[w][kk].x, (float)(kk + 1) * s_W[w][kk].y));
+          const float2 d = cmul(t, cmul(inv, inv));
+          dfw[q] = make_float2(dfw[q].x - d.x, dfw[q].y - d.y);
+        }
+      }
+    }
+  }
+
+  // ---- L2P + epilogue --------------------------------------------------------
+  __syncthreads();
+  const float ir = lp.ir;
+#pragma unroll
+  for (int q = 0; q < kRpt; ++q) {
+    if (!ok[q]) continue;
+    const float2 w = make_float2(dx[q] * ir, dy[q] * ir);
+    float2 f = make_float2(0.f, 0.f), df = make_float2(0.f, 0.f);
+    if (p >= 1) {
+      float2 s = s_L[p];
+      for (int l = p - 1; l >= 1; --l) s = cfma(s, w, s_L[l]);
+      f = cmul(s, w);
+      if (JAC) {
+        float2 t = make_float2((float)p * s_L[p].x, (float)p * s_L[p].y);
+        for (int l = p - 1; l >= 1; --l) t = cfma(t, w, make_float2((float)l * s_L[l].x, (float)l * s_L[l].y));
+        df = make_float2(t.x * ir, t.y * ir);
+      }
+    }
+    f = f + fw[q];
+    ff T1 = ff_mul(A.af, ff{dx[q], dxl[q]});
+    T1 = ff_add(T1, -f.x);
+    T1 = ff_add(T1, ff{-n1[q].hi, -n1[q].lo});
+    ff T2 = ff_mul(A.bf, ff{dy[q], dyl[q]});
+    T2 = ff_add(T2, f.y);
+    T2 = ff_add(T2, ff{-n2[q].hi, -n2[q].lo});
+    if (PIX) {
+      PixCorner pc;
+      const ff U = ff_add(lg.U1f, ff_mul(A.iduf, T1));
+      const ff V = ff_add(lg.V1f, ff_mul(A.idvf, T2));
+      bool far = lg.far || !(fabsf(U.hi) < 5.0e8f) || !(fabsf(V.hi) < 5.0e8f);
+      float ku = floorf(U.hi), kv = floorf(V.hi);
+      float fu = (U.hi - ku) + U.lo, fv = (V.hi - kv) + V.lo;
+      if (fu < 0.f) { ku -= 1.f; fu += 1.f; } else if (fu >= 1.f) { ku += 1.f; fu -= 1.f; }
+      if (fv < 0.f) { kv -= 1.f; fv += 1.f; } else if (fv >= 1.f) { kv += 1.f; fv -= 1.f; }
+      // float -> int32 (|k| < 5e8); integer adds only afterwards
+      const int64_t iu = (int64_t)lg.U1i + (int)ku, iv = (int64_t)lg.V1i + (int)kv;
+      far = far || !(iu > -1073741824ll && iu < 1073741824ll && iv > -1073741824ll &&
+                     iv < 1073741824ll);
+      if (!far) {
+        pc.iu = (int)iu; pc.fu = fu; pc.iv = (int)iv; pc.fv = fv;
+      } else {
+        pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
+      }
+      A.pix[oidx[q]] = pc;
+      continue;
+    }
+    A.y[2 * oidx[q]] = lp.K1 + ff_to_double(T1);
+    A.y[2 * oidx[q] + 1] = lp.K2 + ff_to_double(T2);
+    if (JAC) {
+      const double dre = (double)df.x + (double)dfw[q].x + nj1[q].value();
+      const double dim = (double)df.y + (double)dfw[q].y + nj2[q].value();
+      A.jac[4 * oidx[q] + 0] = A.a - dre;
+      A.jac[4 * oidx[q] + 1] = dim;
+      A.jac[4 * oidx[q] + 2] = dim;
+      A.jac[4 * oidx[q] + 3] = A.b + dre;
+    }
+  }
+}
+
+// ---- plan-time preparation ---------------------------------------------------
+__global__ void k_prep_leaf(const int* __restrict__ leaves, int64_t nl, const int* __restrict__ aidx,
+                            const int* __restrict__ level, const int* __restrict__ ix,
+                            const int* __restrict__ iy, double lo_x, double lo_y, double size,
+                            double a, double b, int p, const double2* __restrict__ L,
+                            const int64_t* __restrict__ ustar_cnt, LeafPlan* __restrict__ out,
+                            float2* __restrict__ fL, int64_t* __restrict__ ucnt) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nl) return;
+  const int B = leaves[k];
+  const double r = size / (double)(2ull << level[B]);
+  const double cx = lo_x + (2.0 * ix[B] + 1.0) * r, cy = lo_y + (2.0 * iy[B] + 1.0) * r;
+  const double2* Lb = L + (int64_t)B * (p + 1);
+  const double2 b0 = Lb[0];
+  LeafPlan lp;
+  lp.cx = cx; lp.cy = cy;
+  lp.K1 = a * cx - b0.x;
+  lp.K2 = b * cy + b0.y;
+  lp.ir = (float)(1.0 / r);
+  lp.r = (float)r;
+  out[k] = lp;
+  for (int l = 0; l <= p; ++l) fL[k * (int64_t)(p + 1) + l] = make_float2((float)Lb[l].x, (float)Lb[l].y);
+  ucnt[k] = ustar_cnt[aidx[B]];
+}
+
+__global__ void k_prep_ustars(const int* __restrict__ leaves, int64_t nl, const int* __restrict__ aidx,
+                              const LeafPlan* __restrict__ lp, const int64_t* __restrict__ U_off,
+                              const int* __restrict__ U_list, const int* __restrict__ start,
+                              const int* __restrict__ count, const double2* __restrict__ spos,
+                              const double* __restrict__ smass, const int64_t* __restrict__ uoff,
+                              float4* __restrict__ ust, float* __restrict__ um) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nl) return;
+  const int a = aidx[leaves[k]];
+  const double cx = lp[k].cx, cy = lp[k].cy;
+  int64_t o = uoff[k];
+  for (int64_t e = U_off[a]; e < U_off[a + 1]; ++e) {
+    const int C = U_list[e];
+    for (int j = start[C]; j < start[C] + count[C]; ++j) {
+      const ff fx = ff_of(spos[j].x - cx), fy = ff_of(spos[j].y - cy);
+      ust[o] = make_float4(fx.hi, fy.hi, fx.lo, fy.lo);
+      um[o] = (float)smass[j];
+      ++o;
+    }
+  }
+}
+
+__global__ void k_prep_w(const int* __restrict__ leaves, int64_t nl, const int* __restrict__ aidx,
+                         const LeafPlan* __restrict__ lp, const int64_t* __restrict__ W_off,
+                         const int* __restrict__ W_list, const int* __restrict__ level,
+                         const int* __restrict__ ix, const int* __restrict__ iy, double lo_x,
+                         double lo_y, double size, float4* __restrict__ wgeo) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nl) return;
+  const int a = aidx[leaves[k]];
+  for (int64_t e = W_off[a]; e < W_off[a + 1]; ++e) {
+    const int C = W_list[e];
+    const double r = size / (double)(2ull << level[C]);
+    const double cx = lo_x + (2.0 * ix[C] + 1.0) * r, cy = lo_y + (2.0 * iy[C] + 1.0) * r;
+    wgeo[e] = make_float4((float)(cx - lp[k].cx), (float)(cy - lp[k].cy), (float)r, 0.f);
+  }
+}
+
+__global__ void k_to_f32(const double2* __restrict__ in, int64_t n, float2* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+// ---- per-call grid constants -------------------------------------------------
+__global__ void k_leaf_grid(int64_t nl, const LeafPlan* __restrict__ lp, const int64_t* __restrict__ rect,
+                            double x0, double y0, double h, int pix, double inv_du, double u_off,
+                            double inv_dv, double v_off, LeafGrid* __restrict__ out) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nl) return;
+  const LeafPlan L = lp[k];
+  LeafGrid g{};
+  const double xi = __dadd_rn(x0, __dmul_rn((double)rect[4 * k], h));
+  const double yj = __dadd_rn(y0, __dmul_rn((double)rect[4 * k + 2], h));
+  g.bx = ff_of(xi - L.cx);
+  g.by = ff_of(yj - L.cy);
+  if (pix) {
+    const double U1 = fma(L.K1, inv_du, u_off), V1 = fma(L.K2, inv_dv, v_off);
+    g.far = !(fabs(U1) < 1073741824.0 && fabs(V1) < 1073741824.0);
+    if (!g.far) {
+      const double fu = floor(U1), fv = floor(V1);
+      g.U1i = (int)fu; g.V1i = (int)fv;
+      g.U1f = ff_of(U1 - fu); g.V1f = ff_of(V1 - fv);
+    }
+  }
+  out[k] = g;
+}
+
+E32Args base_args32(Plan& P) {
+  E32Args A{};
+  A.leaf = P.f_leaf; A.leaves = P.active_leaves; A.nleaf = P.n_active_leaves;
+  A.aidx = P.box_aidx; A.count = P.box_count;
+  A.U_off = P.U_off; A.U_list = P.U_list; A.W_off = P.W_off; A.W_list = P.W_list;
+  A.fL = P.f_L; A.fM = P.f_M; A.ust = P.f_ust; A.um = P.f_um; A.uoff = P.f_uoff;
+  A.wgeo = P.f_wgeo;
+  A.p = P.p;
+  A.a = 1.0 - P.kappa_s - P.gamma;
+  A.b = 1.0 - P.kappa_s + P.gamma;
+  A.af = ff_of(A.a);
+  A.bf = ff_of(A.b);
+  return A;
+}
+
+template <bool GRID, bool PIX>
+void launch32(E32Args& A, int64_t total, bool jac, cudaStream_t s) {
+  if (total <= 0) return;
+  if (total > (int64_t)INT32_MAX) fail(LENS_EINVAL, "too many ray tiles in one call");
+  const unsigned g = (unsigned)total;
+  if (jac) k_eval32<true, GRID, PIX><<<g, kT, 0, s>>>(A);
+  else k_eval32<false, GRID, PIX><<<g, kT, 0, s>>>(A);
+  LENS_LAUNCHED("k_eval32");
+}
+
+}  // namespace
+
+void eval32_prepare(Plan& P, cudaStream_t s) {
+  const int64_t nl = P.n_active_leaves;
+  const int P1 = P.p + 1;
+  P.f_leaf = P.dalloc_n<LeafPlan>(nl);
+  P.f_L = P.dalloc_n<float2>((size_t)nl * P1);
+  P.f_M = P.dalloc_n<float2>((size_t)P.nb * P1);
+  P.f_uoff = P.dalloc_n<int64_t>(nl + 1);
+  P.f_wgeo = P.dalloc_n<float4>(P.nW);
+  if (nl == 0) return;
+  const double a = 1.0 - P.kappa_s - P.gamma, b = 1.0 - P.kappa_s + P.gamma;
+  Scratch ucnt(&P.da, sizeof(int64_t) * (nl + 1));
+  LENS_CUDA(cudaMemsetAsync(ucnt.p, 0, ucnt.bytes, s));
+  k_prep_leaf<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx, P.box_level,
+                                                P.box_ix, P.box_iy, P.root_lo[0], P.root_lo[1],
+                                                P.root_size, a, b, P.p, P.L, P.ustar_cnt,
+                                                P.f_leaf, P.f_L, ucnt.as<int64_t>());
+  LENS_LAUNCHED("k_prep_leaf");
+  exclusive_scan_i64(ucnt.as<int64_t>(), P.f_uoff, nl + 1, P.da, s);
+  int64_t total = 0;
+  LENS_CUDA(cudaMemcpyAsync(&total, P.f_uoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaStreamSynchronize(s));
+  P.f_ust = P.dalloc_n<float4>(total);
+  P.f_um = P.dalloc_n<float>(total);
+  k_prep_ustars<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx, P.f_leaf,
+                                                  P.U_off, P.U_list, P.box_start, P.box_count,
+                                                  P.spos, P.smass, P.f_uoff, P.f_ust, P.f_um);
+  LENS_LAUNCHED("k_prep_ustars");
+  k_prep_w<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx, P.f_leaf, P.W_off,
+                                             P.W_list, P.box_level, P.box_ix, P.box_iy,
+                                             P.root_lo[0], P.root_lo[1], P.root_size, P.f_wgeo);
+  LENS_LAUNCHED("k_prep_w");
+  k_to_f32<<<grid_for((int64_t)P.nb * P1, 256, 152 * 16), 256, 0, s>>>(P.M, (int64_t)P.nb * P1,
+                                                                       P.f_M);
+  LENS_LAUNCHED("k_to_f32");
+}
+
+void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t* toff,
+                 int64_t total, double* y, double* jac, PixCorner* pix, const IpmParams* ip,
+                 cudaStream_t s) {
+  const int64_t nl = P.n_active_leaves;
+  Scratch lg(&P.da, sizeof(LeafGrid) * (nl + 1));
+  const bool px = pix != nullptr;
+  k_leaf_grid<<<grid_for(nl, 128), 128, 0, s>>>(
+      nl, P.f_leaf, rect, g.x0, g.y0, g.h, px ? 1 : 0, px ? ip->inv_du : 0.0,
+      px ? -ip->u0 * ip->inv_du : 0.0, px ? ip->inv_dv : 0.0, px ? -ip->v0 * ip->inv_dv : 0.0,
+      lg.as<LeafGrid>());
+  LENS_LAUNCHED("k_leaf_grid");
+  E32Args A = base_args32(P);
+  A.tile_off = toff;
+  A.rect = rect;
+  A.lgrid = lg.as<LeafGrid>();
+  A.hf = ff_of(g.h);
+  A.gnx1 = g.nx + 1;
+  A.grow0 = g.row0;
+  A.y = y; A.jac = jac; A.pix = pix;
+  if (px) { A.iduf = ff_of(ip->inv_du); A.idvf = ff_of(ip->inv_dv); }
+  std::pair<cudaEvent_t, cudaEvent_t> e;
+  if (P.timing) e = event_pair_begin(s);
+  if (px) launch32<true, true>(A, total, false, s);
+  else launch32<true, false>(A, total, jac != nullptr, s);
+  if (P.timing) {
+    event_pair_end(e, s);
+    P.ev_eval.push_back(e);
+  }
+}
+
+void eval32_rays(Plan& P, const double* rays, const int64_t* off, const int* perm,
+                 const int64_t* toff, int64_t total, double* y, double* jac, cudaStream_t s) {
+  E32Args A = base_args32(P);
+  A.tile_off = toff;
+  A.rays = rays; A.ray_off = off; A.perm = perm;
+  A.y = y; A.jac = jac;
+  launch32<false, false>(A, total, jac != nullptr, s);
+}
+
+}  // namespace lens

@@ -69,7 +69,7 @@ __device__ __forceinline__ T pixel_area(const T* qx, const T* qy, T X, T Y) {
 struct IpmArgs {
   const PixCorner* yc;  // (nrows+1) x (nx+1) corners of the chunk
   int64_t nx, ncells;
-  double* map;
+  float* map;           // float32 accumulation map (added to the float64 output at the end)
   double* stats;        // [8]
   int* queue; int* qcount;
   IpmParams ip;
@@ -84,12 +84,12 @@ struct IpmArgs {
 // host multiplies by the cell area.
 struct Ledger {
   float fin = 0.f, fout = 0.f;
-  unsigned ndrop = 0, ndeg = 0, nupd = 0;
+  unsigned ndrop = 0, ndeg = 0, nupd = 0, nf64 = 0;
 };
 
 __device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L) {
   __shared__ float shf[2][kIpmThreads / 32];
-  __shared__ unsigned shu[3][kIpmThreads / 32];
+  __shared__ unsigned shu[4][kIpmThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float f0 = L.fin, f1 = L.fout;
 #pragma unroll
@@ -100,18 +100,50 @@ __device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L) 
   const unsigned u0 = __reduce_add_sync(0xffffffffu, L.ndrop);
   const unsigned u1 = __reduce_add_sync(0xffffffffu, L.ndeg);
   const unsigned u2 = __reduce_add_sync(0xffffffffu, L.nupd);
+  const unsigned u3 = __reduce_add_sync(0xffffffffu, L.nf64);
   if (lane == 0) {
     shf[0][w] = f0; shf[1][w] = f1;
-    shu[0][w] = u0; shu[1][w] = u1; shu[2][w] = u2;
+    shu[0][w] = u0; shu[1][w] = u1; shu[2][w] = u2; shu[3][w] = u3;
   }
   __syncthreads();
-  if (threadIdx.x < 5) {
+  if (threadIdx.x < 6) {
     double x = 0;
     for (int q = 0; q < kIpmThreads / 32; ++q)
       x += threadIdx.x < 2 ? (double)shf[threadIdx.x][q] : (double)shu[threadIdx.x - 2][q];
-    const int slot = threadIdx.x < 4 ? 2 + threadIdx.x : 8;
+    const int slot = threadIdx.x < 4 ? 2 + threadIdx.x : (threadIdx.x == 4 ? 8 : 10);
     if (x != 0.0) atomicAdd(&stats[slot], x);
   }
+}
+
+// Does the segment P->Q meet the closed unit square at (ox, oy)?  (float32
+// pre-filter for the float64 path: a pixel that no edge meets is covered by
+// the polygon's winding number exactly.)
+__device__ __forceinline__ bool seg_meets_pixel(float px, float py, float qx, float qy, float ox,
+                                                float oy) {
+  if (fmaxf(px, qx) < ox || fminf(px, qx) > ox + 1.f || fmaxf(py, qy) < oy ||
+      fminf(py, qy) > oy + 1.f)
+    return false;
+  const float dx = qx - px, dy = qy - py;
+  const float c00 = dx * (oy - py) - dy * (ox - px);
+  const float c10 = c00 - dy, c01 = c00 + dx, c11 = c00 + dx - dy;
+  const float lo = fminf(fminf(c00, c10), fminf(c01, c11));
+  const float hi = fmaxf(fmaxf(c00, c10), fmaxf(c01, c11));
+  // a margin covers float32 rounding of the corners: near-misses count as hits
+  const float tol = 1e-5f * (fabsf(dx) + fabsf(dy)) * (1.f + fabsf(ox) + fabsf(oy));
+  return !(lo > tol || hi < -tol);
+}
+
+// winding number of the closed polygon q around (x, y)
+__device__ __forceinline__ int winding4(const float* qx, const float* qy, float x, float y) {
+  int w = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float ax = qx[e], ay = qy[e], bx = qx[(e + 1) & 3], by = qy[(e + 1) & 3];
+    const float cr = (bx - ax) * (y - ay) - (x - ax) * (by - ay);
+    if (ay <= y && by > y && cr > 0.f) ++w;
+    else if (by <= y && ay > y && cr < 0.f) --w;
+  }
+  return w;
 }
 
 constexpr int kSmallBox = 4;  // cells whose pixel box is at most 4 x 4 stay per-thread
@@ -120,7 +152,10 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
   const int64_t c = blockIdx.x * (int64_t)kIpmThreads + threadIdx.x;
   Ledger led;
   if (c < A.ncells) {
-    const int64_t j = c / A.nx, i = c - j * A.nx;
+    // cell index < 2^30 and nx < 2^31: 32-bit division (a 64-bit one is
+    // emulated with float64 instructions)
+    const uint32_t j32 = (uint32_t)c / (uint32_t)A.nx;
+    const int64_t j = j32, i = c - j * A.nx;
     const int64_t W = A.nx + 1;
     PixCorner q4[4];
     q4[0] = A.yc[j * W + i];
@@ -155,10 +190,10 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
                                   (qx[2] - qx[0]) * (qy[3] - qy[0]) - (qx[3] - qx[0]) * (qy[2] - qy[0]));
       const float ext = (xmx - xmn) * (ymx - ymn);
       const bool small = (ix1 - ix0 < kSmallBox) && (iy1 - iy0 < kSmallBox);
-      const bool good = fabsf(A_loc) > 2e-2f * ext && fabsf(A_loc) > A.thr_area;
+      const bool good = fabsf(A_loc) > 1e-3f * ext && fabsf(A_loc) > A.thr_area;
       if (small && good) {
         if (ix0 == ix1 && iy0 == iy1) {
-          atomicAdd(&A.map[(int64_t)iy0 * A.ip.npx + ix0], A.ip.scale);
+          atomicAdd(&A.map[(int64_t)iy0 * A.ip.npx + ix0], A.scale_f);
           led.fin = 1.f;
           led.nupd = 1;
         } else {
@@ -171,7 +206,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
               const float a = pixel_area<float>(qx, qy, (float)(px - ix0), (float)(py - iy0));
               if (a == 0.0f) continue;
               const float fr = a * inv;
-              atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], (double)(A.scale_f * fr));
+              atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], A.scale_f * fr);
               fin += fr;
               led.nupd += 1;
             }
@@ -202,7 +237,10 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&A.stats[9], (double)nq);
   for (int64_t t = wg; t < nq; t += nwarps) {
     const int64_t c = A.queue[t];
-    const int64_t j = c / A.nx, i = c - j * A.nx;
+    // cell index < 2^30 and nx < 2^31: 32-bit division (a 64-bit one is
+    // emulated with float64 instructions)
+    const uint32_t j32 = (uint32_t)c / (uint32_t)A.nx;
+    const int64_t j = j32, i = c - j * A.nx;
     const int64_t W = A.nx + 1;
     PixCorner q4[4];
     q4[0] = A.yc[j * W + i];
@@ -229,25 +267,27 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
     }
     const float A_loc = 0.5f * ((fx[1] - fx[0]) * (fy[2] - fy[0]) - (fx[2] - fx[0]) * (fy[1] - fy[0]) +
                                 (fx[2] - fx[0]) * (fy[3] - fy[0]) - (fx[3] - fx[0]) * (fy[2] - fy[0]));
-    const bool fp32 = fabsf(A_loc) > 2e-2f * (xmx - xmn) * (ymx - ymn) && fabsf(A_loc) > A.thr_area;
+    const bool fp32 = fabsf(A_loc) > 1e-3f * (xmx - xmn) * (ymx - ymn) && fabsf(A_loc) > A.thr_area;
     float fin = 0.f;
     if (fp32) {
       const float inv = 1.0f / A_loc;
       for (int64_t t2 = lane; t2 < npix; t2 += 32) {
-        const int py = cy0 + (int)(t2 / w), px = cx0 + (int)(t2 % w);
+        const uint32_t r32 = (uint32_t)t2 / (uint32_t)w;
+        const int py = cy0 + (int)r32, px = cx0 + (int)((uint32_t)t2 - r32 * (uint32_t)w);
         const float a = pixel_area<float>(fx, fy, (float)(px - ix0), (float)(py - iy0));
         if (a == 0.0f) continue;
         const float fr = a * inv;
-        atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], (double)(A.scale_f * fr));
+        atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], A.scale_f * fr);
         fin += fr;
         led.nupd += 1;
       }
     } else {
+      // float64 in coordinates local to the box (small integers + fraction)
       double u[4], v[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        u[k] = (double)q4[k].iu + (double)q4[k].fu;
-        v[k] = (double)q4[k].iv + (double)q4[k].fv;
+        u[k] = (double)(q4[k].iu - ix0) + (double)q4[k].fu;
+        v[k] = (double)(q4[k].iv - iy0) + (double)q4[k].fv;
       }
       const double A_P = 0.5 * ((u[1] - u[0]) * (v[2] - v[0]) - (u[2] - u[0]) * (v[1] - v[0]) +
                                 (u[2] - u[0]) * (v[3] - v[0]) - (u[3] - u[0]) * (v[2] - v[0]));
@@ -255,17 +295,28 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
         if (lane == 0) led.ndeg += 1;
         continue;
       }
+      if (lane == 0) led.nf64 += 1;
       const double inv = 1.0 / A_P;
+      const float invf = (float)inv;
       for (int64_t t2 = lane; t2 < npix; t2 += 32) {
-        const int64_t py = cy0 + t2 / w, px = cx0 + t2 % w;
-        double qx[4], qy[4];
+        const uint32_t r32 = (uint32_t)t2 / (uint32_t)w;
+        const int oy = cy0 - iy0 + (int)r32, ox = cx0 - ix0 + (int)((uint32_t)t2 - r32 * (uint32_t)w);
+        bool cut = false;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) { qx[k] = u[k] - (double)px; qy[k] = v[k] - (double)py; }
-        const double a = pixel_area<double>(qx, qy, 0.0, 0.0);
-        if (a == 0.0) continue;
-        const double fr = a * inv;
-        atomicAdd(&A.map[py * A.ip.npx + px], A.ip.scale * fr);
-        fin += (float)fr;
+        for (int e = 0; e < 4; ++e)
+          cut |= seg_meets_pixel(fx[e], fy[e], fx[(e + 1) & 3], fy[(e + 1) & 3], (float)ox, (float)oy);
+        float fr;
+        if (cut) {
+          const double a = pixel_area<double>(u, v, (double)ox, (double)oy);
+          fr = (float)(a * inv);
+        } else {
+          const int wn = winding4(fx, fy, (float)ox + 0.5f, (float)oy + 0.5f);
+          fr = (float)wn * invf;
+        }
+        if (fr == 0.0f) continue;
+        const int64_t px = ix0 + ox, py = iy0 + oy;
+        atomicAdd(&A.map[py * A.ip.npx + px], A.scale_f * fr);
+        fin += fr;
         led.nupd += 1;
       }
     }
@@ -289,8 +340,19 @@ void event_pair_end(std::pair<cudaEvent_t, cudaEvent_t>& e, cudaStream_t s) {
   LENS_CUDA(cudaEventRecord(e.second, s));
 }
 
+__global__ void k_map_to_f64(const float* __restrict__ m32, int64_t n, double* __restrict__ m64) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m64[i] = (double)m32[i];
+}
+
+void ipm_finish_map(const float* map32, int64_t n, double* map, cudaStream_t s) {
+  k_map_to_f64<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(map32, n, map);
+  LENS_LAUNCHED("k_map_to_f64");
+}
+
 void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const IpmParams& ip,
-                    double* map, double* stats_dev, int* queue, int* qcount, cudaStream_t s,
+                    float* map, double* stats_dev, int* queue, int* qcount, cudaStream_t s,
                     std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev) {
   const int64_t ncells = nx * nrows_cells;
   if (ncells <= 0) return;

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/lens.h"
+#include "cx.cuh"
 
 namespace lens {
 
@@ -66,6 +67,25 @@ struct Scratch {
 
 constexpr int kMaxDepth = 28;   // quadtree levels below the root (56-bit keys)
 constexpr int kMaxOrder = 64;   // expansion order cap
+
+// Float32 evaluation kernel geometry (eval32.cu): threads per CTA, rays per thread.
+constexpr int kEval32Threads = 128;
+constexpr int kEval32Rpt = 4;
+
+// Per active leaf, float64 constants formed once per plan (eval32.cu).
+struct LeafPlan {
+  double cx, cy;  // leaf centre
+  double K1, K2;  // a c1 - b0_1 and b c2 + b0_2 (lens equation at the centre)
+  float ir, r;    // 1/r and r (half-side)
+};
+// Per active leaf and call on the grid path (eval32.cu).
+struct LeafGrid {
+  ff bx, by;      // offset of the leaf's first grid ray from its centre
+  ff U1f, V1f;    // fractional part of the centre's pixel reference (map path)
+  int U1i, V1i;   // integer part
+  int far;        // the reference lies beyond 2^30 pixels
+  int pad;
+};
 
 // Host-built float64 tables for one order p (device copies owned by the plan).
 struct FmmTables {
@@ -131,6 +151,15 @@ struct Plan {
   double2* M = nullptr;
   double2* L = nullptr;
   FmmTables tab;
+
+  // float32-bulk evaluation data (eval32_prepare)
+  LeafPlan* f_leaf = nullptr;   // per active leaf
+  float2* f_L = nullptr;        // per active leaf, (p+1) local coefficients
+  float2* f_M = nullptr;        // per box, (p+1) multipole coefficients
+  float4* f_ust = nullptr;      // U-list stars of every active leaf (float-float offsets)
+  float* f_um = nullptr;        // their masses
+  int64_t* f_uoff = nullptr;    // CSR offsets into f_ust by active-leaf index
+  float4* f_wgeo = nullptr;     // per W entry: centre offset from the leaf centre, radius
 
   double ms_build = 0;
   int64_t build_launches = 0;
@@ -199,8 +228,16 @@ struct __align__(16) PixCorner {
 void evaluate_grid_pix(Plan& P, const GridRows& g, PixCorner* out, const IpmParams& ip,
                        cudaStream_t s);
 void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const IpmParams& ip,
-                    double* map, double* stats_dev, int* queue, int* qcount, cudaStream_t s,
+                    float* map32, double* stats_dev, int* queue, int* qcount, cudaStream_t s,
                     std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev);
+void eval32_prepare(Plan& P, cudaStream_t s);
+void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t* toff,
+                 int64_t total, double* y, double* jac, PixCorner* pix, const IpmParams* ip,
+                 cudaStream_t s);
+void eval32_rays(Plan& P, const double* rays, const int64_t* off, const int* perm,
+                 const int64_t* toff, int64_t total, double* y, double* jac, cudaStream_t s);
+// map32 (float32 accumulation) -> map (float64 output)
+void ipm_finish_map(const float* map32, int64_t n, double* map, cudaStream_t s);
 // a pair of recorded events bracketing work on a stream
 std::pair<cudaEvent_t, cudaEvent_t> event_pair_begin(cudaStream_t s);
 void event_pair_end(std::pair<cudaEvent_t, cudaEvent_t>& e, cudaStream_t s);
