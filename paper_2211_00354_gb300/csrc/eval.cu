@@ -608,19 +608,17 @@ void evaluate_grid_pix(Plan& P, const GridRows& g, PixCorner* out, const IpmPara
   grid_impl<true>(P, g, nullptr, nullptr, out, &ip, s);
 }
 
-void evaluate_rays(Plan& P, const double* rays, int64_t m, double* y, double* jac, cudaStream_t s) {
+void bucket_rays(Plan& P, const double* rays, int64_t m, int tile, RayBuckets& B, cudaStream_t s) {
   const int64_t nl = P.n_active_leaves;
-  if (m == 0) return;
   if (nl == 0) fail(LENS_EDOMAIN, "plan has no active leaves");
-  const int tile = tile_rays(P);
   Scratch slot(&P.da, sizeof(int) * m);
   Scratch cnt(&P.da, sizeof(int64_t) * (nl + 1));
-  Scratch off(&P.da, sizeof(int64_t) * (nl + 1));
   Scratch cur(&P.da, sizeof(int64_t) * (nl + 1));
-  Scratch perm(&P.da, sizeof(int) * m);
   Scratch tiles(&P.da, sizeof(int64_t) * (nl + 1));
-  Scratch toff(&P.da, sizeof(int64_t) * (nl + 1));
   Scratch err(&P.da, sizeof(int) * 4);
+  B.off = Scratch(&P.da, sizeof(int64_t) * (nl + 1));
+  B.perm = Scratch(&P.da, sizeof(int) * m);
+  B.toff = Scratch(&P.da, sizeof(int64_t) * (nl + 1));
   LENS_CUDA(cudaMemsetAsync(cnt.p, 0, cnt.bytes, s));
   LENS_CUDA(cudaMemsetAsync(cur.p, 0, cur.bytes, s));
   LENS_CUDA(cudaMemsetAsync(err.p, 0, err.bytes, s));
@@ -629,29 +627,36 @@ void evaluate_rays(Plan& P, const double* rays, int64_t m, double* y, double* ja
                                               P.root_lo[1], scale, P.depth, slot.as<int>(),
                                               cnt.as<int64_t>(), err.as<int>());
   LENS_LAUNCHED("k_ray_leaf");
-  exclusive_scan_i64(cnt.as<int64_t>(), off.as<int64_t>(), nl + 1, P.da, s);
-  k_ray_scatter<<<grid_for(m, 256), 256, 0, s>>>(slot.as<int>(), m, off.as<int64_t>(),
-                                                 cur.as<int64_t>(), perm.as<int>());
+  exclusive_scan_i64(cnt.as<int64_t>(), B.off.as<int64_t>(), nl + 1, P.da, s);
+  k_ray_scatter<<<grid_for(m, 256), 256, 0, s>>>(slot.as<int>(), m, B.off.as<int64_t>(),
+                                                 cur.as<int64_t>(), B.perm.as<int>());
   LENS_LAUNCHED("k_ray_scatter");
   k_tiles_from_counts<<<grid_for(nl + 1, 256), 256, 0, s>>>(cnt.as<int64_t>(), nl + 1, tile,
                                                             tiles.as<int64_t>());
   LENS_LAUNCHED("k_tiles_from_counts");
-  exclusive_scan_i64(tiles.as<int64_t>(), toff.as<int64_t>(), nl + 1, P.da, s);
-  int64_t total = 0;
+  exclusive_scan_i64(tiles.as<int64_t>(), B.toff.as<int64_t>(), nl + 1, P.da, s);
   int herr[4] = {0, 0, 0, 0};
-  LENS_CUDA(cudaMemcpyAsync(&total, toff.as<int64_t>() + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  B.total = 0;
+  LENS_CUDA(cudaMemcpyAsync(&B.total, B.toff.as<int64_t>() + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   LENS_CUDA(cudaMemcpyAsync(herr, err.p, sizeof(herr), cudaMemcpyDeviceToHost, s));
   LENS_CUDA(cudaStreamSynchronize(s));
   if (herr[0]) fail(LENS_EDOMAIN, "a ray lies outside the plan's target region (or is not finite)");
+}
+
+void evaluate_rays(Plan& P, const double* rays, int64_t m, double* y, double* jac, cudaStream_t s) {
+  if (m == 0) return;
+  RayBuckets B;
+  bucket_rays(P, rays, m, tile_rays(P), B, s);
   if (P.prec == LENS_FP32_BULK) {
-    eval32_rays(P, rays, off.as<int64_t>(), perm.as<int>(), toff.as<int64_t>(), total, y, jac, s);
+    eval32_rays(P, rays, B.off.as<int64_t>(), B.perm.as<int>(), B.toff.as<int64_t>(), B.total, y,
+                jac, s);
     return;
   }
   EvalArgs A = base_args(P);
-  A.tile_off = toff.as<int64_t>();
-  A.rays = rays; A.ray_off = off.as<int64_t>(); A.perm = perm.as<int>();
+  A.tile_off = B.toff.as<int64_t>();
+  A.rays = rays; A.ray_off = B.off.as<int64_t>(); A.perm = B.perm.as<int>();
   A.y = y; A.jac = jac;
-  launch_eval<false, false>(P, A, total, jac != nullptr, s);
+  launch_eval<false, false>(P, A, B.total, jac != nullptr, s);
 }
 
 }  // namespace lens

@@ -213,6 +213,13 @@ struct GridRows {  // a band of corner rows of a grid
 void evaluate_grid(Plan& P, const GridRows& g, double* y, double* jac, cudaStream_t s);
 void evaluate_rays(Plan& P, const double* rays, int64_t m, double* y, double* jac,
                    cudaStream_t s);
+// Rays bucketed by active leaf: perm (ray ids in leaf order), off (per leaf,
+// CSR into perm) and toff (per leaf, first tile of `tile` rays).
+struct RayBuckets {
+  Scratch perm, off, toff;
+  int64_t total = 0;  // tiles
+};
+void bucket_rays(Plan& P, const double* rays, int64_t m, int tile, RayBuckets& B, cudaStream_t s);
 
 struct IpmParams {
   double u0, v0, inv_du, inv_dv;  // source-plane window origin, inverse pixel size
