@@ -205,6 +205,31 @@ lens_status lens_direct_deflect(const double* stars_xy, const double* masses,
                                 double* y_out, double* jac_out,
                                 const lens_allocator* allocator, void* stream);
 
+/* ---- Direct sum without allocation ----------------------------------------
+ * The paper has no counterpart: this is a service for callers that may not
+ * allocate device memory (a host application that owns the whole device
+ * memory budget and passes the library only its inputs and outputs, a
+ * memory-capped service whose pool must not grow, a loop that cannot let an
+ * allocation stall or fail mid-step).  Same result as lens_direct_deflect
+ * with prec = LENS_FP32_BULK; its scratch (n split stars) lives in one fixed
+ * static device array of 262144 stars (5 MiB) that every GPU loading the
+ * library holds until exit.  Rules:
+ *   - n <= 262144, else LENS_EINVAL before any launch;
+ *   - the first call on a device looks up the array's address (with that
+ *     device current) and caches it; make that first call before any stream
+ *     capture;
+ *   - calls share the one array: two calls that overlap on the GPU (other
+ *     streams, other host threads) race, so the caller must order them; each
+ *     call rewrites all scratch it reads, nothing has to start at zero;
+ *   - no cudaMalloc, cudaFree or allocating library call is made.
+ * Buffers as in lens_direct_deflect (dev pointers; jac_out may be NULL). */
+lens_status lens_direct_deflect_noalloc(const double* stars_xy,
+                                        const double* masses, int64_t n,
+                                        double kappa_s, double gamma,
+                                        const double* rays_xy, int64_t m,
+                                        double* y_out, double* jac_out,
+                                        void* stream);
+
 /* ---- Gaussian-source light curve (differentiable loss) --------------------
  * F_k = sum_r w_ray exp(-|y_r - s_k|^2 / (2 sigma^2)) / (2 pi sigma^2) for
  * |y_r - s_k| <= trunc sigma: the magnification of a Gaussian source (Sec.

@@ -175,4 +175,20 @@ void direct_deflect(const double* stars, const double* masses, int64_t n, double
   LENS_LAUNCHED("k_direct_f32");
 }
 
+// The float32 direct sum with caller-provided scratch for the split stars
+// (n float4 + n float); used by the allocation-free entry point.
+void direct_f32_into(const double* stars, const double* masses, int64_t n, double ks, double g,
+                     const double* rays, int64_t m, double* y, double* jac, float4* hl, float* mf,
+                     cudaStream_t s) {
+  const double a = 1.0 - ks - g, b = 1.0 - ks + g;
+  if (m == 0) return;
+  k_split_stars<<<grid_for(n, 256), 256, 0, s>>>(stars, masses, n, hl, mf);
+  LENS_LAUNCHED("k_split_stars");
+  constexpr int RPT = 4;
+  const unsigned blocks = grid_for(m, kThreads * RPT);
+  if (jac) k_direct_f32<RPT, true><<<blocks, kThreads, 0, s>>>(hl, mf, n, rays, m, a, b, y, jac);
+  else k_direct_f32<RPT, false><<<blocks, kThreads, 0, s>>>(hl, mf, n, rays, m, a, b, y, jac);
+  LENS_LAUNCHED("k_direct_f32");
+}
+
 }  // namespace lens

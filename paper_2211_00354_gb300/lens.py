@@ -34,7 +34,8 @@ FP32_BULK = 1
 # Every symbol include/lens.h declares (checked by the ABI tests).
 EXPORTED = ("lens_fmm_build", "lens_deflect", "lens_deflect_grid", "lens_ipm_map",
             "lens_deflect_adjoint", "lens_plan_info_get", "lens_plan_destroy",
-            "lens_direct_deflect", "lens_light_curve", "lens_light_curve_grad",
+            "lens_direct_deflect", "lens_direct_deflect_noalloc", "lens_light_curve",
+            "lens_light_curve_grad",
             "lens_last_error", "lens_version")
 
 
@@ -133,6 +134,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lens_direct_deflect.argtypes = [vp, vp, i64, d, d, vp, i64, i, vp, vp,
                                         ctypes.POINTER(lens_allocator), vp]
     lib.lens_direct_deflect.restype = st
+    lib.lens_direct_deflect_noalloc.argtypes = [vp, vp, i64, d, d, vp, i64, vp, vp, vp]
+    lib.lens_direct_deflect_noalloc.restype = st
     lib.lens_light_curve.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp]
     lib.lens_light_curve.restype = st
     lib.lens_light_curve_grad.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp, vp, vp]
@@ -315,6 +318,28 @@ def direct_deflect(stars, masses, kappa_s, gamma, rays, prec=FP64, jacobian=Fals
                                    float(kappa_s), float(gamma), rays.data_ptr(), rays.shape[0],
                                    int(prec), y.data_ptr(), jac.data_ptr() if jacobian else None,
                                    ctypes.byref(TORCH_ALLOCATOR), _stream_ptr(stream)))
+    return (y, jac) if jacobian else y
+
+
+NOALLOC_MAX_STARS = 1 << 18
+
+
+def direct_deflect_noalloc(stars, masses, kappa_s, gamma, rays, jacobian=False, out=None,
+                           stream=None):
+    """Float32 direct sum through lens_direct_deflect_noalloc: the library
+    allocates no device memory for it (fixed static scratch, <= 262144 stars).
+    Pass ``out`` (m, 2) to avoid even the output allocation on this side."""
+    lib = load()
+    stars = _dev(stars, "stars", 2)
+    masses = _dev(masses, "masses").reshape(-1)
+    rays = _dev(rays, "rays", 2)
+    y = out if out is not None else torch.empty_like(rays)
+    jac = torch.empty((rays.shape[0], 2, 2), dtype=torch.float64, device=rays.device) if jacobian else None
+    _check(lib.lens_direct_deflect_noalloc(stars.data_ptr(), masses.data_ptr(), stars.shape[0],
+                                           float(kappa_s), float(gamma), rays.data_ptr(),
+                                           rays.shape[0], y.data_ptr(),
+                                           jac.data_ptr() if jacobian else None,
+                                           _stream_ptr(stream)))
     return (y, jac) if jacobian else y
 
 
