@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--h", type=float, default=0.063)
     ap.add_argument("--cap", type=int, default=64)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--shard", default="independent", choices=["independent", "strips"],
+                    help="N>1: independent maps per rank (weak scaling) or one map split in "
+                         "row strips with a final sum all-reduce (strong scaling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -196,10 +199,16 @@ def main():
         if world > 1:
             dist.barrier()
 
-    f = workload(args, args.seed + rank)
-    g = f.grid
+    from paper_2211_00354_gb300 import dist as ldist
+    strips = world > 1 and args.shard == "strips"
+    f = workload(args, args.seed if strips else args.seed + rank)
+    g_full = f.grid
+    g = g_full
+    if strips:
+        r0, nr = ldist.row_strips(g_full.ny, world)[rank]
+        g = ldist.strip_grid(g_full, r0, nr)
     prec = lens.FP32_BULK if args.prec == "fp32" else lens.FP64
-    target = (g.x0, g.x0 + g.nx * g.h, g.y0, g.y0 + g.ny * g.h)
+    target = (g_full.x0, g_full.x0 + g_full.nx * g_full.h, g_full.y0, g_full.y0 + g_full.ny * g_full.h)
     stars = torch.tensor(f.stars, device=dev)
     masses = torch.tensor(f.masses, device=dev)
     mp = torch.empty((f.npy, f.npx), dtype=torch.float64, device=dev)
@@ -210,6 +219,8 @@ def main():
         P = lens.LensFMM(stars, masses, f.kappa_s, f.gamma, p=args.p, leaf_size=args.leaf,
                          prec=prec, target_box=target)
         _, st = P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp)
+        if strips:
+            ldist.allreduce_map(mp)  # the path's one exchange: sum of the strip maps
         info = P.info()
         return P, st, info
 
@@ -243,12 +254,9 @@ def main():
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     ms = tot_ms / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = ldist.max_over_ranks(ms, dev)
     rays_step = stats[-1]["rays"]
-    total_rays = rays_step * world
+    total_rays = ldist.allreduce_ledger({"r": rays_step}, ("r",), dev)["r"] if world > 1 else rays_step
     value = total_rays / (ms / 1e3)
 
     # ---- kernel-level roofline (live CUDA events inside the library) -----
@@ -333,6 +341,8 @@ def main():
             P = lens.LensFMM(d_stars, d_masses, f.kappa_s, f.gamma, p=args.p, leaf_size=args.leaf,
                              prec=prec, target_box=target)
             P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp)
+            if strips:
+                ldist.allreduce_map(mp)
             h_map.copy_(mp, non_blocking=True)
             e1.record(stream)
             torch.cuda.synchronize()
@@ -340,10 +350,7 @@ def main():
             if it > 0:
                 e_ms += e0.elapsed_time(e1)
         e_ms /= args.steps
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = ldist.max_over_ranks(e_ms, dev)
         e2e = {"value": total_rays / (e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(h_stars.numel() * 8 + h_masses.numel() * 8),
                "d2h_bytes_per_step": int(h_map.numel() * 8), "ms_per_step": e_ms}
@@ -362,14 +369,16 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "scaling": "strong" if strips else "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
             "config": {"workload": workload_name(args), "n_stars": f.n, "cells": g.n_cells,
                        "grid": [g.nx, g.ny], "npix": [f.npx, f.npy], "p": args.p,
                        "leaf_size": args.leaf, "bbox_cap_px": args.cap,
                        "l2": "flushed between steps (256 MiB write)" if not args.no_flush else "not flushed",
-                       "parallelism": "independent map per GPU" if world > 1 else "1 GPU"},
-            "map_ms": ms, "maps_per_s": world / (ms / 1e3),
-            "omega_per_s": 10.0 * f.npx * f.npy * f.n * world / (ms / 1e3),
+                       "parallelism": ("one map in %d row strips + map all-reduce" % world if strips
+                                       else "independent map per GPU" if world > 1 else "1 GPU")},
+            "map_ms": ms, "maps_per_s": (1 if strips else world) / (ms / 1e3),
+            "omega_per_s": 10.0 * f.npx * f.npy * f.n * (1 if strips else world) / (ms / 1e3),
             "phase_ms": {"build": info["ms_build"], "deflect": st["ms_deflect"],
                          "ipm": st["ms_ipm"], "eval_kernel": ms_eval, "ipm_kernels": ms_ipm},
             "work": {"rays": rays_step, "p2p_pairs": pairs, "m2p_evals": m2p,
