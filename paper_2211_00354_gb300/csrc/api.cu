@@ -323,8 +323,12 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
   // ~mu n_0 of them; float32 keeps ~1e-6 relative) and is written out in
   // float64 once at the end, so no float64 conversion runs per increment
   Scratch map32(&P.da, sizeof(float) * (size_t)npx * (size_t)npy);
+  // whole-pixel runs of large cells enter as +v / -v at the ends of the run
+  // in a per-row difference array, prefix-summed into the map at the end
+  Scratch rowdiff(&P.da, sizeof(float) * ((size_t)npx + 1) * (size_t)npy);
   int* qcount = queue.as<int>() + (size_t)rows * (size_t)nx;
   LENS_CUDA(cudaMemsetAsync(map32.p, 0, map32.bytes, s));
+  LENS_CUDA(cudaMemsetAsync(rowdiff.p, 0, rowdiff.bytes, s));
   LENS_CUDA(cudaMemsetAsync(sdev.p, 0, sdev.bytes, s));
   P.ev_clear();
   P.timing = true;
@@ -348,11 +352,11 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     mark();
     evaluate_grid_pix(P, g, corners.as<PixCorner>(), ip, s);
     mark();
-    ipm_accumulate(corners.as<PixCorner>(), nx, nr, ip, map32.as<float>(), sdev.as<double>(),
-                   queue.as<int>(), qcount, s, &P.ev_ipm);
+    ipm_accumulate(corners.as<PixCorner>(), nx, nr, ip, map32.as<float>(), rowdiff.as<float>(),
+                   sdev.as<double>(), queue.as<int>(), qcount, s, &P.ev_ipm);
     ++chunks;
   }
-  ipm_finish_map(map32.as<float>(), (int64_t)npx * npy, map_out, s);
+  ipm_finish_map(map32.as<float>(), rowdiff.as<float>(), npx, npy, map_out, s);
   mark();
   double hs[16];
   LENS_CUDA(cudaMemcpyAsync(hs, sdev.p, sizeof(hs), cudaMemcpyDeviceToHost, s));

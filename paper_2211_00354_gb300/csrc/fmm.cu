@@ -71,36 +71,52 @@ __global__ void k_p2m(const double2* __restrict__ spos, const double* __restrict
   for (int k = 0; k <= p; ++k) out[k] = a[k * st];
 }
 
-// ---- M2M: one warp per internal box of a level -------------------------------
-__global__ void k_m2m(const int* __restrict__ child, const int* __restrict__ count, int64_t b0,
-                      int64_t b1, int p, const double2* __restrict__ T, double2* __restrict__ M) {
-  const int lane = threadIdx.x & 31;
-  const int64_t b = b0 + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+// ---- M2M: one thread per internal box of a level ---------------------------
+// The four child offsets are d_q = w i^m_q with w = (1+i)/2 and m_q = 2, 3,
+// 1, 0 for quadrants (-,-), (+,-), (-,+), (+,+).  Since d_q^(l-k) depends on
+// q only through i^(m_q (l-k)), which repeats with period 4 in l-k,
+//   A^P_l = w^l sum_{k<=l} C(l,k) conj(w)^k G_{(l-k) mod 4}[k],
+//   G_r[k] = sum_m i^(m r) A^(child m)_k      (a 4-point DFT over quadrants:
+//                                              additions only),
+// one REAL binomial matrix on four complex vectors instead of four complex
+// matrices: about a third of the float64 operations of the direct form, and
+// every thread runs the same loop bounds (no idle lanes).  w^k and
+// conj(w)^k are exact, so the rounding is that of the direct form.
+constexpr int kM2MThreads = 32;
+
+__global__ void __launch_bounds__(kM2MThreads)
+k_m2m(const int* __restrict__ child, int64_t b0, int64_t b1, int p,
+      const double* __restrict__ binom, int ldb, const double2* __restrict__ wpow,
+      double2* __restrict__ M) {
+  extern __shared__ double2 H[];  // [4][p+1][kM2MThreads]
+  const int t = threadIdx.x;
+  const int64_t b = b0 + blockIdx.x * (int64_t)kM2MThreads + t;
   if (b >= b1) return;
   const int c0 = child[b];
   if (c0 < 0) return;
   const int P1 = p + 1;
-  double2 acc[3];
-#pragma unroll
-  for (int s = 0; s < 3; ++s) acc[s] = make_double2(0.0, 0.0);
-  for (int q = 0; q < 4; ++q) {
-    if (count[c0 + q] == 0) continue;
-    const double2* A = M + (int64_t)(c0 + q) * P1;
-    const double2* Tq = T + (int64_t)q * P1 * P1;
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      const int l = lane + 32 * s;
-      if (l > p) break;
-      double2 v = acc[s];
-      for (int k = 0; k <= l; ++k) v = cfma(ld2(Tq + l * P1 + k), ld2(A + k), v);
-      acc[s] = v;
-    }
+  const double2* A = M + (int64_t)c0 * P1;  // children c0..c0+3 are contiguous
+  for (int k = 0; k <= p; ++k) {
+    const double2 B0 = ld2(A + 3 * P1 + k), B1 = ld2(A + 2 * P1 + k);
+    const double2 B2 = ld2(A + k), B3 = ld2(A + P1 + k);
+    const double2 s02 = B0 + B2, d02 = B0 - B2, s13 = B1 + B3, d13 = B1 - B3;
+    double2 w = ld2(wpow + k);
+    w.y = -w.y;
+    H[(0 * P1 + k) * kM2MThreads + t] = cmul(w, s02 + s13);
+    H[(1 * P1 + k) * kM2MThreads + t] = cmul(w, make_double2(d02.x - d13.y, d02.y + d13.x));
+    H[(2 * P1 + k) * kM2MThreads + t] = cmul(w, s02 - s13);
+    H[(3 * P1 + k) * kM2MThreads + t] = cmul(w, make_double2(d02.x + d13.y, d02.y - d13.x));
   }
   double2* out = M + b * (int64_t)P1;
-#pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    const int l = lane + 32 * s;
-    if (l <= p) out[l] = acc[s];
+  for (int l = 0; l <= p; ++l) {
+    double sx = 0.0, sy = 0.0;
+    for (int k = 0; k <= l; ++k) {
+      const double c = __ldg(binom + (int64_t)l * ldb + k);
+      const double2 h = H[(((l - k) & 3) * P1 + k) * kM2MThreads + t];
+      sx = fma(c, h.x, sx);
+      sy = fma(c, h.y, sy);
+    }
+    out[l] = cmul(ld2(wpow + l), make_double2(sx, sy));
   }
 }
 
@@ -120,8 +136,11 @@ struct DownArgs {
   int p;
 };
 
+// Shared memory per warp: (p+1) x 32 complex values plus 64 ints.
+__host__ __device__ inline size_t downward_smem_per_warp(int p) { return sizeof(double2) * (size_t)(p + 1) * 32 + 64 * sizeof(int); }
+
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_downward(DownArgs A) {
-  __shared__ double2 sbuf[kWarpsPerBlock][kMaxOrder + 1];
+  extern __shared__ double2 dsm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t a = A.a0 + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
   if (a >= A.a1) return;
@@ -149,7 +168,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_downward(DownArgs A) {
     }
   }
   // M2L from V
-  double2* buf = sbuf[wib];
+  double2* buf = dsm + (int64_t)wib * (downward_smem_per_warp(p) / sizeof(double2));
   const int bx = A.ix[B], by = A.iy[B];
   for (int64_t e = A.V_off[a]; e < A.V_off[a + 1]; ++e) {
     const int C = A.V_list[e];
@@ -176,29 +195,59 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_downward(DownArgs A) {
     }
     __syncwarp();
   }
-  // P2L from X (each star expanded about the box centre)
+  // P2L from X.  The stars of the X boxes are taken 32 at a time across box
+  // boundaries: lane j forms the series -m_j/(z_j-c) (r/(z_j-c))^l of its
+  // star by recurrence into shared memory, then lane l sums column l.  (One
+  // star at a time with per-lane powers would idle most of the warp when the
+  // X boxes hold a few stars each.)
   const double cx = A.lo_x + (2.0 * bx + 1.0) * r, cy = A.lo_y + (2.0 * by + 1.0) * r;
-  for (int64_t e = A.X_off[a]; e < A.X_off[a + 1]; ++e) {
-    const int C = A.X_list[e];
-    const int s0 = A.start[C], ns = A.count[C];
-    for (int j = 0; j < ns; ++j) {
-      const double2 z = A.spos[s0 + j];
-      const double m = A.smass[s0 + j];
-      const double2 inv = cinv(make_double2(z.x - cx, z.y - cy));  // 1/(z-c)
-      const double2 q = make_double2(inv.x * r, inv.y * r);        // r/(z-c)
-      const double2 lead = make_double2(-m * inv.x, -m * inv.y);   // -m/(z-c)
+  int* xs = reinterpret_cast<int*>(buf + (int64_t)P1 * 32);  // [32] inclusive counts, [32] starts
+  for (int64_t eb = A.X_off[a]; eb < A.X_off[a + 1]; eb += 32) {
+    const int ne = (int)min64(32, A.X_off[a + 1] - eb);
+    int cnt = 0, st = 0;
+    if (lane < ne) {
+      const int C = A.X_list[eb + lane];
+      cnt = A.count[C];
+      st = A.start[C];
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    xs[lane] = incl;
+    xs[32 + lane] = st;
+    __syncwarp();
+    for (int f0 = 0; f0 < total; f0 += 32) {
+      const int f = f0 + lane;
+      if (f < total) {
+        int e = 0;
+        while (xs[e] <= f) ++e;  // first box whose inclusive count exceeds f
+        const int j = xs[32 + e] + f - (e ? xs[e - 1] : 0);
+        const double2 z = A.spos[j];
+        const double m = A.smass[j];
+        const double2 inv = cinv(make_double2(z.x - cx, z.y - cy));  // 1/(z-c)
+        const double2 q = make_double2(inv.x * r, inv.y * r);        // r/(z-c)
+        double2 v = make_double2(-m * inv.x, -m * inv.y);            // -m/(z-c)
+        for (int l = 0; l <= p; ++l) {
+          buf[l * 32 + lane] = v;
+          v = cmul(v, q);
+        }
+      }
+      __syncwarp();
+      const int nv = min(32, total - f0);
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
         const int l = lane + 32 * s;
         if (l > p) break;
-        // q^l by binary powering
-        double2 pw = make_double2(1.0, 0.0), bse = q;
-        for (int e2 = l; e2 > 0; e2 >>= 1) {
-          if (e2 & 1) pw = cmul(pw, bse);
-          bse = cmul(bse, bse);
-        }
-        acc[s] = cfma(lead, pw, acc[s]);
+        double2 v = acc[s];
+        for (int jj = 0; jj < nv; ++jj) v = v + buf[l * 32 + jj];
+        acc[s] = v;
       }
+      __syncwarp();
     }
   }
   double2* out = A.L + (int64_t)B * P1;
@@ -277,14 +326,22 @@ void fmm_tables(Plan& P, cudaStream_t s) {
         pr = nr; pi = ni;
       }
     }
+  // ((1+i)/2)^k: Gaussian integers over powers of two, exact in float64
+  std::vector<double2> wp((size_t)P1);
+  for (int k = 0; k <= p; ++k) {
+    auto w = cpow(0.5, 0.5, k);
+    wp[(size_t)k] = make_double2(w.first, w.second);
+  }
   t.binom = P.dalloc_n<double>(bin.size());
   t.m2m = P.dalloc_n<double2>(m2m.size());
   t.l2l = P.dalloc_n<double2>(l2l.size());
   t.upow = P.dalloc_n<double2>(up.size());
+  t.wpow = P.dalloc_n<double2>(wp.size());
   LENS_CUDA(cudaMemcpyAsync(t.binom, bin.data(), bin.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   LENS_CUDA(cudaMemcpyAsync(t.m2m, m2m.data(), m2m.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
   LENS_CUDA(cudaMemcpyAsync(t.l2l, l2l.data(), l2l.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
   LENS_CUDA(cudaMemcpyAsync(t.upow, up.data(), up.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  LENS_CUDA(cudaMemcpyAsync(t.wpow, wp.data(), wp.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
   // host vectors must stay alive until the copies have run
   LENS_CUDA(cudaStreamSynchronize(s));
 }
@@ -306,10 +363,13 @@ void fmm_p2m(Plan& P, cudaStream_t s) {
 
 void fmm_m2m(Plan& P, cudaStream_t s) {
   const FmmTables& t = P.tab;
+  const size_t smem = sizeof(double2) * 4 * (size_t)(P.p + 1) * kM2MThreads;
+  if (smem > 48 * 1024)
+    LENS_CUDA(cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int l = P.nlevels - 2; l >= 0; --l) {
     const int64_t b0 = P.level_off[l], b1 = P.level_off[l + 1];
-    k_m2m<<<grid_for((b1 - b0) * 32, 128), 128, 0, s>>>(P.box_child, P.box_count, b0, b1, P.p,
-                                                        t.m2m, P.M);
+    k_m2m<<<grid_for(b1 - b0, kM2MThreads), kM2MThreads, smem, s>>>(P.box_child, b0, b1, P.p,
+                                                                     t.binom, t.ldb, t.wpow, P.M);
     LENS_LAUNCHED("k_m2m");
   }
 }
@@ -324,11 +384,14 @@ void fmm_downward(Plan& P, cudaStream_t s) {
   A.V_off = P.V_off; A.V_list = P.V_list; A.X_off = P.X_off; A.X_list = P.X_list;
   A.spos = P.spos; A.smass = P.smass; A.M = P.M; A.L = P.L; A.tab = t;
   A.lo_x = P.root_lo[0]; A.lo_y = P.root_lo[1]; A.root_size = P.root_size; A.p = P.p;
+  const size_t smem = downward_smem_per_warp(P.p) * kWarpsPerBlock;
+  if (smem > 48 * 1024)
+    LENS_CUDA(cudaFuncSetAttribute(k_downward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int l = 0; l < P.nlevels; ++l) {
     A.a0 = P.active_level_off[l];
     A.a1 = P.active_level_off[l + 1];
     if (A.a1 <= A.a0) continue;
-    k_downward<<<grid_for((A.a1 - A.a0) * 32, 32 * kWarpsPerBlock), 32 * kWarpsPerBlock, 0, s>>>(A);
+    k_downward<<<grid_for((A.a1 - A.a0) * 32, 32 * kWarpsPerBlock), 32 * kWarpsPerBlock, smem, s>>>(A);
     LENS_LAUNCHED("k_downward");
   }
 }

@@ -70,6 +70,8 @@ struct IpmArgs {
   const PixCorner* yc;  // (nrows+1) x (nx+1) corners of the chunk
   int64_t nx, ncells;
   float* map;           // float32 accumulation map (added to the float64 output at the end)
+  float* D;             // per-row difference array, npy x (npx + 1): prefix-summed at the end
+  int64_t ldd;          // npx + 1
   double* stats;        // [8]
   int* queue; int* qcount;
   IpmParams ip;
@@ -227,8 +229,16 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
 // ill-conditioned polygon), lanes striding over the cell's pixels.
 // Well-conditioned cells run in float32 in coordinates local to their box;
 // ill-conditioned ones (|A_P| small against the box) run the clip in float64.
+// Per-warp staging of the scanline pass: 32 rows x 4 edges.
+struct QueueShared {
+  float xa[kIpmThreads / 32][128], xb[kIpmThreads / 32][128], dy[kIpmThreads / 32][128];
+  int pa[kIpmThreads / 32][128], n[kIpmThreads / 32][128];
+  int row[kIpmThreads / 32][32], cum[kIpmThreads / 32][32];
+};
+
 __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
-  const int lane = threadIdx.x & 31;
+  __shared__ QueueShared sh;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t wg = (blockIdx.x * (int64_t)kIpmThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kIpmThreads) >> 5;
   const int nq = *A.qcount;
@@ -271,15 +281,84 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
     float fin = 0.f;
     if (fp32) {
       const float inv = 1.0f / A_loc;
-      for (int64_t t2 = lane; t2 < npix; t2 += 32) {
-        const uint32_t r32 = (uint32_t)t2 / (uint32_t)w;
-        const int py = cy0 + (int)r32, px = cx0 + (int)((uint32_t)t2 - r32 * (uint32_t)w);
-        const float a = pixel_area<float>(fx, fy, (float)(px - ix0), (float)(py - iy0));
-        if (a == 0.0f) continue;
-        const float fr = a * inv;
-        atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], A.scale_f * fr);
-        fin += fr;
-        led.nupd += 1;
+      const float kf = A.scale_f * inv;  // map increment per unit of pixel area
+      const int lx0 = cx0 - ix0, lx1 = cx1 - ix0;
+      const int nrow = cy1 - cy0 + 1;
+      for (int r0 = 0; r0 < nrow; r0 += 32) {
+        // lane r owns map row cy0 + r0 + r (local band Y <= y <= Y + 1)
+        const int r = r0 + lane;
+        int cnt = 0;
+        if (r < nrow) {
+          const float Y = (float)(cy0 - iy0 + r);
+          const int64_t drow = (int64_t)(cy0 + r) * A.ldd;
+          float vsum = 0.f, frow = 0.f;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int t = lane * 4 + e;
+            int n = 0;
+            const float x0 = fx[e], y0 = fy[e], x1 = fx[(e + 1) & 3], y1 = fy[(e + 1) & 3];
+            const float ya = fminf(fmaxf(y0, Y), Y + 1.f), yb = fminf(fmaxf(y1, Y), Y + 1.f);
+            if (y1 != y0 && ya != yb) {
+              // the same clipped segment and slope as pixel_area()
+              const float sl = (x1 - x0) / (y1 - y0);
+              const float xa = x0 + (ya - y0) * sl, xb = x0 + (yb - y0) * sl;
+              const float dy = yb - ya;
+              const int Xa = (int)floorf(fminf(xa, xb)), Xb = (int)ceilf(fmaxf(xa, xb)) - 1;
+              // whole-pixel run [lx0, Xa): g = 1, each pixel gains dy
+              const int hi = min(Xa, lx1 + 1);
+              if (hi > lx0) {
+                const float v = dy * kf;
+                atomicAdd(&A.D[drow + ix0 + hi], -v);
+                vsum += v;
+                frow += dy * (float)(hi - lx0);
+                led.nupd += 1;
+              }
+              // pixels the segment crosses: [max(Xa, lx0), min(Xb, lx1)]
+              const int pa = max(Xa, lx0), pb = min(Xb, lx1);
+              if (pb >= pa) {
+                n = pb - pa + 1;
+                sh.xa[wib][t] = xa; sh.xb[wib][t] = xb; sh.dy[wib][t] = dy; sh.pa[wib][t] = pa;
+              }
+            }
+            sh.n[wib][t] = n;
+            cnt += n;
+          }
+          if (vsum != 0.f) { atomicAdd(&A.D[drow + cx0], vsum); led.nupd += 1; }
+          fin += frow * inv;
+          sh.row[wib][lane] = cy0 + r;
+        }
+        // crossed pixels of the 32 rows, spread evenly over the lanes
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        sh.cum[wib][lane] = incl;
+        __syncwarp();
+        for (int f0 = 0; f0 < total; f0 += 32) {
+          const int f = f0 + lane;
+          if (f < total) {
+            int L = 0;  // first lane whose inclusive count exceeds f
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1)
+              if (sh.cum[wib][L + st - 1] <= f) L += st;
+            int off = f - (L ? sh.cum[wib][L - 1] : 0);
+            int t = L * 4;
+            while (off >= sh.n[wib][t]) { off -= sh.n[wib][t]; ++t; }
+            const int X = sh.pa[wib][t] + off;
+            const float a = sh.dy[wib][t] * mean_clamp01<float>(sh.xa[wib][t] - (float)X,
+                                                                 sh.xb[wib][t] - (float)X);
+            if (a != 0.0f) {
+              const float fr = a * inv;
+              atomicAdd(&A.map[(int64_t)sh.row[wib][L] * A.ip.npx + ix0 + X], A.scale_f * fr);
+              fin += fr;
+              led.nupd += 1;
+            }
+          }
+        }
+        __syncwarp();
       }
     } else {
       // float64 in coordinates local to the box (small integers + fraction)
@@ -340,24 +419,57 @@ void event_pair_end(std::pair<cudaEvent_t, cudaEvent_t>& e, cudaStream_t s) {
   LENS_CUDA(cudaEventRecord(e.second, s));
 }
 
-__global__ void k_map_to_f64(const float* __restrict__ m32, int64_t n, double* __restrict__ m64) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    m64[i] = (double)m32[i];
+// map = map32 + row-wise prefix sum of the difference array (float64), one
+// block per map row: each thread sums a contiguous run of columns, a block
+// scan gives each run its offset, and the run is written out.
+constexpr int kFinishThreads = 256;
+
+__global__ void __launch_bounds__(kFinishThreads)
+k_map_finish(const float* __restrict__ m32, const float* __restrict__ D, int npx, int npy,
+             int64_t ldd, double* __restrict__ out) {
+  __shared__ double wsum[kFinishThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int run = (npx + kFinishThreads - 1) / kFinishThreads;
+  const int c0 = min(npx, t * run), c1 = min(npx, c0 + run);
+  for (int64_t row = blockIdx.x; row < npy; row += gridDim.x) {
+    const float* d = D + row * ldd;
+    double s = 0.0;
+    for (int c = c0; c < c1; ++c) s += (double)d[c];
+    double incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    __syncthreads();  // the previous row's readers of wsum are done
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    double base = incl - s;
+    for (int q = 0; q < w; ++q) base += wsum[q];
+    const float* m = m32 + row * (int64_t)npx;
+    double* o = out + row * (int64_t)npx;
+    for (int c = c0; c < c1; ++c) {
+      base += (double)d[c];
+      o[c] = (double)m[c] + base;
+    }
+  }
 }
 
-void ipm_finish_map(const float* map32, int64_t n, double* map, cudaStream_t s) {
-  k_map_to_f64<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(map32, n, map);
-  LENS_LAUNCHED("k_map_to_f64");
+void ipm_finish_map(const float* map32, const float* rowdiff, int npx, int npy, double* map,
+                    cudaStream_t s) {
+  const unsigned blocks = (unsigned)std::min<int64_t>(npy, 152 * 8);
+  k_map_finish<<<blocks, kFinishThreads, 0, s>>>(map32, rowdiff, npx, npy, (int64_t)npx + 1, map);
+  LENS_LAUNCHED("k_map_finish");
 }
 
 void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const IpmParams& ip,
-                    float* map, double* stats_dev, int* queue, int* qcount, cudaStream_t s,
-                    std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev) {
+                    float* map, float* rowdiff, double* stats_dev, int* queue, int* qcount,
+                    cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev) {
   const int64_t ncells = nx * nrows_cells;
   if (ncells <= 0) return;
   IpmArgs A{};
   A.yc = yc; A.nx = nx; A.ncells = ncells; A.map = map; A.stats = stats_dev;
+  A.D = rowdiff; A.ldd = (int64_t)ip.npx + 1;
   A.queue = queue; A.qcount = qcount; A.ip = ip;
   A.thr_area = (float)(1e-13 * ip.a_cell / ip.s_star);
   A.scale_f = (float)ip.scale;

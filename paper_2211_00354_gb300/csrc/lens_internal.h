@@ -94,6 +94,7 @@ struct FmmTables {
   double2* m2m = nullptr;    // [4][p+1][p+1]: row l, col k (k <= l)
   double2* l2l = nullptr;    // [4][p+1][p+1]: row j, col l (l >= j)
   double2* upow = nullptr;   // [49][p+2]: u^k for offset (dx,dy) in [-3,3]^2
+  double2* wpow = nullptr;   // [p+1]: ((1+i)/2)^k, exact in float64
 };
 
 struct Plan {
@@ -234,17 +235,20 @@ struct __align__(16) PixCorner {
 };
 void evaluate_grid_pix(Plan& P, const GridRows& g, PixCorner* out, const IpmParams& ip,
                        cudaStream_t s);
+// map32: float32 accumulation map (npy x npx); rowdiff: float32 per-row
+// difference array (npy x (npx + 1)) for whole-pixel runs of large cells.
 void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const IpmParams& ip,
-                    float* map32, double* stats_dev, int* queue, int* qcount, cudaStream_t s,
-                    std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev);
+                    float* map32, float* rowdiff, double* stats_dev, int* queue, int* qcount,
+                    cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev);
 void eval32_prepare(Plan& P, cudaStream_t s);
 void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t* toff,
                  int64_t total, double* y, double* jac, PixCorner* pix, const IpmParams* ip,
                  cudaStream_t s);
 void eval32_rays(Plan& P, const double* rays, const int64_t* off, const int* perm,
                  const int64_t* toff, int64_t total, double* y, double* jac, cudaStream_t s);
-// map32 (float32 accumulation) -> map (float64 output)
-void ipm_finish_map(const float* map32, int64_t n, double* map, cudaStream_t s);
+// map (float64 output) = map32 + row-wise prefix sums of rowdiff
+void ipm_finish_map(const float* map32, const float* rowdiff, int npx, int npy, double* map,
+                    cudaStream_t s);
 // a pair of recorded events bracketing work on a stream
 std::pair<cudaEvent_t, cudaEvent_t> event_pair_begin(cudaStream_t s);
 void event_pair_end(std::pair<cudaEvent_t, cudaEvent_t>& e, cudaStream_t s);
