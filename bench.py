@@ -283,7 +283,7 @@ def main():
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                 "ms_per_launch": ms_eval / launches}
     else:
-        roof = {"bound": "hbm", "kernel": "k_ipm_fast+k_ipm_slow", "achieved": ipm_gbs,
+        roof = {"bound": "hbm", "kernel": "k_ipm_cells+k_ipm_f64", "achieved": ipm_gbs,
                 "peak": hbm_peak, "unit": "GB/s", "frac": ipm_gbs / hbm_peak, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                 "ms_per_launch": ms_ipm / launches}
@@ -393,6 +393,8 @@ def main():
             "roofline": roof,
             "ipm_roofline": {"bound": "hbm", "achieved": ipm_gbs, "peak": hbm_peak,
                              "unit": "GB/s", "frac": ipm_gbs / hbm_peak},
+            "eval_roofline": {"bound": "alu", "achieved": eval_tflops, "peak": FP32_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": eval_tflops / FP32_PEAK_TFLOPS},
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,

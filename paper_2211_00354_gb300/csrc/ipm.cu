@@ -8,13 +8,13 @@
 //
 // Corners arrive in pixel coordinates u = (y1 - u0)/du, v = (y2 - v0)/dv,
 // split as (floor, float fraction) by the deflection epilogue, so the common
-// case needs no float64 at all:
-//   fast path (one thread per cell): pixel bounding box at most 4 x 4 and a
-//     well-conditioned polygon -> float32 in coordinates local to the box
-//     (a single-pixel box needs no overlap at all: the fraction is 1);
-//   queued path (one warp per cell, lanes striding over the cell's pixels):
-//     larger cells in float32, ill-conditioned cells (|A_P| small against
-//     the box) in float64.
+// case needs no float64 at all.  One warp takes 32 consecutive cells
+// (k_ipm_cells): single-pixel cells add their whole area; cells with a pixel
+// box up to 4 x 4 get one overlap per pixel; larger cells are swept row band
+// by row band, whole-pixel runs going to a per-row difference array and
+// only the pixels an edge crosses getting an overlap; all three kinds of
+// work are spread evenly over the warp's lanes.  Ill-conditioned cells
+// (|A_P| small against the box) are queued for float64 (k_ipm_f64).
 // Overlaps come from Green's theorem, edge by edge (the apportioning rule of
 // Sec. 2.3): the result is the winding-number-weighted area, so inverted and
 // self-intersecting (critical) cells are handled "naively", as the
@@ -82,16 +82,16 @@ struct IpmArgs {
 // Ledger of one thread: fractions in float32, counts in integers (no
 // float64 per cell).  Device stats slots: [2] sum of in-map fractions,
 // [3] sum of outside fractions (cells wholly outside count 1), [4] dropped
-// cells, [5] degenerate cells, [8] map increments, [9] queued cells; the
-// host multiplies by the cell area.
+// cells, [5] degenerate cells, [8] map increments, [9] cells on the large-cell
+// or float64 path, [10] float64 cells; the host multiplies by the cell area.
 struct Ledger {
   float fin = 0.f, fout = 0.f;
-  unsigned ndrop = 0, ndeg = 0, nupd = 0, nf64 = 0;
+  unsigned ndrop = 0, ndeg = 0, nupd = 0, nq = 0, nf64 = 0;
 };
 
 __device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L) {
   __shared__ float shf[2][kIpmThreads / 32];
-  __shared__ unsigned shu[4][kIpmThreads / 32];
+  __shared__ unsigned shu[5][kIpmThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float f0 = L.fin, f1 = L.fout;
 #pragma unroll
@@ -102,17 +102,19 @@ __device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L) 
   const unsigned u0 = __reduce_add_sync(0xffffffffu, L.ndrop);
   const unsigned u1 = __reduce_add_sync(0xffffffffu, L.ndeg);
   const unsigned u2 = __reduce_add_sync(0xffffffffu, L.nupd);
-  const unsigned u3 = __reduce_add_sync(0xffffffffu, L.nf64);
+  const unsigned u3 = __reduce_add_sync(0xffffffffu, L.nq);
+  const unsigned u4 = __reduce_add_sync(0xffffffffu, L.nf64);
   if (lane == 0) {
     shf[0][w] = f0; shf[1][w] = f1;
-    shu[0][w] = u0; shu[1][w] = u1; shu[2][w] = u2; shu[3][w] = u3;
+    shu[0][w] = u0; shu[1][w] = u1; shu[2][w] = u2; shu[3][w] = u3; shu[4][w] = u4;
   }
   __syncthreads();
-  if (threadIdx.x < 6) {
+  if (threadIdx.x < 7) {
     double x = 0;
     for (int q = 0; q < kIpmThreads / 32; ++q)
       x += threadIdx.x < 2 ? (double)shf[threadIdx.x][q] : (double)shu[threadIdx.x - 2][q];
-    const int slot = threadIdx.x < 4 ? 2 + threadIdx.x : (threadIdx.x == 4 ? 8 : 10);
+    // slots 2, 3, 4, 5, 8, 9, 10
+    const int slot = threadIdx.x < 4 ? 2 + threadIdx.x : 4 + threadIdx.x;
     if (x != 0.0) atomicAdd(&stats[slot], x);
   }
 }
@@ -148,107 +150,263 @@ __device__ __forceinline__ int winding4(const float* qx, const float* qy, float 
   return w;
 }
 
-constexpr int kSmallBox = 4;  // cells whose pixel box is at most 4 x 4 stay per-thread
-
-__global__ void __launch_bounds__(kIpmThreads) k_ipm_fast(IpmArgs A) {
-  const int64_t c = blockIdx.x * (int64_t)kIpmThreads + threadIdx.x;
-  Ledger led;
-  if (c < A.ncells) {
-    // cell index < 2^30 and nx < 2^31: 32-bit division (a 64-bit one is
-    // emulated with float64 instructions)
-    const uint32_t j32 = (uint32_t)c / (uint32_t)A.nx;
-    const int64_t j = j32, i = c - j * A.nx;
-    const int64_t W = A.nx + 1;
-    PixCorner q4[4];
-    q4[0] = A.yc[j * W + i];
-    q4[1] = A.yc[j * W + i + 1];
-    q4[2] = A.yc[(j + 1) * W + i + 1];
-    q4[3] = A.yc[(j + 1) * W + i];
-    bool far = false;
-    int ix0 = kFar, ix1 = -kFar, iy0 = kFar, iy1 = -kFar;
+// Inclusive warp scan of per-lane counts; cum[] receives the 32 inclusive
+// sums, the return value is the warp total.
+__device__ __forceinline__ int warp_counts(int cnt, int* cum, int lane) {
+  int incl = cnt;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      far |= (q4[k].iu == kFar) | (q4[k].iv == kFar);
-      ix0 = min(ix0, q4[k].iu); ix1 = max(ix1, q4[k].iu);
-      iy0 = min(iy0, q4[k].iv); iy1 = max(iy1, q4[k].iv);
-    }
-    if (far) {
-      led.ndrop = 1;
-    } else if (ix1 < 0 || iy1 < 0 || ix0 > A.ip.npx - 1 || iy0 > A.ip.npy - 1) {
-      led.fout = 1.f;
-    } else if (A.ip.cap > 0 && ((int64_t)ix1 - ix0 + 1 > A.ip.cap || (int64_t)iy1 - iy0 + 1 > A.ip.cap)) {
-      led.ndrop = 1;
-    } else {
-      float qx[4], qy[4];
-      float xmn = 1e30f, xmx = -1e30f, ymn = 1e30f, ymx = -1e30f;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  cum[lane] = incl;
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, incl, 31);
+}
+// Owner of flat task f: the first lane whose inclusive count exceeds f, and
+// f's offset within that lane's tasks.
+__device__ __forceinline__ int warp_owner(const int* cum, int f, int& off) {
+  int L = 0;
+#pragma unroll
+  for (int st = 16; st > 0; st >>= 1)
+    if (cum[L + st - 1] <= f) L += st;
+  off = f - (L ? cum[L - 1] : 0);
+  return L;
+}
+
+constexpr int kSmallBox = 4;  // pixel boxes up to 4 x 4: overlap pixel by pixel
+constexpr int kWarps = kIpmThreads / 32;
+
+// Per-warp staging: the warp's 32 cells, then up to 32 rows x 4 edge
+// segments of large cells.
+struct CellShared {
+  float qx[4][kWarps][32], qy[4][kWarps][32];  // polygon, pixel units local to (ix0, iy0)
+  float inv[kWarps][32];                        // 1 / A_P
+  int ix0[kWarps][32], iy0[kWarps][32];
+  int cx0[kWarps][32], cx1[kWarps][32], cy0[kWarps][32];  // box clipped to the map
+  int cum[kWarps][32], cum2[kWarps][32];
+  float xa[kWarps][128], xb[kWarps][128], dy[kWarps][128];
+  int pa[kWarps][128], n[kWarps][128];
+  int row[kWarps][32], cell[kWarps][32];
+};
+
+// One warp per 32 consecutive cells of a grid row (grid-stride over chunks).
+//  A. lane = cell: corners (coalesced), pixel box, ledger of cells that are
+//     dropped or outside, single-pixel cells (fraction 1), hand-off of
+//     ill-conditioned cells to the float64 queue;
+//  B. small cells (box <= 4 x 4): the warp's (cell, pixel) pairs spread over
+//     the lanes, one Green's-theorem overlap each;
+//  C. large cells: the warp's (cell, row) pairs spread over the lanes; in the
+//     band Y <= y <= Y+1 an edge whose clipped part runs (xa,ya)->(xb,yb)
+//     adds dy = yb - ya to each pixel X with X + 1 <= min(xa, xb): that
+//     whole-pixel run enters the per-row difference array as +v / -v at its
+//     ends, and only the pixels the segment crosses get an explicit overlap
+//     (the same Green's-theorem terms as pixel_area()), again spread over
+//     the lanes.  Work per large cell follows its perimeter in pixels, not
+//     its area.
+__global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
+  __shared__ CellShared sh;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t nchunks = (A.ncells + 31) >> 5;
+  const int64_t W = A.nx + 1;
+  const int npx = A.ip.npx, npy = A.ip.npy;
+  Ledger led;
+  for (int64_t ch = (blockIdx.x * (int64_t)kIpmThreads + threadIdx.x) >> 5; ch < nchunks;
+       ch += ((int64_t)gridDim.x * kIpmThreads) >> 5) {
+    // ---- A: one cell per lane ------------------------------------------------
+    const int64_t c = ch * 32 + lane;
+    int nsmall = 0, nrows = 0;
+    bool f64 = false;
+    if (c < A.ncells) {
+      // cell index < 2^30 and nx < 2^31: 32-bit division
+      const uint32_t j32 = (uint32_t)c / (uint32_t)A.nx;
+      const int64_t j = j32, i = c - j * A.nx;
+      PixCorner q4[4];
+      q4[0] = A.yc[j * W + i];
+      q4[1] = A.yc[j * W + i + 1];
+      q4[2] = A.yc[(j + 1) * W + i + 1];
+      q4[3] = A.yc[(j + 1) * W + i];
+      bool far = false;
+      int ix0 = kFar, ix1 = -kFar, iy0 = kFar, iy1 = -kFar;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        qx[k] = (float)(q4[k].iu - ix0) + q4[k].fu;
-        qy[k] = (float)(q4[k].iv - iy0) + q4[k].fv;
-        xmn = fminf(xmn, qx[k]); xmx = fmaxf(xmx, qx[k]);
-        ymn = fminf(ymn, qy[k]); ymx = fmaxf(ymx, qy[k]);
+        far |= (q4[k].iu == kFar) | (q4[k].iv == kFar);
+        ix0 = min(ix0, q4[k].iu); ix1 = max(ix1, q4[k].iu);
+        iy0 = min(iy0, q4[k].iv); iy1 = max(iy1, q4[k].iv);
       }
-      const float A_loc = 0.5f * ((qx[1] - qx[0]) * (qy[2] - qy[0]) - (qx[2] - qx[0]) * (qy[1] - qy[0]) +
-                                  (qx[2] - qx[0]) * (qy[3] - qy[0]) - (qx[3] - qx[0]) * (qy[2] - qy[0]));
-      const float ext = (xmx - xmn) * (ymx - ymn);
-      const bool small = (ix1 - ix0 < kSmallBox) && (iy1 - iy0 < kSmallBox);
-      const bool good = fabsf(A_loc) > 1e-3f * ext && fabsf(A_loc) > A.thr_area;
-      if (small && good) {
-        if (ix0 == ix1 && iy0 == iy1) {
-          atomicAdd(&A.map[(int64_t)iy0 * A.ip.npx + ix0], A.scale_f);
-          led.fin = 1.f;
-          led.nupd = 1;
-        } else {
-          const float inv = 1.0f / A_loc;
-          float fin = 0.f;
-          const int py0 = max(iy0, 0), py1 = min(iy1, A.ip.npy - 1);
-          const int px0 = max(ix0, 0), px1 = min(ix1, A.ip.npx - 1);
-          for (int py = py0; py <= py1; ++py) {
-            for (int px = px0; px <= px1; ++px) {
-              const float a = pixel_area<float>(qx, qy, (float)(px - ix0), (float)(py - iy0));
-              if (a == 0.0f) continue;
-              const float fr = a * inv;
-              atomicAdd(&A.map[(int64_t)py * A.ip.npx + px], A.scale_f * fr);
-              fin += fr;
-              led.nupd += 1;
-            }
-          }
-          led.fin = fin;
-          led.fout = 1.f - fin;
-        }
+      if (far) {
+        led.ndrop += 1;
+      } else if (ix1 < 0 || iy1 < 0 || ix0 > npx - 1 || iy0 > npy - 1) {
+        led.fout += 1.f;
+      } else if (A.ip.cap > 0 && ((int64_t)ix1 - ix0 + 1 > A.ip.cap || (int64_t)iy1 - iy0 + 1 > A.ip.cap)) {
+        led.ndrop += 1;
       } else {
-        const int slot = atomicAdd(A.qcount, 1);
-        A.queue[slot] = (int)c;
+        float qx[4], qy[4];
+        float xmn = 1e30f, xmx = -1e30f, ymn = 1e30f, ymx = -1e30f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          qx[k] = (float)(q4[k].iu - ix0) + q4[k].fu;
+          qy[k] = (float)(q4[k].iv - iy0) + q4[k].fv;
+          xmn = fminf(xmn, qx[k]); xmx = fmaxf(xmx, qx[k]);
+          ymn = fminf(ymn, qy[k]); ymx = fmaxf(ymx, qy[k]);
+        }
+        const float A_loc = 0.5f * ((qx[1] - qx[0]) * (qy[2] - qy[0]) - (qx[2] - qx[0]) * (qy[1] - qy[0]) +
+                                    (qx[2] - qx[0]) * (qy[3] - qy[0]) - (qx[3] - qx[0]) * (qy[2] - qy[0]));
+        const bool good = fabsf(A_loc) > 1e-3f * (xmx - xmn) * (ymx - ymn) && fabsf(A_loc) > A.thr_area;
+        if (!good) {
+          f64 = true;
+          led.nq += 1;
+        } else if (ix0 == ix1 && iy0 == iy1) {
+          atomicAdd(&A.map[(int64_t)iy0 * npx + ix0], A.scale_f);
+          led.fin += 1.f;
+          led.nupd += 1;
+        } else {
+          const int cx0 = max(ix0, 0), cx1 = min(ix1, npx - 1);
+          const int cy0 = max(iy0, 0), cy1 = min(iy1, npy - 1);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) { sh.qx[k][w][lane] = qx[k]; sh.qy[k][w][lane] = qy[k]; }
+          sh.inv[w][lane] = 1.0f / A_loc;
+          sh.ix0[w][lane] = ix0; sh.iy0[w][lane] = iy0;
+          sh.cx0[w][lane] = cx0; sh.cx1[w][lane] = cx1; sh.cy0[w][lane] = cy0;
+          // every fraction that lands in the map is moved from fout to fin
+          led.fout += 1.f;
+          if (ix1 - ix0 < kSmallBox && iy1 - iy0 < kSmallBox) {
+            nsmall = (cx1 - cx0 + 1) * (cy1 - cy0 + 1);
+          } else {
+            nrows = cy1 - cy0 + 1;
+            led.nq += 1;
+          }
+        }
       }
     }
+    // ill-conditioned cells: one queue slot per cell, one atomic per warp
+    const unsigned fm = __ballot_sync(0xffffffffu, f64);
+    if (fm) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(A.qcount, __popc(fm));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (f64) A.queue[base + __popc(fm & ((1u << lane) - 1u))] = (int)c;
+    }
+    // ---- B: pixels of small cells -------------------------------------------
+    const int tot1 = warp_counts(nsmall, sh.cum[w], lane);
+    for (int f0 = 0; f0 < tot1; f0 += 32) {
+      const int f = f0 + lane;
+      if (f < tot1) {
+        int off;
+        const int L = warp_owner(sh.cum[w], f, off);
+        const int cx0 = sh.cx0[w][L], wd = sh.cx1[w][L] - cx0 + 1;
+        const int r = off / wd;
+        const int px = cx0 + off - r * wd, py = sh.cy0[w][L] + r;
+        float qx[4], qy[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { qx[k] = sh.qx[k][w][L]; qy[k] = sh.qy[k][w][L]; }
+        const float a = pixel_area<float>(qx, qy, (float)(px - sh.ix0[w][L]), (float)(py - sh.iy0[w][L]));
+        if (a != 0.0f) {
+          const float fr = a * sh.inv[w][L];
+          atomicAdd(&A.map[(int64_t)py * npx + px], A.scale_f * fr);
+          led.fin += fr;
+          led.fout -= fr;
+          led.nupd += 1;
+        }
+      }
+    }
+    // ---- C: rows of large cells ---------------------------------------------
+    const int tot2 = warp_counts(nrows, sh.cum2[w], lane);
+    for (int f0 = 0; f0 < tot2; f0 += 32) {
+      const int f = f0 + lane;
+      int cnt = 0;
+      if (f < tot2) {
+        int r;
+        const int L = warp_owner(sh.cum2[w], f, r);
+        const int ix0 = sh.ix0[w][L], cx0 = sh.cx0[w][L];
+        const int lx0 = cx0 - ix0, lx1 = sh.cx1[w][L] - ix0;
+        const float inv = sh.inv[w][L];
+        const float kf = A.scale_f * inv;  // map increment per unit of pixel area
+        const int py = sh.cy0[w][L] + r;
+        const float Y = (float)(py - sh.iy0[w][L]);
+        const int64_t drow = (int64_t)py * A.ldd;
+        float vsum = 0.f, frow = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int t = lane * 4 + e;
+          int n = 0;
+          const float x0 = sh.qx[e][w][L], y0 = sh.qy[e][w][L];
+          const float x1 = sh.qx[(e + 1) & 3][w][L], y1 = sh.qy[(e + 1) & 3][w][L];
+          const float ya = fminf(fmaxf(y0, Y), Y + 1.f), yb = fminf(fmaxf(y1, Y), Y + 1.f);
+          if (y1 != y0 && ya != yb) {
+            // the same clipped segment and slope as pixel_area()
+            const float sl = (x1 - x0) / (y1 - y0);
+            const float xa = x0 + (ya - y0) * sl, xb = x0 + (yb - y0) * sl;
+            const float dy = yb - ya;
+            const int Xa = (int)floorf(fminf(xa, xb)), Xb = (int)ceilf(fmaxf(xa, xb)) - 1;
+            // whole-pixel run [lx0, Xa): each pixel gains dy
+            const int hi = min(Xa, lx1 + 1);
+            if (hi > lx0) {
+              const float v = dy * kf;
+              atomicAdd(&A.D[drow + ix0 + hi], -v);
+              vsum += v;
+              frow += dy * (float)(hi - lx0);
+              led.nupd += 1;
+            }
+            // pixels the segment crosses: [max(Xa, lx0), min(Xb, lx1)]
+            const int pa = max(Xa, lx0), pb = min(Xb, lx1);
+            if (pb >= pa) {
+              n = pb - pa + 1;
+              sh.xa[w][t] = xa; sh.xb[w][t] = xb; sh.dy[w][t] = dy; sh.pa[w][t] = pa;
+            }
+          }
+          sh.n[w][t] = n;
+          cnt += n;
+        }
+        if (vsum != 0.f) { atomicAdd(&A.D[drow + cx0], vsum); led.nupd += 1; }
+        led.fin += frow * inv;
+        led.fout -= frow * inv;
+        sh.row[w][lane] = py;
+        sh.cell[w][lane] = L;
+      }
+      // crossed pixels of these 32 rows, spread over the lanes
+      int* cum = sh.cum[w];  // the small-cell counts are no longer needed
+      __syncwarp();
+      const int totp = warp_counts(cnt, cum, lane);
+      for (int g0 = 0; g0 < totp; g0 += 32) {
+        const int g = g0 + lane;
+        if (g < totp) {
+          int off;
+          const int L = warp_owner(cum, g, off);
+          int t = L * 4;
+          while (off >= sh.n[w][t]) { off -= sh.n[w][t]; ++t; }
+          const int X = sh.pa[w][t] + off;
+          const float a = sh.dy[w][t] * mean_clamp01<float>(sh.xa[w][t] - (float)X, sh.xb[w][t] - (float)X);
+          if (a != 0.0f) {
+            const int cl = sh.cell[w][L];
+            const float fr = a * sh.inv[w][cl];
+            atomicAdd(&A.map[(int64_t)sh.row[w][L] * npx + sh.ix0[w][cl] + X], A.scale_f * fr);
+            led.fin += fr;
+            led.fout -= fr;
+            led.nupd += 1;
+          }
+        }
+      }
+      __syncwarp();
+    }
+    __syncwarp();  // the next chunk overwrites this one's staging
   }
   block_add_stats(A.stats, led);
 }
 
-// One warp per queued cell (pixel box larger than 4 x 4, or an
-// ill-conditioned polygon), lanes striding over the cell's pixels.
-// Well-conditioned cells run in float32 in coordinates local to their box;
-// ill-conditioned ones (|A_P| small against the box) run the clip in float64.
-// Per-warp staging of the scanline pass: 32 rows x 4 edges.
-struct QueueShared {
-  float xa[kIpmThreads / 32][128], xb[kIpmThreads / 32][128], dy[kIpmThreads / 32][128];
-  int pa[kIpmThreads / 32][128], n[kIpmThreads / 32][128];
-  int row[kIpmThreads / 32][32], cum[kIpmThreads / 32][32];
-};
-
-__global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
-  __shared__ QueueShared sh;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+// Ill-conditioned cells (|A_P| small against the pixel box): one warp per
+// cell, lanes over the box's pixels, the overlap in float64 in coordinates
+// local to the box; a float32 test first finds the pixels no edge meets,
+// whose coverage is the winding number exactly.
+__global__ void __launch_bounds__(kIpmThreads) k_ipm_f64(IpmArgs A) {
+  const int lane = threadIdx.x & 31;
   const int64_t wg = (blockIdx.x * (int64_t)kIpmThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kIpmThreads) >> 5;
   const int nq = *A.qcount;
   const double ac = A.ip.a_cell;
   Ledger led;
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&A.stats[9], (double)nq);
   for (int64_t t = wg; t < nq; t += nwarps) {
     const int64_t c = A.queue[t];
-    // cell index < 2^30 and nx < 2^31: 32-bit division (a 64-bit one is
-    // emulated with float64 instructions)
     const uint32_t j32 = (uint32_t)c / (uint32_t)A.nx;
     const int64_t j = j32, i = c - j * A.nx;
     const int64_t W = A.nx + 1;
@@ -265,139 +423,46 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_queue(IpmArgs A) {
     }
     const int cx0 = max(ix0, 0), cx1 = min(ix1, A.ip.npx - 1);
     const int cy0 = max(iy0, 0), cy1 = min(iy1, A.ip.npy - 1);
-    const int64_t w = (int64_t)cx1 - cx0 + 1, npix = w * ((int64_t)cy1 - cy0 + 1);
+    const int64_t wd = (int64_t)cx1 - cx0 + 1, npix = wd * ((int64_t)cy1 - cy0 + 1);
     float fx[4], fy[4];
-    float xmn = 1e30f, xmx = -1e30f, ymn = 1e30f, ymx = -1e30f;
+    double u[4], v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       fx[k] = (float)(q4[k].iu - ix0) + q4[k].fu;
       fy[k] = (float)(q4[k].iv - iy0) + q4[k].fv;
-      xmn = fminf(xmn, fx[k]); xmx = fmaxf(xmx, fx[k]);
-      ymn = fminf(ymn, fy[k]); ymx = fmaxf(ymx, fy[k]);
+      u[k] = (double)(q4[k].iu - ix0) + (double)q4[k].fu;
+      v[k] = (double)(q4[k].iv - iy0) + (double)q4[k].fv;
     }
-    const float A_loc = 0.5f * ((fx[1] - fx[0]) * (fy[2] - fy[0]) - (fx[2] - fx[0]) * (fy[1] - fy[0]) +
-                                (fx[2] - fx[0]) * (fy[3] - fy[0]) - (fx[3] - fx[0]) * (fy[2] - fy[0]));
-    const bool fp32 = fabsf(A_loc) > 1e-3f * (xmx - xmn) * (ymx - ymn) && fabsf(A_loc) > A.thr_area;
+    const double A_P = 0.5 * ((u[1] - u[0]) * (v[2] - v[0]) - (u[2] - u[0]) * (v[1] - v[0]) +
+                              (u[2] - u[0]) * (v[3] - v[0]) - (u[3] - u[0]) * (v[2] - v[0]));
+    if (!(fabs(A_P) * A.ip.s_star > 1e-14 * ac)) {
+      if (lane == 0) led.ndeg += 1;
+      continue;
+    }
+    if (lane == 0) led.nf64 += 1;
+    const double inv = 1.0 / A_P;
+    const float invf = (float)inv;
     float fin = 0.f;
-    if (fp32) {
-      const float inv = 1.0f / A_loc;
-      const float kf = A.scale_f * inv;  // map increment per unit of pixel area
-      const int lx0 = cx0 - ix0, lx1 = cx1 - ix0;
-      const int nrow = cy1 - cy0 + 1;
-      for (int r0 = 0; r0 < nrow; r0 += 32) {
-        // lane r owns map row cy0 + r0 + r (local band Y <= y <= Y + 1)
-        const int r = r0 + lane;
-        int cnt = 0;
-        if (r < nrow) {
-          const float Y = (float)(cy0 - iy0 + r);
-          const int64_t drow = (int64_t)(cy0 + r) * A.ldd;
-          float vsum = 0.f, frow = 0.f;
+    for (int64_t t2 = lane; t2 < npix; t2 += 32) {
+      const uint32_t r32 = (uint32_t)t2 / (uint32_t)wd;
+      const int oy = cy0 - iy0 + (int)r32, ox = cx0 - ix0 + (int)((uint32_t)t2 - r32 * (uint32_t)wd);
+      bool cut = false;
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int t = lane * 4 + e;
-            int n = 0;
-            const float x0 = fx[e], y0 = fy[e], x1 = fx[(e + 1) & 3], y1 = fy[(e + 1) & 3];
-            const float ya = fminf(fmaxf(y0, Y), Y + 1.f), yb = fminf(fmaxf(y1, Y), Y + 1.f);
-            if (y1 != y0 && ya != yb) {
-              // the same clipped segment and slope as pixel_area()
-              const float sl = (x1 - x0) / (y1 - y0);
-              const float xa = x0 + (ya - y0) * sl, xb = x0 + (yb - y0) * sl;
-              const float dy = yb - ya;
-              const int Xa = (int)floorf(fminf(xa, xb)), Xb = (int)ceilf(fmaxf(xa, xb)) - 1;
-              // whole-pixel run [lx0, Xa): g = 1, each pixel gains dy
-              const int hi = min(Xa, lx1 + 1);
-              if (hi > lx0) {
-                const float v = dy * kf;
-                atomicAdd(&A.D[drow + ix0 + hi], -v);
-                vsum += v;
-                frow += dy * (float)(hi - lx0);
-                led.nupd += 1;
-              }
-              // pixels the segment crosses: [max(Xa, lx0), min(Xb, lx1)]
-              const int pa = max(Xa, lx0), pb = min(Xb, lx1);
-              if (pb >= pa) {
-                n = pb - pa + 1;
-                sh.xa[wib][t] = xa; sh.xb[wib][t] = xb; sh.dy[wib][t] = dy; sh.pa[wib][t] = pa;
-              }
-            }
-            sh.n[wib][t] = n;
-            cnt += n;
-          }
-          if (vsum != 0.f) { atomicAdd(&A.D[drow + cx0], vsum); led.nupd += 1; }
-          fin += frow * inv;
-          sh.row[wib][lane] = cy0 + r;
-        }
-        // crossed pixels of the 32 rows, spread evenly over the lanes
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        sh.cum[wib][lane] = incl;
-        __syncwarp();
-        for (int f0 = 0; f0 < total; f0 += 32) {
-          const int f = f0 + lane;
-          if (f < total) {
-            int L = 0;  // first lane whose inclusive count exceeds f
-#pragma unroll
-            for (int st = 16; st > 0; st >>= 1)
-              if (sh.cum[wib][L + st - 1] <= f) L += st;
-            int off = f - (L ? sh.cum[wib][L - 1] : 0);
-            int t = L * 4;
-            while (off >= sh.n[wib][t]) { off -= sh.n[wib][t]; ++t; }
-            const int X = sh.pa[wib][t] + off;
-            const float a = sh.dy[wib][t] * mean_clamp01<float>(sh.xa[wib][t] - (float)X,
-                                                                 sh.xb[wib][t] - (float)X);
-            if (a != 0.0f) {
-              const float fr = a * inv;
-              atomicAdd(&A.map[(int64_t)sh.row[wib][L] * A.ip.npx + ix0 + X], A.scale_f * fr);
-              fin += fr;
-              led.nupd += 1;
-            }
-          }
-        }
-        __syncwarp();
+      for (int e = 0; e < 4; ++e)
+        cut |= seg_meets_pixel(fx[e], fy[e], fx[(e + 1) & 3], fy[(e + 1) & 3], (float)ox, (float)oy);
+      float fr;
+      if (cut) {
+        const double a = pixel_area<double>(u, v, (double)ox, (double)oy);
+        fr = (float)(a * inv);
+      } else {
+        const int wn = winding4(fx, fy, (float)ox + 0.5f, (float)oy + 0.5f);
+        fr = (float)wn * invf;
       }
-    } else {
-      // float64 in coordinates local to the box (small integers + fraction)
-      double u[4], v[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        u[k] = (double)(q4[k].iu - ix0) + (double)q4[k].fu;
-        v[k] = (double)(q4[k].iv - iy0) + (double)q4[k].fv;
-      }
-      const double A_P = 0.5 * ((u[1] - u[0]) * (v[2] - v[0]) - (u[2] - u[0]) * (v[1] - v[0]) +
-                                (u[2] - u[0]) * (v[3] - v[0]) - (u[3] - u[0]) * (v[2] - v[0]));
-      if (!(fabs(A_P) * A.ip.s_star > 1e-14 * ac)) {
-        if (lane == 0) led.ndeg += 1;
-        continue;
-      }
-      if (lane == 0) led.nf64 += 1;
-      const double inv = 1.0 / A_P;
-      const float invf = (float)inv;
-      for (int64_t t2 = lane; t2 < npix; t2 += 32) {
-        const uint32_t r32 = (uint32_t)t2 / (uint32_t)w;
-        const int oy = cy0 - iy0 + (int)r32, ox = cx0 - ix0 + (int)((uint32_t)t2 - r32 * (uint32_t)w);
-        bool cut = false;
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          cut |= seg_meets_pixel(fx[e], fy[e], fx[(e + 1) & 3], fy[(e + 1) & 3], (float)ox, (float)oy);
-        float fr;
-        if (cut) {
-          const double a = pixel_area<double>(u, v, (double)ox, (double)oy);
-          fr = (float)(a * inv);
-        } else {
-          const int wn = winding4(fx, fy, (float)ox + 0.5f, (float)oy + 0.5f);
-          fr = (float)wn * invf;
-        }
-        if (fr == 0.0f) continue;
-        const int64_t px = ix0 + ox, py = iy0 + oy;
-        atomicAdd(&A.map[py * A.ip.npx + px], A.scale_f * fr);
-        fin += fr;
-        led.nupd += 1;
-      }
+      if (fr == 0.0f) continue;
+      const int64_t px = ix0 + ox, py = iy0 + oy;
+      atomicAdd(&A.map[py * A.ip.npx + px], A.scale_f * fr);
+      fin += fr;
+      led.nupd += 1;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fin += __shfl_xor_sync(0xffffffffu, fin, o);
@@ -476,12 +541,13 @@ void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const 
   LENS_CUDA(cudaMemsetAsync(qcount, 0, sizeof(int), s));
   std::pair<cudaEvent_t, cudaEvent_t> e;
   if (ev) e = event_pair_begin(s);
-  k_ipm_fast<<<grid_for(ncells, kIpmThreads), kIpmThreads, 0, s>>>(A);
-  LENS_LAUNCHED("k_ipm_fast");
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  k_ipm_queue<<<sms * 8, kIpmThreads, 0, s>>>(A);
-  LENS_LAUNCHED("k_ipm_queue");
+  const int64_t chunk_blocks = (ncells + kIpmThreads - 1) / kIpmThreads;
+  k_ipm_cells<<<(unsigned)std::min<int64_t>(chunk_blocks, (int64_t)sms * 8), kIpmThreads, 0, s>>>(A);
+  LENS_LAUNCHED("k_ipm_cells");
+  k_ipm_f64<<<sms * 2, kIpmThreads, 0, s>>>(A);
+  LENS_LAUNCHED("k_ipm_f64");
   if (ev) {
     event_pair_end(e, s);
     ev->push_back(e);
