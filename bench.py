@@ -268,7 +268,10 @@ def main():
     eval_flops = 10.0 * pairs + 8.0 * (args.p + 1) * (rays_step + m2p)
     launches = stats[-1]["chunks"]
     eval_tflops = eval_flops / (ms_eval / 1e3) / 1e12
-    ipm_bytes = 16.0 * rays_step + 16.0 * stats[-1]["ipm_updates"]
+    # IPM algorithmic bytes: the 16 B pixel-coordinate corner read per grid
+    # ray plus 8 B (read + write of a float) per atomic map or difference
+    # array update
+    ipm_bytes = 16.0 * rays_step + 8.0 * stats[-1]["ipm_updates"]
     ipm_gbs = ipm_bytes / (ms_ipm / 1e3) / 1e9
     peaks = {}
     try:

@@ -14,35 +14,60 @@ import torch
 from . import lens
 
 
+# Above this many stars the backward pass rebuilds the tree and expansions
+# instead of keeping the forward plan alive between forward and backward
+# (between them only the inputs are held).
+RECOMPUTE_MIN_STARS = 10_000_000
+
+
 class LensDeflect(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, stars, masses, kappa_s, gamma, rays, p, leaf_size, prec, target_box):
-        plan = lens.LensFMM(stars.detach().contiguous(), masses.detach().contiguous(),
-                            float(kappa_s), float(gamma), p=p, leaf_size=leaf_size, prec=prec,
-                            target_box=target_box)
+    def forward(ctx, stars, masses, kappa_s, gamma, rays, p, leaf_size, prec, target_box,
+                recompute):
+        st = stars.detach().contiguous()
+        ms = masses.detach().contiguous()
+        args = (float(kappa_s), float(gamma))
+        kw = dict(p=p, leaf_size=leaf_size, prec=prec, target_box=target_box)
+        plan = lens.LensFMM(st, ms, *args, **kw)
         rays_c = rays.detach().contiguous()
         y = plan.deflect(rays_c)
+        if recompute is None:
+            recompute = st.shape[0] >= RECOMPUTE_MIN_STARS
+        if recompute:
+            plan.close()
+            plan = None
+            ctx.save_for_backward(rays_c, st, ms)
+        else:
+            ctx.save_for_backward(rays_c)
         ctx.plan = plan
-        ctx.save_for_backward(rays_c)
+        ctx.rebuild = (args, kw)
         ctx.ks_is_tensor = isinstance(kappa_s, torch.Tensor)
         ctx.g_is_tensor = isinstance(gamma, torch.Tensor)
         return y
 
     @staticmethod
     def backward(ctx, grad_y):
-        (rays,) = ctx.saved_tensors
-        gxy, gm, gkg = ctx.plan.adjoint(rays, grad_y.contiguous())
-        ctx.plan.close()
+        saved = ctx.saved_tensors
+        rays = saved[0]
+        plan = ctx.plan
+        if plan is None:
+            args, kw = ctx.rebuild
+            plan = lens.LensFMM(saved[1], saved[2], *args, **kw)
+        gxy, gm, gkg = plan.adjoint(rays, grad_y.contiguous())
+        plan.close()
         ctx.plan = None
         gks = gkg[0] if ctx.ks_is_tensor else None
         gg = gkg[1] if ctx.g_is_tensor else None
-        return gxy, gm, gks, gg, None, None, None, None, None
+        return gxy, gm, gks, gg, None, None, None, None, None, None
 
 
 def deflect(stars, masses, kappa_s, gamma, rays, p=24, leaf_size=16, prec=lens.FP64,
-            target_box=None):
-    """Differentiable y(rays) = lens equation with FMM deflections."""
-    return LensDeflect.apply(stars, masses, kappa_s, gamma, rays, p, leaf_size, prec, target_box)
+            target_box=None, recompute=None):
+    """Differentiable y(rays) = lens equation with FMM deflections.  With
+    ``recompute`` (default: N* >= 1e7) the tree and expansions are rebuilt in
+    the backward pass instead of being held since the forward pass."""
+    return LensDeflect.apply(stars, masses, kappa_s, gamma, rays, p, leaf_size, prec, target_box,
+                             recompute)
 
 
 class LightCurve(torch.autograd.Function):

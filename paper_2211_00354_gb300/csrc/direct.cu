@@ -63,9 +63,11 @@ k_direct_f32(const float4* __restrict__ shl, const float* __restrict__ sm, int64
       for (int k = 0; k < RPT; ++k) {
         const float d1 = (rxh[k] - s.x) + (rxl[k] - s.z);
         const float d2 = (ryh[k] - s.y) + (ryl[k] - s.w);
-        const float r2 = fmaf(d1, d1, d2 * d2);
-        // a star exactly on the ray contributes nothing
-        const float inv = r2 > 0.f ? frcp_fast(r2) : 0.f;
+        // a star exactly on the ray contributes nothing: without the
+        // Jacobian a tiny floor on r2 does it (w * d = 0 with w finite),
+        // with it the select (w * w would overflow)
+        const float r2 = JAC ? fmaf(d1, d1, d2 * d2) : fmaf(d1, d1, fmaf(d2, d2, 1e-30f));
+        const float inv = JAC ? (r2 > 0.f ? frcp_fast(r2) : 0.f) : frcp_fast(r2);
         const float w = ms * inv;
         px[k] = fmaf(w, d1, px[k]);
         py[k] = fmaf(w, d2, py[k]);

@@ -35,7 +35,8 @@ namespace {
 constexpr int kT = kEval32Threads;
 constexpr int kRpt = kEval32Rpt;
 constexpr int kSeg = 64;
-constexpr int kChunk = 1024;
+constexpr int kChunk = 512;
+static_assert(kRpt % 2 == 0, "rays are paired for float2 arithmetic");
 constexpr int kWChunk = 8;
 
 struct E32Args {
@@ -61,7 +62,9 @@ struct E32Args {
 
 template <bool JAC, bool GRID, bool PIX>
 __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
-  __shared__ float s_x[kChunk], s_y[kChunk], s_xl[kChunk], s_yl[kChunk], s_m[kChunk];
+  // staged stars, each value duplicated into both halves of a float2 (the
+  // offsets negated, so that d = x + (-s) is the plain difference)
+  __shared__ float2 s_x[kChunk], s_y[kChunk], s_xl[kChunk], s_yl[kChunk], s_m[kChunk];
   __shared__ int s_pre[kSeg + 1];
   __shared__ float2 s_L[kMaxOrder + 1];
   __shared__ float2 s_W[kWChunk][kMaxOrder + 1];
@@ -156,8 +159,10 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
       for (int f = tid; f < nf; f += kT) {
         const int64_t g = star0 + star_done + f0 + f;
         const float4 v = A.ust[g];
-        s_x[f] = v.x; s_y[f] = v.y; s_xl[f] = v.z; s_yl[f] = v.w;
-        s_m[f] = A.um[g];
+        const float mm = A.um[g];
+        s_x[f] = make_float2(-v.x, -v.x); s_y[f] = make_float2(-v.y, -v.y);
+        s_xl[f] = make_float2(-v.z, -v.z); s_yl[f] = make_float2(-v.w, -v.w);
+        s_m[f] = make_float2(mm, mm);
       }
       __syncthreads();
       for (int e = 0; e < ne; ++e) {
@@ -165,20 +170,54 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
         const int hi = min(s_pre[e + 1], f0 + nf) - f0;
         if (hi <= lo) continue;
         float p1[kRpt], p2[kRpt], pj1[kRpt], pj2[kRpt];
+        if (!JAC) {
+          // rays (2h, 2h+1) side by side in float2 pair arithmetic
+          // (Blackwell's two-lane FP32 instructions, IEEE round-to-nearest
+          // per lane): the same operations as the scalar loop below in half
+          // the issue slots.  A star exactly on the ray contributes nothing:
+          // the floor on r2 keeps w finite and w * d = 0.
+          float2 P1[kRpt / 2], P2[kRpt / 2], DX[kRpt / 2], DY[kRpt / 2], DXL[kRpt / 2], DYL[kRpt / 2];
 #pragma unroll
-        for (int q = 0; q < kRpt; ++q) { p1[q] = 0.f; p2[q] = 0.f; pj1[q] = 0.f; pj2[q] = 0.f; }
-        for (int j = lo; j < hi; ++j) {
-          const float sx = s_x[j], sy = s_y[j], sxl = s_xl[j], syl = s_yl[j], sm = s_m[j];
+          for (int h = 0; h < kRpt / 2; ++h) {
+            P1[h] = make_float2(0.f, 0.f); P2[h] = make_float2(0.f, 0.f);
+            DX[h] = make_float2(dx[2 * h], dx[2 * h + 1]); DY[h] = make_float2(dy[2 * h], dy[2 * h + 1]);
+            DXL[h] = make_float2(dxl[2 * h], dxl[2 * h + 1]); DYL[h] = make_float2(dyl[2 * h], dyl[2 * h + 1]);
+          }
+          const float2 tiny = make_float2(1e-30f, 1e-30f);
+          for (int j = lo; j < hi; ++j) {
+            const float2 nsx = s_x[j], nsy = s_y[j], nsxl = s_xl[j], nsyl = s_yl[j], sm = s_m[j];
 #pragma unroll
-          for (int q = 0; q < kRpt; ++q) {
-            const float d1 = (dx[q] - sx) + (dxl[q] - sxl);
-            const float d2 = (dy[q] - sy) + (dyl[q] - syl);
-            const float r2 = fmaf(d1, d1, d2 * d2);
-            const float inv = r2 > 0.f ? frcp_fast(r2) : 0.f;
-            const float w = sm * inv;
-            p1[q] = fmaf(w, d1, p1[q]);
-            p2[q] = fmaf(w, d2, p2[q]);
-            if (JAC) {
+            for (int h = 0; h < kRpt / 2; ++h) {
+              const float2 d1 = __fadd2_rn(__fadd2_rn(DX[h], nsx), __fadd2_rn(DXL[h], nsxl));
+              const float2 d2 = __fadd2_rn(__fadd2_rn(DY[h], nsy), __fadd2_rn(DYL[h], nsyl));
+              const float2 r2 = __ffma2_rn(d1, d1, __ffma2_rn(d2, d2, tiny));
+              const float2 w = __fmul2_rn(sm, make_float2(frcp_fast(r2.x), frcp_fast(r2.y)));
+              P1[h] = __ffma2_rn(w, d1, P1[h]);
+              P2[h] = __ffma2_rn(w, d2, P2[h]);
+            }
+          }
+#pragma unroll
+          for (int h = 0; h < kRpt / 2; ++h) {
+            p1[2 * h] = P1[h].x; p1[2 * h + 1] = P1[h].y;
+            p2[2 * h] = P2[h].x; p2[2 * h + 1] = P2[h].y;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < kRpt; ++q) { p1[q] = 0.f; p2[q] = 0.f; pj1[q] = 0.f; pj2[q] = 0.f; }
+          for (int j = lo; j < hi; ++j) {
+            const float sx = -s_x[j].x, sy = -s_y[j].x, sxl = -s_xl[j].x, syl = -s_yl[j].x;
+            const float sm = s_m[j].x;
+#pragma unroll
+            for (int q = 0; q < kRpt; ++q) {
+              const float d1 = (dx[q] - sx) + (dxl[q] - sxl);
+              const float d2 = (dy[q] - sy) + (dyl[q] - syl);
+              // a star exactly on the ray contributes nothing (w * w would
+              // overflow with a floor on r2, hence the select)
+              const float r2 = fmaf(d1, d1, d2 * d2);
+              const float inv = r2 > 0.f ? frcp_fast(r2) : 0.f;
+              const float w = sm * inv;
+              p1[q] = fmaf(w, d1, p1[q]);
+              p2[q] = fmaf(w, d2, p2[q]);
               const float w2 = w * inv;
               pj1[q] = fmaf(w2, (d2 - d1) * (d2 + d1), pj1[q]);
               pj2[q] = fmaf(w2, 2.f * d1 * d2, pj2[q]);

@@ -66,6 +66,37 @@ __device__ __forceinline__ T pixel_area(const T* qx, const T* qy, T X, T Y) {
   return s;
 }
 
+// float32 form of mean_clamp01 without branches (the lanes of a warp take
+// different cases): the pure cases (all below 0, all above 1, all inside)
+// are selected exactly, the mixed case is the integral over the length.
+__device__ __forceinline__ float mean_clamp01f(float a, float b) {
+  const float lo = fminf(a, b), hi = fmaxf(a, b);
+  const float l0 = fmaxf(lo, 0.f), h1 = fminf(hi, 1.f);
+  const float I = 0.5f * fmaxf(h1 - l0, 0.f) * (h1 + l0) + fmaxf(hi - fmaxf(lo, 1.f), 0.f);
+  const float d = hi - lo;
+  const float mid = 0.5f * (lo + hi);
+  float r = d > 1e-30f ? I * frcp_fast(d) : fminf(fmaxf(mid, 0.f), 1.f);
+  r = (lo >= 0.f && hi <= 1.f) ? mid : r;
+  r = hi <= 0.f ? 0.f : r;
+  r = lo >= 1.f ? 1.f : r;
+  return r;
+}
+
+// pixel_area() in float32 with the edge slopes dx/dy given (0 for a
+// horizontal edge, whose clipped part then has ya == yb and adds nothing).
+__device__ __forceinline__ float pixel_area_f(const float* qx, const float* qy, const float* sl,
+                                              float X, float Y) {
+  float s = 0.f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float x0 = qx[e], y0 = qy[e], y1 = qy[(e + 1) & 3];
+    const float ya = fminf(fmaxf(y0, Y), Y + 1.f), yb = fminf(fmaxf(y1, Y), Y + 1.f);
+    const float xa = x0 + (ya - y0) * sl[e], xb = x0 + (yb - y0) * sl[e];
+    s += (yb - ya) * mean_clamp01f(xa - X, xb - X);
+  }
+  return s;
+}
+
 struct IpmArgs {
   const PixCorner* yc;  // (nrows+1) x (nx+1) corners of the chunk
   int64_t nx, ncells;
@@ -181,6 +212,7 @@ constexpr int kWarps = kIpmThreads / 32;
 // segments of large cells.
 struct CellShared {
   float qx[4][kWarps][32], qy[4][kWarps][32];  // polygon, pixel units local to (ix0, iy0)
+  float sl[4][kWarps][32];                      // edge slopes dx/dy (0 if horizontal)
   float inv[kWarps][32];                        // 1 / A_P
   int ix0[kWarps][32], iy0[kWarps][32];
   int cx0[kWarps][32], cx1[kWarps][32], cy0[kWarps][32];  // box clipped to the map
@@ -264,7 +296,12 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
           const int cx0 = max(ix0, 0), cx1 = min(ix1, npx - 1);
           const int cy0 = max(iy0, 0), cy1 = min(iy1, npy - 1);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) { sh.qx[k][w][lane] = qx[k]; sh.qy[k][w][lane] = qy[k]; }
+          for (int k = 0; k < 4; ++k) {
+            sh.qx[k][w][lane] = qx[k];
+            sh.qy[k][w][lane] = qy[k];
+            const float ey = qy[(k + 1) & 3] - qy[k];
+            sh.sl[k][w][lane] = ey != 0.f ? (qx[(k + 1) & 3] - qx[k]) / ey : 0.f;
+          }
           sh.inv[w][lane] = 1.0f / A_loc;
           sh.ix0[w][lane] = ix0; sh.iy0[w][lane] = iy0;
           sh.cx0[w][lane] = cx0; sh.cx1[w][lane] = cx1; sh.cy0[w][lane] = cy0;
@@ -297,10 +334,10 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
         const int cx0 = sh.cx0[w][L], wd = sh.cx1[w][L] - cx0 + 1;
         const int r = off / wd;
         const int px = cx0 + off - r * wd, py = sh.cy0[w][L] + r;
-        float qx[4], qy[4];
+        float qx[4], qy[4], sl[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) { qx[k] = sh.qx[k][w][L]; qy[k] = sh.qy[k][w][L]; }
-        const float a = pixel_area<float>(qx, qy, (float)(px - sh.ix0[w][L]), (float)(py - sh.iy0[w][L]));
+        for (int k = 0; k < 4; ++k) { qx[k] = sh.qx[k][w][L]; qy[k] = sh.qy[k][w][L]; sl[k] = sh.sl[k][w][L]; }
+        const float a = pixel_area_f(qx, qy, sl, (float)(px - sh.ix0[w][L]), (float)(py - sh.iy0[w][L]));
         if (a != 0.0f) {
           const float fr = a * sh.inv[w][L];
           atomicAdd(&A.map[(int64_t)py * npx + px], A.scale_f * fr);
@@ -331,11 +368,11 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
           const int t = lane * 4 + e;
           int n = 0;
           const float x0 = sh.qx[e][w][L], y0 = sh.qy[e][w][L];
-          const float x1 = sh.qx[(e + 1) & 3][w][L], y1 = sh.qy[(e + 1) & 3][w][L];
+          const float y1 = sh.qy[(e + 1) & 3][w][L];
           const float ya = fminf(fmaxf(y0, Y), Y + 1.f), yb = fminf(fmaxf(y1, Y), Y + 1.f);
-          if (y1 != y0 && ya != yb) {
-            // the same clipped segment and slope as pixel_area()
-            const float sl = (x1 - x0) / (y1 - y0);
+          if (ya != yb) {
+            // the clipped segment of pixel_area_f()
+            const float sl = sh.sl[e][w][L];
             const float xa = x0 + (ya - y0) * sl, xb = x0 + (yb - y0) * sl;
             const float dy = yb - ya;
             const int Xa = (int)floorf(fminf(xa, xb)), Xb = (int)ceilf(fmaxf(xa, xb)) - 1;
@@ -376,7 +413,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
           int t = L * 4;
           while (off >= sh.n[w][t]) { off -= sh.n[w][t]; ++t; }
           const int X = sh.pa[w][t] + off;
-          const float a = sh.dy[w][t] * mean_clamp01<float>(sh.xa[w][t] - (float)X, sh.xb[w][t] - (float)X);
+          const float a = sh.dy[w][t] * mean_clamp01f(sh.xa[w][t] - (float)X, sh.xb[w][t] - (float)X);
           if (a != 0.0f) {
             const int cl = sh.cell[w][L];
             const float fr = a * sh.inv[w][cl];

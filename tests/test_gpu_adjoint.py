@@ -58,6 +58,29 @@ def test_adjoint_on_clustered_tree():
     assert rel_norm(gm.cpu().numpy(), rgm) < 1e-10
 
 
+@pytest.mark.parametrize("prec", [lens.FP64, lens.FP32_BULK])
+def test_recomputed_tree_gives_the_same_gradient(prec):
+    # backward with the tree rebuilt (the large-N* mode) = backward on the
+    # forward pass's tree; both match the oracle's float64 gradient
+    f = reduced_c5(n=700, seed=3)
+    L = 4.0
+    rays = T(synth.random_rays(9, 5000, (-L, -L), (L, L)))
+    W = np.random.default_rng(10).normal(size=(5000, 2))
+    grads = []
+    for rec in (False, True):
+        stars = T(f.stars).requires_grad_(True)
+        masses = T(f.masses).requires_grad_(True)
+        y = autograd.deflect(stars, masses, f.kappa_s, f.gamma, rays, p=40, leaf_size=8, prec=prec,
+                             target_box=(-L, L, -L, L), recompute=rec)
+        (y * T(W)).sum().backward()
+        grads.append((stars.grad.cpu().numpy(), masses.grad.cpu().numpy()))
+    assert rel_norm(grads[1][0], grads[0][0]) < 1e-12
+    assert rel_norm(grads[1][1], grads[0][1]) < 1e-12
+    rgxy, rgm, _ = oracle.adjoint(f.stars, f.masses, rays.cpu().numpy(), W)
+    assert rel_norm(grads[1][0], rgxy) < 1e-9
+    assert rel_norm(grads[1][1], rgm) < 1e-9
+
+
 def test_autograd_matches_central_differences():
     f = reduced_c5(n=400, seed=2)
     L = 4.0

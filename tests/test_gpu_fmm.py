@@ -113,6 +113,25 @@ def test_jacobian(prec, tol):
     assert (d / sc).max() < tol
 
 
+@pytest.mark.parametrize("prec,tol", [(lens.FP64, 1e-10), (lens.FP32_BULK, 2e-5)])
+def test_rays_exactly_on_stars(prec, tol):
+    # a star exactly at a ray contributes nothing (the oracle skips r == 0);
+    # with and without the Jacobian, through the near field of every leaf
+    f = synth.config_uniform(seed=4, n=600, kappa_star=0.3, kappa_s=0.1, gamma=0.2)
+    inside = np.all(np.abs(f.stars) < 4.0, axis=1)
+    x = np.concatenate([f.stars[inside][:200], synth.random_rays(8, 100, (-4, -4), (4, 4))])
+    y_ref, jac_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x, jacobian=True)
+    with plan_for(f, 40, 8, prec, (-4, 4, -4, 4)) as P:
+        y = P.deflect(T(x)).cpu().numpy()
+        yj, jac = P.deflect(T(x), jacobian=True)
+    assert np.all(np.isfinite(y)) and np.all(np.isfinite(jac.cpu().numpy()))
+    assert alpha_rel_err(y, y_ref, x, f.kappa_s, f.gamma).max() < tol
+    assert alpha_rel_err(yj.cpu().numpy(), y_ref, x, f.kappa_s, f.gamma).max() < tol
+    d = np.abs(jac.cpu().numpy() - jac_ref).reshape(-1, 4).max(1)
+    sc = np.maximum(np.abs(jac_ref).reshape(-1, 4).max(1), 1.0)
+    assert (d / sc).max() < (1e-8 if prec == lens.FP64 else 2e-4)
+
+
 def test_tiny_fields():
     for n, leaf in ((1, 16), (5, 16), (40, 1), (17, 16)):
         f = synth.config_uniform(seed=n, n=n, kappa_star=0.3, kappa_s=0.0, gamma=0.1)
