@@ -178,6 +178,25 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def measured_traffic(kernel, src, rays_per_launch):
+    """DRAM bytes (read + write) per launch of `kernel`, scaled from the ncu
+    figure per corner ray in profiles/<kernel>_c2_reduced_dram.md; None when
+    the kernel source has changed since that capture."""
+    import hashlib
+    import re
+    try:
+        txt = open(os.path.join(HERE, "profiles", kernel + "_c2_reduced_dram.md")).read()
+        sha = re.search(r"traffic-source-sha256: ([0-9a-f]{64})", txt).group(1)
+        per = float(re.search(r"dram-bytes-per-corner-ray: ([0-9.]+)", txt).group(1))
+    except (OSError, AttributeError):
+        return None
+    h = hashlib.sha256()
+    for f in (src, "cx.cuh", "lens_internal.h"):
+        with open(os.path.join(HERE, "paper_2211_00354_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return per * rays_per_launch if h.hexdigest() == sha else None
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -279,15 +298,17 @@ def main():
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ipm_traffic = measured_traffic("k_ipm_cells", "ipm.cu", rays_step / launches)
+    eval_traffic = measured_traffic("k_eval32", "eval32.cu", rays_step / launches)
     if ms_eval >= ms_ipm:
         roof = {"bound": "alu", "kernel": "k_eval (fused L2P+P2P+M2P)",
                 "achieved": eval_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": eval_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": eval_tflops / FP32_PEAK_TFLOPS, "traffic": eval_traffic,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                 "ms_per_launch": ms_eval / launches}
     else:
         roof = {"bound": "hbm", "kernel": "k_ipm_cells+k_ipm_f64", "achieved": ipm_gbs,
-                "peak": hbm_peak, "unit": "GB/s", "frac": ipm_gbs / hbm_peak, "traffic": None,
+                "peak": hbm_peak, "unit": "GB/s", "frac": ipm_gbs / hbm_peak, "traffic": ipm_traffic,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                 "ms_per_launch": ms_ipm / launches}
 
