@@ -432,11 +432,14 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
 }
 
 // Ill-conditioned cells (|A_P| small against the pixel box): one warp per
-// cell, lanes over the box's pixels, the overlap in float64 in coordinates
-// local to the box; a float32 test first finds the pixels no edge meets,
-// whose coverage is the winding number exactly.
+// cell, lanes over the box's pixels.  A float32 test finds the pixels no
+// edge meets, whose coverage is the winding number exactly; the pixels an
+// edge cuts are collected in shared memory and their overlaps taken in
+// float64 (coordinates local to the box) 32 at a time, so every float64
+// warp instruction runs on full lanes.
 __global__ void __launch_bounds__(kIpmThreads) k_ipm_f64(IpmArgs A) {
-  const int lane = threadIdx.x & 31;
+  __shared__ int cut_x[kWarps][64], cut_y[kWarps][64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t wg = (blockIdx.x * (int64_t)kIpmThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kIpmThreads) >> 5;
   const int nq = *A.qcount;
@@ -460,7 +463,8 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_f64(IpmArgs A) {
     }
     const int cx0 = max(ix0, 0), cx1 = min(ix1, A.ip.npx - 1);
     const int cy0 = max(iy0, 0), cy1 = min(iy1, A.ip.npy - 1);
-    const int64_t wd = (int64_t)cx1 - cx0 + 1, npix = wd * ((int64_t)cy1 - cy0 + 1);
+    const int wd = cx1 - cx0 + 1;
+    const int npix = wd * (cy1 - cy0 + 1);  // the box is at most cap x cap, or clipped to the map
     float fx[4], fy[4];
     double u[4], v[4];
 #pragma unroll
@@ -480,26 +484,59 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_f64(IpmArgs A) {
     const double inv = 1.0 / A_P;
     const float invf = (float)inv;
     float fin = 0.f;
-    for (int64_t t2 = lane; t2 < npix; t2 += 32) {
-      const uint32_t r32 = (uint32_t)t2 / (uint32_t)wd;
-      const int oy = cy0 - iy0 + (int)r32, ox = cx0 - ix0 + (int)((uint32_t)t2 - r32 * (uint32_t)wd);
+    int ncut = 0;  // warp-uniform: entries waiting in cut_x[w], cut_y[w]
+    for (int base = 0; base < npix; base += 32) {
+      const int t2 = base + lane;
       bool cut = false;
+      int ox = 0, oy = 0;
+      if (t2 < npix) {
+        const int r = t2 / wd;
+        oy = cy0 - iy0 + r;
+        ox = cx0 - ix0 + (t2 - r * wd);
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
-        cut |= seg_meets_pixel(fx[e], fy[e], fx[(e + 1) & 3], fy[(e + 1) & 3], (float)ox, (float)oy);
-      float fr;
-      if (cut) {
-        const double a = pixel_area<double>(u, v, (double)ox, (double)oy);
-        fr = (float)(a * inv);
-      } else {
-        const int wn = winding4(fx, fy, (float)ox + 0.5f, (float)oy + 0.5f);
-        fr = (float)wn * invf;
+        for (int e = 0; e < 4; ++e)
+          cut |= seg_meets_pixel(fx[e], fy[e], fx[(e + 1) & 3], fy[(e + 1) & 3], (float)ox, (float)oy);
+        if (!cut) {
+          const int wn = winding4(fx, fy, (float)ox + 0.5f, (float)oy + 0.5f);
+          const float fr = (float)wn * invf;
+          if (fr != 0.0f) {
+            atomicAdd(&A.map[(int64_t)(iy0 + oy) * A.ip.npx + ix0 + ox], A.scale_f * fr);
+            fin += fr;
+            led.nupd += 1;
+          }
+        }
       }
-      if (fr == 0.0f) continue;
-      const int64_t px = ix0 + ox, py = iy0 + oy;
-      atomicAdd(&A.map[py * A.ip.npx + px], A.scale_f * fr);
-      fin += fr;
-      led.nupd += 1;
+      const unsigned m = __ballot_sync(0xffffffffu, cut);
+      if (cut) {
+        const int slot = ncut + __popc(m & ((1u << lane) - 1u));  // < 64: ncut < 32 here
+        cut_x[w][slot] = ox;
+        cut_y[w][slot] = oy;
+      }
+      ncut += __popc(m);
+      const bool last = base + 32 >= npix;
+      while (ncut >= 32 || (last && ncut > 0)) {
+        __syncwarp();
+        const int take = min(ncut, 32);
+        if (lane < take) {
+          const int px = cut_x[w][lane], py = cut_y[w][lane];
+          const double a = pixel_area<double>(u, v, (double)px, (double)py);
+          const float fr = (float)(a * inv);
+          if (fr != 0.0f) {
+            atomicAdd(&A.map[(int64_t)(iy0 + py) * A.ip.npx + ix0 + px], A.scale_f * fr);
+            fin += fr;
+            led.nupd += 1;
+          }
+        }
+        __syncwarp();
+        // move the rest (at most 31) to the front
+        const int rest = ncut - take;
+        int kx = 0, ky = 0;
+        if (lane < rest) { kx = cut_x[w][take + lane]; ky = cut_y[w][take + lane]; }
+        __syncwarp();
+        if (lane < rest) { cut_x[w][lane] = kx; cut_y[w][lane] = ky; }
+        __syncwarp();
+        ncut = rest;
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fin += __shfl_xor_sync(0xffffffffu, fin, o);

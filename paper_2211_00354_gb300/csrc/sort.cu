@@ -2,10 +2,11 @@
 // device-wide exclusive scans.  Used for the Morton-order quadtree build
 // (Appendix A, step 1) and for the ordered split-node list.
 //
-// Each 8-bit pass is reduce-then-scan: (1) per-tile digit histograms,
-// (2) one exclusive scan over the digit-major histogram matrix, (3) a stable
-// scatter in which every warp ranks its keys with __match_any_sync and the
-// block combines the per-warp counts.  No kernel waits on another block, so
+// Each 8-bit pass is reduce-then-scan: (1) per-tile digit histograms plus
+// the digit totals (atomics), (2) one block per digit scans its row of the
+// digit-major histogram matrix and adds the keys of smaller digits, (3) a
+// stable scatter in which every warp ranks its keys with __match_any_sync and
+// the block combines the per-warp counts.  No kernel waits on another block, so
 // nothing can spin: there is no decoupled look-back and no device-side wait.
 #include "cx.cuh"
 #include "lens_internal.h"
@@ -20,7 +21,7 @@ constexpr int kSortTile = kSortThreads * kIPT;
 
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, int nblocks,
-             uint32_t* __restrict__ hist) {
+             uint32_t* __restrict__ hist, uint32_t* __restrict__ dtot) {
   __shared__ uint32_t cnt[256];
   cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -32,28 +33,48 @@ k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, int nblock
   }
   __syncthreads();
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+  if (cnt[threadIdx.x]) atomicAdd(&dtot[threadIdx.x], cnt[threadIdx.x]);
 }
 
-// In-place exclusive scan of a uint32 array by one block (n up to a few 1e6).
-__global__ void __launch_bounds__(1024) k_scan_u32_single(uint32_t* __restrict__ a, int64_t n) {
-  __shared__ uint32_t part[1024];
-  const int64_t per = (n + 1023) / 1024;
-  const int64_t lo = threadIdx.x * per, hi = min64(n, lo + per);
-  uint32_t s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += a[i];
-  part[threadIdx.x] = s;
+// Scatter offsets: hist[d][b] <- (keys with a digit below d) + (keys with
+// digit d in blocks before b).  One block per digit; the digit totals come
+// from the histogram pass, so no block waits on another.
+constexpr int kDigitScanThreads = 512;
+
+__global__ void __launch_bounds__(kDigitScanThreads)
+k_scan_digits(uint32_t* __restrict__ hist, int nblocks, const uint32_t* __restrict__ dtot) {
+  __shared__ uint32_t wsum[kDigitScanThreads / 32];
+  __shared__ uint32_t carry;
+  const int d = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  // keys with a smaller digit
+  uint32_t below = (t < d) ? dtot[t] : 0u;
+  below = __reduce_add_sync(0xffffffffu, below);
+  if (lane == 0) wsum[w] = below;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  if (t == 0) {
+    uint32_t b = 0;
+    for (int q = 0; q < kDigitScanThreads / 32; ++q) b += wsum[q];
+    carry = b;
   }
-  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-  for (int64_t i = lo; i < hi; ++i) {
-    uint32_t v = a[i];
-    a[i] = run;
-    run += v;
+  __syncthreads();
+  uint32_t* row = hist + (int64_t)d * nblocks;
+  for (int c0 = 0; c0 < nblocks; c0 += kDigitScanThreads) {
+    const int i = c0 + t;
+    const uint32_t v = i < nblocks ? row[i] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    __syncthreads();  // wsum and carry of the previous chunk are consumed
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    uint32_t off = carry;
+    for (int q = 0; q < w; ++q) off += wsum[q];
+    if (i < nblocks) row[i] = off + x - v;
+    __syncthreads();
+    if (t == kDigitScanThreads - 1) carry = off + x;
   }
 }
 
@@ -181,16 +202,20 @@ void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, DeviceA
   Scratch k2(&da, sizeof(uint64_t) * (size_t)n);
   Scratch v2(&da, vals ? sizeof(uint32_t) * (size_t)n : 0);
   Scratch hist(&da, sizeof(uint32_t) * 256 * (size_t)nblocks);
+  const int npass = (bits + 7) / 8;
+  Scratch dtot(&da, sizeof(uint32_t) * 256 * (size_t)npass);
+  LENS_CUDA(cudaMemsetAsync(dtot.p, 0, dtot.bytes, s));
   uint64_t* ka = keys;
   uint64_t* kb = k2.as<uint64_t>();
   uint32_t* va = vals;
   uint32_t* vb = v2.as<uint32_t>();
   int passes = 0;
   for (int shift = 0; shift < bits; shift += 8, ++passes) {
-    k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(ka, n, shift, nblocks, hist.as<uint32_t>());
+    uint32_t* dt = dtot.as<uint32_t>() + 256 * passes;
+    k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(ka, n, shift, nblocks, hist.as<uint32_t>(), dt);
     LENS_LAUNCHED("k_radix_hist");
-    k_scan_u32_single<<<1, 1024, 0, s>>>(hist.as<uint32_t>(), (int64_t)256 * nblocks);
-    LENS_LAUNCHED("k_scan_u32_single");
+    k_scan_digits<<<256, kDigitScanThreads, 0, s>>>(hist.as<uint32_t>(), nblocks, dt);
+    LENS_LAUNCHED("k_scan_digits");
     k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, nblocks,
                                                      hist.as<uint32_t>());
     LENS_LAUNCHED("k_radix_scatter");
