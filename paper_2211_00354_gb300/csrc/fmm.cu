@@ -20,6 +20,7 @@
 // Every step here is float64 (the precision split keeps translations in
 // float64).  On GB300 the float64 pipe is ~60x slower than float32, so these
 // kernels are written to issue as few DFMAs as the series allow.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -134,10 +135,21 @@ struct DownArgs {
   FmmTables tab;
   double lo_x, lo_y, root_size;
   int p;
+  int group;         // V entries per M2L pass
+  size_t smem_warp;  // shared bytes per warp (multiple of 16)
 };
 
-// Shared memory per warp: (p+1) x 32 complex values plus 64 ints.
-__host__ __device__ inline size_t downward_smem_per_warp(int p) { return sizeof(double2) * (size_t)(p + 1) * 32 + 64 * sizeof(int); }
+// V entries per M2L pass: 32, fewer for large p so that a warp's buffers
+// (2 G (p+1) complex values) stay within 24 KB.
+inline int downward_group(int p) { return std::max(1, std::min(32, 24576 / (32 * (p + 1)))); }
+// Shared bytes per warp: the larger of the P2L buffer ((p+1) x 32 complex +
+// 64 ints) and the M2L buffers (2 G (p+1) complex + G ints).
+inline size_t downward_smem_per_warp(int p) {
+  const size_t p2l = sizeof(double2) * (size_t)(p + 1) * 32 + 64 * sizeof(int);
+  const size_t g = (size_t)downward_group(p);
+  const size_t m2l = sizeof(double2) * 2 * g * (size_t)(p + 1) + g * sizeof(int);
+  return (std::max(p2l, m2l) + 15) / 16 * 16;
+}
 
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_downward(DownArgs A) {
   extern __shared__ double2 dsm[];
@@ -167,31 +179,55 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_downward(DownArgs A) {
       acc[s] = v;
     }
   }
-  // M2L from V
-  double2* buf = dsm + (int64_t)wib * (downward_smem_per_warp(p) / sizeof(double2));
+  // M2L from V.  Up to G entries at a time, their (entry, coefficient) pairs
+  // spread over the lanes (p + 1 = 17 coefficients would leave 15 of 32 lanes
+  // idle with one entry per pass):
+  //   H[e][k] = A_k u_e^k                       (pre-scale)
+  //   T[e][l] = (-1)^l u_e^(l+1) / r * sum_k C(k+l, k) H[e][k]
+  //   B_l    += sum_e T[e][l]
+  double2* buf = dsm + (int64_t)wib * (A.smem_warp / sizeof(double2));
+  const int G = A.group;
+  double2* H = buf;
+  double2* T = buf + (int64_t)G * P1;
+  int* uo = reinterpret_cast<int*>(T + (int64_t)G * P1);  // [G] offset-table rows
   const int bx = A.ix[B], by = A.iy[B];
-  for (int64_t e = A.V_off[a]; e < A.V_off[a + 1]; ++e) {
-    const int C = A.V_list[e];
-    const int dx = A.ix[C] - bx, dy = A.iy[C] - by;
-    const double2* up = A.tab.upow + (int64_t)((dy + 3) * 7 + (dx + 3)) * (p + 2);
-    const double2* Ac = A.M + (int64_t)C * P1;
-    for (int k = lane; k <= p; k += 32) buf[k] = cmul(ld2(Ac + k), ld2(up + k));
+  for (int64_t eb = A.V_off[a]; eb < A.V_off[a + 1]; eb += G) {
+    const int ne = (int)min64(G, A.V_off[a + 1] - eb);
+    for (int e = lane; e < ne; e += 32) {
+      const int C = A.V_list[eb + e];
+      uo[e] = ((A.iy[C] - by + 3) * 7 + (A.ix[C] - bx + 3)) * (p + 2);
+    }
+    __syncwarp();
+    const int ntask = ne * P1;
+    for (int t = lane; t < ntask; t += 32) {
+      const int e = t / P1, k = t - e * P1;
+      const int C = A.V_list[eb + e];
+      H[t] = cmul(ld2(A.M + (int64_t)C * P1 + k), ld2(A.tab.upow + uo[e] + k));
+    }
+    __syncwarp();
+    for (int t = lane; t < ntask; t += 32) {
+      const int e = t / P1, l = t - e * P1;
+      const double2* He = H + e * P1;
+      double sx = 0.0, sy = 0.0;
+      for (int k = 0; k <= p; ++k) {
+        // C(k+l, k) = binom[(k+l)*ldb + k]
+        const double c = __ldg(A.tab.binom + (int64_t)(k + l) * A.tab.ldb + k);
+        const double2 v = He[k];
+        sx = fma(c, v.x, sx);
+        sy = fma(c, v.y, sy);
+      }
+      double2 post = ld2(A.tab.upow + uo[e] + l + 1);
+      if (l & 1) post = make_double2(-post.x, -post.y);
+      T[t] = cmul(post, make_double2(sx * ir, sy * ir));
+    }
     __syncwarp();
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
       const int l = lane + 32 * s;
       if (l > p) break;
-      double sx = 0.0, sy = 0.0;
-      for (int k = 0; k <= p; ++k) {
-        // C(k+l, k) = binom[(k+l)*ldb + k]
-        const double c = __ldg(A.tab.binom + (int64_t)(k + l) * A.tab.ldb + k);
-        const double2 v = buf[k];
-        sx = fma(c, v.x, sx);
-        sy = fma(c, v.y, sy);
-      }
-      double2 post = ld2(up + l + 1);
-      if (l & 1) post = make_double2(-post.x, -post.y);
-      acc[s] = cfma(post, make_double2(sx * ir, sy * ir), acc[s]);
+      double2 v = acc[s];
+      for (int e = 0; e < ne; ++e) v = v + T[e * P1 + l];
+      acc[s] = v;
     }
     __syncwarp();
   }
@@ -384,7 +420,9 @@ void fmm_downward(Plan& P, cudaStream_t s) {
   A.V_off = P.V_off; A.V_list = P.V_list; A.X_off = P.X_off; A.X_list = P.X_list;
   A.spos = P.spos; A.smass = P.smass; A.M = P.M; A.L = P.L; A.tab = t;
   A.lo_x = P.root_lo[0]; A.lo_y = P.root_lo[1]; A.root_size = P.root_size; A.p = P.p;
-  const size_t smem = downward_smem_per_warp(P.p) * kWarpsPerBlock;
+  A.group = downward_group(P.p);
+  A.smem_warp = downward_smem_per_warp(P.p);
+  const size_t smem = A.smem_warp * kWarpsPerBlock;
   if (smem > 48 * 1024)
     LENS_CUDA(cudaFuncSetAttribute(k_downward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int l = 0; l < P.nlevels; ++l) {
