@@ -440,20 +440,28 @@ __global__ void k_grid_rects(const int* __restrict__ leaves, int64_t nleaf,
   tiles[k] = (ni * nj + tile - 1) / tile;
 }
 
-// algorithmic work of one grid band: rays, ray-star pairs, ray-box M2P evals
+// algorithmic work of one grid band: rays, ray-star pairs, ray-box M2P evals.
+// FP64 form: near stars and W boxes per active box (ustar, W_off); FP32 form
+// (near_by_leaf != null): per active leaf, after small W boxes moved to P2P.
 __global__ void k_work_count(const int* __restrict__ leaves, int64_t nleaf,
                              const int* __restrict__ aidx, const int64_t* __restrict__ rect,
                              const int64_t* __restrict__ ustar, const int64_t* __restrict__ W_off,
-                             double* __restrict__ work) {
+                             const int64_t* __restrict__ near_by_leaf,
+                             const int64_t* __restrict__ far_by_leaf, double* __restrict__ work) {
   __shared__ double sh[3][128];
   double r = 0, pp = 0, mw = 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nleaf;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const int a = aidx[leaves[k]];
     const double nr = (double)rect[4 * k + 1] * (double)rect[4 * k + 3];
     r += nr;
-    pp += nr * (double)ustar[a];
-    mw += nr * (double)(W_off[a + 1] - W_off[a]);
+    if (near_by_leaf) {
+      pp += nr * (double)near_by_leaf[k];
+      mw += nr * (double)far_by_leaf[k];
+    } else {
+      const int a = aidx[leaves[k]];
+      pp += nr * (double)ustar[a];
+      mw += nr * (double)(W_off[a + 1] - W_off[a]);
+    }
   }
   sh[0][threadIdx.x] = r; sh[1][threadIdx.x] = pp; sh[2][threadIdx.x] = mw;
   __syncthreads();
@@ -571,7 +579,7 @@ void grid_impl(Plan& P, const GridRows& g, double* y, double* jac, PixCorner* pi
   if (P.work) {
     k_work_count<<<grid_for(nl, 128, 1024), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx,
                                                         rect.as<int64_t>(), P.ustar_cnt,
-                                                        P.W_off, P.work);
+                                                        P.W_off, P.f_ncnt, P.f_wcnt, P.work);
     LENS_LAUNCHED("k_work_count");
   }
   if (P.prec == LENS_FP32_BULK) {

@@ -8,9 +8,12 @@
 // float32 pair work.  This kernel therefore runs no float64 instruction at
 // all on the grid path.  Everything float64 is done once:
 //   per plan  -- float32 copies of the local (L) and multipole (M)
-//                coefficients; every active leaf's U-list stars as
+//                coefficients; every active leaf's near-field stars (its
+//                U-list leaves and the W boxes with at most (p+1)/2 stars,
+//                for which a direct sum is cheaper than an order-p M2P) as
 //                float-float offsets from the leaf centre plus float32
-//                masses; W-box centre offsets and radii in float32; per-leaf
+//                masses; the remaining W boxes' centre offsets and radii in
+//                float32; per-leaf
 //                constants K1 = a c1 - b0_1, K2 = b c2 + b0_2 (the lens
 //                equation evaluated at the centre with the constant term b0
 //                of the local expansion), 1/r;
@@ -23,6 +26,7 @@
 // with the bracket in float-float (alpha = conj(b0 + f + near)).  On the map
 // path the corner goes straight to pixel coordinates u = U1 + (y1 - K1)/du,
 // split into an integer pixel and a float32 fraction for the IPM kernels.
+#include <algorithm>
 #include <vector>
 
 #include "cx.cuh"
@@ -46,7 +50,9 @@ struct E32Args {
   int64_t nleaf;
   const int* aidx;
   const int* count;
-  const int64_t* U_off; const int* U_list; const int64_t* W_off; const int* W_list;
+  // per active leaf k: near boxes (P2P) nlist[noff[k] .. noff[k+1]), their
+  // stars staged at ust/um[uoff[k] ..]; far W boxes (M2P) wlist[woff[k] ..]
+  const int64_t* noff; const int* nlist; const int64_t* woff; const int* wlist;
   const float2* fL; const float2* fM;
   const float4* ust; const float* um; const int64_t* uoff; const float4* wgeo;
   int p;
@@ -66,8 +72,10 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   // offsets negated, so that d = x + (-s) is the plain difference)
   __shared__ float2 s_x[kChunk], s_y[kChunk], s_xl[kChunk], s_yl[kChunk], s_m[kChunk];
   __shared__ int s_pre[kSeg + 1];
-  __shared__ float2 s_L[kMaxOrder + 1];
-  __shared__ float2 s_W[kWChunk][kMaxOrder + 1];
+  // expansion coefficients with each real / imaginary part duplicated into
+  // both halves of a float2 (operands of the paired-ray arithmetic)
+  __shared__ float2 s_Lx[kMaxOrder + 1], s_Ly[kMaxOrder + 1];
+  __shared__ float2 s_Wx[kWChunk][kMaxOrder + 1], s_Wy[kWChunk][kMaxOrder + 1];
   __shared__ float4 s_wg[kWChunk];
   __shared__ int64_t s_leaf;
   const int tid = threadIdx.x;
@@ -83,10 +91,13 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   __syncthreads();
   const int64_t k = s_leaf;
   const int B = A.leaves[k];
-  const int a = A.aidx[B];
   const int64_t tile = (int64_t)blockIdx.x - A.tile_off[k];
   const LeafPlan lp = A.leaf[k];
-  for (int l = tid; l <= p; l += kT) s_L[l] = A.fL[k * (int64_t)(p + 1) + l];
+  for (int l = tid; l <= p; l += kT) {
+    const float2 c = A.fL[k * (int64_t)(p + 1) + l];
+    s_Lx[l] = make_float2(c.x, c.x);
+    s_Ly[l] = make_float2(c.y, c.y);
+  }
 
   // ---- rays of this tile -------------------------------------------------
   int64_t nr_leaf, i0 = 0, ni = 1, j0 = 0;
@@ -129,7 +140,7 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   }
 
   // ---- P2P over the U list (stars pre-staged per leaf in float-float) -----
-  const int64_t u_beg = A.U_off[a], u_end = A.U_off[a + 1];
+  const int64_t u_beg = A.noff[k], u_end = A.noff[k + 1];
   const int64_t star0 = A.uoff[k];
   int64_t star_done = 0;  // stars of earlier U-entry rounds
   for (int64_t e0 = u_beg; e0 < u_end; e0 += kSeg) {
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
       int base = 0;
       for (int half = 0; half < kSeg / 32; ++half) {
         const int e = half * 32 + tid;
-        const int c = (e < ne) ? A.count[A.U_list[e0 + e]] : 0;
+        const int c = (e < ne) ? A.count[A.nlist[e0 + e]] : 0;
         int incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -234,58 +245,125 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
     star_done += tot;
   }
 
-  // ---- M2P over the W list --------------------------------------------------
+  // ---- M2P over the far W boxes --------------------------------------------
+  // Without the Jacobian, rays (2h, 2h+1) run side by side in paired float32
+  // arithmetic: Horner's rule for f(z) = (1/z) sum_k A_k (r/z)^k takes 4
+  // paired multiply-adds per order for two rays.
   float2 fw[kRpt], dfw[kRpt];
 #pragma unroll
   for (int q = 0; q < kRpt; ++q) { fw[q] = make_float2(0.f, 0.f); dfw[q] = make_float2(0.f, 0.f); }
-  const int64_t w_beg = A.W_off[a], w_end = A.W_off[a + 1];
+  float2 FX[kRpt / 2], FY[kRpt / 2];
+#pragma unroll
+  for (int h = 0; h < kRpt / 2; ++h) { FX[h] = make_float2(0.f, 0.f); FY[h] = make_float2(0.f, 0.f); }
+  const int64_t w_beg = A.woff[k], w_end = A.woff[k + 1];
   for (int64_t e0 = w_beg; e0 < w_end; e0 += kWChunk) {
     const int nw = (int)min64(kWChunk, w_end - e0);
     __syncthreads();
     for (int t = tid; t < nw * (p + 1); t += kT) {
       const int w = t / (p + 1), kk = t - w * (p + 1);
-      s_W[w][kk] = A.fM[(int64_t)A.W_list[e0 + w] * (p + 1) + kk];
+      const float2 c = A.fM[(int64_t)A.wlist[e0 + w] * (p + 1) + kk];
+      s_Wx[w][kk] = make_float2(c.x, c.x);
+      s_Wy[w][kk] = make_float2(c.y, c.y);
     }
     if (tid < nw) s_wg[tid] = A.wgeo[e0 + tid];
     __syncthreads();
     for (int w = 0; w < nw; ++w) {
       const float4 gw = s_wg[w];
+      if (!JAC) {
+        const float2 ngx = make_float2(-gw.x, -gw.x), ngy = make_float2(-gw.y, -gw.y);
+        const float2 gr = make_float2(gw.z, gw.z), ngr = make_float2(-gw.z, -gw.z);
 #pragma unroll
-      for (int q = 0; q < kRpt; ++q) {
-        const float2 z = make_float2(dx[q] - gw.x, dy[q] - gw.y);
-        const float2 inv = cinv(z);
-        const float2 qq = make_float2(inv.x * gw.z, inv.y * gw.z);
-        float2 s = s_W[w][p];
-        for (int kk = p - 1; kk >= 0; --kk) s = cfma(s, qq, s_W[w][kk]);
-        fw[q] = cfma(s, inv, fw[q]);
-        if (JAC) {
-          float2 t = make_float2((float)(p + 1) * s_W[w][p].x, (float)(p + 1) * s_W[w][p].y);
+        for (int h = 0; h < kRpt / 2; ++h) {
+          const float2 zx = __fadd2_rn(make_float2(dx[2 * h], dx[2 * h + 1]), ngx);
+          const float2 zy = __fadd2_rn(make_float2(dy[2 * h], dy[2 * h + 1]), ngy);
+          const float2 n2 = __ffma2_rn(zx, zx, __fmul2_rn(zy, zy));
+          const float2 d = make_float2(frcp_fast(n2.x), frcp_fast(n2.y));
+          const float2 ix = __fmul2_rn(zx, d);   // 1/z = (zx d, -zy d)
+          const float2 niy = __fmul2_rn(zy, d);  // -Im(1/z)
+          const float2 iy = make_float2(-niy.x, -niy.y);
+          const float2 qx = __fmul2_rn(ix, gr), qy = __fmul2_rn(iy, gr);
+          const float2 nqy = __fmul2_rn(iy, ngr);
+          float2 sx = s_Wx[w][p], sy = s_Wy[w][p];
+          for (int kk = p - 1; kk >= 0; --kk) {
+            const float2 tx = __ffma2_rn(sy, nqy, s_Wx[w][kk]);
+            const float2 ty = __ffma2_rn(sy, qx, s_Wy[w][kk]);
+            const float2 nsx = __ffma2_rn(sx, qx, tx);
+            sy = __ffma2_rn(sx, qy, ty);
+            sx = nsx;
+          }
+          FX[h] = __ffma2_rn(sx, ix, __ffma2_rn(sy, niy, FX[h]));
+          FY[h] = __ffma2_rn(sx, iy, __ffma2_rn(sy, ix, FY[h]));
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < kRpt; ++q) {
+          const float2 z = make_float2(dx[q] - gw.x, dy[q] - gw.y);
+          const float2 inv = cinv(z);
+          const float2 qq = make_float2(inv.x * gw.z, inv.y * gw.z);
+          float2 s = make_float2(s_Wx[w][p].x, s_Wy[w][p].x);
+          for (int kk = p - 1; kk >= 0; --kk) s = cfma(s, qq, make_float2(s_Wx[w][kk].x, s_Wy[w][kk].x));
+          fw[q] = cfma(s, inv, fw[q]);
+          float2 t = make_float2((float)(p + 1) * s_Wx[w][p].x, (float)(p + 1) * s_Wy[w][p].x);
           for (int kk = p - 1; kk >= 0; --kk)
-            t = cfma(t, qq, make_float2((float)(kk + 1) * s_W[w][kk].x, (float)(kk + 1) * s_W[w][kk].y));
-          const float2 d = cmul(t, cmul(inv, inv));
-          dfw[q] = make_float2(dfw[q].x - d.x, dfw[q].y - d.y);
+            t = cfma(t, qq, make_float2((float)(kk + 1) * s_Wx[w][kk].x, (float)(kk + 1) * s_Wy[w][kk].x));
+          const float2 dd = cmul(t, cmul(inv, inv));
+          dfw[q] = make_float2(dfw[q].x - dd.x, dfw[q].y - dd.y);
         }
       }
+    }
+  }
+  if (!JAC) {
+#pragma unroll
+    for (int h = 0; h < kRpt / 2; ++h) {
+      fw[2 * h] = make_float2(FX[h].x, FY[h].x);
+      fw[2 * h + 1] = make_float2(FX[h].y, FY[h].y);
     }
   }
 
   // ---- L2P + epilogue --------------------------------------------------------
   __syncthreads();
   const float ir = lp.ir;
+  // L2P by Horner's rule, paired rays without the Jacobian
+  float2 fl[kRpt];
+  if (!JAC) {
+    const float2 irr = make_float2(ir, ir), nirr = make_float2(-ir, -ir);
+#pragma unroll
+    for (int h = 0; h < kRpt / 2; ++h) {
+      const float2 wx = __fmul2_rn(make_float2(dx[2 * h], dx[2 * h + 1]), irr);
+      const float2 wy = __fmul2_rn(make_float2(dy[2 * h], dy[2 * h + 1]), irr);
+      const float2 nwy = __fmul2_rn(make_float2(dy[2 * h], dy[2 * h + 1]), nirr);
+      float2 fx = make_float2(0.f, 0.f), fy = make_float2(0.f, 0.f);
+      if (p >= 1) {
+        float2 sx = s_Lx[p], sy = s_Ly[p];
+        for (int l = p - 1; l >= 1; --l) {
+          const float2 tx = __ffma2_rn(sy, nwy, s_Lx[l]);
+          const float2 ty = __ffma2_rn(sy, wx, s_Ly[l]);
+          const float2 nsx = __ffma2_rn(sx, wx, tx);
+          sy = __ffma2_rn(sx, wy, ty);
+          sx = nsx;
+        }
+        fx = __ffma2_rn(sx, wx, __fmul2_rn(sy, nwy));
+        fy = __ffma2_rn(sx, wy, __fmul2_rn(sy, wx));
+      }
+      fl[2 * h] = make_float2(fx.x, fy.x);
+      fl[2 * h + 1] = make_float2(fx.y, fy.y);
+    }
+  }
 #pragma unroll
   for (int q = 0; q < kRpt; ++q) {
     if (!ok[q]) continue;
-    const float2 w = make_float2(dx[q] * ir, dy[q] * ir);
     float2 f = make_float2(0.f, 0.f), df = make_float2(0.f, 0.f);
-    if (p >= 1) {
-      float2 s = s_L[p];
-      for (int l = p - 1; l >= 1; --l) s = cfma(s, w, s_L[l]);
+    if (!JAC) {
+      f = fl[q];
+    } else if (p >= 1) {
+      const float2 w = make_float2(dx[q] * ir, dy[q] * ir);
+      float2 s = make_float2(s_Lx[p].x, s_Ly[p].x);
+      for (int l = p - 1; l >= 1; --l) s = cfma(s, w, make_float2(s_Lx[l].x, s_Ly[l].x));
       f = cmul(s, w);
-      if (JAC) {
-        float2 t = make_float2((float)p * s_L[p].x, (float)p * s_L[p].y);
-        for (int l = p - 1; l >= 1; --l) t = cfma(t, w, make_float2((float)l * s_L[l].x, (float)l * s_L[l].y));
-        df = make_float2(t.x * ir, t.y * ir);
-      }
+      float2 t = make_float2((float)p * s_Lx[p].x, (float)p * s_Ly[p].x);
+      for (int l = p - 1; l >= 1; --l)
+        t = cfma(t, w, make_float2((float)l * s_Lx[l].x, (float)l * s_Ly[l].x));
+      df = make_float2(t.x * ir, t.y * ir);
     }
     f = f + fw[q];
     ff T1 = ff_mul(A.af, ff{dx[q], dxl[q]});
@@ -333,8 +411,7 @@ __global__ void k_prep_leaf(const int* __restrict__ leaves, int64_t nl, const in
                             const int* __restrict__ level, const int* __restrict__ ix,
                             const int* __restrict__ iy, double lo_x, double lo_y, double size,
                             double a, double b, int p, const double2* __restrict__ L,
-                            const int64_t* __restrict__ ustar_cnt, LeafPlan* __restrict__ out,
-                            float2* __restrict__ fL, int64_t* __restrict__ ucnt) {
+                            LeafPlan* __restrict__ out, float2* __restrict__ fL) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nl) return;
   const int B = leaves[k];
@@ -350,44 +427,70 @@ __global__ void k_prep_leaf(const int* __restrict__ leaves, int64_t nl, const in
   lp.r = (float)r;
   out[k] = lp;
   for (int l = 0; l <= p; ++l) fL[k * (int64_t)(p + 1) + l] = make_float2((float)Lb[l].x, (float)Lb[l].y);
-  ucnt[k] = ustar_cnt[aidx[B]];
 }
 
-__global__ void k_prep_ustars(const int* __restrict__ leaves, int64_t nl, const int* __restrict__ aidx,
-                              const LeafPlan* __restrict__ lp, const int64_t* __restrict__ U_off,
-                              const int* __restrict__ U_list, const int* __restrict__ start,
-                              const int* __restrict__ count, const double2* __restrict__ spos,
-                              const double* __restrict__ smass, const int64_t* __restrict__ uoff,
-                              float4* __restrict__ ust, float* __restrict__ um) {
+// W boxes of at most this many stars are summed directly (P2P) instead of
+// evaluated from their multipole (M2P): per ray, P2P costs ~8 float32
+// operations per star against ~4(p+1) + 25 for one M2P.
+inline int w_direct_max(int p) { return std::max(1, (p + 1) / 2); }
+
+// Per active leaf: near boxes (U list + small W boxes), their stars, and the
+// far W boxes.
+__global__ void k_prep_counts(const int* __restrict__ leaves, int64_t nl, const int* __restrict__ aidx,
+                              const int64_t* __restrict__ U_off, const int64_t* __restrict__ W_off,
+                              const int* __restrict__ W_list, const int* __restrict__ count,
+                              const int64_t* __restrict__ ustar_cnt, int wmax,
+                              int64_t* __restrict__ ncnt, int64_t* __restrict__ scnt,
+                              int64_t* __restrict__ wcnt) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nl) return;
+  const int a = aidx[leaves[k]];
+  int64_t ne = U_off[a + 1] - U_off[a], ns = ustar_cnt[a], nw = 0;
+  for (int64_t e = W_off[a]; e < W_off[a + 1]; ++e) {
+    const int c = count[W_list[e]];
+    if (c <= wmax) { ++ne; ns += c; } else { ++nw; }
+  }
+  ncnt[k] = ne; scnt[k] = ns; wcnt[k] = nw;
+}
+
+__global__ void k_prep_lists(const int* __restrict__ leaves, int64_t nl, const int* __restrict__ aidx,
+                             const LeafPlan* __restrict__ lp, const int64_t* __restrict__ U_off,
+                             const int* __restrict__ U_list, const int64_t* __restrict__ W_off,
+                             const int* __restrict__ W_list, const int* __restrict__ start,
+                             const int* __restrict__ count, const int* __restrict__ level,
+                             const int* __restrict__ ix, const int* __restrict__ iy, double lo_x,
+                             double lo_y, double size, const double2* __restrict__ spos,
+                             const double* __restrict__ smass, int wmax,
+                             const int64_t* __restrict__ noff, const int64_t* __restrict__ uoff,
+                             const int64_t* __restrict__ woff, int* __restrict__ nlist,
+                             float4* __restrict__ ust, float* __restrict__ um,
+                             int* __restrict__ wlist, float4* __restrict__ wgeo) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nl) return;
   const int a = aidx[leaves[k]];
   const double cx = lp[k].cx, cy = lp[k].cy;
-  int64_t o = uoff[k];
-  for (int64_t e = U_off[a]; e < U_off[a + 1]; ++e) {
-    const int C = U_list[e];
+  int64_t on = noff[k], os = uoff[k], ow = woff[k];
+  auto stage = [&](int C) {
+    nlist[on++] = C;
     for (int j = start[C]; j < start[C] + count[C]; ++j) {
       const ff fx = ff_of(spos[j].x - cx), fy = ff_of(spos[j].y - cy);
-      ust[o] = make_float4(fx.hi, fy.hi, fx.lo, fy.lo);
-      um[o] = (float)smass[j];
-      ++o;
+      ust[os] = make_float4(fx.hi, fy.hi, fx.lo, fy.lo);
+      um[os] = (float)smass[j];
+      ++os;
     }
-  }
-}
-
-__global__ void k_prep_w(const int* __restrict__ leaves, int64_t nl, const int* __restrict__ aidx,
-                         const LeafPlan* __restrict__ lp, const int64_t* __restrict__ W_off,
-                         const int* __restrict__ W_list, const int* __restrict__ level,
-                         const int* __restrict__ ix, const int* __restrict__ iy, double lo_x,
-                         double lo_y, double size, float4* __restrict__ wgeo) {
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= nl) return;
-  const int a = aidx[leaves[k]];
+  };
+  for (int64_t e = U_off[a]; e < U_off[a + 1]; ++e) stage(U_list[e]);
   for (int64_t e = W_off[a]; e < W_off[a + 1]; ++e) {
     const int C = W_list[e];
-    const double r = size / (double)(2ull << level[C]);
-    const double cx = lo_x + (2.0 * ix[C] + 1.0) * r, cy = lo_y + (2.0 * iy[C] + 1.0) * r;
-    wgeo[e] = make_float4((float)(cx - lp[k].cx), (float)(cy - lp[k].cy), (float)r, 0.f);
+    if (count[C] <= wmax) {
+      stage(C);
+    } else {
+      const double r = size / (double)(2ull << level[C]);
+      const double wx = lo_x + (2.0 * ix[C] + 1.0) * r, wy = lo_y + (2.0 * iy[C] + 1.0) * r;
+      wlist[ow] = C;
+      wgeo[ow] = make_float4((float)(wx - cx), (float)(wy - cy), (float)r, 0.f);
+      ++ow;
+    }
   }
 }
 
@@ -425,7 +528,7 @@ E32Args base_args32(Plan& P) {
   E32Args A{};
   A.leaf = P.f_leaf; A.leaves = P.active_leaves; A.nleaf = P.n_active_leaves;
   A.aidx = P.box_aidx; A.count = P.box_count;
-  A.U_off = P.U_off; A.U_list = P.U_list; A.W_off = P.W_off; A.W_list = P.W_list;
+  A.noff = P.f_noff; A.nlist = P.f_nlist; A.woff = P.f_woff; A.wlist = P.f_wlist;
   A.fL = P.f_L; A.fM = P.f_M; A.ust = P.f_ust; A.um = P.f_um; A.uoff = P.f_uoff;
   A.wgeo = P.f_wgeo;
   A.p = P.p;
@@ -454,31 +557,45 @@ void eval32_prepare(Plan& P, cudaStream_t s) {
   P.f_leaf = P.dalloc_n<LeafPlan>(nl);
   P.f_L = P.dalloc_n<float2>((size_t)nl * P1);
   P.f_M = P.dalloc_n<float2>((size_t)P.nb * P1);
+  P.f_noff = P.dalloc_n<int64_t>(nl + 1);
   P.f_uoff = P.dalloc_n<int64_t>(nl + 1);
-  P.f_wgeo = P.dalloc_n<float4>(P.nW);
+  P.f_woff = P.dalloc_n<int64_t>(nl + 1);
+  P.f_ncnt = P.dalloc_n<int64_t>(nl + 1);
+  P.f_wcnt = P.dalloc_n<int64_t>(nl + 1);
   if (nl == 0) return;
   const double a = 1.0 - P.kappa_s - P.gamma, b = 1.0 - P.kappa_s + P.gamma;
-  Scratch ucnt(&P.da, sizeof(int64_t) * (nl + 1));
-  LENS_CUDA(cudaMemsetAsync(ucnt.p, 0, ucnt.bytes, s));
+  const int wmax = w_direct_max(P.p);
   k_prep_leaf<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx, P.box_level,
                                                 P.box_ix, P.box_iy, P.root_lo[0], P.root_lo[1],
-                                                P.root_size, a, b, P.p, P.L, P.ustar_cnt,
-                                                P.f_leaf, P.f_L, ucnt.as<int64_t>());
+                                                P.root_size, a, b, P.p, P.L, P.f_leaf, P.f_L);
   LENS_LAUNCHED("k_prep_leaf");
-  exclusive_scan_i64(ucnt.as<int64_t>(), P.f_uoff, nl + 1, P.da, s);
-  int64_t total = 0;
-  LENS_CUDA(cudaMemcpyAsync(&total, P.f_uoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  Scratch ecnt(&P.da, sizeof(int64_t) * (nl + 1));
+  LENS_CUDA(cudaMemsetAsync(ecnt.p, 0, ecnt.bytes, s));
+  LENS_CUDA(cudaMemsetAsync(P.f_ncnt, 0, sizeof(int64_t) * (nl + 1), s));
+  LENS_CUDA(cudaMemsetAsync(P.f_wcnt, 0, sizeof(int64_t) * (nl + 1), s));
+  k_prep_counts<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx, P.U_off, P.W_off,
+                                                  P.W_list, P.box_count, P.ustar_cnt, wmax,
+                                                  ecnt.as<int64_t>(), P.f_ncnt, P.f_wcnt);
+  LENS_LAUNCHED("k_prep_counts");
+  exclusive_scan_i64(ecnt.as<int64_t>(), P.f_noff, nl + 1, P.da, s);
+  exclusive_scan_i64(P.f_ncnt, P.f_uoff, nl + 1, P.da, s);
+  exclusive_scan_i64(P.f_wcnt, P.f_woff, nl + 1, P.da, s);
+  int64_t tot[3] = {0, 0, 0};
+  LENS_CUDA(cudaMemcpyAsync(&tot[0], P.f_noff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaMemcpyAsync(&tot[1], P.f_uoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaMemcpyAsync(&tot[2], P.f_woff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   LENS_CUDA(cudaStreamSynchronize(s));
-  P.f_ust = P.dalloc_n<float4>(total);
-  P.f_um = P.dalloc_n<float>(total);
-  k_prep_ustars<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx, P.f_leaf,
-                                                  P.U_off, P.U_list, P.box_start, P.box_count,
-                                                  P.spos, P.smass, P.f_uoff, P.f_ust, P.f_um);
-  LENS_LAUNCHED("k_prep_ustars");
-  k_prep_w<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx, P.f_leaf, P.W_off,
-                                             P.W_list, P.box_level, P.box_ix, P.box_iy,
-                                             P.root_lo[0], P.root_lo[1], P.root_size, P.f_wgeo);
-  LENS_LAUNCHED("k_prep_w");
+  P.f_nlist = P.dalloc_n<int>(tot[0]);
+  P.f_ust = P.dalloc_n<float4>(tot[1]);
+  P.f_um = P.dalloc_n<float>(tot[1]);
+  P.f_wlist = P.dalloc_n<int>(tot[2]);
+  P.f_wgeo = P.dalloc_n<float4>(tot[2]);
+  k_prep_lists<<<grid_for(nl, 128), 128, 0, s>>>(
+      P.active_leaves, nl, P.box_aidx, P.f_leaf, P.U_off, P.U_list, P.W_off, P.W_list,
+      P.box_start, P.box_count, P.box_level, P.box_ix, P.box_iy, P.root_lo[0], P.root_lo[1],
+      P.root_size, P.spos, P.smass, wmax, P.f_noff, P.f_uoff, P.f_woff, P.f_nlist, P.f_ust,
+      P.f_um, P.f_wlist, P.f_wgeo);
+  LENS_LAUNCHED("k_prep_lists");
   k_to_f32<<<grid_for((int64_t)P.nb * P1, 256, 152 * 16), 256, 0, s>>>(P.M, (int64_t)P.nb * P1,
                                                                        P.f_M);
   LENS_LAUNCHED("k_to_f32");

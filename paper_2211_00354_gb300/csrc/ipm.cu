@@ -299,10 +299,12 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
           for (int k = 0; k < 4; ++k) {
             sh.qx[k][w][lane] = qx[k];
             sh.qy[k][w][lane] = qy[k];
+            // an edge with |dy| <= 1e-30 adds nothing (its clipped dy is at
+            // most that): slope 0 keeps its terms finite
             const float ey = qy[(k + 1) & 3] - qy[k];
-            sh.sl[k][w][lane] = ey != 0.f ? (qx[(k + 1) & 3] - qx[k]) / ey : 0.f;
+            sh.sl[k][w][lane] = fabsf(ey) > 1e-30f ? __fdividef(qx[(k + 1) & 3] - qx[k], ey) : 0.f;
           }
-          sh.inv[w][lane] = 1.0f / A_loc;
+          sh.inv[w][lane] = frcp_fast(A_loc);  // |A_loc| > 0: the cell is well conditioned
           sh.ix0[w][lane] = ix0; sh.iy0[w][lane] = iy0;
           sh.cx0[w][lane] = cx0; sh.cx1[w][lane] = cx1; sh.cy0[w][lane] = cy0;
           // every fraction that lands in the map is moved from fout to fin

@@ -157,10 +157,18 @@ struct Plan {
   LeafPlan* f_leaf = nullptr;   // per active leaf
   float2* f_L = nullptr;        // per active leaf, (p+1) local coefficients
   float2* f_M = nullptr;        // per box, (p+1) multipole coefficients
-  float4* f_ust = nullptr;      // U-list stars of every active leaf (float-float offsets)
-  float* f_um = nullptr;        // their masses
-  int64_t* f_uoff = nullptr;    // CSR offsets into f_ust by active-leaf index
-  float4* f_wgeo = nullptr;     // per W entry: centre offset from the leaf centre, radius
+  // near field of every active leaf k: the U-list leaves plus the W boxes
+  // small enough for P2P (f_nlist[f_noff[k] ..]); their stars as float-float
+  // offsets from the leaf centre (f_ust / f_um from f_uoff[k]); the far W
+  // boxes left to M2P (f_wlist / f_wgeo from f_woff[k]); per-leaf counts of
+  // near stars (f_ncnt) and far W boxes (f_wcnt) for the work counters
+  int64_t* f_noff = nullptr; int* f_nlist = nullptr;
+  float4* f_ust = nullptr;
+  float* f_um = nullptr;
+  int64_t* f_uoff = nullptr;
+  int64_t* f_woff = nullptr; int* f_wlist = nullptr;
+  float4* f_wgeo = nullptr;     // per far W entry: centre offset from the leaf centre, radius
+  int64_t* f_ncnt = nullptr; int64_t* f_wcnt = nullptr;
 
   double ms_build = 0;
   int64_t build_launches = 0;
