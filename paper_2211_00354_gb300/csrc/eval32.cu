@@ -38,7 +38,7 @@ namespace {
 
 constexpr int kT = kEval32Threads;
 constexpr int kRpt = kEval32Rpt;
-constexpr int kSeg = 64;
+constexpr int kGroup = 8;  // stars per float32 partial sum of the near field
 constexpr int kChunk = 512;
 static_assert(kRpt % 2 == 0, "rays are paired for float2 arithmetic");
 constexpr int kWChunk = 8;
@@ -50,9 +50,10 @@ struct E32Args {
   int64_t nleaf;
   const int* aidx;
   const int* count;
-  // per active leaf k: near boxes (P2P) nlist[noff[k] .. noff[k+1]), their
-  // stars staged at ust/um[uoff[k] ..]; far W boxes (M2P) wlist[woff[k] ..]
-  const int64_t* noff; const int* nlist; const int64_t* woff; const int* wlist;
+  // per active leaf k: its near-field stars (U-list leaves and small W
+  // boxes, P2P) staged at ust/um[uoff[k] .. uoff[k+1]); far W boxes (M2P)
+  // wlist[woff[k] .. woff[k+1])
+  const int64_t* woff; const int* wlist;
   const float2* fL; const float2* fM;
   const float4* ust; const float* um; const int64_t* uoff; const float4* wgeo;
   int p;
@@ -71,7 +72,6 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   // staged stars, each value duplicated into both halves of a float2 (the
   // offsets negated, so that d = x + (-s) is the plain difference)
   __shared__ float2 s_x[kChunk], s_y[kChunk], s_xl[kChunk], s_yl[kChunk], s_m[kChunk];
-  __shared__ int s_pre[kSeg + 1];
   // expansion coefficients with each real / imaginary part duplicated into
   // both halves of a float2 (operands of the paired-ray arithmetic)
   __shared__ float2 s_Lx[kMaxOrder + 1], s_Ly[kMaxOrder + 1];
@@ -139,110 +139,86 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
     }
   }
 
-  // ---- P2P over the U list (stars pre-staged per leaf in float-float) -----
-  const int64_t u_beg = A.noff[k], u_end = A.noff[k + 1];
-  const int64_t star0 = A.uoff[k];
-  int64_t star_done = 0;  // stars of earlier U-entry rounds
-  for (int64_t e0 = u_beg; e0 < u_end; e0 += kSeg) {
-    const int ne = (int)min64(kSeg, u_end - e0);
+  // ---- P2P over the near field (stars pre-staged per leaf in float-float) --
+  // The leaf's near stars are contiguous: they are staged kChunk at a time
+  // and summed in groups of kGroup (8) in plain float32, each group partial then
+  // entering a two-sum (compensated) accumulator.
+  const int64_t star0 = A.uoff[k], nstar = A.uoff[k + 1] - star0;
+  for (int64_t f0 = 0; f0 < nstar; f0 += kChunk) {
+    const int nf = (int)min64(kChunk, nstar - f0);
     __syncthreads();
-    if (tid < 32) {
-      int base = 0;
-      for (int half = 0; half < kSeg / 32; ++half) {
-        const int e = half * 32 + tid;
-        const int c = (e < ne) ? A.count[A.nlist[e0 + e]] : 0;
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (tid >= o) incl += v;
-        }
-        s_pre[e + 1] = base + incl;
-        base += __shfl_sync(0xffffffffu, incl, 31);
-      }
-      if (tid == 0) s_pre[0] = 0;
+    for (int f = tid; f < nf; f += kT) {
+      const int64_t g = star0 + f0 + f;
+      const float4 v = A.ust[g];
+      const float mm = A.um[g];
+      s_x[f] = make_float2(-v.x, -v.x); s_y[f] = make_float2(-v.y, -v.y);
+      s_xl[f] = make_float2(-v.z, -v.z); s_yl[f] = make_float2(-v.w, -v.w);
+      s_m[f] = make_float2(mm, mm);
     }
     __syncthreads();
-    const int tot = s_pre[ne];
-    for (int f0 = 0; f0 < tot; f0 += kChunk) {
-      const int nf = min(kChunk, tot - f0);
-      if (f0 > 0) __syncthreads();
-      for (int f = tid; f < nf; f += kT) {
-        const int64_t g = star0 + star_done + f0 + f;
-        const float4 v = A.ust[g];
-        const float mm = A.um[g];
-        s_x[f] = make_float2(-v.x, -v.x); s_y[f] = make_float2(-v.y, -v.y);
-        s_xl[f] = make_float2(-v.z, -v.z); s_yl[f] = make_float2(-v.w, -v.w);
-        s_m[f] = make_float2(mm, mm);
+    for (int lo = 0; lo < nf; lo += kGroup) {
+      const int hi = min(nf, lo + kGroup);
+      float p1[kRpt], p2[kRpt], pj1[kRpt], pj2[kRpt];
+      if (!JAC) {
+        // rays (2h, 2h+1) side by side in float2 pair arithmetic
+        // (Blackwell's two-lane FP32 instructions, IEEE round-to-nearest
+        // per lane): the same operations as the scalar loop below in half
+        // the issue slots.  A star exactly on the ray contributes nothing:
+        // the floor on r2 keeps w finite and w * d = 0.
+        float2 P1[kRpt / 2], P2[kRpt / 2], DX[kRpt / 2], DY[kRpt / 2], DXL[kRpt / 2], DYL[kRpt / 2];
+#pragma unroll
+        for (int h = 0; h < kRpt / 2; ++h) {
+          P1[h] = make_float2(0.f, 0.f); P2[h] = make_float2(0.f, 0.f);
+          DX[h] = make_float2(dx[2 * h], dx[2 * h + 1]); DY[h] = make_float2(dy[2 * h], dy[2 * h + 1]);
+          DXL[h] = make_float2(dxl[2 * h], dxl[2 * h + 1]); DYL[h] = make_float2(dyl[2 * h], dyl[2 * h + 1]);
+        }
+        const float2 tiny = make_float2(1e-30f, 1e-30f);
+        for (int j = lo; j < hi; ++j) {
+          const float2 nsx = s_x[j], nsy = s_y[j], nsxl = s_xl[j], nsyl = s_yl[j], sm = s_m[j];
+#pragma unroll
+          for (int h = 0; h < kRpt / 2; ++h) {
+            const float2 d1 = __fadd2_rn(__fadd2_rn(DX[h], nsx), __fadd2_rn(DXL[h], nsxl));
+            const float2 d2 = __fadd2_rn(__fadd2_rn(DY[h], nsy), __fadd2_rn(DYL[h], nsyl));
+            const float2 r2 = __ffma2_rn(d1, d1, __ffma2_rn(d2, d2, tiny));
+            const float2 w = __fmul2_rn(sm, make_float2(frcp_fast(r2.x), frcp_fast(r2.y)));
+            P1[h] = __ffma2_rn(w, d1, P1[h]);
+            P2[h] = __ffma2_rn(w, d2, P2[h]);
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < kRpt / 2; ++h) {
+          p1[2 * h] = P1[h].x; p1[2 * h + 1] = P1[h].y;
+          p2[2 * h] = P2[h].x; p2[2 * h + 1] = P2[h].y;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < kRpt; ++q) { p1[q] = 0.f; p2[q] = 0.f; pj1[q] = 0.f; pj2[q] = 0.f; }
+        for (int j = lo; j < hi; ++j) {
+          const float sx = -s_x[j].x, sy = -s_y[j].x, sxl = -s_xl[j].x, syl = -s_yl[j].x;
+          const float sm = s_m[j].x;
+#pragma unroll
+          for (int q = 0; q < kRpt; ++q) {
+            const float d1 = (dx[q] - sx) + (dxl[q] - sxl);
+            const float d2 = (dy[q] - sy) + (dyl[q] - syl);
+            // a star exactly on the ray contributes nothing (w * w would
+            // overflow with a floor on r2, hence the select)
+            const float r2 = fmaf(d1, d1, d2 * d2);
+            const float inv = r2 > 0.f ? frcp_fast(r2) : 0.f;
+            const float w = sm * inv;
+            p1[q] = fmaf(w, d1, p1[q]);
+            p2[q] = fmaf(w, d2, p2[q]);
+            const float w2 = w * inv;
+            pj1[q] = fmaf(w2, (d2 - d1) * (d2 + d1), pj1[q]);
+            pj2[q] = fmaf(w2, 2.f * d1 * d2, pj2[q]);
+          }
+        }
       }
-      __syncthreads();
-      for (int e = 0; e < ne; ++e) {
-        const int lo = max(s_pre[e], f0) - f0;
-        const int hi = min(s_pre[e + 1], f0 + nf) - f0;
-        if (hi <= lo) continue;
-        float p1[kRpt], p2[kRpt], pj1[kRpt], pj2[kRpt];
-        if (!JAC) {
-          // rays (2h, 2h+1) side by side in float2 pair arithmetic
-          // (Blackwell's two-lane FP32 instructions, IEEE round-to-nearest
-          // per lane): the same operations as the scalar loop below in half
-          // the issue slots.  A star exactly on the ray contributes nothing:
-          // the floor on r2 keeps w finite and w * d = 0.
-          float2 P1[kRpt / 2], P2[kRpt / 2], DX[kRpt / 2], DY[kRpt / 2], DXL[kRpt / 2], DYL[kRpt / 2];
 #pragma unroll
-          for (int h = 0; h < kRpt / 2; ++h) {
-            P1[h] = make_float2(0.f, 0.f); P2[h] = make_float2(0.f, 0.f);
-            DX[h] = make_float2(dx[2 * h], dx[2 * h + 1]); DY[h] = make_float2(dy[2 * h], dy[2 * h + 1]);
-            DXL[h] = make_float2(dxl[2 * h], dxl[2 * h + 1]); DYL[h] = make_float2(dyl[2 * h], dyl[2 * h + 1]);
-          }
-          const float2 tiny = make_float2(1e-30f, 1e-30f);
-          for (int j = lo; j < hi; ++j) {
-            const float2 nsx = s_x[j], nsy = s_y[j], nsxl = s_xl[j], nsyl = s_yl[j], sm = s_m[j];
-#pragma unroll
-            for (int h = 0; h < kRpt / 2; ++h) {
-              const float2 d1 = __fadd2_rn(__fadd2_rn(DX[h], nsx), __fadd2_rn(DXL[h], nsxl));
-              const float2 d2 = __fadd2_rn(__fadd2_rn(DY[h], nsy), __fadd2_rn(DYL[h], nsyl));
-              const float2 r2 = __ffma2_rn(d1, d1, __ffma2_rn(d2, d2, tiny));
-              const float2 w = __fmul2_rn(sm, make_float2(frcp_fast(r2.x), frcp_fast(r2.y)));
-              P1[h] = __ffma2_rn(w, d1, P1[h]);
-              P2[h] = __ffma2_rn(w, d2, P2[h]);
-            }
-          }
-#pragma unroll
-          for (int h = 0; h < kRpt / 2; ++h) {
-            p1[2 * h] = P1[h].x; p1[2 * h + 1] = P1[h].y;
-            p2[2 * h] = P2[h].x; p2[2 * h + 1] = P2[h].y;
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < kRpt; ++q) { p1[q] = 0.f; p2[q] = 0.f; pj1[q] = 0.f; pj2[q] = 0.f; }
-          for (int j = lo; j < hi; ++j) {
-            const float sx = -s_x[j].x, sy = -s_y[j].x, sxl = -s_xl[j].x, syl = -s_yl[j].x;
-            const float sm = s_m[j].x;
-#pragma unroll
-            for (int q = 0; q < kRpt; ++q) {
-              const float d1 = (dx[q] - sx) + (dxl[q] - sxl);
-              const float d2 = (dy[q] - sy) + (dyl[q] - syl);
-              // a star exactly on the ray contributes nothing (w * w would
-              // overflow with a floor on r2, hence the select)
-              const float r2 = fmaf(d1, d1, d2 * d2);
-              const float inv = r2 > 0.f ? frcp_fast(r2) : 0.f;
-              const float w = sm * inv;
-              p1[q] = fmaf(w, d1, p1[q]);
-              p2[q] = fmaf(w, d2, p2[q]);
-              const float w2 = w * inv;
-              pj1[q] = fmaf(w2, (d2 - d1) * (d2 + d1), pj1[q]);
-              pj2[q] = fmaf(w2, 2.f * d1 * d2, pj2[q]);
-            }
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < kRpt; ++q) {
-          n1[q].add(p1[q]); n2[q].add(p2[q]);
-          if (JAC) { nj1[q].add(pj1[q]); nj2[q].add(pj2[q]); }
-        }
+      for (int q = 0; q < kRpt; ++q) {
+        n1[q].add(p1[q]); n2[q].add(p2[q]);
+        if (JAC) { nj1[q].add(pj1[q]); nj2[q].add(pj2[q]); }
       }
     }
-    star_done += tot;
   }
 
   // ---- M2P over the far W boxes --------------------------------------------
@@ -437,20 +413,19 @@ inline int w_direct_max(int p) { return std::max(1, (p + 1) / 2); }
 // Per active leaf: near boxes (U list + small W boxes), their stars, and the
 // far W boxes.
 __global__ void k_prep_counts(const int* __restrict__ leaves, int64_t nl, const int* __restrict__ aidx,
-                              const int64_t* __restrict__ U_off, const int64_t* __restrict__ W_off,
+                              const int64_t* __restrict__ W_off,
                               const int* __restrict__ W_list, const int* __restrict__ count,
                               const int64_t* __restrict__ ustar_cnt, int wmax,
-                              int64_t* __restrict__ ncnt, int64_t* __restrict__ scnt,
-                              int64_t* __restrict__ wcnt) {
+                              int64_t* __restrict__ scnt, int64_t* __restrict__ wcnt) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nl) return;
   const int a = aidx[leaves[k]];
-  int64_t ne = U_off[a + 1] - U_off[a], ns = ustar_cnt[a], nw = 0;
+  int64_t ns = ustar_cnt[a], nw = 0;
   for (int64_t e = W_off[a]; e < W_off[a + 1]; ++e) {
     const int c = count[W_list[e]];
-    if (c <= wmax) { ++ne; ns += c; } else { ++nw; }
+    if (c <= wmax) ns += c; else ++nw;
   }
-  ncnt[k] = ne; scnt[k] = ns; wcnt[k] = nw;
+  scnt[k] = ns; wcnt[k] = nw;
 }
 
 __global__ void k_prep_lists(const int* __restrict__ leaves, int64_t nl, const int* __restrict__ aidx,
@@ -461,17 +436,15 @@ __global__ void k_prep_lists(const int* __restrict__ leaves, int64_t nl, const i
                              const int* __restrict__ ix, const int* __restrict__ iy, double lo_x,
                              double lo_y, double size, const double2* __restrict__ spos,
                              const double* __restrict__ smass, int wmax,
-                             const int64_t* __restrict__ noff, const int64_t* __restrict__ uoff,
-                             const int64_t* __restrict__ woff, int* __restrict__ nlist,
+                             const int64_t* __restrict__ uoff, const int64_t* __restrict__ woff,
                              float4* __restrict__ ust, float* __restrict__ um,
                              int* __restrict__ wlist, float4* __restrict__ wgeo) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nl) return;
   const int a = aidx[leaves[k]];
   const double cx = lp[k].cx, cy = lp[k].cy;
-  int64_t on = noff[k], os = uoff[k], ow = woff[k];
+  int64_t os = uoff[k], ow = woff[k];
   auto stage = [&](int C) {
-    nlist[on++] = C;
     for (int j = start[C]; j < start[C] + count[C]; ++j) {
       const ff fx = ff_of(spos[j].x - cx), fy = ff_of(spos[j].y - cy);
       ust[os] = make_float4(fx.hi, fy.hi, fx.lo, fy.lo);
@@ -528,7 +501,7 @@ E32Args base_args32(Plan& P) {
   E32Args A{};
   A.leaf = P.f_leaf; A.leaves = P.active_leaves; A.nleaf = P.n_active_leaves;
   A.aidx = P.box_aidx; A.count = P.box_count;
-  A.noff = P.f_noff; A.nlist = P.f_nlist; A.woff = P.f_woff; A.wlist = P.f_wlist;
+  A.woff = P.f_woff; A.wlist = P.f_wlist;
   A.fL = P.f_L; A.fM = P.f_M; A.ust = P.f_ust; A.um = P.f_um; A.uoff = P.f_uoff;
   A.wgeo = P.f_wgeo;
   A.p = P.p;
@@ -557,7 +530,6 @@ void eval32_prepare(Plan& P, cudaStream_t s) {
   P.f_leaf = P.dalloc_n<LeafPlan>(nl);
   P.f_L = P.dalloc_n<float2>((size_t)nl * P1);
   P.f_M = P.dalloc_n<float2>((size_t)P.nb * P1);
-  P.f_noff = P.dalloc_n<int64_t>(nl + 1);
   P.f_uoff = P.dalloc_n<int64_t>(nl + 1);
   P.f_woff = P.dalloc_n<int64_t>(nl + 1);
   P.f_ncnt = P.dalloc_n<int64_t>(nl + 1);
@@ -569,32 +541,27 @@ void eval32_prepare(Plan& P, cudaStream_t s) {
                                                 P.box_ix, P.box_iy, P.root_lo[0], P.root_lo[1],
                                                 P.root_size, a, b, P.p, P.L, P.f_leaf, P.f_L);
   LENS_LAUNCHED("k_prep_leaf");
-  Scratch ecnt(&P.da, sizeof(int64_t) * (nl + 1));
-  LENS_CUDA(cudaMemsetAsync(ecnt.p, 0, ecnt.bytes, s));
   LENS_CUDA(cudaMemsetAsync(P.f_ncnt, 0, sizeof(int64_t) * (nl + 1), s));
   LENS_CUDA(cudaMemsetAsync(P.f_wcnt, 0, sizeof(int64_t) * (nl + 1), s));
-  k_prep_counts<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx, P.U_off, P.W_off,
+  k_prep_counts<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx, P.W_off,
                                                   P.W_list, P.box_count, P.ustar_cnt, wmax,
-                                                  ecnt.as<int64_t>(), P.f_ncnt, P.f_wcnt);
+                                                  P.f_ncnt, P.f_wcnt);
   LENS_LAUNCHED("k_prep_counts");
-  exclusive_scan_i64(ecnt.as<int64_t>(), P.f_noff, nl + 1, P.da, s);
   exclusive_scan_i64(P.f_ncnt, P.f_uoff, nl + 1, P.da, s);
   exclusive_scan_i64(P.f_wcnt, P.f_woff, nl + 1, P.da, s);
-  int64_t tot[3] = {0, 0, 0};
-  LENS_CUDA(cudaMemcpyAsync(&tot[0], P.f_noff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LENS_CUDA(cudaMemcpyAsync(&tot[1], P.f_uoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LENS_CUDA(cudaMemcpyAsync(&tot[2], P.f_woff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  int64_t tot[2] = {0, 0};
+  LENS_CUDA(cudaMemcpyAsync(&tot[0], P.f_uoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaMemcpyAsync(&tot[1], P.f_woff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   LENS_CUDA(cudaStreamSynchronize(s));
-  P.f_nlist = P.dalloc_n<int>(tot[0]);
-  P.f_ust = P.dalloc_n<float4>(tot[1]);
-  P.f_um = P.dalloc_n<float>(tot[1]);
-  P.f_wlist = P.dalloc_n<int>(tot[2]);
-  P.f_wgeo = P.dalloc_n<float4>(tot[2]);
+  P.f_ust = P.dalloc_n<float4>(tot[0]);
+  P.f_um = P.dalloc_n<float>(tot[0]);
+  P.f_wlist = P.dalloc_n<int>(tot[1]);
+  P.f_wgeo = P.dalloc_n<float4>(tot[1]);
   k_prep_lists<<<grid_for(nl, 128), 128, 0, s>>>(
       P.active_leaves, nl, P.box_aidx, P.f_leaf, P.U_off, P.U_list, P.W_off, P.W_list,
       P.box_start, P.box_count, P.box_level, P.box_ix, P.box_iy, P.root_lo[0], P.root_lo[1],
-      P.root_size, P.spos, P.smass, wmax, P.f_noff, P.f_uoff, P.f_woff, P.f_nlist, P.f_ust,
-      P.f_um, P.f_wlist, P.f_wgeo);
+      P.root_size, P.spos, P.smass, wmax, P.f_uoff, P.f_woff, P.f_ust, P.f_um, P.f_wlist,
+      P.f_wgeo);
   LENS_LAUNCHED("k_prep_lists");
   k_to_f32<<<grid_for((int64_t)P.nb * P1, 256, 152 * 16), 256, 0, s>>>(P.M, (int64_t)P.nb * P1,
                                                                        P.f_M);

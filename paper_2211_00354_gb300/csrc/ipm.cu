@@ -67,19 +67,15 @@ __device__ __forceinline__ T pixel_area(const T* qx, const T* qy, T X, T Y) {
 }
 
 // float32 form of mean_clamp01 without branches (the lanes of a warp take
-// different cases): the pure cases (all below 0, all above 1, all inside)
-// are selected exactly, the mixed case is the integral over the length.
+// different cases): the integral of the clamp over [lo, hi] divided by the
+// length; a vanishing length (a vertical edge) takes the clamped midpoint.
+// All-below-0 gives exactly 0; the other pure cases are within an ulp.
 __device__ __forceinline__ float mean_clamp01f(float a, float b) {
   const float lo = fminf(a, b), hi = fmaxf(a, b);
   const float l0 = fmaxf(lo, 0.f), h1 = fminf(hi, 1.f);
   const float I = 0.5f * fmaxf(h1 - l0, 0.f) * (h1 + l0) + fmaxf(hi - fmaxf(lo, 1.f), 0.f);
   const float d = hi - lo;
-  const float mid = 0.5f * (lo + hi);
-  float r = d > 1e-30f ? I * frcp_fast(d) : fminf(fmaxf(mid, 0.f), 1.f);
-  r = (lo >= 0.f && hi <= 1.f) ? mid : r;
-  r = hi <= 0.f ? 0.f : r;
-  r = lo >= 1.f ? 1.f : r;
-  return r;
+  return d > 1e-30f ? I * frcp_fast(d) : fminf(fmaxf(0.5f * (lo + hi), 0.f), 1.f);
 }
 
 // pixel_area() in float32 with the edge slopes dx/dy given (0 for a

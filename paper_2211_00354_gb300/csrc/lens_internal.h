@@ -157,12 +157,11 @@ struct Plan {
   LeafPlan* f_leaf = nullptr;   // per active leaf
   float2* f_L = nullptr;        // per active leaf, (p+1) local coefficients
   float2* f_M = nullptr;        // per box, (p+1) multipole coefficients
-  // near field of every active leaf k: the U-list leaves plus the W boxes
-  // small enough for P2P (f_nlist[f_noff[k] ..]); their stars as float-float
-  // offsets from the leaf centre (f_ust / f_um from f_uoff[k]); the far W
-  // boxes left to M2P (f_wlist / f_wgeo from f_woff[k]); per-leaf counts of
-  // near stars (f_ncnt) and far W boxes (f_wcnt) for the work counters
-  int64_t* f_noff = nullptr; int* f_nlist = nullptr;
+  // near field of every active leaf k (its U-list leaves plus the W boxes
+  // small enough for P2P): the stars as float-float offsets from the leaf
+  // centre (f_ust / f_um from f_uoff[k]); the far W boxes left to M2P
+  // (f_wlist / f_wgeo from f_woff[k]); per-leaf counts of near stars
+  // (f_ncnt) and far W boxes (f_wcnt) for the work counters
   float4* f_ust = nullptr;
   float* f_um = nullptr;
   int64_t* f_uoff = nullptr;

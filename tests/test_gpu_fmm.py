@@ -72,6 +72,24 @@ def test_full_grid_matches_oracle_and_ray_path():
     np.testing.assert_array_equal(band, yg.reshape(grid.ny + 1, grid.nx + 1, 2)[100:133])
 
 
+def test_full_grid_fp32_bulk_matches_oracle():
+    # the float32-bulk grid path (the map path's kernel, y output) at every
+    # corner of a grid spanning many leaves, ragged tiles included
+    f = synth.config_uniform(seed=9, n=3000, kappa_star=0.4, kappa_s=0.05, gamma=0.3,
+                             radius=15.0)
+    grid = synth.Grid(x0=-6.0, y0=-5.0, h=0.037, nx=301, ny=257)
+    xc = grid.corners().reshape(-1, 2)
+    y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, xc)
+    for leaf in (4, 8, 16):
+        with plan_for(f, 24, leaf, lens.FP32_BULK, (-6.0, 6.0, -5.0, 5.0)) as P:
+            yg = P.deflect_grid(grid).cpu().numpy().reshape(-1, 2)
+            yr = P.deflect(T(xc)).cpu().numpy()
+        eg = alpha_rel_err(yg, y_ref, xc, f.kappa_s, f.gamma)
+        er = alpha_rel_err(yr, y_ref, xc, f.kappa_s, f.gamma)
+        print("leaf %d: grid %.2e ray %.2e" % (leaf, eg.max(), er.max()))
+        assert eg.max() < 2e-5 and er.max() < 2e-5, leaf
+
+
 def clustered(seed=0, nc=30, per=80):
     rng = np.random.default_rng(seed)
     centres = rng.uniform(-8, 8, (nc, 2))
