@@ -1,0 +1,213 @@
+"""Parity at the full sizes of the other workload configurations:
+
+* clustered primordial-black-hole field (1e6 lenses in 1e3 Plummer clusters,
+  log-normal masses, leaf 64, 4096^2 map over 100 ER);
+* extreme magnification near a critical curve (2e5 stars, mu ~ 286,
+  8192^2 map over 2 ER, ~2.2e10 cells in chunks);
+* elliptical NFW halo of 1e7 particles, deflection only on a 4096^2 grid;
+* the differentiation workload (1e5 stars, 3e6 rays, 2048-sample Gaussian
+  light curve): adjoint gradients against central differences.
+
+Deflections are checked on sampled rays against the oracle's direct sum,
+maps on full-width bands against the oracle's IPM of the same deflections,
+whole maps through their ledgers and mean magnification."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_00354_gb300 import autograd, dist as ldist, lens, synth
+from helpers import alpha_rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def grid_box(g):
+    return (g.x0, g.x0 + g.nx * g.h, g.y0, g.y0 + g.ny * g.h)
+
+
+def ledger_ok(st, rel=1e-6):
+    led = st["area_in_map"] + st["area_outside"] + st["area_dropped"] + st["area_degenerate"]
+    return abs(led - st["area_total"]) <= rel * st["area_total"]
+
+
+def band_check(f, P, row0, nrows, cap=64):
+    band = ldist.strip_grid(f.grid, row0, nrows)
+    y = P.deflect_grid(band).cpu().numpy()
+    ref, st_ref = oracle.ipm_map(y, band.h, f.box, f.npx, f.npy, bbox_cap=cap)
+    mp, st = P.ipm_map(band, f.box, f.npx, f.npy, bbox_cap=cap)
+    mp = mp.cpu().numpy()
+    good = np.abs(ref) > 1e-3 * np.abs(ref).max()
+    e = np.mean(np.abs(mp[good] - ref[good]) / np.abs(ref[good]))
+    assert e < 1e-3, e
+    assert st["cells_dropped"] == pytest.approx(st_ref["cells_dropped"], rel=1e-3, abs=5)
+    for k in ("area_in_map", "area_outside"):
+        assert st[k] == pytest.approx(st_ref[k], rel=1e-5, abs=1e-9 * st_ref["area_total"])
+    return e, int(good.sum())
+
+
+@pytest.fixture(scope="module")
+def c3():
+    return synth.c3_clustered(seed=0)
+
+
+def test_clustered_field_deflections(c3):
+    f = c3
+    idx, x = synth.subsample_grid_rays(11, f.grid, 2048)
+    y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x)
+    with lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=16, leaf_size=64,
+                      prec=lens.FP32_BULK, target_box=grid_box(f.grid)) as P:
+        y32 = P.deflect(T(x)).cpu().numpy()
+        info = P.info()
+    with lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=48, leaf_size=64,
+                      prec=lens.FP64, target_box=grid_box(f.grid)) as P:
+        y64 = P.deflect(T(x[:512])).cpu().numpy()
+    e32 = alpha_rel_err(y32, y_ref, x, f.kappa_s, f.gamma)
+    e64 = alpha_rel_err(y64, y_ref[:512], x[:512], f.kappa_s, f.gamma)
+    print("C3: levels %d, FP32-bulk max %.2e, FP64 max %.2e" % (info["levels"], e32.max(), e64.max()))
+    assert info["n_w"] > 0 and info["n_x"] > 0  # the adaptive lists are exercised
+    assert e32.max() < 2e-5
+    assert e64.max() < 1e-10
+
+
+def test_clustered_field_map(c3):
+    f = c3
+    with lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=16, leaf_size=64,
+                      prec=lens.FP32_BULK, target_box=grid_box(f.grid)) as P:
+        e, n = band_check(f, P, f.grid.ny // 2 - 40, 80)
+        mp, st = P.ipm_map(f.grid, f.box, f.npx, f.npy, bbox_cap=64)
+    print("C3 band map: mean rel err %.2e over %d pixels" % (e, n))
+    assert ledger_ok(st)
+    assert abs(mp.sum().item() * (100.0 / 4096) ** 2 - st["area_in_map"]) <= 1e-6 * st["area_total"]
+    assert st["rays"] >= (f.grid.nx + 1) * (f.grid.ny + 1)
+
+
+@pytest.fixture(scope="module")
+def c4():
+    return synth.c4_critical(seed=0)
+
+
+def test_critical_curve_deflections_and_band(c4):
+    f = c4
+    idx, x = synth.subsample_grid_rays(12, f.grid, 2048)
+    y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x)
+    with lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=16, leaf_size=8,
+                      prec=lens.FP32_BULK, target_box=grid_box(f.grid)) as P:
+        y = P.deflect(T(x)).cpu().numpy()
+        e = alpha_rel_err(y, y_ref, x, f.kappa_s, f.gamma)
+        print("C4 sampled: max %.2e" % e.max())
+        assert e.max() < 2e-5
+        eb, n = band_check(f, P, f.grid.ny // 2, 4)
+        print("C4 band map (4 x %d cells): mean rel err %.2e over %d pixels" % (f.grid.nx, eb, n))
+
+
+def test_critical_curve_full_map(c4):
+    # ~2.2e10 cells, split into chunks by free device memory
+    f = c4
+    with lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=16, leaf_size=8,
+                      prec=lens.FP32_BULK, target_box=grid_box(f.grid)) as P:
+        mp, st = P.ipm_map(f.grid, f.box, f.npx, f.npy, bbox_cap=64)
+    assert st["chunks"] >= 2
+    assert ledger_ok(st)
+    assert abs(mp.sum().item() * (2.0 / 8192) ** 2 - st["area_in_map"]) <= 1e-6 * st["area_total"]
+    mu = 1.0 / abs((1 - 0.82) ** 2 - 0.17 ** 2)
+    print("C4: %d chunks, %.3g cells, interior mean magnification %.2f (macro %.2f)"
+          % (st["chunks"], st["cells"], mp[512:-512, 512:-512].mean().item(), mu))
+
+
+def test_critical_curve_mean_magnification(c4):
+    # The workload's shooting region (3% margin) misses rays that stars
+    # deflect into the map: in the direction compressed by |1-k-g| = 0.01 a
+    # source-plane deflection of ~0.3 ER is ~30 ER in the image plane.  With
+    # margins of ~3 |alpha|_rms / |1 -+ k - g| on both axes (and coarser cells,
+    # 0.06 per unlensed pixel) the interior mean returns to the macro value.
+    f = c4
+    h = 1e-3
+    g = synth.shooting_grid(0.82, 0.17, 1.0, h, margin_frac=1.0, margin_min=3.0)
+    with lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=16, leaf_size=8,
+                      prec=lens.FP32_BULK, target_box=grid_box(g)) as P:
+        mp, st = P.ipm_map(g, f.box, 2048, 2048, bbox_cap=64)
+    assert ledger_ok(st)
+    mu = 1.0 / abs((1 - 0.82) ** 2 - 0.17 ** 2)
+    inner = mp[128:-128, 128:-128].mean().item()
+    print("C4 wide margins: %.3g cells, interior mean magnification %.2f (macro %.2f)"
+          % (st["cells"], inner, mu))
+    assert abs(inner / mu - 1) < 0.05
+
+
+def test_nfw_halo_deflections():
+    f = synth.nfw_halo(seed=0)
+    g = f.grid
+    idx, x = synth.subsample_grid_rays(13, g, 384)
+    y_ref = oracle.deflect(f.stars, f.masses, 0.0, 0.0, x)
+    with lens.LensFMM(T(f.stars), T(f.masses), 0.0, 0.0, p=16, leaf_size=16,
+                      prec=lens.FP32_BULK, target_box=grid_box(g)) as P:
+        yg = P.deflect_grid(g)
+        y = yg.cpu().numpy()[idx[:, 1], idx[:, 0]]
+        info = P.info()
+    e = alpha_rel_err(y, y_ref, x, 0.0, 0.0)
+    print("NFW 1e7 particles: %d levels, grid max err %.2e" % (info["levels"], e.max()))
+    assert yg.shape[:2] == (g.ny + 1, g.nx + 1)
+    assert e.max() < 2e-5
+
+
+def test_differentiation_workload_gradients():
+    # full differentiation workload: 1e5 stars, 6000 x 500 cells of rays,
+    # 2048-sample Gaussian light curve (sigma 0.05 ER) against the curve of a
+    # perturbed field; gradients by the adjoint FMM vs central differences
+    f = synth.c5_differentiable(seed=0)
+    g = f.grid
+    rays = T(g.corners().reshape(-1, 2))
+    s = T(synth.light_curve_track(2048, length=5.0))
+    sig, w = 0.05, g.h ** 2
+    box = grid_box(g)
+    ft = synth.perturbed(f, seed=1, sd=0.01)
+    with torch.no_grad():
+        yt = autograd.deflect(T(ft.stars), T(ft.masses), ft.kappa_s, ft.gamma, rays, p=32,
+                              leaf_size=16, target_box=box)
+        Tk = lens.light_curve(yt, w, s, sig)
+
+    def loss(st, ms, k_, g_, prec=lens.FP64):
+        y = autograd.deflect(st, ms, k_, g_, rays, p=32, leaf_size=16, prec=prec, target_box=box)
+        return ((autograd.light_curve(y, w, s, sig) - Tk) ** 2).sum()
+
+    stars = T(f.stars).requires_grad_(True)
+    masses = T(f.masses).requires_grad_(True)
+    ks = torch.tensor(f.kappa_s, dtype=torch.float64, device="cuda", requires_grad=True)
+    gm = torch.tensor(f.gamma, dtype=torch.float64, device="cuda", requires_grad=True)
+    L0 = loss(stars, masses, ks, gm)
+    L0.backward()
+    assert L0.item() > 0
+    # the float32-bulk forward with the same float64 adjoint
+    st32 = T(f.stars).requires_grad_(True)
+    loss(st32, T(f.masses), f.kappa_s, f.gamma, prec=lens.FP32_BULK).backward()
+    inside = np.nonzero((np.abs(f.stars[:, 0]) < 28) & (np.abs(f.stars[:, 1]) < 2.3))[0]
+    gs = stars.grad.cpu().numpy()
+    assert np.linalg.norm(st32.grad.cpu().numpy()[inside] - gs[inside]) <= 1e-3 * np.linalg.norm(gs[inside])
+    h = 1e-5
+    rng = np.random.default_rng(3)
+    with torch.no_grad():
+        for j in rng.choice(inside, 4, replace=False):
+            for c in range(2):
+                sp = stars.detach().clone(); sp[j, c] += h
+                sm = stars.detach().clone(); sm[j, c] -= h
+                fd = (loss(sp, masses.detach(), f.kappa_s, f.gamma) -
+                      loss(sm, masses.detach(), f.kappa_s, f.gamma)).item() / (2 * h)
+                assert gs[j, c] == pytest.approx(fd, rel=1e-5, abs=1e-6 * np.abs(gs).max())
+            mp = masses.detach().clone(); mp[j] += h
+            mm = masses.detach().clone(); mm[j] -= h
+            fd = (loss(stars.detach(), mp, f.kappa_s, f.gamma) -
+                  loss(stars.detach(), mm, f.kappa_s, f.gamma)).item() / (2 * h)
+            assert masses.grad[j].item() == pytest.approx(fd, rel=1e-5, abs=1e-6 * np.abs(gs).max())
+        for var, grad in ((0, ks.grad), (1, gm.grad)):
+            kp = [f.kappa_s, f.gamma]
+            km = list(kp)
+            kp[var] += h
+            km[var] -= h
+            fd = (loss(stars.detach(), masses.detach(), kp[0], kp[1]) -
+                  loss(stars.detach(), masses.detach(), km[0], km[1])).item() / (2 * h)
+            assert grad.item() == pytest.approx(fd, rel=1e-5)
