@@ -72,7 +72,7 @@ __global__ void k_p2m(const double2* __restrict__ spos, const double* __restrict
   for (int k = 0; k <= p; ++k) out[k] = a[k * st];
 }
 
-// ---- M2M: one thread per internal box of a level ---------------------------
+// ---- M2M: one thread per (internal box, coefficient) of a level -------------
 // The four child offsets are d_q = w i^m_q with w = (1+i)/2 and m_q = 2, 3,
 // 1, 0 for quadrants (-,-), (+,-), (-,+), (+,+).  Since d_q^(l-k) depends on
 // q only through i^(m_q (l-k)), which repeats with period 4 in l-k,
@@ -80,44 +80,47 @@ __global__ void k_p2m(const double2* __restrict__ spos, const double* __restrict
 //   G_r[k] = sum_m i^(m r) A^(child m)_k      (a 4-point DFT over quadrants:
 //                                              additions only),
 // one REAL binomial matrix on four complex vectors instead of four complex
-// matrices: about a third of the float64 operations of the direct form, and
-// every thread runs the same loop bounds (no idle lanes).  w^k and
-// conj(w)^k are exact, so the rounding is that of the direct form.
-constexpr int kM2MThreads = 32;
+// matrices: about a third of the float64 operations of the direct form.
+// w^k and conj(w)^k are exact, so the rounding is that of the direct form.
+// Thread (parent, k) forms the four H_r[k] = conj(w)^k G_r[k], then thread
+// (parent, l) sums row l: many short float64 chains instead of one long one
+// per parent, so the pipe is fed from many warps.
+constexpr int kM2MThreads = 128;
 
 __global__ void __launch_bounds__(kM2MThreads)
 k_m2m(const int* __restrict__ child, int64_t b0, int64_t b1, int p,
       const double* __restrict__ binom, int ldb, const double2* __restrict__ wpow,
       double2* __restrict__ M) {
-  extern __shared__ double2 H[];  // [4][p+1][kM2MThreads]
-  const int t = threadIdx.x;
-  const int64_t b = b0 + blockIdx.x * (int64_t)kM2MThreads + t;
-  if (b >= b1) return;
-  const int c0 = child[b];
-  if (c0 < 0) return;
+  extern __shared__ double2 H[];  // [parents per block][4][p+1]
   const int P1 = p + 1;
-  const double2* A = M + (int64_t)c0 * P1;  // children c0..c0+3 are contiguous
-  for (int k = 0; k <= p; ++k) {
+  const int per = kM2MThreads / P1;  // parents per block (>= 1 for p <= 64)
+  const int t = threadIdx.x, pb = t / P1, k = t - pb * P1;
+  const int64_t b = b0 + (int64_t)blockIdx.x * per + pb;
+  const bool on = pb < per && b < b1 && child[b] >= 0;
+  double2* Hp = H + (int64_t)pb * 4 * P1;
+  if (on) {
+    const double2* A = M + (int64_t)child[b] * P1;  // children c0..c0+3 are contiguous
     const double2 B0 = ld2(A + 3 * P1 + k), B1 = ld2(A + 2 * P1 + k);
     const double2 B2 = ld2(A + k), B3 = ld2(A + P1 + k);
     const double2 s02 = B0 + B2, d02 = B0 - B2, s13 = B1 + B3, d13 = B1 - B3;
     double2 w = ld2(wpow + k);
     w.y = -w.y;
-    H[(0 * P1 + k) * kM2MThreads + t] = cmul(w, s02 + s13);
-    H[(1 * P1 + k) * kM2MThreads + t] = cmul(w, make_double2(d02.x - d13.y, d02.y + d13.x));
-    H[(2 * P1 + k) * kM2MThreads + t] = cmul(w, s02 - s13);
-    H[(3 * P1 + k) * kM2MThreads + t] = cmul(w, make_double2(d02.x + d13.y, d02.y - d13.x));
+    Hp[0 * P1 + k] = cmul(w, s02 + s13);
+    Hp[1 * P1 + k] = cmul(w, make_double2(d02.x - d13.y, d02.y + d13.x));
+    Hp[2 * P1 + k] = cmul(w, s02 - s13);
+    Hp[3 * P1 + k] = cmul(w, make_double2(d02.x + d13.y, d02.y - d13.x));
   }
-  double2* out = M + b * (int64_t)P1;
-  for (int l = 0; l <= p; ++l) {
+  __syncthreads();
+  if (on) {
+    const int l = k;
     double sx = 0.0, sy = 0.0;
-    for (int k = 0; k <= l; ++k) {
-      const double c = __ldg(binom + (int64_t)l * ldb + k);
-      const double2 h = H[(((l - k) & 3) * P1 + k) * kM2MThreads + t];
+    for (int kk = 0; kk <= l; ++kk) {
+      const double c = __ldg(binom + (int64_t)l * ldb + kk);
+      const double2 h = Hp[((l - kk) & 3) * P1 + kk];
       sx = fma(c, h.x, sx);
       sy = fma(c, h.y, sy);
     }
-    out[l] = cmul(ld2(wpow + l), make_double2(sx, sy));
+    M[b * (int64_t)P1 + l] = cmul(ld2(wpow + l), make_double2(sx, sy));
   }
 }
 
@@ -399,13 +402,13 @@ void fmm_p2m(Plan& P, cudaStream_t s) {
 
 void fmm_m2m(Plan& P, cudaStream_t s) {
   const FmmTables& t = P.tab;
-  const size_t smem = sizeof(double2) * 4 * (size_t)(P.p + 1) * kM2MThreads;
-  if (smem > 48 * 1024)
-    LENS_CUDA(cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int P1 = P.p + 1;
+  const int per = kM2MThreads / P1;
+  const size_t smem = sizeof(double2) * 4 * (size_t)P1 * per;
   for (int l = P.nlevels - 2; l >= 0; --l) {
     const int64_t b0 = P.level_off[l], b1 = P.level_off[l + 1];
-    k_m2m<<<grid_for(b1 - b0, kM2MThreads), kM2MThreads, smem, s>>>(P.box_child, b0, b1, P.p,
-                                                                     t.binom, t.ldb, t.wpow, P.M);
+    k_m2m<<<grid_for(b1 - b0, per), kM2MThreads, smem, s>>>(P.box_child, b0, b1, P.p, t.binom,
+                                                             t.ldb, t.wpow, P.M);
     LENS_LAUNCHED("k_m2m");
   }
 }
