@@ -123,7 +123,7 @@ typedef struct {
   int levels, p, leaf_size, prec;
   double root_lo[2], root_size;
   int64_t device_bytes;        /* plan-owned device memory */
-  double ms_build;             /* device time of the last build */
+  double ms_build;             /* device time of the build, tree to expansions */
   int64_t build_launches;      /* kernels the build launched */
 } lens_plan_info;
 
@@ -137,7 +137,13 @@ typedef struct {
  *   stars_xy: dev, n x 2; masses: dev, n (any real values); n >= 1.
  *   kappa_s, gamma: smooth field (footnote to Eq. 1).
  *   opts: host; allocator: host or NULL (cudaMallocAsync on stream).
- *   *out receives the plan.  Synchronises `stream` once (tree size).
+ *   *out receives the plan.  Synchronises `stream` a few times (tree and
+ *   list sizes).  The tree and lists are formed on `stream`; the expansions
+ *   then run on a high-priority stream owned by the plan, and the call
+ *   returns without waiting for them: every later call with this plan, on
+ *   any stream, waits for the part it reads (evaluations for the
+ *   expansions, the adjoint for the tree alone), and lens_plan_info_get and
+ *   lens_plan_destroy wait for all of it.
  * Errors: EINVAL (n < 1, p outside 1..64, leaf_size outside 1..1024,
  * non-finite star or mass, bad target box), ENOMEM, ECUDA, EDEPTH. */
 lens_status lens_fmm_build(const double* stars_xy, const double* masses,

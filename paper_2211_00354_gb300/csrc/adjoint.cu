@@ -329,6 +329,7 @@ __global__ void k_adj_out(const double2* Phi, const double2* Psi, const uint32_t
 void adjoint(Plan& P, const double* rays, int64_t m, const double* gy, double* gxy, double* gm,
              double* gkg, cudaStream_t s) {
   const int P1 = P.p + 1;
+  wait_tree(P, s);  // the transposed operators need the tree, not the expansions
   if (gkg) LENS_CUDA(cudaMemsetAsync(gkg, 0, sizeof(double) * 2, s));
   if (m == 0) {
     if (gm) LENS_CUDA(cudaMemsetAsync(gm, 0, sizeof(double) * P.n, s));

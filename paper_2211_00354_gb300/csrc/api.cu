@@ -135,6 +135,13 @@ void check_grid(const Plan& P, const lens_grid* g) {
 }
 }  // namespace
 
+void lens::wait_expansions(Plan& P, cudaStream_t s) {
+  if (P.ev_fmm) LENS_CUDA(cudaStreamWaitEvent(s, P.ev_fmm, 0));
+}
+void lens::wait_tree(Plan& P, cudaStream_t s) {
+  if (P.ev_tree) LENS_CUDA(cudaStreamWaitEvent(s, P.ev_tree, 0));
+}
+
 extern "C" {
 
 const char* lens_last_error(void) { return g_last_error.c_str(); }
@@ -180,25 +187,33 @@ lens_status lens_fmm_build(const double* stars_xy, const double* masses, int64_t
   P.gamma = gamma;
   P.has_target = opts->has_target_box != 0;
   if (P.has_target) std::memcpy(P.target, opts->target_box, sizeof(P.target));
-  cudaEvent_t e0, e1;
-  LENS_CUDA(cudaEventCreate(&e0));
-  LENS_CUDA(cudaEventCreate(&e1));
-  LENS_CUDA(cudaEventRecord(e0, S(stream)));
+  LENS_CUDA(cudaEventCreate(&P.ev_start));
+  LENS_CUDA(cudaEventCreate(&P.ev_tree));
+  LENS_CUDA(cudaEventCreate(&P.ev_fmm));
+  LENS_CUDA(cudaEventRecord(P.ev_start, S(stream)));
   const long long l0 = launch_count();
+  // tree, lists and everything that needs only them, on the caller's stream
   tree_build(P, stars_xy, masses, S(stream));
   fmm_tables(P, S(stream));
-  fmm_p2m(P, S(stream));
-  fmm_m2m(P, S(stream));
-  fmm_downward(P, S(stream));
-  if (P.prec == LENS_FP32_BULK) eval32_prepare(P, S(stream));
-  LENS_CUDA(cudaEventRecord(e1, S(stream)));
-  LENS_CUDA(cudaEventSynchronize(e1));
-  float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  P.ms_build = ms;
+  P.M = P.dalloc_n<double2>((size_t)P.nb * (P.p + 1));
+  P.L = P.dalloc_n<double2>((size_t)P.nb * (P.p + 1));
+  if (P.prec == LENS_FP32_BULK) {
+    eval32_alloc(P);
+    eval32_prepare_tree(P, S(stream));
+  }
+  LENS_CUDA(cudaEventRecord(P.ev_tree, S(stream)));
+  // the expansions on the plan's high-priority stream: the caller's next
+  // near-field work overlaps them (float64 pipe here, float32 there)
+  int lo_prio = 0, hi_prio = 0;
+  LENS_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+  LENS_CUDA(cudaStreamCreateWithPriority(&P.fmm_stream, cudaStreamNonBlocking, hi_prio));
+  LENS_CUDA(cudaStreamWaitEvent(P.fmm_stream, P.ev_tree, 0));
+  fmm_p2m(P, P.fmm_stream);
+  fmm_m2m(P, P.fmm_stream);
+  fmm_downward(P, P.fmm_stream);
+  if (P.prec == LENS_FP32_BULK) eval32_prepare_expansions(P, P.fmm_stream);
+  LENS_CUDA(cudaEventRecord(P.ev_fmm, P.fmm_stream));
   P.build_launches = launch_count() - l0;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   *out = plan;
   plan = nullptr;
   }
@@ -224,6 +239,9 @@ void lens_plan_destroy(lens_plan* plan) {
   for (void* p : P.owned) P.da.release(p);
   cudaStreamSynchronize(P.da.stream);
   P.ev_clear();
+  if (P.fmm_stream) cudaStreamDestroy(P.fmm_stream);
+  for (cudaEvent_t e : {P.ev_start, P.ev_tree, P.ev_fmm})
+    if (e) cudaEventDestroy(e);
   delete plan;
 }
 
@@ -243,7 +261,13 @@ lens_status lens_plan_info_get(const lens_plan* plan, lens_plan_info* info) {
   info->root_lo[0] = P.root_lo[0]; info->root_lo[1] = P.root_lo[1];
   info->root_size = P.root_size;
   info->device_bytes = P.device_bytes;
-  info->ms_build = P.ms_build;
+  // the expansions may still be running on the plan's stream
+  float ms = 0.f;
+  if (P.ev_fmm) {
+    LENS_CUDA(cudaEventSynchronize(P.ev_fmm));
+    LENS_CUDA(cudaEventElapsedTime(&ms, P.ev_start, P.ev_fmm));
+  }
+  info->ms_build = ms;
   info->build_launches = P.build_launches;
   info->n_leaves = -1;  // not tracked separately (n_active_leaves is)
   LENS_API_END

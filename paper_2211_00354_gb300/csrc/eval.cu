@@ -586,6 +586,7 @@ void grid_impl(Plan& P, const GridRows& g, double* y, double* jac, PixCorner* pi
     eval32_grid(P, g, rect.as<int64_t>(), toff.as<int64_t>(), total, y, jac, pix, ip, s);
     return;
   }
+  wait_expansions(P, s);
   EvalArgs A = base_args(P);
   A.tile_off = toff.as<int64_t>();
   A.rect = rect.as<int64_t>();
@@ -660,6 +661,7 @@ void evaluate_rays(Plan& P, const double* rays, int64_t m, double* y, double* ja
                 jac, s);
     return;
   }
+  wait_expansions(P, s);
   EvalArgs A = base_args(P);
   A.tile_off = B.toff.as<int64_t>();
   A.rays = rays; A.ray_off = B.off.as<int64_t>(); A.perm = B.perm.as<int>();

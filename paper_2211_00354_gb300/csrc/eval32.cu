@@ -383,25 +383,36 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
 }
 
 // ---- plan-time preparation ---------------------------------------------------
-__global__ void k_prep_leaf(const int* __restrict__ leaves, int64_t nl, const int* __restrict__ aidx,
-                            const int* __restrict__ level, const int* __restrict__ ix,
-                            const int* __restrict__ iy, double lo_x, double lo_y, double size,
-                            double a, double b, int p, const double2* __restrict__ L,
-                            LeafPlan* __restrict__ out, float2* __restrict__ fL) {
+// per active leaf: centre, 1/r, r (the tree alone)
+__global__ void k_prep_leaf_geo(const int* __restrict__ leaves, int64_t nl,
+                                const int* __restrict__ level, const int* __restrict__ ix,
+                                const int* __restrict__ iy, double lo_x, double lo_y, double size,
+                                LeafPlan* __restrict__ out) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nl) return;
   const int B = leaves[k];
   const double r = size / (double)(2ull << level[B]);
-  const double cx = lo_x + (2.0 * ix[B] + 1.0) * r, cy = lo_y + (2.0 * iy[B] + 1.0) * r;
-  const double2* Lb = L + (int64_t)B * (p + 1);
-  const double2 b0 = Lb[0];
   LeafPlan lp;
-  lp.cx = cx; lp.cy = cy;
-  lp.K1 = a * cx - b0.x;
-  lp.K2 = b * cy + b0.y;
+  lp.cx = lo_x + (2.0 * ix[B] + 1.0) * r;
+  lp.cy = lo_y + (2.0 * iy[B] + 1.0) * r;
+  lp.K1 = 0.0; lp.K2 = 0.0;
   lp.ir = (float)(1.0 / r);
   lp.r = (float)r;
   out[k] = lp;
+}
+
+// per active leaf: the lens equation at the centre with the constant term of
+// the local expansion, and the float32 local coefficients (the expansions)
+__global__ void k_prep_leaf_exp(const int* __restrict__ leaves, int64_t nl, double a, double b,
+                                int p, const double2* __restrict__ L, LeafPlan* __restrict__ out,
+                                float2* __restrict__ fL) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nl) return;
+  const int B = leaves[k];
+  const double2* Lb = L + (int64_t)B * (p + 1);
+  const double2 b0 = Lb[0];
+  out[k].K1 = a * out[k].cx - b0.x;
+  out[k].K2 = b * out[k].cy + b0.y;
   for (int l = 0; l <= p; ++l) fL[k * (int64_t)(p + 1) + l] = make_float2((float)Lb[l].x, (float)Lb[l].y);
 }
 
@@ -474,27 +485,34 @@ __global__ void k_to_f32(const double2* __restrict__ in, int64_t n, float2* __re
 }
 
 // ---- per-call grid constants -------------------------------------------------
+// Per-call leaf constants on the grid path.  parts & 1: the offset of the
+// leaf's first grid ray from its centre (the tree alone); parts & 2: the
+// pixel reference of the centre on the map path (needs the expansions).
 __global__ void k_leaf_grid(int64_t nl, const LeafPlan* __restrict__ lp, const int64_t* __restrict__ rect,
-                            double x0, double y0, double h, int pix, double inv_du, double u_off,
+                            double x0, double y0, double h, int parts, double inv_du, double u_off,
                             double inv_dv, double v_off, LeafGrid* __restrict__ out) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nl) return;
   const LeafPlan L = lp[k];
-  LeafGrid g{};
-  const double xi = __dadd_rn(x0, __dmul_rn((double)rect[4 * k], h));
-  const double yj = __dadd_rn(y0, __dmul_rn((double)rect[4 * k + 2], h));
-  g.bx = ff_of(xi - L.cx);
-  g.by = ff_of(yj - L.cy);
-  if (pix) {
+  if (parts & 1) {
+    const double xi = __dadd_rn(x0, __dmul_rn((double)rect[4 * k], h));
+    const double yj = __dadd_rn(y0, __dmul_rn((double)rect[4 * k + 2], h));
+    out[k].bx = ff_of(xi - L.cx);
+    out[k].by = ff_of(yj - L.cy);
+  }
+  if (parts & 2) {
     const double U1 = fma(L.K1, inv_du, u_off), V1 = fma(L.K2, inv_dv, v_off);
-    g.far = !(fabs(U1) < 1073741824.0 && fabs(V1) < 1073741824.0);
-    if (!g.far) {
+    const int far = !(fabs(U1) < 1073741824.0 && fabs(V1) < 1073741824.0);
+    out[k].far = far;
+    if (!far) {
       const double fu = floor(U1), fv = floor(V1);
-      g.U1i = (int)fu; g.V1i = (int)fv;
-      g.U1f = ff_of(U1 - fu); g.V1f = ff_of(V1 - fv);
+      out[k].U1i = (int)fu; out[k].V1i = (int)fv;
+      out[k].U1f = ff_of(U1 - fu); out[k].V1f = ff_of(V1 - fv);
+    } else {
+      out[k].U1i = 0; out[k].V1i = 0;
+      out[k].U1f = ff{0.f, 0.f}; out[k].V1f = ff{0.f, 0.f};
     }
   }
-  out[k] = g;
 }
 
 E32Args base_args32(Plan& P) {
@@ -524,7 +542,7 @@ void launch32(E32Args& A, int64_t total, bool jac, cudaStream_t s) {
 
 }  // namespace
 
-void eval32_prepare(Plan& P, cudaStream_t s) {
+void eval32_alloc(Plan& P) {
   const int64_t nl = P.n_active_leaves;
   const int P1 = P.p + 1;
   P.f_leaf = P.dalloc_n<LeafPlan>(nl);
@@ -534,13 +552,16 @@ void eval32_prepare(Plan& P, cudaStream_t s) {
   P.f_woff = P.dalloc_n<int64_t>(nl + 1);
   P.f_ncnt = P.dalloc_n<int64_t>(nl + 1);
   P.f_wcnt = P.dalloc_n<int64_t>(nl + 1);
+}
+
+void eval32_prepare_tree(Plan& P, cudaStream_t s) {
+  const int64_t nl = P.n_active_leaves;
   if (nl == 0) return;
-  const double a = 1.0 - P.kappa_s - P.gamma, b = 1.0 - P.kappa_s + P.gamma;
   const int wmax = w_direct_max(P.p);
-  k_prep_leaf<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx, P.box_level,
-                                                P.box_ix, P.box_iy, P.root_lo[0], P.root_lo[1],
-                                                P.root_size, a, b, P.p, P.L, P.f_leaf, P.f_L);
-  LENS_LAUNCHED("k_prep_leaf");
+  k_prep_leaf_geo<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_level, P.box_ix,
+                                                    P.box_iy, P.root_lo[0], P.root_lo[1],
+                                                    P.root_size, P.f_leaf);
+  LENS_LAUNCHED("k_prep_leaf_geo");
   LENS_CUDA(cudaMemsetAsync(P.f_ncnt, 0, sizeof(int64_t) * (nl + 1), s));
   LENS_CUDA(cudaMemsetAsync(P.f_wcnt, 0, sizeof(int64_t) * (nl + 1), s));
   k_prep_counts<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx, P.W_off,
@@ -563,6 +584,17 @@ void eval32_prepare(Plan& P, cudaStream_t s) {
       P.root_size, P.spos, P.smass, wmax, P.f_uoff, P.f_woff, P.f_ust, P.f_um, P.f_wlist,
       P.f_wgeo);
   LENS_LAUNCHED("k_prep_lists");
+}
+
+void eval32_prepare_expansions(Plan& P, cudaStream_t s) {
+  const int64_t nl = P.n_active_leaves;
+  const int P1 = P.p + 1;
+  const double a = 1.0 - P.kappa_s - P.gamma, b = 1.0 - P.kappa_s + P.gamma;
+  if (nl > 0) {
+    k_prep_leaf_exp<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, a, b, P.p, P.L,
+                                                      P.f_leaf, P.f_L);
+    LENS_LAUNCHED("k_prep_leaf_exp");
+  }
   k_to_f32<<<grid_for((int64_t)P.nb * P1, 256, 152 * 16), 256, 0, s>>>(P.M, (int64_t)P.nb * P1,
                                                                        P.f_M);
   LENS_LAUNCHED("k_to_f32");
@@ -574,11 +606,13 @@ void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t*
   const int64_t nl = P.n_active_leaves;
   Scratch lg(&P.da, sizeof(LeafGrid) * (nl + 1));
   const bool px = pix != nullptr;
-  k_leaf_grid<<<grid_for(nl, 128), 128, 0, s>>>(
-      nl, P.f_leaf, rect, g.x0, g.y0, g.h, px ? 1 : 0, px ? ip->inv_du : 0.0,
-      px ? -ip->u0 * ip->inv_du : 0.0, px ? ip->inv_dv : 0.0, px ? -ip->v0 * ip->inv_dv : 0.0,
-      lg.as<LeafGrid>());
-  LENS_LAUNCHED("k_leaf_grid");
+  auto leaf_grid = [&](int parts) {
+    k_leaf_grid<<<grid_for(nl, 128), 128, 0, s>>>(
+        nl, P.f_leaf, rect, g.x0, g.y0, g.h, parts, px ? ip->inv_du : 0.0,
+        px ? -ip->u0 * ip->inv_du : 0.0, px ? ip->inv_dv : 0.0, px ? -ip->v0 * ip->inv_dv : 0.0,
+        lg.as<LeafGrid>());
+    LENS_LAUNCHED("k_leaf_grid");
+  };
   E32Args A = base_args32(P);
   A.tile_off = toff;
   A.rect = rect;
@@ -590,6 +624,8 @@ void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t*
   if (px) { A.iduf = ff_of(ip->inv_du); A.idvf = ff_of(ip->inv_dv); }
   std::pair<cudaEvent_t, cudaEvent_t> e;
   if (P.timing) e = event_pair_begin(s);
+  wait_expansions(P, s);
+  leaf_grid(px ? 3 : 1);
   if (px) launch32<true, true>(A, total, false, s);
   else launch32<true, false>(A, total, jac != nullptr, s);
   if (P.timing) {
@@ -600,6 +636,7 @@ void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t*
 
 void eval32_rays(Plan& P, const double* rays, const int64_t* off, const int* perm,
                  const int64_t* toff, int64_t total, double* y, double* jac, cudaStream_t s) {
+  wait_expansions(P, s);
   E32Args A = base_args32(P);
   A.tile_off = toff;
   A.rays = rays; A.ray_off = off; A.perm = perm;

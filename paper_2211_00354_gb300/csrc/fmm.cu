@@ -387,7 +387,7 @@ void fmm_tables(Plan& P, cudaStream_t s) {
 
 void fmm_p2m(Plan& P, cudaStream_t s) {
   const int p = P.p, P1 = p + 1;
-  P.M = P.dalloc_n<double2>((size_t)P.nb * P1);
+  if (!P.M) P.M = P.dalloc_n<double2>((size_t)P.nb * P1);
   // P2M on every leaf (thread per box), all levels at once
   const int tpb = 32;
   const size_t smem = sizeof(double2) * (size_t)P1 * tpb;
@@ -415,7 +415,7 @@ void fmm_m2m(Plan& P, cudaStream_t s) {
 
 void fmm_downward(Plan& P, cudaStream_t s) {
   const FmmTables& t = P.tab;
-  P.L = P.dalloc_n<double2>((size_t)P.nb * (P.p + 1));
+  if (!P.L) P.L = P.dalloc_n<double2>((size_t)P.nb * (P.p + 1));
   DownArgs A{};
   A.active = P.active;
   A.parent = P.box_parent; A.child = P.box_child; A.level = P.box_level;

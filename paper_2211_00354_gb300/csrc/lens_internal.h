@@ -172,6 +172,14 @@ struct Plan {
   double ms_build = 0;
   int64_t build_launches = 0;
 
+  // The expansions (P2M, M2M, downward pass, their float32 copies) run on a
+  // high-priority stream of the plan after the tree; ev_fmm marks their end.
+  // Work that reads M or L waits on ev_fmm (wait_expansions); the near field
+  // needs only the tree and runs meanwhile.
+  cudaStream_t fmm_stream = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_tree = nullptr, ev_fmm = nullptr;
+  bool build_timed = false;
+
   // per-active-index count of stars in the U list (work accounting)
   int64_t* ustar_cnt = nullptr;
   // optional kernel timing and work counters (lens_ipm_map turns them on)
@@ -247,7 +255,17 @@ void evaluate_grid_pix(Plan& P, const GridRows& g, PixCorner* out, const IpmPara
 void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const IpmParams& ip,
                     float* map32, float* rowdiff, double* stats_dev, int* queue, int* qcount,
                     cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev);
-void eval32_prepare(Plan& P, cudaStream_t s);
+// float32 evaluation data that needs only the tree (leaf geometry, staged
+// near-field stars, far W boxes), and the part that needs the expansions
+// (constants of the lens equation per leaf, float32 copies of L and M);
+// eval32_alloc reserves both before the expansions start
+void eval32_alloc(Plan& P);
+void eval32_prepare_tree(Plan& P, cudaStream_t s);
+void eval32_prepare_expansions(Plan& P, cudaStream_t s);
+// make stream s wait for the plan's expansions (which implies its tree), or
+// for its tree and tree-only data alone
+void wait_expansions(Plan& P, cudaStream_t s);
+void wait_tree(Plan& P, cudaStream_t s);
 void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t* toff,
                  int64_t total, double* y, double* jac, PixCorner* pix, const IpmParams* ip,
                  cudaStream_t s);

@@ -150,6 +150,29 @@ def test_rays_exactly_on_stars(prec, tol):
     assert (d / sc).max() < (1e-8 if prec == lens.FP64 else 2e-4)
 
 
+def test_evaluation_on_another_stream_waits_for_the_build():
+    # the expansions finish on the plan's own stream after the build returns;
+    # calls on any stream wait for them (and the adjoint for the tree)
+    f = synth.config_uniform(seed=5, n=20000, kappa_star=0.4, kappa_s=0.1, gamma=0.2)
+    x = synth.random_rays(6, 50000, (-20, -20), (20, 20))
+    box = (-20, 20, -20, 20)
+    xs = T(x)
+    gy = T(np.random.default_rng(2).normal(size=x.shape))
+    ref = {}
+    for prec in (lens.FP32_BULK, lens.FP64):
+        with plan_for(f, 24, 8, prec, box) as P:
+            ref[prec] = (P.deflect(xs).cpu().numpy(), P.adjoint(xs, gy)[0].cpu().numpy())
+        s2 = torch.cuda.Stream()
+        with plan_for(f, 24, 8, prec, box) as P:
+            with torch.cuda.stream(s2):
+                y2 = P.deflect(xs, stream=s2)
+                g2 = P.adjoint(xs, gy, stream=s2)[0]
+            s2.synchronize()
+            np.testing.assert_array_equal(y2.cpu().numpy(), ref[prec][0])
+            np.testing.assert_allclose(g2.cpu().numpy(), ref[prec][1], rtol=1e-12, atol=1e-12)
+            assert P.info()["ms_build"] > 0
+
+
 def test_tiny_fields():
     for n, leaf in ((1, 16), (5, 16), (40, 1), (17, 16)):
         f = synth.config_uniform(seed=n, n=n, kappa_star=0.3, kappa_s=0.0, gamma=0.1)
