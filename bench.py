@@ -331,6 +331,30 @@ def main():
         extra["error_vs_gpu_direct_fp64"] = {"max": float(err.max()),
                                              "p99.9": float(torch.quantile(err, 0.999)),
                                              "rays": 4096}
+
+        def rel_err(yy):
+            e = (yy - y_ref).norm(dim=1) / torch.clamp(mag, min=1e-3 * mag.pow(2).mean().sqrt())
+            return float(e.max())
+
+        # the FP64 form of the FMM (order 32) on the same field: plan build +
+        # deflection of a 512-row band of the workload grid (device time),
+        # and its error on the same 4096 corners
+        band = ldist.strip_grid(g, g.ny // 2 - 256, 512)
+        P64 = lens.LensFMM(stars, masses, f.kappa_s, f.gamma, p=32, leaf_size=args.leaf,
+                           prec=lens.FP64, target_box=target)
+        build64 = P64.info()["ms_build"]
+        P64.deflect_grid(band, nrows=8)  # warm-up
+        t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        P64.deflect_grid(band)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        y64 = P64.deflect(xs_t)
+        P64.close()
+        extra["fmm_fp64"] = {"p": 32, "deflect_rays_per_s": band.n_rays / (t0.elapsed_time(t1) / 1e3),
+                             "rays": band.n_rays, "build_ms": build64,
+                             "error_vs_gpu_direct_fp64_max": rel_err(y64)}
         # GPU direct-sum throughput on the same workload (FP32 and FP64 forms)
         _, xd = synth.subsample_grid_rays(args.seed + 8, g, 1 << 19)
         xd_t = torch.tensor(xd, device=dev)
