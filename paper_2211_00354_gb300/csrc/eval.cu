@@ -57,39 +57,18 @@ __device__ __forceinline__ double grid_coord(double x0, int64_t i, double h) {
   return __dadd_rn(x0, __dmul_rn((double)i, h));
 }
 
-template <typename R> struct Acc;
-template <> struct Acc<float> {
-  fcomp v;
-  __device__ __forceinline__ void zero() { v.hi = 0.f; v.lo = 0.f; }
-  __device__ __forceinline__ void add(float x) { v.add(x); }
-  __device__ __forceinline__ double value() const { return v.value(); }
-};
-template <> struct Acc<double> {
-  double v;
-  __device__ __forceinline__ void zero() { v = 0.0; }
-  __device__ __forceinline__ void add(double x) { v += x; }
-  __device__ __forceinline__ double value() const { return v; }
-};
-
-template <typename R> __device__ __forceinline__ R rcp_r(R x);
-template <> __device__ __forceinline__ float rcp_r<float>(float x) { return frcp_fast(x); }
-template <> __device__ __forceinline__ double rcp_r<double>(double x) { return 1.0 / x; }
-
-template <typename R, bool JAC, bool GRID, bool PIX, int RPT>
+// The float64 form of the fused evaluation (the float32-bulk form is
+// eval32.cu): one CTA per (leaf, tile of rays), the leaf's U-list stars
+// staged in shared memory in rounds, M2P for the W list, L2P by Horner, and
+// the lens equation y = diag(a, b) x - alpha in float64.
+template <bool JAC, bool GRID, bool PIX, int RPT>
 __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
-  using C = typename cx_t<R>::type;
-  // In the float32 form a near-field difference is taken on split offsets,
-  // d = (x_hi - s_hi) + (x_lo - s_lo): the hi difference is exact when the
-  // star is close to the ray, so d keeps float32 relative accuracy even when
-  // |d| is far below the leaf size.
-  constexpr bool SPLIT = sizeof(R) == 4;
-  __shared__ R s_x[kChunk], s_y[kChunk], s_m[kChunk];
-  __shared__ R s_xl[SPLIT ? kChunk : 1], s_yl[SPLIT ? kChunk : 1];
+  __shared__ double s_x[kChunk], s_y[kChunk], s_m[kChunk];
   __shared__ int s_pre[kSeg + 1];
   __shared__ int s_box[kSeg];
-  __shared__ C s_L[kMaxOrder + 1];
-  __shared__ C s_W[kWChunk][kMaxOrder + 1];
-  __shared__ R s_wx[kWChunk], s_wy[kWChunk], s_wr[kWChunk];
+  __shared__ double2 s_L[kMaxOrder + 1];
+  __shared__ double2 s_W[kWChunk][kMaxOrder + 1];
+  __shared__ double s_wx[kWChunk], s_wy[kWChunk], s_wr[kWChunk];
   __shared__ int64_t s_leaf;
   const int tid = threadIdx.x;
   const int p = A.p;
@@ -111,10 +90,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
   const double cx = A.lo_x + (2.0 * A.ix[B] + 1.0) * r;
   const double cy = A.lo_y + (2.0 * A.iy[B] + 1.0) * r;
   const double2* Lb = A.L + (int64_t)B * (p + 1);
-  for (int l = tid; l <= p; l += kEvalThreads) {
-    const double2 v = Lb[l];
-    s_L[l] = mk<R>((R)v.x, (R)v.y);
-  }
+  for (int l = tid; l <= p; l += kEvalThreads) s_L[l] = Lb[l];
   // rays of this tile
   int64_t nr_leaf, i0 = 0, ni = 1, j0 = 0;
   if (GRID) {
@@ -123,26 +99,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
   } else {
     nr_leaf = A.ray_off[k + 1] - A.ray_off[k];
   }
-  R dx[RPT], dy[RPT], dxl[RPT], dyl[RPT];
-  double x1[RPT], x2[RPT];  // float64 ray positions (float64 form, and the ray path)
+  double dx[RPT], dy[RPT], x1[RPT], x2[RPT];
   int64_t oidx[RPT];
   bool ok[RPT];
-  Acc<R> n1[RPT], n2[RPT], nj1[RPT], nj2[RPT];
-  // float32 form on the grid: a ray's offset from the leaf centre is
-  // (x(i0) - c) + (i - i0) h, formed in float-float from per-CTA float64
-  // constants, so no float64 instruction runs per ray.
-  ff bx{0.f, 0.f}, by{0.f, 0.f}, hf{0.f, 0.f};
-  if (SPLIT && GRID) {
-    bx = ff_of(grid_coord(A.gx0, i0, A.gh) - cx);
-    by = ff_of(grid_coord(A.gy0, j0, A.gh) - cy);
-    hf = ff_of(A.gh);
-  }
+  double n1[RPT], n2[RPT], nj1[RPT], nj2[RPT];
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int64_t loc = tile * (kEvalThreads * RPT) + (int64_t)q * kEvalThreads + tid;
     ok[q] = loc < nr_leaf;
     x1[q] = cx; x2[q] = cy; oidx[q] = 0;
-    dx[q] = 0; dy[q] = 0; dxl[q] = 0; dyl[q] = 0;
     if (ok[q]) {
       if (GRID) {
         // 32-bit division: a 64-bit one is emulated with float64 instructions
@@ -151,31 +116,18 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
         const int64_t dj = dj32, di = (int64_t)(l32 - dj32 * n32);
         const int64_t i = i0 + di, j = j0 + dj;
         oidx[q] = (j - A.grow0) * A.gnx1 + i;
-        if (SPLIT) {
-          // int32 -> float: an int64 conversion runs on the float64 pipe
-          const ff ox = ff_add(bx, ff_mul(hf, (float)(int)di));
-          const ff oy = ff_add(by, ff_mul(hf, (float)(int)dj));
-          dx[q] = (R)ox.hi; dxl[q] = (R)ox.lo;
-          dy[q] = (R)oy.hi; dyl[q] = (R)oy.lo;
-        } else {
-          x1[q] = grid_coord(A.gx0, i, A.gh);
-          x2[q] = grid_coord(A.gy0, j, A.gh);
-        }
+        x1[q] = grid_coord(A.gx0, i, A.gh);
+        x2[q] = grid_coord(A.gy0, j, A.gh);
       } else {
         const int64_t ridx = A.perm[A.ray_off[k] + loc];
         x1[q] = A.rays[2 * ridx];
         x2[q] = A.rays[2 * ridx + 1];
         oidx[q] = ridx;
       }
-      if (!(SPLIT && GRID)) {
-        const double ox = x1[q] - cx, oy = x2[q] - cy;
-        dx[q] = (R)ox;
-        dy[q] = (R)oy;
-        dxl[q] = SPLIT ? (R)(ox - (double)dx[q]) : (R)0;
-        dyl[q] = SPLIT ? (R)(oy - (double)dy[q]) : (R)0;
-      }
     }
-    n1[q].zero(); n2[q].zero(); nj1[q].zero(); nj2[q].zero();
+    dx[q] = x1[q] - cx;
+    dy[q] = x2[q] - cy;
+    n1[q] = 0.0; n2[q] = 0.0; nj1[q] = 0.0; nj2[q] = 0.0;
   }
   // ---- P2P over the U list ----------------------------------------------
   const int64_t u_beg = A.U_off[a], u_end = A.U_off[a + 1];
@@ -213,192 +165,128 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
         }
         const int st = A.start[s_box[lo]] + (ff - s_pre[lo]);
         const double2 z = A.spos[st];
-        const double ox = z.x - cx, oy = z.y - cy;
-        s_x[f] = (R)ox;
-        s_y[f] = (R)oy;
-        if (SPLIT) {
-          s_xl[f] = (R)(ox - (double)s_x[f]);
-          s_yl[f] = (R)(oy - (double)s_y[f]);
-        }
-        s_m[f] = (R)A.smass[st];
+        s_x[f] = z.x - cx;
+        s_y[f] = z.y - cy;
+        s_m[f] = A.smass[st];
       }
       __syncthreads();
       for (int e = 0; e < ne; ++e) {
         const int lo = max(s_pre[e], f0) - f0;
         const int hi = min(s_pre[e + 1], f0 + nf) - f0;
         if (hi <= lo) continue;
-        R p1[RPT], p2[RPT], pj1[RPT], pj2[RPT];
+        double p1[RPT], p2[RPT], pj1[RPT], pj2[RPT];
 #pragma unroll
         for (int q = 0; q < RPT; ++q) { p1[q] = 0; p2[q] = 0; pj1[q] = 0; pj2[q] = 0; }
         for (int j = lo; j < hi; ++j) {
-          const R sx = s_x[j], sy = s_y[j], sm = s_m[j];
-          const R sxl = SPLIT ? s_xl[j] : (R)0, syl = SPLIT ? s_yl[j] : (R)0;
+          const double sx = s_x[j], sy = s_y[j], sm = s_m[j];
 #pragma unroll
           for (int q = 0; q < RPT; ++q) {
-            const R d1 = SPLIT ? (dx[q] - sx) + (dxl[q] - sxl) : dx[q] - sx;
-            const R d2 = SPLIT ? (dy[q] - sy) + (dyl[q] - syl) : dy[q] - sy;
-            const R r2 = d1 * d1 + d2 * d2;
-            const R inv = r2 > (R)0 ? rcp_r<R>(r2) : (R)0;
-            const R w = sm * inv;
+            const double d1 = dx[q] - sx, d2 = dy[q] - sy;
+            const double r2 = d1 * d1 + d2 * d2;
+            // a star exactly on the ray contributes nothing
+            const double inv = r2 > 0.0 ? 1.0 / r2 : 0.0;
+            const double w = sm * inv;
             p1[q] += w * d1;
             p2[q] += w * d2;
             if (JAC) {
-              const R w2 = w * inv;
+              const double w2 = w * inv;
               pj1[q] += w2 * (d2 - d1) * (d2 + d1);  // Re f'
-              pj2[q] += w2 * ((R)2 * d1 * d2);       // Im f'
+              pj2[q] += w2 * (2.0 * d1 * d2);        // Im f'
             }
           }
         }
+        // per-source-leaf partial sums
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
-          n1[q].add(p1[q]); n2[q].add(p2[q]);
-          if (JAC) { nj1[q].add(pj1[q]); nj2[q].add(pj2[q]); }
+          n1[q] += p1[q]; n2[q] += p2[q];
+          if (JAC) { nj1[q] += pj1[q]; nj2[q] += pj2[q]; }
         }
       }
     }
   }
   // ---- M2P over the W list ----------------------------------------------
-  C fw[RPT], dfw[RPT];
+  double2 fw[RPT], dfw[RPT];
 #pragma unroll
-  for (int q = 0; q < RPT; ++q) { fw[q] = mk<R>(0, 0); dfw[q] = mk<R>(0, 0); }
+  for (int q = 0; q < RPT; ++q) { fw[q] = make_double2(0, 0); dfw[q] = make_double2(0, 0); }
   const int64_t w_beg = A.W_off[a], w_end = A.W_off[a + 1];
   for (int64_t e0 = w_beg; e0 < w_end; e0 += kWChunk) {
     const int nw = (int)min64(kWChunk, w_end - e0);
     __syncthreads();
     for (int t = tid; t < nw * (p + 1); t += kEvalThreads) {
       const int w = t / (p + 1), kk = t - w * (p + 1);
-      const double2 v = A.M[(int64_t)A.W_list[e0 + w] * (p + 1) + kk];
-      s_W[w][kk] = mk<R>((R)v.x, (R)v.y);
+      s_W[w][kk] = A.M[(int64_t)A.W_list[e0 + w] * (p + 1) + kk];
     }
     if (tid < nw) {
       const int Wb = A.W_list[e0 + tid];
       const double rw = A.root_size / (double)(2ull << A.level[Wb]);
-      const double wcx = A.lo_x + (2.0 * A.ix[Wb] + 1.0) * rw;
-      const double wcy = A.lo_y + (2.0 * A.iy[Wb] + 1.0) * rw;
-      s_wx[tid] = (R)(wcx - cx);
-      s_wy[tid] = (R)(wcy - cy);
-      s_wr[tid] = (R)rw;
+      s_wx[tid] = A.lo_x + (2.0 * A.ix[Wb] + 1.0) * rw - cx;
+      s_wy[tid] = A.lo_y + (2.0 * A.iy[Wb] + 1.0) * rw - cy;
+      s_wr[tid] = rw;
     }
     __syncthreads();
     for (int w = 0; w < nw; ++w) {
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
-        const C z = mk<R>(dx[q] - s_wx[w], dy[q] - s_wy[w]);
-        const C inv = cinv(z);
-        const C qq = mk<R>(inv.x * s_wr[w], inv.y * s_wr[w]);
-        C s = s_W[w][p];
+        const double2 z = make_double2(dx[q] - s_wx[w], dy[q] - s_wy[w]);
+        const double2 inv = cinv(z);
+        const double2 qq = make_double2(inv.x * s_wr[w], inv.y * s_wr[w]);
+        double2 s = s_W[w][p];
         for (int kk = p - 1; kk >= 0; --kk) s = cfma(s, qq, s_W[w][kk]);
         fw[q] = cfma(s, inv, fw[q]);
         if (JAC) {
-          C t = mk<R>((R)(p + 1) * s_W[w][p].x, (R)(p + 1) * s_W[w][p].y);
+          double2 t = make_double2((double)(p + 1) * s_W[w][p].x, (double)(p + 1) * s_W[w][p].y);
           for (int kk = p - 1; kk >= 0; --kk)
-            t = cfma(t, qq, mk<R>((R)(kk + 1) * s_W[w][kk].x, (R)(kk + 1) * s_W[w][kk].y));
-          const C inv2 = cmul(inv, inv);
-          const C d = cmul(t, inv2);
-          dfw[q] = mk<R>(dfw[q].x - d.x, dfw[q].y - d.y);
+            t = cfma(t, qq, make_double2((double)(kk + 1) * s_W[w][kk].x, (double)(kk + 1) * s_W[w][kk].y));
+          const double2 d = cmul(t, cmul(inv, inv));
+          dfw[q] = make_double2(dfw[q].x - d.x, dfw[q].y - d.y);
         }
       }
     }
   }
-  // ---- L2P + epilogue ----------------------------------------------------
-  // y1 = a x1 - alpha1 = (a c1 - b0_1) + (a dx - f_1 - near_1)
-  // y2 = b x2 - alpha2 = (b c2 + b0_2) + (b dy + f_2 - near_2)
-  // (alpha = conj(f_total), f_total = b0 + f + near).  The bracketed leaf
-  // constants are float64 once per CTA; the per-ray parts are float-float in
-  // the float32 form.
+  // ---- L2P + lens equation ------------------------------------------------
+  // alpha = conj(f_total), f_total = b0 + f + near:
+  // y1 = a x1 - (Re b0 + Re f + near_1), y2 = b x2 - (-Im b0 - Im f + near_2)
   __syncthreads();
-  const R ir = (R)(1.0 / r);
+  const double ir = 1.0 / r;
   const double2 b0 = Lb[0];
-  const double K1 = A.a * cx - b0.x, K2 = A.b * cy + b0.y;
-  const ff af = ff_of(A.a), bf = ff_of(A.b);
-  ff U1f{0.f, 0.f}, V1f{0.f, 0.f}, iduf{0.f, 0.f}, idvf{0.f, 0.f};
-  int64_t U1i = 0, V1i = 0;
-  bool far_leaf = false;
-  if (PIX) {
-    const double U1 = fma(K1, A.pinv_du, A.pu_off), V1 = fma(K2, A.pinv_dv, A.pv_off);
-    far_leaf = !(fabs(U1) < 1073741824.0 && fabs(V1) < 1073741824.0);
-    if (!far_leaf) {
-      const double fu = floor(U1), fv = floor(V1);
-      U1i = (int64_t)fu; V1i = (int64_t)fv;
-      U1f = ff_of(U1 - fu); V1f = ff_of(V1 - fv);
-    }
-    iduf = ff_of(A.pinv_du); idvf = ff_of(A.pinv_dv);
-  }
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     if (!ok[q]) continue;
-    const C w = mk<R>(dx[q] * ir, dy[q] * ir);
-    C f = mk<R>(0, 0);
-    C df = mk<R>(0, 0);
+    const double2 w = make_double2(dx[q] * ir, dy[q] * ir);
+    double2 f = make_double2(0, 0), df = make_double2(0, 0);
     if (p >= 1) {
-      C s = s_L[p];
+      double2 s = s_L[p];
       for (int l = p - 1; l >= 1; --l) s = cfma(s, w, s_L[l]);
       f = cmul(s, w);
       if (JAC) {
-        C t = mk<R>((R)p * s_L[p].x, (R)p * s_L[p].y);
-        for (int l = p - 1; l >= 1; --l) t = cfma(t, w, mk<R>((R)l * s_L[l].x, (R)l * s_L[l].y));
-        df = mk<R>(t.x * ir, t.y * ir);
+        double2 t = make_double2((double)p * s_L[p].x, (double)p * s_L[p].y);
+        for (int l = p - 1; l >= 1; --l) t = cfma(t, w, make_double2((double)l * s_L[l].x, (double)l * s_L[l].y));
+        df = make_double2(t.x * ir, t.y * ir);
       }
     }
     f = f + fw[q];
-    double y1, y2;
-    if constexpr (SPLIT) {
-      ff T1 = ff_mul(af, ff{(float)dx[q], (float)dxl[q]});
-      T1 = ff_add(T1, -(float)f.x);
-      T1 = ff_add(T1, ff{-n1[q].v.hi, -n1[q].v.lo});
-      ff T2 = ff_mul(bf, ff{(float)dy[q], (float)dyl[q]});
-      T2 = ff_add(T2, (float)f.y);
-      T2 = ff_add(T2, ff{-n2[q].v.hi, -n2[q].v.lo});
-      if (PIX) {
-        PixCorner pc;
-        const ff U = ff_add(U1f, ff_mul(iduf, T1));
-        const ff V = ff_add(V1f, ff_mul(idvf, T2));
-        bool far = far_leaf || !(fabsf(U.hi) < 5.0e8f) || !(fabsf(V.hi) < 5.0e8f);
-        float ku = floorf(U.hi), kv = floorf(V.hi);
-        float fu = (U.hi - ku) + U.lo, fv = (V.hi - kv) + V.lo;
-        if (fu < 0.f) { ku -= 1.f; fu += 1.f; } else if (fu >= 1.f) { ku += 1.f; fu -= 1.f; }
-        if (fv < 0.f) { kv -= 1.f; fv += 1.f; } else if (fv >= 1.f) { kv += 1.f; fv -= 1.f; }
-        // float -> int32 (|k| < 5e8); a float -> int64 conversion would run
-        // on the float64 pipe
-        const int64_t iu = U1i + (int)ku, iv = V1i + (int)kv;
-        far = far || !(iu > -1073741824ll && iu < 1073741824ll && iv > -1073741824ll &&
-                       iv < 1073741824ll);
-        if (!far) {
-          pc.iu = (int)iu; pc.fu = fu; pc.iv = (int)iv; pc.fv = fv;
-        } else {
-          pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
-        }
-        A.pix[oidx[q]] = pc;
-        continue;
+    const double al1 = b0.x + f.x + n1[q];
+    const double al2 = -(b0.y + f.y) + n2[q];
+    const double y1 = fma(A.a, x1[q], -al1);
+    const double y2 = fma(A.b, x2[q], -al2);
+    if (PIX) {
+      const double u = fma(y1, A.pinv_du, A.pu_off), v = fma(y2, A.pinv_dv, A.pv_off);
+      PixCorner pc;
+      if (fabs(u) < 1073741824.0 && fabs(v) < 1073741824.0) {
+        const double fu = floor(u), fv = floor(v);
+        pc.iu = (int)fu; pc.fu = (float)(u - fu);
+        pc.iv = (int)fv; pc.fv = (float)(v - fv);
+      } else {
+        pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
       }
-      y1 = K1 + ff_to_double(T1);
-      y2 = K2 + ff_to_double(T2);
-    } else {
-      const double fre = b0.x + (double)f.x;
-      const double fim = b0.y + (double)f.y;
-      const double al1 = fre + n1[q].value();
-      const double al2 = -fim + n2[q].value();
-      y1 = fma(A.a, x1[q], -al1);
-      y2 = fma(A.b, x2[q], -al2);
-      if (PIX) {
-        const double u = fma(y1, A.pinv_du, A.pu_off), v = fma(y2, A.pinv_dv, A.pv_off);
-        PixCorner pc;
-        if (fabs(u) < 1073741824.0 && fabs(v) < 1073741824.0) {
-          const double fu = floor(u), fv = floor(v);
-          pc.iu = (int)fu; pc.fu = (float)(u - fu);
-          pc.iv = (int)fv; pc.fv = (float)(v - fv);
-        } else {
-          pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
-        }
-        A.pix[oidx[q]] = pc;
-        continue;
-      }
+      A.pix[oidx[q]] = pc;
+      continue;
     }
     A.y[2 * oidx[q]] = y1;
     A.y[2 * oidx[q] + 1] = y2;
     if (JAC) {
-      const double dre = (double)df.x + (double)dfw[q].x + nj1[q].value();
-      const double dim = (double)df.y + (double)dfw[q].y + nj2[q].value();
+      const double dre = df.x + dfw[q].x + nj1[q];
+      const double dim = df.y + dfw[q].y + nj2[q];
       A.jac[4 * oidx[q] + 0] = A.a - dre;
       A.jac[4 * oidx[q] + 1] = dim;
       A.jac[4 * oidx[q] + 2] = dim;
@@ -528,8 +416,8 @@ void launch_eval(Plan& P, EvalArgs& A, int64_t total_tiles, bool jac, cudaStream
   if (total_tiles > (int64_t)INT32_MAX) fail(LENS_EINVAL, "too many ray tiles in one call");
   const unsigned g = (unsigned)total_tiles;
   // float64 form only; the float32-bulk form runs k_eval32 (eval32.cu)
-  if (jac) k_eval<double, true, GRID, PIX, kRptD><<<g, kEvalThreads, 0, s>>>(A);
-  else k_eval<double, false, GRID, PIX, kRptD><<<g, kEvalThreads, 0, s>>>(A);
+  if (jac) k_eval<true, GRID, PIX, kRptD><<<g, kEvalThreads, 0, s>>>(A);
+  else k_eval<false, GRID, PIX, kRptD><<<g, kEvalThreads, 0, s>>>(A);
   LENS_LAUNCHED("k_eval");
 }
 
