@@ -170,7 +170,9 @@ lens_status lens_deflect_grid(lens_plan* plan, const lens_grid* grid,
 
 /* FMM-IPM magnification map (Sec. 2.4 steps 2-4): the grid is split into row
  * chunks of at most max_cells_per_chunk cells (0 = sized from free device
- * memory); each chunk's corner rays are deflected and each cell's mapped
+ * memory; never more than 64 cells per map pixel, after which the float32
+ * accumulators are flushed into the float64 map); each chunk's corner rays
+ * are deflected and each cell's mapped
  * quadrilateral is apportioned over the pixels it overlaps (signed-area
  * fraction, Sec. 2.3), accumulating
  *     map[pix] = sum_cells h^2 * a_pix / A_P / S*     (S* = pixel area).

@@ -327,6 +327,13 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     max_cells = (int64_t)std::min<double>((double)fr / 4.0 / 20.0, (double)(1ll << 30));
   }
   max_cells = std::min<int64_t>(max_cells, 1ll << 30);
+  // The float32 accumulators are flushed into the float64 map once about
+  // kFlushCellsPerPixel cells per map pixel have entered them, so a pixel
+  // sums a bounded number of float32 increments whatever the grid size
+  // (a pixel under n equal increments drifts by up to ~n 2^-25 relative).
+  constexpr int64_t kFlushCellsPerPixel = 64;
+  const int64_t flush_cells = std::min<int64_t>(kFlushCellsPerPixel * npx * npy, 1ll << 30);
+  max_cells = std::min(max_cells, flush_cells);
   int64_t rows = std::max<int64_t>(1, max_cells / nx);
   rows = std::min<int64_t>(rows, ny);
   need(rows * nx <= (1ll << 30) || rows == 1, "grid rows too wide for one chunk");
@@ -368,19 +375,26 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     LENS_CUDA(cudaEventRecord(e, s));
     ev.push_back(e);
   };
-  int64_t chunks = 0;
+  int64_t chunks = 0, pending = 0;
+  bool flushed = false;
   const long long l0 = launch_count();
   for (int64_t r0 = 0; r0 < ny; r0 += rows) {
     const int64_t nr = std::min<int64_t>(rows, ny - r0);
+    if (pending > 0 && pending + nr * nx > flush_cells) {
+      ipm_finish_map(map32.as<float>(), rowdiff.as<float>(), npx, npy, map_out, flushed, true, s);
+      flushed = true;
+      pending = 0;
+    }
     GridRows g{grid->x0, grid->y0, grid->h, nx, ny, r0, nr + 1};
     mark();
     evaluate_grid_pix(P, g, corners.as<PixCorner>(), ip, s);
     mark();
     ipm_accumulate(corners.as<PixCorner>(), nx, nr, ip, map32.as<float>(), rowdiff.as<float>(),
                    sdev.as<double>(), queue.as<int>(), qcount, s, &P.ev_ipm);
+    pending += nr * nx;
     ++chunks;
   }
-  ipm_finish_map(map32.as<float>(), rowdiff.as<float>(), npx, npy, map_out, s);
+  ipm_finish_map(map32.as<float>(), rowdiff.as<float>(), npx, npy, map_out, flushed, false, s);
   mark();
   double hs[16];
   LENS_CUDA(cudaMemcpyAsync(hs, sdev.p, sizeof(hs), cudaMemcpyDeviceToHost, s));

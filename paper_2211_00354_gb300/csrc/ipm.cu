@@ -100,7 +100,7 @@ struct IpmArgs {
   float* D;             // per-row difference array, npy x (npx + 1): prefix-summed at the end
   int64_t ldd;          // npx + 1
   double* stats;        // [8]
-  int* queue; int* qcount;
+  int* queue; int* qcount;   // qcount[0] queue length, qcount[1] chunk counter
   IpmParams ip;
   float thr_area;       // fast-path lower bound on |A_P| in pixel units
   float scale_f;        // ip.scale in float32
@@ -207,16 +207,19 @@ constexpr int kWarps = kIpmThreads / 32;
 // Per-warp staging: the warp's 32 cells, then up to 32 rows x 4 edge
 // segments of large cells.
 struct CellShared {
-  float qx[4][kWarps][32], qy[4][kWarps][32];  // polygon, pixel units local to (ix0, iy0)
-  float sl[4][kWarps][32];                      // edge slopes dx/dy (0 if horizontal)
-  float inv[kWarps][32];                        // 1 / A_P
-  int ix0[kWarps][32], iy0[kWarps][32];
-  int cx0[kWarps][32], cx1[kWarps][32], cy0[kWarps][32];  // box clipped to the map
+  float4 qx[kWarps][32], qy[kWarps][32];  // polygon, pixel units local to (ix0, iy0)
+  float4 sl[kWarps][32];                  // edge slopes dx/dy (0 if horizontal)
+  int4 box[kWarps][32];                   // ix0, iy0, cx0, cy0 (box clipped to the map at cx0, cy0)
+  int2 ext[kWarps][32];                   // clipped box width, 1 / A_P (float bits)
   int cum[kWarps][32], cum2[kWarps][32];
-  float xa[kWarps][128], xb[kWarps][128], dy[kWarps][128];
-  int pa[kWarps][128], n[kWarps][128];
+  float4 seg[kWarps][128];                // crossing segments: xa, xb, dy, first pixel (int bits)
+  int n[kWarps][128];
   int row[kWarps][32], cell[kWarps][32];
 };
+
+__device__ __forceinline__ void unpack4(float (&a)[4], const float4 v) {
+  a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+}
 
 // One warp per 32 consecutive cells of a grid row (grid-stride over chunks).
 //  A. lane = cell: corners (coalesced), pixel box, ledger of cells that are
@@ -232,15 +235,21 @@ struct CellShared {
 //     (the same Green's-theorem terms as pixel_area()), again spread over
 //     the lanes.  Work per large cell follows its perimeter in pixels, not
 //     its area.
-__global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
+__global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
   __shared__ CellShared sh;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nchunks = (A.ncells + 31) >> 5;
   const int64_t W = A.nx + 1;
   const int npx = A.ip.npx, npy = A.ip.npy;
   Ledger led;
-  for (int64_t ch = (blockIdx.x * (int64_t)kIpmThreads + threadIdx.x) >> 5; ch < nchunks;
-       ch += ((int64_t)gridDim.x * kIpmThreads) >> 5) {
+  // chunks of 32 cells are handed out by a counter (qcount[1]), so the
+  // warps of a block finish together however the large cells fall
+  unsigned* next = reinterpret_cast<unsigned*>(A.qcount) + 1;
+  unsigned ch_u = 0;
+  if (lane == 0) ch_u = atomicAdd(next, 1u);
+  for (int64_t ch = __shfl_sync(0xffffffffu, ch_u, 0); ch < nchunks;) {
+    // the following chunk's index is fetched while this one is processed
+    if (lane == 0) ch_u = atomicAdd(next, 1u);
     // ---- A: one cell per lane ------------------------------------------------
     const int64_t c = ch * 32 + lane;
     int nsmall = 0, nrows = 0;
@@ -291,18 +300,20 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
         } else {
           const int cx0 = max(ix0, 0), cx1 = min(ix1, npx - 1);
           const int cy0 = max(iy0, 0), cy1 = min(iy1, npy - 1);
+          float slk[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            sh.qx[k][w][lane] = qx[k];
-            sh.qy[k][w][lane] = qy[k];
             // an edge with |dy| <= 1e-30 adds nothing (its clipped dy is at
             // most that): slope 0 keeps its terms finite
             const float ey = qy[(k + 1) & 3] - qy[k];
-            sh.sl[k][w][lane] = fabsf(ey) > 1e-30f ? __fdividef(qx[(k + 1) & 3] - qx[k], ey) : 0.f;
+            slk[k] = fabsf(ey) > 1e-30f ? __fdividef(qx[(k + 1) & 3] - qx[k], ey) : 0.f;
           }
-          sh.inv[w][lane] = frcp_fast(A_loc);  // |A_loc| > 0: the cell is well conditioned
-          sh.ix0[w][lane] = ix0; sh.iy0[w][lane] = iy0;
-          sh.cx0[w][lane] = cx0; sh.cx1[w][lane] = cx1; sh.cy0[w][lane] = cy0;
+          sh.qx[w][lane] = make_float4(qx[0], qx[1], qx[2], qx[3]);
+          sh.qy[w][lane] = make_float4(qy[0], qy[1], qy[2], qy[3]);
+          sh.sl[w][lane] = make_float4(slk[0], slk[1], slk[2], slk[3]);
+          sh.box[w][lane] = make_int4(ix0, iy0, cx0, cy0);
+          // |A_loc| > 0: the cell is well conditioned
+          sh.ext[w][lane] = make_int2(cx1 - cx0 + 1, __float_as_int(frcp_fast(A_loc)));
           // every fraction that lands in the map is moved from fout to fin
           led.fout += 1.f;
           if (ix1 - ix0 < kSmallBox && iy1 - iy0 < kSmallBox) {
@@ -329,15 +340,18 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
       if (f < tot1) {
         int off;
         const int L = warp_owner(sh.cum[w], f, off);
-        const int cx0 = sh.cx0[w][L], wd = sh.cx1[w][L] - cx0 + 1;
+        const int4 bx = sh.box[w][L];
+        const int2 ex = sh.ext[w][L];
+        const int wd = ex.x;
         const int r = off / wd;
-        const int px = cx0 + off - r * wd, py = sh.cy0[w][L] + r;
+        const int px = bx.z + off - r * wd, py = bx.w + r;
         float qx[4], qy[4], sl[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) { qx[k] = sh.qx[k][w][L]; qy[k] = sh.qy[k][w][L]; sl[k] = sh.sl[k][w][L]; }
-        const float a = pixel_area_f(qx, qy, sl, (float)(px - sh.ix0[w][L]), (float)(py - sh.iy0[w][L]));
+        unpack4(qx, sh.qx[w][L]);
+        unpack4(qy, sh.qy[w][L]);
+        unpack4(sl, sh.sl[w][L]);
+        const float a = pixel_area_f(qx, qy, sl, (float)(px - bx.x), (float)(py - bx.y));
         if (a != 0.0f) {
-          const float fr = a * sh.inv[w][L];
+          const float fr = a * __int_as_float(ex.y);
           atomicAdd(&A.map[(int64_t)py * npx + px], A.scale_f * fr);
           led.fin += fr;
           led.fout -= fr;
@@ -353,24 +367,30 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
       if (f < tot2) {
         int r;
         const int L = warp_owner(sh.cum2[w], f, r);
-        const int ix0 = sh.ix0[w][L], cx0 = sh.cx0[w][L];
-        const int lx0 = cx0 - ix0, lx1 = sh.cx1[w][L] - ix0;
-        const float inv = sh.inv[w][L];
+        const int4 bx = sh.box[w][L];
+        const int2 ex = sh.ext[w][L];
+        const int ix0 = bx.x, cx0 = bx.z;
+        const int lx0 = cx0 - ix0, lx1 = lx0 + ex.x - 1;
+        const float inv = __int_as_float(ex.y);
         const float kf = A.scale_f * inv;  // map increment per unit of pixel area
-        const int py = sh.cy0[w][L] + r;
-        const float Y = (float)(py - sh.iy0[w][L]);
+        const int py = bx.w + r;
+        const float Y = (float)(py - bx.y);
         const int64_t drow = (int64_t)py * A.ldd;
+        float qx[4], qy[4], slp[4];
+        unpack4(qx, sh.qx[w][L]);
+        unpack4(qy, sh.qy[w][L]);
+        unpack4(slp, sh.sl[w][L]);
         float vsum = 0.f, frow = 0.f;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int t = lane * 4 + e;
           int n = 0;
-          const float x0 = sh.qx[e][w][L], y0 = sh.qy[e][w][L];
-          const float y1 = sh.qy[(e + 1) & 3][w][L];
+          const float x0 = qx[e], y0 = qy[e];
+          const float y1 = qy[(e + 1) & 3];
           const float ya = fminf(fmaxf(y0, Y), Y + 1.f), yb = fminf(fmaxf(y1, Y), Y + 1.f);
           if (ya != yb) {
             // the clipped segment of pixel_area_f()
-            const float sl = sh.sl[e][w][L];
+            const float sl = slp[e];
             const float xa = x0 + (ya - y0) * sl, xb = x0 + (yb - y0) * sl;
             const float dy = yb - ya;
             const int Xa = (int)floorf(fminf(xa, xb)), Xb = (int)ceilf(fmaxf(xa, xb)) - 1;
@@ -387,7 +407,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
             const int pa = max(Xa, lx0), pb = min(Xb, lx1);
             if (pb >= pa) {
               n = pb - pa + 1;
-              sh.xa[w][t] = xa; sh.xb[w][t] = xb; sh.dy[w][t] = dy; sh.pa[w][t] = pa;
+              sh.seg[w][t] = make_float4(xa, xb, dy, __int_as_float(pa));
             }
           }
           sh.n[w][t] = n;
@@ -410,12 +430,14 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
           const int L = warp_owner(cum, g, off);
           int t = L * 4;
           while (off >= sh.n[w][t]) { off -= sh.n[w][t]; ++t; }
-          const int X = sh.pa[w][t] + off;
-          const float a = sh.dy[w][t] * mean_clamp01f(sh.xa[w][t] - (float)X, sh.xb[w][t] - (float)X);
+          const float4 sg = sh.seg[w][t];
+          const int X = __float_as_int(sg.w) + off;
+          const float a = sg.z * mean_clamp01f(sg.x - (float)X, sg.y - (float)X);
           if (a != 0.0f) {
             const int cl = sh.cell[w][L];
-            const float fr = a * sh.inv[w][cl];
-            atomicAdd(&A.map[(int64_t)sh.row[w][L] * npx + sh.ix0[w][cl] + X], A.scale_f * fr);
+            const int2 ex = sh.ext[w][cl];
+            const float fr = a * __int_as_float(ex.y);
+            atomicAdd(&A.map[(int64_t)sh.row[w][L] * npx + sh.box[w][cl].x + X], A.scale_f * fr);
             led.fin += fr;
             led.fout -= fr;
             led.nupd += 1;
@@ -425,6 +447,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_cells(IpmArgs A) {
       __syncwarp();
     }
     __syncwarp();  // the next chunk overwrites this one's staging
+    ch = __shfl_sync(0xffffffffu, ch_u, 0);
   }
   block_add_stats(A.stats, led);
 }
@@ -556,20 +579,22 @@ void event_pair_end(std::pair<cudaEvent_t, cudaEvent_t>& e, cudaStream_t s) {
   LENS_CUDA(cudaEventRecord(e.second, s));
 }
 
-// map = map32 + row-wise prefix sum of the difference array (float64), one
-// block per map row: each thread sums a contiguous run of columns, a block
-// scan gives each run its offset, and the run is written out.
+// map (+)= map32 + row-wise prefix sum of the difference array (float64),
+// one block per map row: each thread sums a contiguous run of columns, a
+// block scan gives each run its offset, and the run is written out.  With
+// `clear` the float32 accumulators are zeroed behind the read, so the next
+// cells start from zero (a flush between chunks).
 constexpr int kFinishThreads = 256;
 
 __global__ void __launch_bounds__(kFinishThreads)
-k_map_finish(const float* __restrict__ m32, const float* __restrict__ D, int npx, int npy,
-             int64_t ldd, double* __restrict__ out) {
+k_map_finish(float* __restrict__ m32, float* __restrict__ D, int npx, int npy, int64_t ldd,
+             double* __restrict__ out, bool accumulate, bool clear) {
   __shared__ double wsum[kFinishThreads / 32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int run = (npx + kFinishThreads - 1) / kFinishThreads;
   const int c0 = min(npx, t * run), c1 = min(npx, c0 + run);
   for (int64_t row = blockIdx.x; row < npy; row += gridDim.x) {
-    const float* d = D + row * ldd;
+    float* d = D + row * ldd;
     double s = 0.0;
     for (int c = c0; c < c1; ++c) s += (double)d[c];
     double incl = s;
@@ -583,19 +608,24 @@ k_map_finish(const float* __restrict__ m32, const float* __restrict__ D, int npx
     __syncthreads();
     double base = incl - s;
     for (int q = 0; q < w; ++q) base += wsum[q];
-    const float* m = m32 + row * (int64_t)npx;
+    float* m = m32 + row * (int64_t)npx;
     double* o = out + row * (int64_t)npx;
     for (int c = c0; c < c1; ++c) {
       base += (double)d[c];
-      o[c] = (double)m[c] + base;
+      const double v = (double)m[c] + base;
+      o[c] = accumulate ? o[c] + v : v;
+      if (clear) { m[c] = 0.f; d[c] = 0.f; }
     }
+    // column npx of the difference array only ever receives run ends
+    if (clear && t == 0) d[npx] = 0.f;
   }
 }
 
-void ipm_finish_map(const float* map32, const float* rowdiff, int npx, int npy, double* map,
-                    cudaStream_t s) {
+void ipm_finish_map(float* map32, float* rowdiff, int npx, int npy, double* map, bool accumulate,
+                    bool clear, cudaStream_t s) {
   const unsigned blocks = (unsigned)std::min<int64_t>(npy, 152 * 8);
-  k_map_finish<<<blocks, kFinishThreads, 0, s>>>(map32, rowdiff, npx, npy, (int64_t)npx + 1, map);
+  k_map_finish<<<blocks, kFinishThreads, 0, s>>>(map32, rowdiff, npx, npy, (int64_t)npx + 1, map,
+                                                 accumulate, clear);
   LENS_LAUNCHED("k_map_finish");
 }
 
@@ -610,11 +640,13 @@ void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const 
   A.queue = queue; A.qcount = qcount; A.ip = ip;
   A.thr_area = (float)(1e-13 * ip.a_cell / ip.s_star);
   A.scale_f = (float)ip.scale;
-  LENS_CUDA(cudaMemsetAsync(qcount, 0, sizeof(int), s));
+  // qcount[0]: float64 queue length; qcount[1]: chunk counter of k_ipm_cells
+  LENS_CUDA(cudaMemsetAsync(qcount, 0, 2 * sizeof(int), s));
   std::pair<cudaEvent_t, cudaEvent_t> e;
   if (ev) e = event_pair_begin(s);
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  int dev = 0, sms = 152;
+  LENS_CUDA(cudaGetDevice(&dev));
+  LENS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t chunk_blocks = (ncells + kIpmThreads - 1) / kIpmThreads;
   k_ipm_cells<<<(unsigned)std::min<int64_t>(chunk_blocks, (int64_t)sms * 8), kIpmThreads, 0, s>>>(A);
   LENS_LAUNCHED("k_ipm_cells");

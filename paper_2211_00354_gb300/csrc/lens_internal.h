@@ -271,9 +271,10 @@ void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t*
                  cudaStream_t s);
 void eval32_rays(Plan& P, const double* rays, const int64_t* off, const int* perm,
                  const int64_t* toff, int64_t total, double* y, double* jac, cudaStream_t s);
-// map (float64 output) = map32 + row-wise prefix sums of rowdiff
-void ipm_finish_map(const float* map32, const float* rowdiff, int npx, int npy, double* map,
-                    cudaStream_t s);
+// map (float64 output) = map32 + row-wise prefix sums of rowdiff, or += with
+// `accumulate`; `clear` zeroes map32 and rowdiff behind the read
+void ipm_finish_map(float* map32, float* rowdiff, int npx, int npy, double* map, bool accumulate,
+                    bool clear, cudaStream_t s);
 // a pair of recorded events bracketing work on a stream
 std::pair<cudaEvent_t, cudaEvent_t> event_pair_begin(cudaStream_t s);
 void event_pair_end(std::pair<cudaEvent_t, cudaEvent_t>& e, cudaStream_t s);
