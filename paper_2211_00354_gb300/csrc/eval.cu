@@ -36,7 +36,7 @@ struct EvalArgs {
   const int64_t* U_off; const int* U_list; const int64_t* W_off; const int* W_list;
   const double2* M; const double2* L;
   const int* leaves;
-  const int64_t* tile_off;
+  const int2* tile_leaf;  // (leaf, tile within the leaf) of each block
   int64_t nleaf;
   double lo_x, lo_y, root_size;
   int p;
@@ -69,22 +69,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(EvalArgs A) {
   __shared__ double2 s_L[kMaxOrder + 1];
   __shared__ double2 s_W[kWChunk][kMaxOrder + 1];
   __shared__ double s_wx[kWChunk], s_wy[kWChunk], s_wr[kWChunk];
-  __shared__ int64_t s_leaf;
   const int tid = threadIdx.x;
   const int p = A.p;
-  if (tid == 0) {
-    int64_t lo = 0, hi = A.nleaf;  // largest k with tile_off[k] <= blockIdx.x
-    while (hi - lo > 1) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (A.tile_off[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid;
-    }
-    s_leaf = lo;
-  }
-  __syncthreads();
-  const int64_t k = s_leaf;
+  const int2 kt = A.tile_leaf[blockIdx.x];
+  const int64_t k = kt.x;
   const int B = A.leaves[k];
   const int a = A.aidx[B];
-  const int64_t tile = (int64_t)blockIdx.x - A.tile_off[k];
+  const int64_t tile = kt.y;
   const int lv = A.level[B];
   const double r = A.root_size / (double)(2ull << lv);
   const double cx = A.lo_x + (2.0 * A.ix[B] + 1.0) * r;
@@ -410,6 +401,23 @@ __global__ void k_tiles_from_counts(const int64_t* __restrict__ counts, int64_t 
   tiles[k] = (counts[k] + tile - 1) / tile;
 }
 
+// (leaf, tile within the leaf) of every ray tile, from the tile offsets:
+// each block of the evaluation kernels finds its leaf with one load
+__global__ void k_tile_leaf(const int64_t* __restrict__ toff, int64_t nl, int2* __restrict__ out) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nl) return;
+  const int64_t t0 = toff[k], t1 = toff[k + 1];
+  for (int64_t t = t0; t < t1; ++t) out[t] = make_int2((int)k, (int)(t - t0));
+}
+
+Scratch tile_leaves(Plan& P, const int64_t* toff, int64_t nl, int64_t total, cudaStream_t s) {
+  if (total > (int64_t)INT32_MAX) fail(LENS_EINVAL, "too many ray tiles in one call");
+  Scratch tl(&P.da, sizeof(int2) * (size_t)std::max<int64_t>(total, 1));
+  k_tile_leaf<<<grid_for(nl, 128), 128, 0, s>>>(toff, nl, tl.as<int2>());
+  LENS_LAUNCHED("k_tile_leaf");
+  return tl;
+}
+
 template <bool GRID, bool PIX>
 void launch_eval(Plan& P, EvalArgs& A, int64_t total_tiles, bool jac, cudaStream_t s) {
   if (total_tiles <= 0) return;
@@ -470,13 +478,14 @@ void grid_impl(Plan& P, const GridRows& g, double* y, double* jac, PixCorner* pi
                                                         P.W_off, P.f_ncnt, P.f_wcnt, P.work);
     LENS_LAUNCHED("k_work_count");
   }
+  Scratch tl = tile_leaves(P, toff.as<int64_t>(), nl, total, s);
   if (P.prec == LENS_FP32_BULK) {
-    eval32_grid(P, g, rect.as<int64_t>(), toff.as<int64_t>(), total, y, jac, pix, ip, s);
+    eval32_grid(P, g, rect.as<int64_t>(), tl.as<int2>(), total, y, jac, pix, ip, s);
     return;
   }
   wait_expansions(P, s);
   EvalArgs A = base_args(P);
-  A.tile_off = toff.as<int64_t>();
+  A.tile_leaf = tl.as<int2>();
   A.rect = rect.as<int64_t>();
   A.gx0 = g.x0; A.gy0 = g.y0; A.gh = g.h;
   A.gnx1 = g.nx + 1; A.grow0 = g.row0;
@@ -544,14 +553,14 @@ void evaluate_rays(Plan& P, const double* rays, int64_t m, double* y, double* ja
   if (m == 0) return;
   RayBuckets B;
   bucket_rays(P, rays, m, tile_rays(P), B, s);
+  Scratch tl = tile_leaves(P, B.toff.as<int64_t>(), P.n_active_leaves, B.total, s);
   if (P.prec == LENS_FP32_BULK) {
-    eval32_rays(P, rays, B.off.as<int64_t>(), B.perm.as<int>(), B.toff.as<int64_t>(), B.total, y,
-                jac, s);
+    eval32_rays(P, rays, B.off.as<int64_t>(), B.perm.as<int>(), tl.as<int2>(), B.total, y, jac, s);
     return;
   }
   wait_expansions(P, s);
   EvalArgs A = base_args(P);
-  A.tile_off = B.toff.as<int64_t>();
+  A.tile_leaf = tl.as<int2>();
   A.rays = rays; A.ray_off = B.off.as<int64_t>(); A.perm = B.perm.as<int>();
   A.y = y; A.jac = jac;
   launch_eval<false, false>(P, A, B.total, jac != nullptr, s);

@@ -46,7 +46,7 @@ constexpr int kWChunk = 8;
 struct E32Args {
   const LeafPlan* leaf;
   const int* leaves;
-  const int64_t* tile_off;
+  const int2* tile_leaf;  // (leaf, tile within the leaf) of each block
   int64_t nleaf;
   const int* aidx;
   const int* count;
@@ -77,21 +77,11 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   __shared__ float2 s_Lx[kMaxOrder + 1], s_Ly[kMaxOrder + 1];
   __shared__ float2 s_Wx[kWChunk][kMaxOrder + 1], s_Wy[kWChunk][kMaxOrder + 1];
   __shared__ float4 s_wg[kWChunk];
-  __shared__ int64_t s_leaf;
   const int tid = threadIdx.x;
   const int p = A.p;
-  if (tid == 0) {
-    int64_t lo = 0, hi = A.nleaf;  // largest k with tile_off[k] <= blockIdx.x
-    while (hi - lo > 1) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (A.tile_off[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid;
-    }
-    s_leaf = lo;
-  }
-  __syncthreads();
-  const int64_t k = s_leaf;
-  const int B = A.leaves[k];
-  const int64_t tile = (int64_t)blockIdx.x - A.tile_off[k];
+  const int2 kt = A.tile_leaf[blockIdx.x];
+  const int64_t k = kt.x;
+  const int64_t tile = kt.y;
   const LeafPlan lp = A.leaf[k];
   for (int l = tid; l <= p; l += kT) {
     const float2 c = A.fL[k * (int64_t)(p + 1) + l];
@@ -600,7 +590,7 @@ void eval32_prepare_expansions(Plan& P, cudaStream_t s) {
   LENS_LAUNCHED("k_to_f32");
 }
 
-void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t* toff,
+void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int2* tile_leaf,
                  int64_t total, double* y, double* jac, PixCorner* pix, const IpmParams* ip,
                  cudaStream_t s) {
   const int64_t nl = P.n_active_leaves;
@@ -614,7 +604,7 @@ void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t*
     LENS_LAUNCHED("k_leaf_grid");
   };
   E32Args A = base_args32(P);
-  A.tile_off = toff;
+  A.tile_leaf = tile_leaf;
   A.rect = rect;
   A.lgrid = lg.as<LeafGrid>();
   A.hf = ff_of(g.h);
@@ -635,10 +625,10 @@ void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t*
 }
 
 void eval32_rays(Plan& P, const double* rays, const int64_t* off, const int* perm,
-                 const int64_t* toff, int64_t total, double* y, double* jac, cudaStream_t s) {
+                 const int2* tile_leaf, int64_t total, double* y, double* jac, cudaStream_t s) {
   wait_expansions(P, s);
   E32Args A = base_args32(P);
-  A.tile_off = toff;
+  A.tile_leaf = tile_leaf;
   A.rays = rays; A.ray_off = off; A.perm = perm;
   A.y = y; A.jac = jac;
   launch32<false, false>(A, total, jac != nullptr, s);

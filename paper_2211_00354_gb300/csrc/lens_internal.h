@@ -266,11 +266,11 @@ void eval32_prepare_expansions(Plan& P, cudaStream_t s);
 // for its tree and tree-only data alone
 void wait_expansions(Plan& P, cudaStream_t s);
 void wait_tree(Plan& P, cudaStream_t s);
-void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int64_t* toff,
+void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int2* tile_leaf,
                  int64_t total, double* y, double* jac, PixCorner* pix, const IpmParams* ip,
                  cudaStream_t s);
 void eval32_rays(Plan& P, const double* rays, const int64_t* off, const int* perm,
-                 const int64_t* toff, int64_t total, double* y, double* jac, cudaStream_t s);
+                 const int2* tile_leaf, int64_t total, double* y, double* jac, cudaStream_t s);
 // map (float64 output) = map32 + row-wise prefix sums of rowdiff, or += with
 // `accumulate`; `clear` zeroes map32 and rowdiff behind the read
 void ipm_finish_map(float* map32, float* rowdiff, int npx, int npy, double* map, bool accumulate,
