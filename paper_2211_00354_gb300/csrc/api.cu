@@ -195,8 +195,7 @@ lens_status lens_fmm_build(const double* stars_xy, const double* masses, int64_t
   // tree, lists and everything that needs only them, on the caller's stream
   tree_build(P, stars_xy, masses, S(stream));
   fmm_tables(P, S(stream));
-  P.M = P.dalloc_n<double2>((size_t)P.nb * (P.p + 1));
-  P.L = P.dalloc_n<double2>((size_t)P.nb * (P.p + 1));
+  fmm_alloc(P);
   if (P.prec == LENS_FP32_BULK) {
     eval32_alloc(P);
     eval32_prepare_tree(P, S(stream));

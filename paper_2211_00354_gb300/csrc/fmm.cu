@@ -36,22 +36,57 @@ constexpr int kWarpsPerBlock = 4;
 __device__ __forceinline__ double2 ld2(const double2* p) { return __ldg(p); }
 
 // ---- P2M: one thread per leaf, accumulators in shared memory -----------------
+// Leaves sorted by star count (counting sort, largest first), so that the
+// lanes of a P2M warp run loops of equal length: with leaves of 1..leaf_size
+// stars in tree order a warp would run its longest leaf's loop on all lanes.
+// PASS 0 counts the non-empty leaves per star count and zeroes the expansions
+// of empty leaves; PASS 1 places each leaf at offs[count] + rank.
+template <int PASS>
+__global__ void k_leaf_bins(const int* __restrict__ count, const int* __restrict__ child,
+                            int64_t nb, int p, int leaf_size, int* __restrict__ bins,
+                            int* __restrict__ offs, int* __restrict__ list,
+                            double2* __restrict__ M) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int key = -1;
+  if (b < nb && child[b] < 0) {
+    const int nst = count[b];
+    if (nst > 0) {
+      key = min(nst, leaf_size);  // a leaf holds at most leaf_size stars
+    } else if (PASS == 0) {
+      double2* out = M + b * (int64_t)(p + 1);
+      for (int k = 0; k <= p; ++k) out[k] = make_double2(0.0, 0.0);
+    }
+  }
+  // one atomic per distinct count in the warp
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (key > 0 && lane == leader) base = atomicAdd(&bins[key], __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (PASS == 1 && key > 0) list[offs[key] + base + __popc(peers & ((1u << lane) - 1u))] = (int)b;
+}
+
+// offs[k] for counts k = leaf_size .. 1 (descending), offs[0] = total
+__global__ void k_bin_offsets(const int* __restrict__ bins, int leaf_size, int* __restrict__ offs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int acc = 0;
+  for (int k = leaf_size; k >= 1; --k) { offs[k] = acc; acc += bins[k]; }
+  offs[0] = acc;
+}
+
 __global__ void k_p2m(const double2* __restrict__ spos, const double* __restrict__ smass,
                       const int* __restrict__ start, const int* __restrict__ count,
-                      const int* __restrict__ child, const int* __restrict__ level,
-                      const int* __restrict__ ix, const int* __restrict__ iy, int64_t b0,
-                      int64_t b1, double lo_x, double lo_y, double root_size, int p,
-                      double2* __restrict__ M) {
+                      const int* __restrict__ level, const int* __restrict__ ix,
+                      const int* __restrict__ iy, const int* __restrict__ list,
+                      const int* __restrict__ total, double lo_x, double lo_y, double root_size,
+                      int p, double2* __restrict__ M) {
   extern __shared__ double2 acc[];  // [(p+1)][blockDim.x]
-  const int64_t b = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (b >= b1) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= *total) return;
+  const int64_t b = list[i];
   const int nst = count[b];
   double2* out = M + b * (int64_t)(p + 1);
-  if (child[b] >= 0) return;  // internal: M2M fills it
-  if (nst == 0) {
-    for (int k = 0; k <= p; ++k) out[k] = make_double2(0.0, 0.0);
-    return;
-  }
   const double r = root_size / (double)(2ull << level[b]);
   const double cx = lo_x + (2.0 * ix[b] + 1.0) * r, cy = lo_y + (2.0 * iy[b] + 1.0) * r;
   const double ir = 1.0 / r;
@@ -84,22 +119,27 @@ __global__ void k_p2m(const double2* __restrict__ spos, const double* __restrict
 // w^k and conj(w)^k are exact, so the rounding is that of the direct form.
 // Thread (parent, k) forms the four H_r[k] = conj(w)^k G_r[k], then thread
 // (parent, l) sums row l: many short float64 chains instead of one long one
-// per parent, so the pipe is fed from many warps.
+// per parent, so the pipe is fed from many warps.  A level's parents are
+// walked through their children: the boxes of level l+1 are the groups of
+// four children of the level-l splits, so group g (boxes c0+4g .. c0+4g+3)
+// has one parent and no thread lands on a leaf.
 constexpr int kM2MThreads = 128;
 
 __global__ void __launch_bounds__(kM2MThreads)
-k_m2m(const int* __restrict__ child, int64_t b0, int64_t b1, int p,
+k_m2m(const int* __restrict__ parent, int64_t c0, int64_t ngroups, int p,
       const double* __restrict__ binom, int ldb, const double2* __restrict__ wpow,
       double2* __restrict__ M) {
   extern __shared__ double2 H[];  // [parents per block][4][p+1]
   const int P1 = p + 1;
   const int per = kM2MThreads / P1;  // parents per block (>= 1 for p <= 64)
   const int t = threadIdx.x, pb = t / P1, k = t - pb * P1;
-  const int64_t b = b0 + (int64_t)blockIdx.x * per + pb;
-  const bool on = pb < per && b < b1 && child[b] >= 0;
+  const int64_t g = (int64_t)blockIdx.x * per + pb;
+  const bool on = pb < per && g < ngroups;
+  const int64_t c = c0 + 4 * g;     // first child of the group
+  const int64_t b = on ? parent[c] : 0;
   double2* Hp = H + (int64_t)pb * 4 * P1;
   if (on) {
-    const double2* A = M + (int64_t)child[b] * P1;  // children c0..c0+3 are contiguous
+    const double2* A = M + c * P1;  // children c .. c+3 are contiguous
     const double2 B0 = ld2(A + 3 * P1 + k), B1 = ld2(A + 2 * P1 + k);
     const double2 B2 = ld2(A + k), B3 = ld2(A + P1 + k);
     const double2 s02 = B0 + B2, d02 = B0 - B2, s13 = B1 + B3, d13 = B1 - B3;
@@ -115,16 +155,23 @@ k_m2m(const int* __restrict__ child, int64_t b0, int64_t b1, int p,
     const int l = k;
     double sx = 0.0, sy = 0.0;
     for (int kk = 0; kk <= l; ++kk) {
-      const double c = __ldg(binom + (int64_t)l * ldb + kk);
+      const double cb = __ldg(binom + (int64_t)l * ldb + kk);
       const double2 h = Hp[((l - kk) & 3) * P1 + kk];
-      sx = fma(c, h.x, sx);
-      sy = fma(c, h.y, sy);
+      sx = fma(cb, h.x, sx);
+      sy = fma(cb, h.y, sy);
     }
     M[b * (int64_t)P1 + l] = cmul(ld2(wpow + l), make_double2(sx, sy));
   }
 }
 
-// ---- downward: L2L + M2L (V) + P2L (X), one warp per active box -----------
+// ---- downward pass ---------------------------------------------------------
+// The far-field part of each local expansion (M2L over the V list, P2L over
+// the X list) reads only multipole expansions and stars, so one launch forms
+// it for the active boxes of every level at once, one warp per box: the
+// float64 work of the coarse levels, a few boxes each, spreads over the whole
+// GPU instead of a handful of SMs per level.  L2L, the only level-to-level
+// dependence, then runs level by level from the top, one thread per
+// (box, coefficient).
 struct DownArgs {
   const int* active;
   int64_t a0, a1;
@@ -154,7 +201,7 @@ inline size_t downward_smem_per_warp(int p) {
   return (std::max(p2l, m2l) + 15) / 16 * 16;
 }
 
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_downward(DownArgs A) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_far_local(DownArgs A) {
   extern __shared__ double2 dsm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t a = A.a0 + (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
@@ -167,21 +214,6 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_downward(DownArgs A) {
   double2 acc[3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) acc[s] = make_double2(0.0, 0.0);
-  // L2L from the parent (levels >= 2; the parent's local expansion is 0 above)
-  const int par = A.parent[B];
-  if (lv >= 2) {
-    const int q = B - A.child[par];
-    const double2* Lp = A.L + (int64_t)par * P1;
-    const double2* S = A.tab.l2l + (int64_t)q * P1 * P1;
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      const int j = lane + 32 * s;
-      if (j > p) break;
-      double2 v = make_double2(0.0, 0.0);
-      for (int l = j; l <= p; ++l) v = cfma(ld2(S + j * P1 + l), ld2(Lp + l), v);
-      acc[s] = v;
-    }
-  }
   // M2L from V.  Up to G entries at a time, their (entry, coefficient) pairs
   // spread over the lanes (p + 1 = 17 coefficients would leave 15 of 32 lanes
   // idle with one entry per pass):
@@ -297,6 +329,29 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_downward(DownArgs A) {
   }
 }
 
+// L2L of the active boxes of one level (>= 2; above it the parent's local
+// expansion is zero), one thread per (box, coefficient j):
+//   L_B[j] += sum_{l >= j} S_q[j][l] L_parent[l],  q = the box's quadrant.
+// The parent of an active box is active and its expansion is final.
+__global__ void k_l2l(const int* __restrict__ active, int64_t a0, int64_t a1,
+                      const int* __restrict__ parent, const int* __restrict__ child,
+                      const double2* __restrict__ l2l, int p, double2* __restrict__ L) {
+  const int P1 = p + 1;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = a0 + t / P1;
+  if (a >= a1) return;
+  const int j = (int)(t - (a - a0) * P1);
+  const int B = active[a];
+  const int par = parent[B];
+  const int q = B - child[par];
+  const double2* Lp = L + (int64_t)par * P1;
+  const double2* S = l2l + ((int64_t)q * P1 + j) * P1;
+  double2 v = make_double2(0.0, 0.0);
+  for (int l = j; l <= p; ++l) v = cfma(ld2(S + l), ld2(Lp + l), v);
+  double2* o = L + (int64_t)B * P1 + j;
+  *o = *o + v;
+}
+
 }  // namespace
 
 // ---- host: tables ----------------------------------------------------------
@@ -385,18 +440,41 @@ void fmm_tables(Plan& P, cudaStream_t s) {
   LENS_CUDA(cudaStreamSynchronize(s));
 }
 
+void fmm_alloc(Plan& P) {
+  const size_t P1 = (size_t)P.p + 1;
+  if (!P.M) P.M = P.dalloc_n<double2>((size_t)P.nb * P1);
+  if (!P.L) P.L = P.dalloc_n<double2>((size_t)P.nb * P1);
+  if (!P.p2m_list) P.p2m_list = P.dalloc_n<int>((size_t)P.nb);
+  if (!P.p2m_bins) P.p2m_bins = P.dalloc_n<int>(2 * ((size_t)P.leaf + 1));
+}
+
 void fmm_p2m(Plan& P, cudaStream_t s) {
   const int p = P.p, P1 = p + 1;
-  if (!P.M) P.M = P.dalloc_n<double2>((size_t)P.nb * P1);
-  // P2M on every leaf (thread per box), all levels at once
+  if (!P.M || !P.p2m_list || !P.p2m_bins) fail(LENS_ECUDA, "internal: expansion buffers not allocated");
+  // P2M on every non-empty leaf (thread per leaf, leaves sorted by star
+  // count), all levels at once
+  const int L = P.leaf;
+  int* cnt = P.p2m_bins;
+  int* offs = cnt + (L + 1);
+  int* list = P.p2m_list;
+  LENS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(L + 1), s));
+  k_leaf_bins<0><<<grid_for(P.nb, 256), 256, 0, s>>>(P.box_count, P.box_child, P.nb, p, L, cnt, offs,
+                                                      list, P.M);
+  LENS_LAUNCHED("k_leaf_bins<count>");
+  k_bin_offsets<<<1, 32, 0, s>>>(cnt, L, offs);
+  LENS_LAUNCHED("k_bin_offsets");
+  LENS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(L + 1), s));
+  k_leaf_bins<1><<<grid_for(P.nb, 256), 256, 0, s>>>(P.box_count, P.box_child, P.nb, p, L, cnt, offs,
+                                                      list, P.M);
+  LENS_LAUNCHED("k_leaf_bins<place>");
   const int tpb = 32;
   const size_t smem = sizeof(double2) * (size_t)P1 * tpb;
   if (smem > 48 * 1024)
     LENS_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_p2m<<<grid_for(P.nb, tpb), tpb, smem, s>>>(P.spos, P.smass, P.box_start, P.box_count,
-                                                P.box_child, P.box_level, P.box_ix, P.box_iy, 0,
-                                                P.nb, P.root_lo[0], P.root_lo[1], P.root_size, p,
-                                                P.M);
+                                                P.box_level, P.box_ix, P.box_iy, list,
+                                                offs, P.root_lo[0], P.root_lo[1], P.root_size,
+                                                p, P.M);
   LENS_LAUNCHED("k_p2m");
 }
 
@@ -406,9 +484,11 @@ void fmm_m2m(Plan& P, cudaStream_t s) {
   const int per = kM2MThreads / P1;
   const size_t smem = sizeof(double2) * 4 * (size_t)P1 * per;
   for (int l = P.nlevels - 2; l >= 0; --l) {
-    const int64_t b0 = P.level_off[l], b1 = P.level_off[l + 1];
-    k_m2m<<<grid_for(b1 - b0, per), kM2MThreads, smem, s>>>(P.box_child, b0, b1, P.p, t.binom,
-                                                             t.ldb, t.wpow, P.M);
+    // level l+1 holds the children of the level-l splits, four per split
+    const int64_t c0 = P.level_off[l + 1], ng = (P.level_off[l + 2] - c0) / 4;
+    if (ng <= 0) continue;
+    k_m2m<<<grid_for(ng, per), kM2MThreads, smem, s>>>(P.box_parent, c0, ng, P.p, t.binom,
+                                                       t.ldb, t.wpow, P.M);
     LENS_LAUNCHED("k_m2m");
   }
 }
@@ -427,13 +507,20 @@ void fmm_downward(Plan& P, cudaStream_t s) {
   A.smem_warp = downward_smem_per_warp(P.p);
   const size_t smem = A.smem_warp * kWarpsPerBlock;
   if (smem > 48 * 1024)
-    LENS_CUDA(cudaFuncSetAttribute(k_downward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  for (int l = 0; l < P.nlevels; ++l) {
-    A.a0 = P.active_level_off[l];
-    A.a1 = P.active_level_off[l + 1];
-    if (A.a1 <= A.a0) continue;
-    k_downward<<<grid_for((A.a1 - A.a0) * 32, 32 * kWarpsPerBlock), 32 * kWarpsPerBlock, smem, s>>>(A);
-    LENS_LAUNCHED("k_downward");
+    LENS_CUDA(cudaFuncSetAttribute(k_far_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  A.a0 = 0;
+  A.a1 = P.n_active;
+  if (A.a1 > 0) {
+    k_far_local<<<grid_for(A.a1 * 32, 32 * kWarpsPerBlock), 32 * kWarpsPerBlock, smem, s>>>(A);
+    LENS_LAUNCHED("k_far_local");
+  }
+  const int P1 = P.p + 1;
+  for (int l = 2; l < P.nlevels; ++l) {
+    const int64_t a0 = P.active_level_off[l], a1 = P.active_level_off[l + 1];
+    if (a1 <= a0) continue;
+    k_l2l<<<grid_for((a1 - a0) * P1, 128), 128, 0, s>>>(P.active, a0, a1, P.box_parent,
+                                                       P.box_child, t.l2l, P.p, P.L);
+    LENS_LAUNCHED("k_l2l");
   }
 }
 

@@ -151,6 +151,8 @@ struct Plan {
   // expansions: (p+1) complex coefficients per box, scaled (see fmm.cu)
   double2* M = nullptr;
   double2* L = nullptr;
+  int* p2m_list = nullptr;  // non-empty leaves sorted by star count (nb slots)
+  int* p2m_bins = nullptr;  // 2 (leaf_size + 1): counts and offsets per star count
   FmmTables tab;
 
   // float32-bulk evaluation data (eval32_prepare)
@@ -217,6 +219,9 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, DeviceAlloc&
 
 void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t s);
 void fmm_tables(Plan& P, cudaStream_t s);
+// expansion buffers (M, L, P2M leaf order), allocated on the caller's stream
+// before the expansions are handed to the plan's own stream
+void fmm_alloc(Plan& P);
 void fmm_p2m(Plan& P, cudaStream_t s);
 void fmm_m2m(Plan& P, cudaStream_t s);
 void fmm_downward(Plan& P, cudaStream_t s);
