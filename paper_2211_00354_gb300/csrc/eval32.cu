@@ -132,22 +132,29 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   // ---- P2P over the near field (stars pre-staged per leaf in float-float) --
   // The leaf's near stars are contiguous: they are staged kChunk at a time
   // and summed in groups of kGroup (8) in plain float32, each group partial then
-  // entering a two-sum (compensated) accumulator.
+  // entering a two-sum (compensated) accumulator.  The staged chunk is padded
+  // with massless stars to whole groups, so every group loop has a fixed trip
+  // count and unrolls (a massless star adds exactly zero: w = 0 * finite).
+  static_assert(kChunk % kGroup == 0, "chunks hold whole groups");
   const int64_t star0 = A.uoff[k], nstar = A.uoff[k + 1] - star0;
   for (int64_t f0 = 0; f0 < nstar; f0 += kChunk) {
     const int nf = (int)min64(kChunk, nstar - f0);
+    const int nfg = (nf + kGroup - 1) / kGroup * kGroup;
     __syncthreads();
-    for (int f = tid; f < nf; f += kT) {
-      const int64_t g = star0 + f0 + f;
-      const float4 v = A.ust[g];
-      const float mm = A.um[g];
+    for (int f = tid; f < nfg; f += kT) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      float mm = 0.f;
+      if (f < nf) {
+        const int64_t g = star0 + f0 + f;
+        v = A.ust[g];
+        mm = A.um[g];
+      }
       s_x[f] = make_float2(-v.x, -v.x); s_y[f] = make_float2(-v.y, -v.y);
       s_xl[f] = make_float2(-v.z, -v.z); s_yl[f] = make_float2(-v.w, -v.w);
       s_m[f] = make_float2(mm, mm);
     }
     __syncthreads();
-    for (int lo = 0; lo < nf; lo += kGroup) {
-      const int hi = min(nf, lo + kGroup);
+    for (int lo = 0; lo < nfg; lo += kGroup) {
       float p1[kRpt], p2[kRpt], pj1[kRpt], pj2[kRpt];
       if (!JAC) {
         // rays (2h, 2h+1) side by side in float2 pair arithmetic
@@ -163,7 +170,9 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
           DXL[h] = make_float2(dxl[2 * h], dxl[2 * h + 1]); DYL[h] = make_float2(dyl[2 * h], dyl[2 * h + 1]);
         }
         const float2 tiny = make_float2(1e-30f, 1e-30f);
-        for (int j = lo; j < hi; ++j) {
+#pragma unroll
+        for (int jj = 0; jj < kGroup; ++jj) {
+          const int j = lo + jj;
           const float2 nsx = s_x[j], nsy = s_y[j], nsxl = s_xl[j], nsyl = s_yl[j], sm = s_m[j];
 #pragma unroll
           for (int h = 0; h < kRpt / 2; ++h) {
@@ -183,7 +192,9 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
       } else {
 #pragma unroll
         for (int q = 0; q < kRpt; ++q) { p1[q] = 0.f; p2[q] = 0.f; pj1[q] = 0.f; pj2[q] = 0.f; }
-        for (int j = lo; j < hi; ++j) {
+#pragma unroll
+        for (int jj = 0; jj < kGroup; ++jj) {
+          const int j = lo + jj;
           const float sx = -s_x[j].x, sy = -s_y[j].x, sxl = -s_xl[j].x, syl = -s_yl[j].x;
           const float sm = s_m[j].x;
 #pragma unroll

@@ -50,17 +50,17 @@ __device__ __forceinline__ T mean_clamp01(T a, T b) {
 // the row band Y <= y <= Y+1, dg/dx is the pixel's indicator, so the area is
 // the contour integral of g dy; on each straight edge g is piecewise linear,
 // giving (y_b - y_a) * mean(g) over the edge's part inside the band.
+// The edge slopes sl[e] = (x1 - x0) / (y1 - y0) are formed once per cell by
+// the caller (any value for a horizontal edge, whose clipped part is empty).
 template <typename T>
-__device__ __forceinline__ T pixel_area(const T* qx, const T* qy, T X, T Y) {
+__device__ __forceinline__ T pixel_area(const T* qx, const T* qy, const T* sl, T X, T Y) {
   T s = (T)0;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    const T x0 = qx[e], y0 = qy[e], x1 = qx[(e + 1) & 3], y1 = qy[(e + 1) & 3];
-    if (y1 == y0) continue;
+    const T x0 = qx[e], y0 = qy[e], y1 = qy[(e + 1) & 3];
     const T ya = fmin(fmax(y0, Y), Y + (T)1), yb = fmin(fmax(y1, Y), Y + (T)1);
     if (ya == yb) continue;
-    const T sl = (x1 - x0) / (y1 - y0);
-    const T xa = x0 + (ya - y0) * sl, xb = x0 + (yb - y0) * sl;
+    const T xa = x0 + (ya - y0) * sl[e], xb = x0 + (yb - y0) * sl[e];
     s += (yb - ya) * mean_clamp01<T>(xa - X, xb - X);
   }
   return s;
@@ -503,6 +503,12 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_f64(IpmArgs A) {
     }
     if (lane == 0) led.nf64 += 1;
     const double inv = 1.0 / A_P;
+    double sl[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double ey = v[(k + 1) & 3] - v[k];
+      sl[k] = ey != 0.0 ? (u[(k + 1) & 3] - u[k]) / ey : 0.0;
+    }
     const float invf = (float)inv;
     float fin = 0.f;
     int ncut = 0;  // warp-uniform: entries waiting in cut_x[w], cut_y[w]
@@ -540,7 +546,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_f64(IpmArgs A) {
         const int take = min(ncut, 32);
         if (lane < take) {
           const int px = cut_x[w][lane], py = cut_y[w][lane];
-          const double a = pixel_area<double>(u, v, (double)px, (double)py);
+          const double a = pixel_area<double>(u, v, sl, (double)px, (double)py);
           const float fr = (float)(a * inv);
           if (fr != 0.0f) {
             atomicAdd(&A.map[(int64_t)(iy0 + py) * A.ip.npx + ix0 + px], A.scale_f * fr);
