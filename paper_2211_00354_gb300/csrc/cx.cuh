@@ -71,6 +71,23 @@ struct fcomp {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Two compensated accumulators side by side (one per ray of a pair) on
+// Blackwell's two-lane float32 instructions: the same two-sum as
+// fcomp::add, with a - b formed as fma(b, -1, a) (exactly a - b: the product
+// is exact and the sum rounds once).
+struct fcomp2 {
+  float2 hi, lo;
+  __device__ __forceinline__ void add(float2 x) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 s = __fadd2_rn(hi, x);
+    const float2 bb = __ffma2_rn(hi, m1, s);  // s - hi
+    const float2 t = __ffma2_rn(bb, m1, s);   // s - bb
+    const float2 e = __fadd2_rn(__ffma2_rn(t, m1, hi), __ffma2_rn(bb, m1, x));  // (hi - t) + (x - bb)
+    hi = s;
+    lo = __fadd2_rn(lo, e);
+  }
+};
+
 // Spread the low 32 bits of x to the even bit positions of a 64-bit word.
 __host__ __device__ __forceinline__ uint64_t spread2(uint64_t x) {
   x &= 0xffffffffull;
@@ -147,4 +164,65 @@ __device__ __forceinline__ ff ff_mul(ff a, float b) {
   return ff_norm(p, e);
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// The same float-float operations on two values side by side (one per ray of
+// a pair), on the two-lane float32 instructions; a - b is fma(b, -1, a), and
+// -round(x*y) is round(-x*y), so every lane computes exactly what the scalar
+// form computes.
+struct ff2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
+__device__ __forceinline__ ff2 ff2_norm(float2 s, float2 e) {  // |s| >= |e|
+  ff2 r;
+  r.hi = __fadd2_rn(s, e);
+  r.lo = fsub2(e, fsub2(r.hi, s));
+  return r;
+}
+// a + b (sign = +1) or a - b (sign = -1), two-sum of the high parts
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = __fadd2_rn(a, b);
+  const float2 bb = fsub2(s, a);
+  e = __fadd2_rn(fsub2(a, fsub2(s, bb)), fsub2(b, bb));
+}
+__device__ __forceinline__ void two_diff2(float2 a, float2 b, float2& s, float2& e) {
+  s = fsub2(a, b);
+  const float2 bb = fsub2(s, a);
+  e = fsub2(fsub2(a, fsub2(s, bb)), __fadd2_rn(b, bb));
+}
+__device__ __forceinline__ ff2 ff2_add(ff2 a, ff2 b) {
+  float2 s, e;
+  two_sum2(a.hi, b.hi, s, e);
+  e = __fadd2_rn(e, __fadd2_rn(a.lo, b.lo));
+  return ff2_norm(s, e);
+}
+__device__ __forceinline__ ff2 ff2_add(ff a, ff2 b) {  // a the same in both lanes
+  return ff2_add(ff2{f2(a.hi), f2(a.lo)}, b);
+}
+__device__ __forceinline__ ff2 ff2_sub(ff2 a, ff2 b) {
+  float2 s, e;
+  two_diff2(a.hi, b.hi, s, e);
+  e = __fadd2_rn(e, fsub2(a.lo, b.lo));
+  return ff2_norm(s, e);
+}
+__device__ __forceinline__ ff2 ff2_add(ff2 a, float2 b) {
+  float2 s, e;
+  two_sum2(a.hi, b, s, e);
+  e = __fadd2_rn(e, a.lo);
+  return ff2_norm(s, e);
+}
+__device__ __forceinline__ ff2 ff2_sub(ff2 a, float2 b) {
+  float2 s, e;
+  two_diff2(a.hi, b, s, e);
+  e = __fadd2_rn(e, a.lo);
+  return ff2_norm(s, e);
+}
+__device__ __forceinline__ ff2 ff2_mul(ff a, ff2 b) {  // a the same in both lanes
+  const float2 ah = f2(a.hi);
+  const float2 p = __fmul2_rn(ah, b.hi);
+  float2 e = __ffma2_rn(ah, b.hi, __fmul2_rn(f2(-a.hi), b.hi));  // a.hi b.hi - p, exact
+  e = __ffma2_rn(ah, b.lo, __ffma2_rn(f2(a.lo), b.hi, e));
+  return ff2_norm(p, e);
+}
 }  // namespace lens

@@ -103,6 +103,12 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   int64_t oidx[kRpt];
   bool ok[kRpt];
   fcomp n1[kRpt], n2[kRpt], nj1[kRpt], nj2[kRpt];
+  fcomp2 N1[kRpt / 2], N2[kRpt / 2];  // paired accumulators of the Jacobian-free path
+#pragma unroll
+  for (int h = 0; h < kRpt / 2; ++h) {
+    N1[h] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    N2[h] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  }
 #pragma unroll
   for (int q = 0; q < kRpt; ++q) {
     const int64_t loc = tile * (kT * kRpt) + (int64_t)q * kT + tid;
@@ -186,8 +192,8 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
         }
 #pragma unroll
         for (int h = 0; h < kRpt / 2; ++h) {
-          p1[2 * h] = P1[h].x; p1[2 * h + 1] = P1[h].y;
-          p2[2 * h] = P2[h].x; p2[2 * h + 1] = P2[h].y;
+          N1[h].add(P1[h]);
+          N2[h].add(P2[h]);
         }
       } else {
 #pragma unroll
@@ -214,10 +220,12 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
           }
         }
       }
+      if (JAC) {
 #pragma unroll
-      for (int q = 0; q < kRpt; ++q) {
-        n1[q].add(p1[q]); n2[q].add(p2[q]);
-        if (JAC) { nj1[q].add(pj1[q]); nj2[q].add(pj2[q]); }
+        for (int q = 0; q < kRpt; ++q) {
+          n1[q].add(p1[q]); n2[q].add(p2[q]);
+          nj1[q].add(pj1[q]); nj2[q].add(pj2[q]);
+        }
       }
     }
   }
@@ -289,26 +297,21 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
       }
     }
   }
-  if (!JAC) {
-#pragma unroll
-    for (int h = 0; h < kRpt / 2; ++h) {
-      fw[2 * h] = make_float2(FX[h].x, FY[h].x);
-      fw[2 * h + 1] = make_float2(FX[h].y, FY[h].y);
-    }
-  }
 
   // ---- L2P + epilogue --------------------------------------------------------
   __syncthreads();
   const float ir = lp.ir;
-  // L2P by Horner's rule, paired rays without the Jacobian
-  float2 fl[kRpt];
-  if (!JAC) {
+  if constexpr (!JAC) {
+    // L2P by Horner's rule and the float-float lens equation for rays
+    // (2h, 2h+1) side by side in the two-lane float32 instructions
     const float2 irr = make_float2(ir, ir), nirr = make_float2(-ir, -ir);
 #pragma unroll
     for (int h = 0; h < kRpt / 2; ++h) {
-      const float2 wx = __fmul2_rn(make_float2(dx[2 * h], dx[2 * h + 1]), irr);
-      const float2 wy = __fmul2_rn(make_float2(dy[2 * h], dy[2 * h + 1]), irr);
-      const float2 nwy = __fmul2_rn(make_float2(dy[2 * h], dy[2 * h + 1]), nirr);
+      const float2 DXh = make_float2(dx[2 * h], dx[2 * h + 1]);
+      const float2 DYh = make_float2(dy[2 * h], dy[2 * h + 1]);
+      const float2 wx = __fmul2_rn(DXh, irr);
+      const float2 wy = __fmul2_rn(DYh, irr);
+      const float2 nwy = __fmul2_rn(DYh, nirr);
       float2 fx = make_float2(0.f, 0.f), fy = make_float2(0.f, 0.f);
       if (p >= 1) {
         float2 sx = s_Lx[p], sy = s_Ly[p];
@@ -322,63 +325,111 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
         fx = __ffma2_rn(sx, wx, __fmul2_rn(sy, nwy));
         fy = __ffma2_rn(sx, wy, __fmul2_rn(sy, wx));
       }
-      fl[2 * h] = make_float2(fx.x, fy.x);
-      fl[2 * h + 1] = make_float2(fx.y, fy.y);
-    }
-  }
+      // f = L2P + M2P (the far W boxes)
+      fx = __fadd2_rn(fx, FX[h]);
+      fy = __fadd2_rn(fy, FY[h]);
+      // y1 = a x1 - Re f - near1, y2 = b x2 + Im f - near2 (alpha = conj f)
+      ff2 T1 = ff2_mul(A.af, ff2{DXh, make_float2(dxl[2 * h], dxl[2 * h + 1])});
+      T1 = ff2_sub(T1, fx);
+      T1 = ff2_sub(T1, ff2{N1[h].hi, N1[h].lo});
+      ff2 T2 = ff2_mul(A.bf, ff2{DYh, make_float2(dyl[2 * h], dyl[2 * h + 1])});
+      T2 = ff2_add(T2, fy);
+      T2 = ff2_sub(T2, ff2{N2[h].hi, N2[h].lo});
+      if (PIX) {
+        const ff2 U = ff2_add(lg.U1f, ff2_mul(A.iduf, T1));
+        const ff2 V = ff2_add(lg.V1f, ff2_mul(A.idvf, T2));
+        const float2 ku2 = make_float2(floorf(U.hi.x), floorf(U.hi.y));
+        const float2 kv2 = make_float2(floorf(V.hi.x), floorf(V.hi.y));
+        const float2 fu2 = __fadd2_rn(fsub2(U.hi, ku2), U.lo);
+        const float2 fv2 = __fadd2_rn(fsub2(V.hi, kv2), V.lo);
 #pragma unroll
-  for (int q = 0; q < kRpt; ++q) {
-    if (!ok[q]) continue;
-    float2 f = make_float2(0.f, 0.f), df = make_float2(0.f, 0.f);
-    if (!JAC) {
-      f = fl[q];
-    } else if (p >= 1) {
-      const float2 w = make_float2(dx[q] * ir, dy[q] * ir);
-      float2 s = make_float2(s_Lx[p].x, s_Ly[p].x);
-      for (int l = p - 1; l >= 1; --l) s = cfma(s, w, make_float2(s_Lx[l].x, s_Ly[l].x));
-      f = cmul(s, w);
-      float2 t = make_float2((float)p * s_Lx[p].x, (float)p * s_Ly[p].x);
-      for (int l = p - 1; l >= 1; --l)
-        t = cfma(t, w, make_float2((float)l * s_Lx[l].x, (float)l * s_Ly[l].x));
-      df = make_float2(t.x * ir, t.y * ir);
-    }
-    f = f + fw[q];
-    ff T1 = ff_mul(A.af, ff{dx[q], dxl[q]});
-    T1 = ff_add(T1, -f.x);
-    T1 = ff_add(T1, ff{-n1[q].hi, -n1[q].lo});
-    ff T2 = ff_mul(A.bf, ff{dy[q], dyl[q]});
-    T2 = ff_add(T2, f.y);
-    T2 = ff_add(T2, ff{-n2[q].hi, -n2[q].lo});
-    if (PIX) {
-      PixCorner pc;
-      const ff U = ff_add(lg.U1f, ff_mul(A.iduf, T1));
-      const ff V = ff_add(lg.V1f, ff_mul(A.idvf, T2));
-      bool far = lg.far || !(fabsf(U.hi) < 5.0e8f) || !(fabsf(V.hi) < 5.0e8f);
-      float ku = floorf(U.hi), kv = floorf(V.hi);
-      float fu = (U.hi - ku) + U.lo, fv = (V.hi - kv) + V.lo;
-      if (fu < 0.f) { ku -= 1.f; fu += 1.f; } else if (fu >= 1.f) { ku += 1.f; fu -= 1.f; }
-      if (fv < 0.f) { kv -= 1.f; fv += 1.f; } else if (fv >= 1.f) { kv += 1.f; fv -= 1.f; }
-      // float -> int32 (|k| < 5e8); integer adds only afterwards
-      const int64_t iu = (int64_t)lg.U1i + (int)ku, iv = (int64_t)lg.V1i + (int)kv;
-      far = far || !(iu > -1073741824ll && iu < 1073741824ll && iv > -1073741824ll &&
-                     iv < 1073741824ll);
-      if (!far) {
-        pc.iu = (int)iu; pc.fu = fu; pc.iv = (int)iv; pc.fv = fv;
+        for (int c = 0; c < 2; ++c) {
+          const int q = 2 * h + c;
+          if (!ok[q]) continue;
+          const float uh = c ? U.hi.y : U.hi.x, vh = c ? V.hi.y : V.hi.x;
+          float ku = c ? ku2.y : ku2.x, kv = c ? kv2.y : kv2.x;
+          float fu = c ? fu2.y : fu2.x, fv = c ? fv2.y : fv2.x;
+          bool far = lg.far || !(fabsf(uh) < 5.0e8f) || !(fabsf(vh) < 5.0e8f);
+          if (fu < 0.f) { ku -= 1.f; fu += 1.f; } else if (fu >= 1.f) { ku += 1.f; fu -= 1.f; }
+          if (fv < 0.f) { kv -= 1.f; fv += 1.f; } else if (fv >= 1.f) { kv += 1.f; fv -= 1.f; }
+          // float -> int32 (|k| < 5e8); integer adds only afterwards
+          const int64_t iu = (int64_t)lg.U1i + (int)ku, iv = (int64_t)lg.V1i + (int)kv;
+          far = far || !(iu > -1073741824ll && iu < 1073741824ll && iv > -1073741824ll &&
+                         iv < 1073741824ll);
+          PixCorner pc;
+          if (!far) {
+            pc.iu = (int)iu; pc.fu = fu; pc.iv = (int)iv; pc.fv = fv;
+          } else {
+            pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
+          }
+          A.pix[oidx[q]] = pc;
+        }
       } else {
-        pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int q = 2 * h + c;
+          if (!ok[q]) continue;
+          const ff t1 = c ? ff{T1.hi.y, T1.lo.y} : ff{T1.hi.x, T1.lo.x};
+          const ff t2 = c ? ff{T2.hi.y, T2.lo.y} : ff{T2.hi.x, T2.lo.x};
+          A.y[2 * oidx[q]] = lp.K1 + ff_to_double(t1);
+          A.y[2 * oidx[q] + 1] = lp.K2 + ff_to_double(t2);
+        }
       }
-      A.pix[oidx[q]] = pc;
-      continue;
     }
-    A.y[2 * oidx[q]] = lp.K1 + ff_to_double(T1);
-    A.y[2 * oidx[q] + 1] = lp.K2 + ff_to_double(T2);
-    if (JAC) {
-      const double dre = (double)df.x + (double)dfw[q].x + nj1[q].value();
-      const double dim = (double)df.y + (double)dfw[q].y + nj2[q].value();
-      A.jac[4 * oidx[q] + 0] = A.a - dre;
-      A.jac[4 * oidx[q] + 1] = dim;
-      A.jac[4 * oidx[q] + 2] = dim;
-      A.jac[4 * oidx[q] + 3] = A.b + dre;
+  } else {
+    // with the Jacobian: one ray at a time
+#pragma unroll
+    for (int q = 0; q < kRpt; ++q) {
+      if (!ok[q]) continue;
+      float2 f = make_float2(0.f, 0.f), df = make_float2(0.f, 0.f);
+      if (p >= 1) {
+        const float2 w = make_float2(dx[q] * ir, dy[q] * ir);
+        float2 s = make_float2(s_Lx[p].x, s_Ly[p].x);
+        for (int l = p - 1; l >= 1; --l) s = cfma(s, w, make_float2(s_Lx[l].x, s_Ly[l].x));
+        f = cmul(s, w);
+        float2 t = make_float2((float)p * s_Lx[p].x, (float)p * s_Ly[p].x);
+        for (int l = p - 1; l >= 1; --l)
+          t = cfma(t, w, make_float2((float)l * s_Lx[l].x, (float)l * s_Ly[l].x));
+        df = make_float2(t.x * ir, t.y * ir);
+      }
+      f = f + fw[q];
+      ff T1 = ff_mul(A.af, ff{dx[q], dxl[q]});
+      T1 = ff_add(T1, -f.x);
+      T1 = ff_add(T1, ff{-n1[q].hi, -n1[q].lo});
+      ff T2 = ff_mul(A.bf, ff{dy[q], dyl[q]});
+      T2 = ff_add(T2, f.y);
+      T2 = ff_add(T2, ff{-n2[q].hi, -n2[q].lo});
+      if (PIX) {
+        PixCorner pc;
+        const ff U = ff_add(lg.U1f, ff_mul(A.iduf, T1));
+        const ff V = ff_add(lg.V1f, ff_mul(A.idvf, T2));
+        bool far = lg.far || !(fabsf(U.hi) < 5.0e8f) || !(fabsf(V.hi) < 5.0e8f);
+        float ku = floorf(U.hi), kv = floorf(V.hi);
+        float fu = (U.hi - ku) + U.lo, fv = (V.hi - kv) + V.lo;
+        if (fu < 0.f) { ku -= 1.f; fu += 1.f; } else if (fu >= 1.f) { ku += 1.f; fu -= 1.f; }
+        if (fv < 0.f) { kv -= 1.f; fv += 1.f; } else if (fv >= 1.f) { kv += 1.f; fv -= 1.f; }
+        // float -> int32 (|k| < 5e8); integer adds only afterwards
+        const int64_t iu = (int64_t)lg.U1i + (int)ku, iv = (int64_t)lg.V1i + (int)kv;
+        far = far || !(iu > -1073741824ll && iu < 1073741824ll && iv > -1073741824ll &&
+                       iv < 1073741824ll);
+        if (!far) {
+          pc.iu = (int)iu; pc.fu = fu; pc.iv = (int)iv; pc.fv = fv;
+        } else {
+          pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
+        }
+        A.pix[oidx[q]] = pc;
+        continue;
+      }
+      A.y[2 * oidx[q]] = lp.K1 + ff_to_double(T1);
+      A.y[2 * oidx[q] + 1] = lp.K2 + ff_to_double(T2);
+      if (JAC) {
+        const double dre = (double)df.x + (double)dfw[q].x + nj1[q].value();
+        const double dim = (double)df.y + (double)dfw[q].y + nj2[q].value();
+        A.jac[4 * oidx[q] + 0] = A.a - dre;
+        A.jac[4 * oidx[q] + 1] = dim;
+        A.jac[4 * oidx[q] + 2] = dim;
+        A.jac[4 * oidx[q] + 3] = A.b + dre;
+      }
     }
   }
 }
