@@ -138,7 +138,7 @@ __device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L) 
   __syncthreads();
   if (threadIdx.x < 7) {
     double x = 0;
-    for (int q = 0; q < kIpmThreads / 32; ++q)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
       x += threadIdx.x < 2 ? (double)shf[threadIdx.x][q] : (double)shu[threadIdx.x - 2][q];
     // slots 2, 3, 4, 5, 8, 9, 10
     const int slot = threadIdx.x < 4 ? 2 + threadIdx.x : 4 + threadIdx.x;
@@ -212,6 +212,8 @@ struct CellShared {
   int4 box[kWarps][32];                   // ix0, iy0, cx0, cy0 (box clipped to the map at cx0, cy0)
   int2 ext[kWarps][32];                   // clipped box width, 1 / A_P (float bits)
   int cum[kWarps][32], cum2[kWarps][32];
+  // owner lane of each (cell, pixel) task of the small cells (<= 32 x 16)
+  unsigned char own[kWarps][32 * kSmallBox * kSmallBox];
   float4 seg[kWarps][128];                // crossing segments: xa, xb, dy, first pixel (int bits)
   int n[kWarps][128];
   int row[kWarps][32], cell[kWarps][32];
@@ -335,15 +337,23 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
     }
     // ---- B: pixels of small cells -------------------------------------------
     const int tot1 = warp_counts(nsmall, sh.cum[w], lane);
+    {
+      // each lane marks its tasks with its index: one byte load finds a
+      // task's cell
+      const int st = sh.cum[w][lane] - nsmall;
+      for (int i = 0; i < nsmall; ++i) sh.own[w][st + i] = (unsigned char)lane;
+      __syncwarp();
+    }
     for (int f0 = 0; f0 < tot1; f0 += 32) {
       const int f = f0 + lane;
       if (f < tot1) {
-        int off;
-        const int L = warp_owner(sh.cum[w], f, off);
+        const int L = sh.own[w][f];
+        const int off = f - (L ? sh.cum[w][L - 1] : 0);
         const int4 bx = sh.box[w][L];
         const int2 ex = sh.ext[w][L];
         const int wd = ex.x;
-        const int r = off / wd;
+        // off < 16 and wd <= 4: off / wd without a division
+        const int r = wd == 3 ? (off * 21846) >> 16 : off >> (wd >> 1);
         const int px = bx.z + off - r * wd, py = bx.w + r;
         float qx[4], qy[4], sl[4];
         unpack4(qx, sh.qx[w][L]);
@@ -461,8 +471,8 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
 __global__ void __launch_bounds__(kIpmThreads) k_ipm_f64(IpmArgs A) {
   __shared__ int cut_x[kWarps][64], cut_y[kWarps][64];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t wg = (blockIdx.x * (int64_t)kIpmThreads + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * kIpmThreads) >> 5;
+  const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int nq = *A.qcount;
   const double ac = A.ip.a_cell;
   Ledger led;
