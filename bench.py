@@ -427,7 +427,8 @@ def main():
                                        else "independent map per GPU" if world > 1 else "1 GPU")},
             "map_ms": ms, "maps_per_s": (1 if strips else world) / (ms / 1e3),
             "omega_per_s": 10.0 * f.npx * f.npy * f.n * (1 if strips else world) / (ms / 1e3),
-            "phase_ms": {"build": info["ms_build"], "deflect": st["ms_deflect"],
+            "phase_ms": {"build": info["ms_build"], "tree": info["ms_tree"],
+                         "deflect": st["ms_deflect"],
                          "ipm": st["ms_ipm"], "eval_kernel": ms_eval, "ipm_kernels": ms_ipm},
             "work": {"rays": rays_step, "p2p_pairs": pairs, "m2p_evals": m2p,
                      "ipm_updates": st["ipm_updates"], "cells_queued": st["cells_queued"],

@@ -20,9 +20,10 @@
  *     "host" pointers are ordinary host memory.  All floating-point arrays are
  *     float64, C-contiguous.  Positions are interleaved pairs (x1, x2).
  *   - The caller owns every buffer it passes.  A plan owns its internal
- *     arrays, which it obtains from the caller's lens_allocator (or from
- *     cudaMallocAsync when the allocator pointer is NULL) and frees in
- *     lens_plan_destroy.
+ *     arrays, which it obtains from the caller's lens_allocator (or, when the
+ *     allocator pointer is NULL, from a stream-ordered memory pool the library
+ *     keeps per device, which retains up to 16 GiB of freed blocks for reuse)
+ *     and frees in lens_plan_destroy.
  *   - Every call returns a lens_status; on error the outputs are undefined
  *     and lens_last_error() gives a message (thread-local).  No call aborts
  *     or throws across the ABI.
@@ -125,6 +126,7 @@ typedef struct {
   int64_t device_bytes;        /* plan-owned device memory */
   double ms_build;             /* device time of the build, tree to expansions */
   int64_t build_launches;      /* kernels the build launched */
+  double ms_tree;              /* of ms_build: tree, lists and near-field staging */
 } lens_plan_info;
 
 /* ---- FMM plan ------------------------------------------------------------
@@ -136,7 +138,9 @@ typedef struct {
  * box that meets the target region.
  *   stars_xy: dev, n x 2; masses: dev, n (any real values); n >= 1.
  *   kappa_s, gamma: smooth field (footnote to Eq. 1).
- *   opts: host; allocator: host or NULL (cudaMallocAsync on stream).
+ *   opts: host; allocator: host or NULL (the library's stream-ordered pool on
+ *   `stream`, one per device, which keeps up to 16 GiB of freed blocks for
+ *   reuse).
  *   *out receives the plan.  Synchronises `stream` a few times (tree and
  *   list sizes).  The tree and lists are formed on `stream`; the expansions
  *   then run on a high-priority stream owned by the plan, and the call

@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -64,6 +66,35 @@ void fault_point_alloc() {
   if (fault_spec().alloc_at == k) fail(LENS_EFAULT_INJECTED, "injected allocation fault");
 }
 
+// Without a caller allocator, device memory comes from one stream-ordered
+// pool per device owned by the library.  Freed blocks stay reserved for reuse
+// (up to kPoolKeepBytes across synchronisations), so the next plan or map
+// reuses them instead of mapping fresh memory: with the default pool, which
+// returns freed memory at every synchronisation, the tree build's allocations
+// between its size read-backs cost ~0.7 ms per build.
+constexpr uint64_t kPoolKeepBytes = 16ull << 30;
+
+static cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  LENS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  LENS_CUDA(cudaMemPoolCreate(&pool, &props));
+  uint64_t keep = kPoolKeepBytes;
+  LENS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  pools[dev] = pool;
+  return pool;
+}
+
 void* DeviceAlloc::alloc(size_t bytes) {
   fault_point_alloc();
   if (bytes == 0) bytes = 16;
@@ -72,10 +103,10 @@ void* DeviceAlloc::alloc(size_t bytes) {
     p = a.alloc(bytes, (void*)stream, a.ctx);
     if (!p) fail(LENS_ENOMEM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
   } else {
-    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, library_pool(), stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      fail(LENS_ENOMEM, "cudaMallocAsync(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+      fail(LENS_ENOMEM, "cudaMallocFromPoolAsync(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
   }
   return p;
@@ -189,26 +220,31 @@ lens_status lens_fmm_build(const double* stars_xy, const double* masses, int64_t
   if (P.has_target) std::memcpy(P.target, opts->target_box, sizeof(P.target));
   LENS_CUDA(cudaEventCreate(&P.ev_start));
   LENS_CUDA(cudaEventCreate(&P.ev_tree));
+  LENS_CUDA(cudaEventCreateWithFlags(&P.ev_boxes, cudaEventDisableTiming));
   LENS_CUDA(cudaEventCreate(&P.ev_fmm));
   LENS_CUDA(cudaEventRecord(P.ev_start, S(stream)));
   const long long l0 = launch_count();
-  // tree, lists and everything that needs only them, on the caller's stream
-  tree_build(P, stars_xy, masses, S(stream));
+  // The tree on the caller's stream.  The upward pass (P2M, M2M) needs only
+  // the boxes, so it runs on the plan's high-priority stream while the
+  // caller's stream forms the active boxes, the interaction lists and the
+  // float32 near-field staging; the downward pass follows the lists.
   fmm_tables(P, S(stream));
+  tree_build_boxes(P, stars_xy, masses, S(stream));
   fmm_alloc(P);
+  LENS_CUDA(cudaEventRecord(P.ev_boxes, S(stream)));
+  int lo_prio = 0, hi_prio = 0;
+  LENS_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+  LENS_CUDA(cudaStreamCreateWithPriority(&P.fmm_stream, cudaStreamNonBlocking, hi_prio));
+  LENS_CUDA(cudaStreamWaitEvent(P.fmm_stream, P.ev_boxes, 0));
+  fmm_p2m(P, P.fmm_stream);
+  fmm_m2m(P, P.fmm_stream);
+  tree_build_lists(P, S(stream));
   if (P.prec == LENS_FP32_BULK) {
     eval32_alloc(P);
     eval32_prepare_tree(P, S(stream));
   }
   LENS_CUDA(cudaEventRecord(P.ev_tree, S(stream)));
-  // the expansions on the plan's high-priority stream: the caller's next
-  // near-field work overlaps them (float64 pipe here, float32 there)
-  int lo_prio = 0, hi_prio = 0;
-  LENS_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
-  LENS_CUDA(cudaStreamCreateWithPriority(&P.fmm_stream, cudaStreamNonBlocking, hi_prio));
   LENS_CUDA(cudaStreamWaitEvent(P.fmm_stream, P.ev_tree, 0));
-  fmm_p2m(P, P.fmm_stream);
-  fmm_m2m(P, P.fmm_stream);
   fmm_downward(P, P.fmm_stream);
   if (P.prec == LENS_FP32_BULK) eval32_prepare_expansions(P, P.fmm_stream);
   LENS_CUDA(cudaEventRecord(P.ev_fmm, P.fmm_stream));
@@ -239,7 +275,7 @@ void lens_plan_destroy(lens_plan* plan) {
   cudaStreamSynchronize(P.da.stream);
   P.ev_clear();
   if (P.fmm_stream) cudaStreamDestroy(P.fmm_stream);
-  for (cudaEvent_t e : {P.ev_start, P.ev_tree, P.ev_fmm})
+  for (cudaEvent_t e : {P.ev_start, P.ev_boxes, P.ev_tree, P.ev_fmm})
     if (e) cudaEventDestroy(e);
   delete plan;
 }
@@ -261,12 +297,14 @@ lens_status lens_plan_info_get(const lens_plan* plan, lens_plan_info* info) {
   info->root_size = P.root_size;
   info->device_bytes = P.device_bytes;
   // the expansions may still be running on the plan's stream
-  float ms = 0.f;
+  float ms = 0.f, ms_tree = 0.f;
   if (P.ev_fmm) {
     LENS_CUDA(cudaEventSynchronize(P.ev_fmm));
     LENS_CUDA(cudaEventElapsedTime(&ms, P.ev_start, P.ev_fmm));
+    LENS_CUDA(cudaEventElapsedTime(&ms_tree, P.ev_start, P.ev_tree));
   }
   info->ms_build = ms;
+  info->ms_tree = ms_tree;
   info->build_launches = P.build_launches;
   info->n_leaves = -1;  // not tracked separately (n_active_leaves is)
   LENS_API_END

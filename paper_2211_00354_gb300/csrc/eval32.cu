@@ -623,9 +623,8 @@ void eval32_prepare_tree(Plan& P, cudaStream_t s) {
   exclusive_scan_i64(P.f_ncnt, P.f_uoff, nl + 1, P.da, s);
   exclusive_scan_i64(P.f_wcnt, P.f_woff, nl + 1, P.da, s);
   int64_t tot[2] = {0, 0};
-  LENS_CUDA(cudaMemcpyAsync(&tot[0], P.f_uoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LENS_CUDA(cudaMemcpyAsync(&tot[1], P.f_woff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LENS_CUDA(cudaStreamSynchronize(s));
+  const int64_t* addr[2] = {P.f_uoff + nl, P.f_woff + nl};
+  read_i64(addr, 2, tot, P.da, s);
   P.f_ust = P.dalloc_n<float4>(tot[0]);
   P.f_um = P.dalloc_n<float>(tot[0]);
   P.f_wlist = P.dalloc_n<int>(tot[1]);

@@ -174,12 +174,13 @@ struct Plan {
   double ms_build = 0;
   int64_t build_launches = 0;
 
-  // The expansions (P2M, M2M, downward pass, their float32 copies) run on a
-  // high-priority stream of the plan after the tree; ev_fmm marks their end.
-  // Work that reads M or L waits on ev_fmm (wait_expansions); the near field
-  // needs only the tree and runs meanwhile.
+  // The expansions run on a high-priority stream of the plan: P2M and M2M
+  // once the boxes exist (ev_boxes), the downward pass and the float32 copies
+  // once the lists exist (ev_tree); ev_fmm marks their end.  Work that reads
+  // M or L waits on ev_fmm (wait_expansions); work that needs only the tree
+  // waits on ev_tree.
   cudaStream_t fmm_stream = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_tree = nullptr, ev_fmm = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_boxes = nullptr, ev_tree = nullptr, ev_fmm = nullptr;
   bool build_timed = false;
 
   // per-active-index count of stars in the U list (work accounting)
@@ -212,12 +213,21 @@ void direct_deflect(const double* stars, const double* masses, int64_t n,
                     double ks, double g, const double* rays, int64_t m, int prec,
                     double* y, double* jac, DeviceAlloc& da, cudaStream_t s);
 
+// Stable LSD sort of (keys, vals) by key bits [lo_bit, bits), 8 bits a pass.
 void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits,
-                    DeviceAlloc& da, cudaStream_t s);
+                    DeviceAlloc& da, cudaStream_t s, int lo_bit = 0);
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, DeviceAlloc& da,
                         cudaStream_t s);
+// host[i] = *addrs[i] (device int64 values, n <= kMaxPick): one small kernel,
+// one copy and one synchronisation instead of a round trip per value (a
+// device-to-pageable copy returns only when it is done)
+constexpr int kMaxPick = 64;
+void read_i64(const int64_t* const* addrs, int n, int64_t* host, DeviceAlloc& da, cudaStream_t s);
 
-void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t s);
+// Tree build in two halves: the boxes (bounds, keys, sort, splits: all the
+// upward pass needs), then the active boxes and the interaction lists.
+void tree_build_boxes(Plan& P, const double* stars, const double* masses, cudaStream_t s);
+void tree_build_lists(Plan& P, cudaStream_t s);
 void fmm_tables(Plan& P, cudaStream_t s);
 // expansion buffers (M, L, P2M leaf order), allocated on the caller's stream
 // before the expansions are handed to the plan's own stream

@@ -196,13 +196,13 @@ k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ til
 }  // namespace
 
 void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, DeviceAlloc& da,
-                    cudaStream_t s) {
-  if (n <= 1 || bits <= 0) return;
+                    cudaStream_t s, int lo_bit) {
+  if (n <= 1 || bits <= lo_bit) return;
   const int nblocks = (int)((n + kSortTile - 1) / kSortTile);
   Scratch k2(&da, sizeof(uint64_t) * (size_t)n);
   Scratch v2(&da, vals ? sizeof(uint32_t) * (size_t)n : 0);
   Scratch hist(&da, sizeof(uint32_t) * 256 * (size_t)nblocks);
-  const int npass = (bits + 7) / 8;
+  const int npass = (bits - lo_bit + 7) / 8;
   Scratch dtot(&da, sizeof(uint32_t) * 256 * (size_t)npass);
   LENS_CUDA(cudaMemsetAsync(dtot.p, 0, dtot.bytes, s));
   uint64_t* ka = keys;
@@ -210,7 +210,7 @@ void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, DeviceA
   uint32_t* va = vals;
   uint32_t* vb = v2.as<uint32_t>();
   int passes = 0;
-  for (int shift = 0; shift < bits; shift += 8, ++passes) {
+  for (int shift = lo_bit; shift < bits; shift += 8, ++passes) {
     uint32_t* dt = dtot.as<uint32_t>() + 256 * passes;
     k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(ka, n, shift, nblocks, hist.as<uint32_t>(), dt);
     LENS_LAUNCHED("k_radix_hist");
@@ -226,6 +226,31 @@ void radix_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, int bits, DeviceA
     LENS_CUDA(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
     if (vals) LENS_CUDA(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
   }
+}
+
+// ---- batched read-back of int64 values ------------------------------------
+namespace {
+struct PickArgs {
+  const int64_t* src[kMaxPick];
+  int n;
+};
+__global__ void k_pick_i64(PickArgs a, int64_t* __restrict__ out) {
+  const int i = threadIdx.x;
+  if (i < a.n) out[i] = *a.src[i];
+}
+}  // namespace
+
+void read_i64(const int64_t* const* addrs, int n, int64_t* host, DeviceAlloc& da, cudaStream_t s) {
+  if (n <= 0) return;
+  if (n > kMaxPick) fail(LENS_EINVAL, "internal: too many values in one read-back");
+  PickArgs a{};
+  for (int i = 0; i < n; ++i) a.src[i] = addrs[i];
+  a.n = n;
+  Scratch out(&da, sizeof(int64_t) * (size_t)n);
+  k_pick_i64<<<1, kMaxPick, 0, s>>>(a, out.as<int64_t>());
+  LENS_LAUNCHED("k_pick_i64");
+  LENS_CUDA(cudaMemcpyAsync(host, out.p, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+  LENS_CUDA(cudaStreamSynchronize(s));
 }
 
 // out[i] = sum_{j<i} in[j]; returns nothing (caller reads out[n-1] + in[n-1]

@@ -23,6 +23,7 @@
 // non-adjacent children of adjacent boxes finer than B (M2P).  Empty boxes
 // are skipped in every list.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "cx.cuh"
@@ -114,8 +115,11 @@ __device__ __forceinline__ int first_level(const uint64_t* k, int64_t i, int dep
 
 // Pass 1 (write == false): per-level split counts.  Pass 2: write entries
 // (level << 32 | first star) at per-level cursors.
+// The keys need only be sorted by their level-dcap prefixes (the top 2 dcap
+// of their 2 depth bits): a box of level dcap with more than leaf stars sets
+// deep_flag (the caller then sorts fully, or, at dcap == depth, fails).
 template <bool WRITE>
-__global__ void k_splits(const uint64_t* __restrict__ k, int64_t n, int depth, int leaf,
+__global__ void k_splits(const uint64_t* __restrict__ k, int64_t n, int depth, int dcap, int leaf,
                          unsigned long long* __restrict__ counts, int* __restrict__ deep_flag,
                          unsigned long long* __restrict__ cursor, uint64_t* __restrict__ out) {
   __shared__ unsigned int sc[kMaxDepth + 1];
@@ -129,7 +133,7 @@ __global__ void k_splits(const uint64_t* __restrict__ k, int64_t n, int depth, i
       const uint64_t mask = (l == 0) ? ~0ull : ((1ull << (2 * (depth - l))) - 1ull);
       const int64_t end = (l == 0) ? n : upper_bound(k, i + 1, n, k[i] | mask);
       if (end - i <= leaf) break;
-      if (l == depth) { if (!WRITE) atomicExch(deep_flag, 1); break; }
+      if (l == dcap) { if (!WRITE) atomicExch(deep_flag, 1); break; }
       if (WRITE) {
         unsigned long long pos = atomicAdd(&cursor[l], 1ull);
         out[pos] = ((uint64_t)l << 32) | (uint64_t)i;
@@ -340,9 +344,14 @@ __global__ void k_lists(TreeView T, const int* __restrict__ active, int64_t nact
   }
 }
 
+__global__ void k_sentinels(int64_t* a, int64_t* b, int64_t* c, int64_t* d, int64_t va,
+                            int64_t vb, int64_t vc, int64_t vd) {
+  if (threadIdx.x == 0) { *a = va; *b = vb; *c = vc; *d = vd; }
+}
+
 }  // namespace
 
-void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t s) {
+void tree_build_boxes(Plan& P, const double* stars, const double* masses, cudaStream_t s) {
   const int64_t n = P.n;
   const int depth = P.depth;
   // ---- 1. bounds + finiteness -------------------------------------------
@@ -384,25 +393,42 @@ void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t
   k_keys<<<grid_for(n, 256), 256, 0, s>>>(stars, n, P.root_lo[0], P.root_lo[1], scale, depth,
                                            P.skey, P.sidx);
   LENS_LAUNCHED("k_keys");
-  radix_sort_u64(P.skey, P.sidx, n, 2 * depth, P.da, s);
-  k_gather<<<grid_for(n, 256), 256, 0, s>>>(stars, masses, P.sidx, n, P.spos, P.smass);
-  LENS_LAUNCHED("k_gather");
+  // Sort by the top key bits only, down to a level the tree is unlikely to
+  // pass (6 levels below the depth of a uniform field of n stars, leaf
+  // stars per box); if a box of that level still holds more than leaf stars,
+  // the keys are sorted again in full.
+  int dcap = 6;
+  while (dcap < depth && (double)P.leaf * std::pow(4.0, dcap - 6) < (double)n) ++dcap;
+  dcap = std::min(depth, dcap);
+  const int lo_bit = (2 * (depth - dcap)) / 8 * 8;
+  dcap = depth - lo_bit / 2;  // the levels the sorted bits resolve
+  radix_sort_u64(P.skey, P.sidx, n, 2 * depth, P.da, s, lo_bit);
 
   // ---- 3. split nodes ---------------------------------------------------
   Scratch dcnt(&P.da, sizeof(unsigned long long) * (kMaxDepth + 2) + sizeof(int) * 4);
   unsigned long long* counts = dcnt.as<unsigned long long>();
   int* deep = reinterpret_cast<int*>(counts + kMaxDepth + 2);
-  LENS_CUDA(cudaMemsetAsync(dcnt.p, 0, dcnt.bytes, s));
-  k_splits<false><<<grid_for(n, 256), 256, 0, s>>>(P.skey, n, depth, P.leaf, counts, deep,
-                                                   nullptr, nullptr);
-  LENS_LAUNCHED("k_splits<count>");
   unsigned long long hc[kMaxDepth + 2];
   int hdeep[4];
-  LENS_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
-  LENS_CUDA(cudaMemcpyAsync(hdeep, deep, sizeof(hdeep), cudaMemcpyDeviceToHost, s));
-  LENS_CUDA(cudaStreamSynchronize(s));
-  if (hdeep[0]) fail(LENS_EDEPTH, "a box at the depth cap still holds more than leaf_size stars "
-                                  "(coincident stars?): raise leaf_size or max_depth");
+  for (;;) {
+    LENS_CUDA(cudaMemsetAsync(dcnt.p, 0, dcnt.bytes, s));
+    k_splits<false><<<grid_for(n, 256), 256, 0, s>>>(P.skey, n, depth, dcap, P.leaf, counts, deep,
+                                                     nullptr, nullptr);
+    LENS_LAUNCHED("k_splits<count>");
+    LENS_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    LENS_CUDA(cudaMemcpyAsync(hdeep, deep, sizeof(hdeep), cudaMemcpyDeviceToHost, s));
+    LENS_CUDA(cudaStreamSynchronize(s));
+    if (!hdeep[0]) break;
+    if (dcap == depth)
+      fail(LENS_EDEPTH, "a box at the depth cap still holds more than leaf_size stars "
+                        "(coincident stars?): raise leaf_size or max_depth");
+    // deeper than the partial sort resolves: sort the low bits too (all
+    // passes again, least significant first)
+    radix_sort_u64(P.skey, P.sidx, n, 2 * depth, P.da, s, 0);
+    dcap = depth;
+  }
+  k_gather<<<grid_for(n, 256), 256, 0, s>>>(stars, masses, P.sidx, n, P.spos, P.smass);
+  LENS_LAUNCHED("k_gather");
   LevelOffsets soff{}, boff{};
   int64_t nsplit = 0;
   int maxl = -1;
@@ -444,7 +470,7 @@ void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t
     for (int l = 0; l < kMaxDepth + 2; ++l) hcur[l] = (unsigned long long)soff.off[l];
     LENS_CUDA(cudaMemcpyAsync(dcur.p, hcur.data(), sizeof(unsigned long long) * hcur.size(),
                               cudaMemcpyHostToDevice, s));
-    k_splits<true><<<grid_for(n, 256), 256, 0, s>>>(P.skey, n, depth, P.leaf, nullptr, nullptr,
+    k_splits<true><<<grid_for(n, 256), 256, 0, s>>>(P.skey, n, depth, dcap, P.leaf, nullptr, nullptr,
                                                     dcur.as<unsigned long long>(),
                                                     dspl.as<uint64_t>());
     LENS_LAUNCHED("k_splits<write>");
@@ -457,6 +483,14 @@ void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t
     LENS_LAUNCHED("k_fill_boxes");
   }
 
+}
+
+void tree_build_lists(Plan& P, cudaStream_t s) {
+  const int64_t nb = P.nb;
+  LevelOffsets boff{};
+  for (int l = 0; l <= kMaxDepth + 1; ++l)
+    boff.off[l] = l <= P.nlevels ? P.level_off[l] : P.nb;
+  boff.nlevels = P.nlevels;
   // ---- 4. active boxes -------------------------------------------------
   TreeView T{P.box_start, P.box_count, P.box_child, P.box_level, P.box_ix, P.box_iy,
              P.box_code, boff};
@@ -470,14 +504,20 @@ void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t
   exclusive_scan_i64(fl.as<int64_t>(), pl.as<int64_t>(), nb, P.da, s);
   std::vector<int64_t> hpos(P.nlevels + 1);
   int64_t lastf[2], lastp[2];
-  for (int l = 0; l < P.nlevels; ++l)
-    LENS_CUDA(cudaMemcpyAsync(&hpos[l], pa.as<int64_t>() + P.level_off[l], sizeof(int64_t),
-                              cudaMemcpyDeviceToHost, s));
-  LENS_CUDA(cudaMemcpyAsync(&lastf[0], fa.as<int64_t>() + nb - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LENS_CUDA(cudaMemcpyAsync(&lastp[0], pa.as<int64_t>() + nb - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LENS_CUDA(cudaMemcpyAsync(&lastf[1], fl.as<int64_t>() + nb - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LENS_CUDA(cudaMemcpyAsync(&lastp[1], pl.as<int64_t>() + nb - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  LENS_CUDA(cudaStreamSynchronize(s));
+  {
+    // level starts of the active list and the two totals, in one read-back
+    std::vector<const int64_t*> addr;
+    for (int l = 0; l < P.nlevels; ++l) addr.push_back(pa.as<int64_t>() + P.level_off[l]);
+    addr.push_back(fa.as<int64_t>() + nb - 1);
+    addr.push_back(pa.as<int64_t>() + nb - 1);
+    addr.push_back(fl.as<int64_t>() + nb - 1);
+    addr.push_back(pl.as<int64_t>() + nb - 1);
+    std::vector<int64_t> v(addr.size());
+    read_i64(addr.data(), (int)addr.size(), v.data(), P.da, s);
+    for (int l = 0; l < P.nlevels; ++l) hpos[l] = v[l];
+    lastf[0] = v[P.nlevels]; lastp[0] = v[P.nlevels + 1];
+    lastf[1] = v[P.nlevels + 2]; lastp[1] = v[P.nlevels + 3];
+  }
   P.n_active = lastf[0] + lastp[0];
   P.n_active_leaves = lastf[1] + lastp[1];
   hpos[P.nlevels] = P.n_active;
@@ -509,12 +549,6 @@ void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t
   }
   // totals: last offset + last count; also total U stars
   std::vector<int64_t> hl(10, 0);
-  for (int q = 0; q < 4; ++q) {
-    if (na > 0) {
-      LENS_CUDA(cudaMemcpyAsync(&hl[2 * q], offs[q] + na - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-      LENS_CUDA(cudaMemcpyAsync(&hl[2 * q + 1], c + q * na + na - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    }
-  }
   P.ustar_cnt = P.dalloc_n<int64_t>(na + 1);
   if (na > 0)
     LENS_CUDA(cudaMemcpyAsync(P.ustar_cnt, c + 4 * na, sizeof(int64_t) * na,
@@ -522,15 +556,22 @@ void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t
   Scratch usum(&P.da, sizeof(int64_t) * (na + 1));
   if (na > 0) {
     exclusive_scan_i64(c + 4 * na, usum.as<int64_t>(), na, P.da, s);
-    LENS_CUDA(cudaMemcpyAsync(&hl[8], usum.as<int64_t>() + na - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    LENS_CUDA(cudaMemcpyAsync(&hl[9], c + 4 * na + na - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    const int64_t* addr[10];
+    for (int q = 0; q < 4; ++q) {
+      addr[2 * q] = offs[q] + na - 1;
+      addr[2 * q + 1] = c + q * na + na - 1;
+    }
+    addr[8] = usum.as<int64_t>() + na - 1;
+    addr[9] = c + 4 * na + na - 1;
+    read_i64(addr, 10, hl.data(), P.da, s);
   }
-  LENS_CUDA(cudaStreamSynchronize(s));
   for (int q = 0; q < 4; ++q) tot[q] = hl[2 * q] + hl[2 * q + 1];
   P.u_stars = hl[8] + hl[9];
-  // write the totals as the sentinel offsets[na]
-  for (int q = 0; q < 4; ++q)
-    LENS_CUDA(cudaMemcpyAsync(offs[q] + na, &tot[q], sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  // write the totals as the sentinel offsets[na] (kernel parameters: no host
+  // buffer has to outlive the call)
+  k_sentinels<<<1, 32, 0, s>>>(offs[0] + na, offs[1] + na, offs[2] + na, offs[3] + na, tot[0],
+                               tot[1], tot[2], tot[3]);
+  LENS_LAUNCHED("k_sentinels");
   P.nV = tot[0]; P.nX = tot[1]; P.nU = tot[2]; P.nW = tot[3];
   P.V_list = P.dalloc_n<int>(tot[0]);
   P.X_list = P.dalloc_n<int>(tot[1]);
@@ -544,8 +585,6 @@ void tree_build(Plan& P, const double* stars, const double* masses, cudaStream_t
   P.X_off = offs[1];
   P.U_off = offs[2];
   P.W_off = offs[3];
-  // the host copies of the totals must outlive the async H2D copies above
-  LENS_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace lens

@@ -2,8 +2,10 @@
 
 Argument marshalling only: every step of the hot path runs in the library's
 CUDA kernels.  Tensors are torch float64 CUDA tensors; the binding passes
-their data pointers and the current CUDA stream.  Plan-owned device memory
-comes from torch's caching allocator through the C ABI's allocator hook.
+their data pointers and the current CUDA stream.  Plan memory comes from the
+library's own stream-ordered pool (no Python call per allocation), or, with
+use_torch_allocator=True, from torch's caching allocator through the C ABI's
+allocator hook.
 There is no CPU fallback: if the library cannot be loaded, every call raises.
 """
 from __future__ import annotations
@@ -84,7 +86,7 @@ class lens_plan_info(ctypes.Structure):
                 ("leaf_size", ctypes.c_int), ("prec", ctypes.c_int),
                 ("root_lo", ctypes.c_double * 2), ("root_size", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("ms_build", ctypes.c_double),
-                ("build_launches", ctypes.c_int64)]
+                ("build_launches", ctypes.c_int64), ("ms_tree", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -207,7 +209,7 @@ class LensFMM:
 
     def __init__(self, stars: torch.Tensor, masses: torch.Tensor, kappa_s: float = 0.0,
                  gamma: float = 0.0, p: int = 16, leaf_size: int = 16, prec: int = FP32_BULK,
-                 target_box=None, max_depth: int = 0, use_torch_allocator: bool = True,
+                 target_box=None, max_depth: int = 0, use_torch_allocator: bool = False,
                  stream=None):
         lib = load()
         stars = _dev(stars, "stars", 2)
