@@ -119,6 +119,28 @@ def test_adaptive_tree_on_clustered_field():
     assert alpha_rel_err(y32, y_ref, x, f.kappa_s, f.gamma).max() < 2e-5
 
 
+def test_tree_deeper_than_the_partial_sort():
+    # 1000 field stars over ~60 ER plus 1000 stars within 1e-5 ER: ~26 levels,
+    # far below the levels the build sorts first for 2000 stars, so the keys
+    # are sorted again in full and the splits recounted
+    rng = np.random.default_rng(5)
+    wide = synth.uniform_disk(rng, 1000, 30.0)
+    tight = synth.uniform_disk(rng, 1000, 1e-5, center=(1.25, -0.75))
+    f = synth.Field(stars=np.concatenate([wide, tight]), masses=rng.uniform(0.5, 1.5, 2000),
+                    kappa_s=0.1, gamma=0.2, kappa_star=0.0)
+    x = np.concatenate([synth.random_rays(6, 1500, (-20, -20), (20, 20)),
+                        tight[::5] + 3e-6, np.array([[1.25, -0.75], [1.25 + 1e-4, -0.75]])])
+    y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x)
+    with plan_for(f, 48, 8, lens.FP64, (-20.5, 20.5, -20.5, 20.5)) as P:
+        y = P.deflect(T(x)).cpu().numpy()
+        info = P.info()
+    assert info["levels"] > 20
+    assert alpha_rel_err(y, y_ref, x, f.kappa_s, f.gamma).max() < 1e-10
+    with plan_for(f, 24, 8, lens.FP32_BULK, (-20.5, 20.5, -20.5, 20.5)) as P:
+        y32 = P.deflect(T(x)).cpu().numpy()
+    assert alpha_rel_err(y32, y_ref, x, f.kappa_s, f.gamma).max() < 2e-5
+
+
 @pytest.mark.parametrize("prec,tol", [(lens.FP64, 1e-8), (lens.FP32_BULK, 2e-4)])
 def test_jacobian(prec, tol):
     f = synth.config_uniform(seed=1, n=800, kappa_star=0.3, kappa_s=0.2, gamma=0.4)
