@@ -215,8 +215,8 @@ struct CellShared {
   // owner lane of each (cell, pixel) task of the small cells (<= 32 x 16)
   unsigned char own[kWarps][32 * kSmallBox * kSmallBox];
   float4 seg[kWarps][128];                // crossing segments: xa, xb, dy, first pixel (int bits)
-  int n[kWarps][128];
-  int row[kWarps][32], cell[kWarps][32];
+  int4 sst[kWarps][32];                   // starts of a row task's segments 1..3 in its pixel list
+  int2 rbi[kWarps][32];                   // row task: map offset of (row, box x0), 1 / A_P (float bits)
 };
 
 __device__ __forceinline__ void unpack4(float (&a)[4], const float4 v) {
@@ -391,10 +391,12 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
         unpack4(qy, sh.qy[w][L]);
         unpack4(slp, sh.sl[w][L]);
         float vsum = 0.f, frow = 0.f;
+        int st[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int t = lane * 4 + e;
           int n = 0;
+          st[e] = cnt;
           const float x0 = qx[e], y0 = qy[e];
           const float y1 = qy[(e + 1) & 3];
           const float ya = fminf(fmaxf(y0, Y), Y + 1.f), yb = fminf(fmaxf(y1, Y), Y + 1.f);
@@ -420,14 +422,14 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
               sh.seg[w][t] = make_float4(xa, xb, dy, __int_as_float(pa));
             }
           }
-          sh.n[w][t] = n;
           cnt += n;
         }
         if (vsum != 0.f) { atomicAdd(&A.D[drow + cx0], vsum); led.nupd += 1; }
         led.fin += frow * inv;
         led.fout -= frow * inv;
-        sh.row[w][lane] = py;
-        sh.cell[w][lane] = L;
+        sh.sst[w][lane] = make_int4(st[1], st[2], st[3], cnt);
+        // npx * npy < 2^31 and |ix0| < 2^30: the offset fits an int
+        sh.rbi[w][lane] = make_int2(py * npx + ix0, __float_as_int(inv));
       }
       // crossed pixels of these 32 rows, spread over the lanes
       int* cum = sh.cum[w];  // the small-cell counts are no longer needed
@@ -438,16 +440,18 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
         if (g < totp) {
           int off;
           const int L = warp_owner(cum, g, off);
-          int t = L * 4;
-          while (off >= sh.n[w][t]) { off -= sh.n[w][t]; ++t; }
-          const float4 sg = sh.seg[w][t];
+          // segment k of row task L: the last one starting at or before off
+          // (an empty segment shares its start with the next one)
+          const int4 ss = sh.sst[w][L];
+          const int k = (off >= ss.x) + (off >= ss.y) + (off >= ss.z);
+          off -= k == 0 ? 0 : k == 1 ? ss.x : k == 2 ? ss.y : ss.z;
+          const float4 sg = sh.seg[w][L * 4 + k];
           const int X = __float_as_int(sg.w) + off;
           const float a = sg.z * mean_clamp01f(sg.x - (float)X, sg.y - (float)X);
           if (a != 0.0f) {
-            const int cl = sh.cell[w][L];
-            const int2 ex = sh.ext[w][cl];
-            const float fr = a * __int_as_float(ex.y);
-            atomicAdd(&A.map[(int64_t)sh.row[w][L] * npx + sh.box[w][cl].x + X], A.scale_f * fr);
+            const int2 rb = sh.rbi[w][L];
+            const float fr = a * __int_as_float(rb.y);
+            atomicAdd(&A.map[rb.x + X], A.scale_f * fr);
             led.fin += fr;
             led.fout -= fr;
             led.nupd += 1;
