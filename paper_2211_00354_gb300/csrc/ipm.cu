@@ -29,6 +29,7 @@ namespace lens {
 namespace {
 
 constexpr int kIpmThreads = 256;
+constexpr int kChunksPerGrab = 4;  // 32-cell chunks per fetch of the chunk counter
 constexpr int kFar = 0x7fffffff;
 
 // Mean of clamp(g, 0, 1) for g running linearly from a to b, written so that
@@ -244,14 +245,17 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
   const int64_t W = A.nx + 1;
   const int npx = A.ip.npx, npy = A.ip.npy;
   Ledger led;
-  // chunks of 32 cells are handed out by a counter (qcount[1]), so the
-  // warps of a block finish together however the large cells fall
+  // Chunks of 32 cells are handed out by a counter (qcount[1]), so the
+  // warps of a block finish together however the large cells fall; one
+  // fetch takes kChunksPerGrab chunks (a single address serves all warps, and
+  // a fetch per chunk made it the bound of a pass without B and C work).
   unsigned* next = reinterpret_cast<unsigned*>(A.qcount) + 1;
-  unsigned ch_u = 0;
-  if (lane == 0) ch_u = atomicAdd(next, 1u);
-  for (int64_t ch = __shfl_sync(0xffffffffu, ch_u, 0); ch < nchunks;) {
-    // the following chunk's index is fetched while this one is processed
-    if (lane == 0) ch_u = atomicAdd(next, 1u);
+  unsigned g_u = 0;
+  if (lane == 0) g_u = atomicAdd(next, 1u);
+  int left = kChunksPerGrab;
+  for (int64_t ch = (int64_t)__shfl_sync(0xffffffffu, g_u, 0) * kChunksPerGrab; ch < nchunks;) {
+    // the following grab is fetched while this one is processed
+    if (lane == 0 && left == kChunksPerGrab) g_u = atomicAdd(next, 1u);
     // ---- A: one cell per lane ------------------------------------------------
     const int64_t c = ch * 32 + lane;
     int nsmall = 0, nrows = 0;
@@ -461,7 +465,12 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
       __syncwarp();
     }
     __syncwarp();  // the next chunk overwrites this one's staging
-    ch = __shfl_sync(0xffffffffu, ch_u, 0);
+    if (--left > 0) {
+      ++ch;
+    } else {
+      left = kChunksPerGrab;
+      ch = (int64_t)__shfl_sync(0xffffffffu, g_u, 0) * kChunksPerGrab;
+    }
   }
   block_add_stats(A.stats, led);
 }

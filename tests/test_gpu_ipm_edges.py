@@ -83,3 +83,26 @@ def test_every_cell_degenerate():
     assert np.all(mp == 0) and np.all(ref == 0)
     assert st["cells_degenerate"] == st_ref["cells_degenerate"] == grid.nx * grid.ny
     assert st["area_degenerate"] == pytest.approx(st["area_total"], rel=1e-9)
+
+
+def test_cells_spanning_the_whole_map_without_a_cap():
+    # a point lens inside a coarse grid: the cells next to the lens map to
+    # polygons hundreds of pixels across (rows of a large cell wider than the
+    # per-warp staging), no cap, so every one is apportioned
+    f = synth.Field(stars=np.array([[0.013, -0.021]]), masses=np.array([1.0]), kappa_s=0.0,
+                    gamma=0.0, kappa_star=0.0)
+    grid = synth.Grid(x0=-1.5, y0=-1.5, h=0.05, nx=60, ny=60)
+    box = (-3.0, 3.0, -3.0, 3.0)
+    npx = npy = 300
+    mp, st, ref, st_ref = gpu_and_oracle_maps(f, grid, box, npx, npy, cap=0)
+    # the widest polygon's pixel box, from the oracle's deflections
+    y = oracle.deflect(f.stars, f.masses, 0.0, 0.0, grid.corners().reshape(-1, 2))
+    y = y.reshape(grid.ny + 1, grid.nx + 1, 2)
+    u = (y[..., 0] - box[0]) / 0.02
+    wmax = max(np.ptp(u[j:j + 2, i:i + 2]) for j in range(grid.ny) for i in range(grid.nx))
+    assert wmax > 200
+    good = np.abs(ref) > 1e-3 * np.abs(ref).max()
+    assert np.mean(np.abs(mp[good] - ref[good]) / np.abs(ref[good])) < 1e-3
+    for k in ("area_in_map", "area_outside"):
+        assert st[k] == pytest.approx(st_ref[k], rel=1e-5, abs=1e-6 * st_ref["area_total"])
+    assert st["cells_dropped"] == 0
