@@ -307,7 +307,7 @@ def main():
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                 "ms_per_launch": ms_eval / launches}
     else:
-        roof = {"bound": "hbm", "kernel": "k_ipm_cells+k_ipm_f64", "achieved": ipm_gbs,
+        roof = {"bound": "hbm", "kernel": "k_ipm_cells+k_ipm_ext", "achieved": ipm_gbs,
                 "peak": hbm_peak, "unit": "GB/s", "frac": ipm_gbs / hbm_peak, "traffic": ipm_traffic,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                 "ms_per_launch": ms_ipm / launches}
@@ -432,7 +432,7 @@ def main():
                          "ipm": st["ms_ipm"], "eval_kernel": ms_eval, "ipm_kernels": ms_ipm},
             "work": {"rays": rays_step, "p2p_pairs": pairs, "m2p_evals": m2p,
                      "ipm_updates": st["ipm_updates"], "cells_queued": st["cells_queued"],
-                     "cells_fp64": st["cells_fp64"],
+                     "cells_ext": st["cells_ext"],
                      "pairs_per_ray": pairs / rays_step},
             "tree": {k: info[k] for k in ("n_boxes", "n_active_boxes", "n_active_leaves", "n_v",
                                           "n_x", "n_u", "n_w", "levels")},

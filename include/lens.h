@@ -111,7 +111,7 @@ typedef struct {
   double m2p_evals;    /* ray-box multipole evaluations (W lists) */
   double ipm_updates;  /* (cell, pixel) map increments */
   double cells_queued; /* cells sent to the warp-per-cell path */
-  double cells_fp64;   /* of those, ill-conditioned cells redone in float64 */
+  double cells_ext;    /* of those, ill-conditioned cells redone in float-float (~48 bits) */
   double ms_eval_kernel;
   double ms_ipm_kernel;
   int64_t launches;    /* kernels this call launched */

@@ -470,7 +470,7 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     stats->m2p_evals = hs[14];
     stats->ipm_updates = hs[8];
     stats->cells_queued = hs[9];
-    stats->cells_fp64 = hs[10];
+    stats->cells_ext = hs[10];
     stats->ms_eval_kernel = mse;
     stats->ms_ipm_kernel = msk;
     stats->launches = launch_count() - l0;

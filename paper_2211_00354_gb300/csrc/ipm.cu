@@ -7,14 +7,14 @@
 //     map[pix] += (h^2 / S*) * a_pix / A_P.
 //
 // Corners arrive in pixel coordinates u = (y1 - u0)/du, v = (y2 - v0)/dv,
-// split as (floor, float fraction) by the deflection epilogue, so the common
-// case needs no float64 at all.  One warp takes 32 consecutive cells
+// split as (floor, float fraction) by the deflection epilogue, so no step
+// needs float64.  One warp takes 32 consecutive cells
 // (k_ipm_cells): single-pixel cells add their whole area; cells with a pixel
 // box up to 4 x 4 get one overlap per pixel; larger cells are swept row band
 // by row band, whole-pixel runs going to a per-row difference array and
 // only the pixels an edge crosses getting an overlap; all three kinds of
 // work are spread evenly over the warp's lanes.  Ill-conditioned cells
-// (|A_P| small against the box) are queued for float64 (k_ipm_f64).
+// (|A_P| small against the box) are queued for float-float (k_ipm_ext).
 // Overlaps come from Green's theorem, edge by edge (the apportioning rule of
 // Sec. 2.3): the result is the winding-number-weighted area, so inverted and
 // self-intersecting (critical) cells are handled "naively", as the
@@ -32,45 +32,11 @@ constexpr int kIpmThreads = 256;
 constexpr int kChunksPerGrab = 4;  // 32-cell chunks per fetch of the chunk counter
 constexpr int kFar = 0x7fffffff;
 
-// Mean of clamp(g, 0, 1) for g running linearly from a to b, written so that
-// no branch cancels digits: equal-region cases are exact, and a kink inside
-// [a, b] contributes each region's piece separately.
-template <typename T>
-__device__ __forceinline__ T mean_clamp01(T a, T b) {
-  if (a > b) { const T t = a; a = b; b = t; }
-  if (b <= (T)0) return (T)0;
-  if (a >= (T)1) return (T)1;
-  if (a >= (T)0 && b <= (T)1) return (T)0.5 * (a + b);
-  const T lo = a > (T)0 ? a : (T)0, hi = b < (T)1 ? b : (T)1;
-  const T I = (T)0.5 * (hi - lo) * (hi + lo) + (b > (T)1 ? b - (T)1 : (T)0);
-  return I / (b - a);
-}
-
-// Signed (winding-weighted) area of the quadrilateral q inside the unit pixel
-// [X, X+1] x [Y, Y+1] by Green's theorem: with g(x) = clamp(x - X, 0, 1) on
-// the row band Y <= y <= Y+1, dg/dx is the pixel's indicator, so the area is
-// the contour integral of g dy; on each straight edge g is piecewise linear,
-// giving (y_b - y_a) * mean(g) over the edge's part inside the band.
-// The edge slopes sl[e] = (x1 - x0) / (y1 - y0) are formed once per cell by
-// the caller (any value for a horizontal edge, whose clipped part is empty).
-template <typename T>
-__device__ __forceinline__ T pixel_area(const T* qx, const T* qy, const T* sl, T X, T Y) {
-  T s = (T)0;
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const T x0 = qx[e], y0 = qy[e], y1 = qy[(e + 1) & 3];
-    const T ya = fmin(fmax(y0, Y), Y + (T)1), yb = fmin(fmax(y1, Y), Y + (T)1);
-    if (ya == yb) continue;
-    const T xa = x0 + (ya - y0) * sl[e], xb = x0 + (yb - y0) * sl[e];
-    s += (yb - ya) * mean_clamp01<T>(xa - X, xb - X);
-  }
-  return s;
-}
-
-// float32 form of mean_clamp01 without branches (the lanes of a warp take
-// different cases): the integral of the clamp over [lo, hi] divided by the
-// length; a vanishing length (a vertical edge) takes the clamped midpoint.
-// All-below-0 gives exactly 0; the other pure cases are within an ulp.
+// Mean of clamp(g, 0, 1) for g running linearly from a to b, without
+// branches (the lanes of a warp take different cases): the integral of the
+// clamp over [lo, hi] divided by the length; a vanishing length (a vertical
+// edge) takes the clamped midpoint.  All-below-0 gives exactly 0; the other
+// pure cases are within an ulp.
 __device__ __forceinline__ float mean_clamp01f(float a, float b) {
   const float lo = fminf(a, b), hi = fmaxf(a, b);
   const float l0 = fmaxf(lo, 0.f), h1 = fminf(hi, 1.f);
@@ -79,8 +45,13 @@ __device__ __forceinline__ float mean_clamp01f(float a, float b) {
   return d > 1e-30f ? I * frcp_fast(d) : fminf(fmaxf(0.5f * (lo + hi), 0.f), 1.f);
 }
 
-// pixel_area() in float32 with the edge slopes dx/dy given (0 for a
-// horizontal edge, whose clipped part then has ya == yb and adds nothing).
+// Signed (winding-weighted) area of the quadrilateral q inside the unit pixel
+// [X, X+1] x [Y, Y+1] by Green's theorem: with g(x) = clamp(x - X, 0, 1) on
+// the row band Y <= y <= Y+1, dg/dx is the pixel's indicator, so the area is
+// the contour integral of g dy; on each straight edge g is piecewise linear,
+// giving (y_b - y_a) * mean(g) over the edge's part inside the band.  The
+// edge slopes dx/dy are given (0 for a horizontal edge, whose clipped part
+// then has ya == yb and adds nothing).
 __device__ __forceinline__ float pixel_area_f(const float* qx, const float* qy, const float* sl,
                                               float X, float Y) {
   float s = 0.f;
@@ -104,6 +75,7 @@ struct IpmArgs {
   int* queue; int* qcount;   // qcount[0] queue length, qcount[1] chunk counter
   IpmParams ip;
   float thr_area;       // fast-path lower bound on |A_P| in pixel units
+  float thr_degen;      // |A_P| (pixel units) at or below which a cell is degenerate
   float scale_f;        // ip.scale in float32
 };
 
@@ -111,10 +83,10 @@ struct IpmArgs {
 // float64 per cell).  Device stats slots: [2] sum of in-map fractions,
 // [3] sum of outside fractions (cells wholly outside count 1), [4] dropped
 // cells, [5] degenerate cells, [8] map increments, [9] cells on the large-cell
-// or float64 path, [10] float64 cells; the host multiplies by the cell area.
+// or float-float path, [10] float-float cells; the host multiplies by the cell area.
 struct Ledger {
   float fin = 0.f, fout = 0.f;
-  unsigned ndrop = 0, ndeg = 0, nupd = 0, nq = 0, nf64 = 0;
+  unsigned ndrop = 0, ndeg = 0, nupd = 0, nq = 0, nff = 0;
 };
 
 __device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L) {
@@ -131,7 +103,7 @@ __device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L) 
   const unsigned u1 = __reduce_add_sync(0xffffffffu, L.ndeg);
   const unsigned u2 = __reduce_add_sync(0xffffffffu, L.nupd);
   const unsigned u3 = __reduce_add_sync(0xffffffffu, L.nq);
-  const unsigned u4 = __reduce_add_sync(0xffffffffu, L.nf64);
+  const unsigned u4 = __reduce_add_sync(0xffffffffu, L.nff);
   if (lane == 0) {
     shf[0][w] = f0; shf[1][w] = f1;
     shu[0][w] = u0; shu[1][w] = u1; shu[2][w] = u2; shu[3][w] = u3; shu[4][w] = u4;
@@ -148,7 +120,7 @@ __device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L) 
 }
 
 // Does the segment P->Q meet the closed unit square at (ox, oy)?  (float32
-// pre-filter for the float64 path: a pixel that no edge meets is covered by
+// pre-filter for the float-float path: a pixel that no edge meets is covered by
 // the polygon's winding number exactly.)
 __device__ __forceinline__ bool seg_meets_pixel(float px, float py, float qx, float qy, float ox,
                                                 float oy) {
@@ -227,7 +199,7 @@ __device__ __forceinline__ void unpack4(float (&a)[4], const float4 v) {
 // One warp per 32 consecutive cells of a grid row (grid-stride over chunks).
 //  A. lane = cell: corners (coalesced), pixel box, ledger of cells that are
 //     dropped or outside, single-pixel cells (fraction 1), hand-off of
-//     ill-conditioned cells to the float64 queue;
+//     ill-conditioned cells to the float-float queue;
 //  B. small cells (box <= 4 x 4): the warp's (cell, pixel) pairs spread over
 //     the lanes, one Green's-theorem overlap each;
 //  C. large cells: the warp's (cell, row) pairs spread over the lanes; in the
@@ -235,7 +207,7 @@ __device__ __forceinline__ void unpack4(float (&a)[4], const float4 v) {
 //     adds dy = yb - ya to each pixel X with X + 1 <= min(xa, xb): that
 //     whole-pixel run enters the per-row difference array as +v / -v at its
 //     ends, and only the pixels the segment crosses get an explicit overlap
-//     (the same Green's-theorem terms as pixel_area()), again spread over
+//     (the same Green's-theorem terms as pixel_area_f()), again spread over
 //     the lanes.  Work per large cell follows its perimeter in pixels, not
 //     its area.
 __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
@@ -475,19 +447,61 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
   block_add_stats(A.stats, led);
 }
 
+// ---- float-float (about 48-bit) arithmetic for ill-conditioned cells -------
+// The pieces of lens::ff (cx.cuh) plus subtraction, order and division, all
+// on the float32 pipe (the float64 pipe is ~60x slower on this GPU).
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.hi, -b.lo}); }
+__device__ __forceinline__ bool ff_lt(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ ff ff_min(ff a, ff b) { return ff_lt(b, a) ? b : a; }
+__device__ __forceinline__ ff ff_max(ff a, ff b) { return ff_lt(a, b) ? b : a; }
+__device__ __forceinline__ ff ff_div(ff a, ff b) {  // b != 0
+  const float q1 = a.hi / b.hi;
+  const ff r = ff_sub(a, ff_mul(b, q1));
+  return ff_norm(q1, r.hi / b.hi);
+}
+__device__ __forceinline__ ff ff_half(ff a) { return ff{0.5f * a.hi, 0.5f * a.lo}; }
+
+// mean_clamp01f() in float-float.
+__device__ __forceinline__ ff mean_clamp01_ff(ff a, ff b) {
+  const ff zero{0.f, 0.f}, one{1.f, 0.f};
+  const ff lo = ff_min(a, b), hi = ff_max(a, b);
+  const ff l0 = ff_max(lo, zero), h1 = ff_min(hi, one);
+  const ff I = ff_add(ff_mul(ff_half(ff_max(ff_sub(h1, l0), zero)), ff_add(h1, l0)),
+                      ff_max(ff_sub(hi, ff_max(lo, one)), zero));
+  const ff d = ff_sub(hi, lo);
+  if (d.hi > 1e-30f) return ff_div(I, d);
+  return ff_min(ff_max(ff_half(ff_add(lo, hi)), zero), one);
+}
+
+// pixel_area_f() in float-float, slopes given (0 for a horizontal edge)
+__device__ __forceinline__ ff pixel_area_ff(const ff* qx, const ff* qy, const ff* sl, int X, int Y) {
+  const ff Yl{(float)Y, 0.f}, Yh{(float)(Y + 1), 0.f};
+  ff s{0.f, 0.f};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const ff y0 = qy[e], y1 = qy[(e + 1) & 3];
+    const ff ya = ff_min(ff_max(y0, Yl), Yh), yb = ff_min(ff_max(y1, Yl), Yh);
+    if (ya.hi == yb.hi && ya.lo == yb.lo) continue;
+    const ff xa = ff_add(qx[e], ff_mul(ff_sub(ya, y0), sl[e]));
+    const ff xb = ff_add(qx[e], ff_mul(ff_sub(yb, y0), sl[e]));
+    const ff m = mean_clamp01_ff(ff_add(xa, -(float)X), ff_add(xb, -(float)X));
+    s = ff_add(s, ff_mul(ff_sub(yb, ya), m));
+  }
+  return s;
+}
+
 // Ill-conditioned cells (|A_P| small against the pixel box): one warp per
 // cell, lanes over the box's pixels.  A float32 test finds the pixels no
 // edge meets, whose coverage is the winding number exactly; the pixels an
 // edge cuts are collected in shared memory and their overlaps taken in
-// float64 (coordinates local to the box) 32 at a time, so every float64
-// warp instruction runs on full lanes.
-__global__ void __launch_bounds__(kIpmThreads) k_ipm_f64(IpmArgs A) {
+// float-float (coordinates local to the box, exact from the corners' integer
+// and fractional parts) 32 at a time.
+__global__ void __launch_bounds__(kIpmThreads) k_ipm_ext(IpmArgs A) {
   __shared__ int cut_x[kWarps][64], cut_y[kWarps][64];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int nq = *A.qcount;
-  const double ac = A.ip.a_cell;
   Ledger led;
   for (int64_t t = wg; t < nq; t += nwarps) {
     const int64_t c = A.queue[t];
@@ -510,29 +524,34 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_f64(IpmArgs A) {
     const int wd = cx1 - cx0 + 1;
     const int npix = wd * (cy1 - cy0 + 1);  // the box is at most cap x cap, or clipped to the map
     float fx[4], fy[4];
-    double u[4], v[4];
+    ff u[4], v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       fx[k] = (float)(q4[k].iu - ix0) + q4[k].fu;
       fy[k] = (float)(q4[k].iv - iy0) + q4[k].fv;
-      u[k] = (double)(q4[k].iu - ix0) + (double)q4[k].fu;
-      v[k] = (double)(q4[k].iv - iy0) + (double)q4[k].fv;
+      // integer part (< 2^24 in the box) + fraction: exact as a two-sum
+      float sh, eh;
+      two_sum((float)(q4[k].iu - ix0), q4[k].fu, sh, eh);
+      u[k] = ff{sh, eh};
+      two_sum((float)(q4[k].iv - iy0), q4[k].fv, sh, eh);
+      v[k] = ff{sh, eh};
     }
-    const double A_P = 0.5 * ((u[1] - u[0]) * (v[2] - v[0]) - (u[2] - u[0]) * (v[1] - v[0]) +
-                              (u[2] - u[0]) * (v[3] - v[0]) - (u[3] - u[0]) * (v[2] - v[0]));
-    if (!(fabs(A_P) * A.ip.s_star > 1e-14 * ac)) {
+    // shoelace over the diagonals: 2 A_P = (u2-u0)(v3-v1) - (u3-u1)(v2-v0)
+    const ff A_P = ff_half(ff_sub(ff_mul(ff_sub(u[2], u[0]), ff_sub(v[3], v[1])),
+                                  ff_mul(ff_sub(u[3], u[1]), ff_sub(v[2], v[0]))));
+    if (!(fabsf(A_P.hi) > A.thr_degen)) {
       if (lane == 0) led.ndeg += 1;
       continue;
     }
-    if (lane == 0) led.nf64 += 1;
-    const double inv = 1.0 / A_P;
-    double sl[4];
+    if (lane == 0) led.nff += 1;
+    const ff inv = ff_div(ff{1.f, 0.f}, A_P);
+    ff sl[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const double ey = v[(k + 1) & 3] - v[k];
-      sl[k] = ey != 0.0 ? (u[(k + 1) & 3] - u[k]) / ey : 0.0;
+      const ff ey = ff_sub(v[(k + 1) & 3], v[k]);
+      sl[k] = ey.hi != 0.f ? ff_div(ff_sub(u[(k + 1) & 3], u[k]), ey) : ff{0.f, 0.f};
     }
-    const float invf = (float)inv;
+    const float invf = inv.hi;
     float fin = 0.f;
     int ncut = 0;  // warp-uniform: entries waiting in cut_x[w], cut_y[w]
     for (int base = 0; base < npix; base += 32) {
@@ -569,8 +588,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_f64(IpmArgs A) {
         const int take = min(ncut, 32);
         if (lane < take) {
           const int px = cut_x[w][lane], py = cut_y[w][lane];
-          const double a = pixel_area<double>(u, v, sl, (double)px, (double)py);
-          const float fr = (float)(a * inv);
+          const float fr = ff_mul(pixel_area_ff(u, v, sl, px, py), inv).hi;
           if (fr != 0.0f) {
             atomicAdd(&A.map[(int64_t)(iy0 + py) * A.ip.npx + ix0 + px], A.scale_f * fr);
             fin += fr;
@@ -668,8 +686,9 @@ void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const 
   A.D = rowdiff; A.ldd = (int64_t)ip.npx + 1;
   A.queue = queue; A.qcount = qcount; A.ip = ip;
   A.thr_area = (float)(1e-13 * ip.a_cell / ip.s_star);
+  A.thr_degen = (float)(1e-14 * ip.a_cell / ip.s_star);
   A.scale_f = (float)ip.scale;
-  // qcount[0]: float64 queue length; qcount[1]: chunk counter of k_ipm_cells
+  // qcount[0]: float-float queue length; qcount[1]: chunk counter of k_ipm_cells
   LENS_CUDA(cudaMemsetAsync(qcount, 0, 2 * sizeof(int), s));
   std::pair<cudaEvent_t, cudaEvent_t> e;
   if (ev) e = event_pair_begin(s);
@@ -679,8 +698,8 @@ void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const 
   const int64_t chunk_blocks = (ncells + kIpmThreads - 1) / kIpmThreads;
   k_ipm_cells<<<(unsigned)std::min<int64_t>(chunk_blocks, (int64_t)sms * 8), kIpmThreads, 0, s>>>(A);
   LENS_LAUNCHED("k_ipm_cells");
-  k_ipm_f64<<<sms * 2, kIpmThreads, 0, s>>>(A);
-  LENS_LAUNCHED("k_ipm_f64");
+  k_ipm_ext<<<sms * 2, kIpmThreads, 0, s>>>(A);
+  LENS_LAUNCHED("k_ipm_ext");
   if (ev) {
     event_pair_end(e, s);
     ev->push_back(e);

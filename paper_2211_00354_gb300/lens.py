@@ -72,7 +72,7 @@ class lens_ipm_stats(ctypes.Structure):
                 ("ms_ipm", ctypes.c_double), ("rays", ctypes.c_double),
                 ("p2p_pairs", ctypes.c_double), ("m2p_evals", ctypes.c_double),
                 ("ipm_updates", ctypes.c_double), ("cells_queued", ctypes.c_double),
-                ("cells_fp64", ctypes.c_double),
+                ("cells_ext", ctypes.c_double),
                 ("ms_eval_kernel", ctypes.c_double),
                 ("ms_ipm_kernel", ctypes.c_double), ("launches", ctypes.c_int64)]
 
