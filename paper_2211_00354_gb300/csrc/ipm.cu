@@ -29,7 +29,7 @@ namespace lens {
 namespace {
 
 constexpr int kIpmThreads = 256;
-constexpr int kChunksPerGrab = 4;  // 32-cell chunks per fetch of the chunk counter
+constexpr int kChunksPerGrab = 8;  // 32-cell chunks per fetch of the chunk counter
 constexpr int kFar = 0x7fffffff;
 
 // Mean of clamp(g, 0, 1) for g running linearly from a to b, without
