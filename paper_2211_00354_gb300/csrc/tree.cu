@@ -129,10 +129,13 @@ __global__ void k_splits(const uint64_t* __restrict__ k, int64_t n, int depth, i
   }
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) {
+    const uint64_t ki = k[i];
+    // star i + leaf shares the level-l prefix exactly when the box starting
+    // at i holds more than leaf stars (the keys are sorted by prefix)
+    const uint64_t kl = i + leaf < n ? k[i + leaf] : ~ki;
     for (int l = first_level(k, i, depth); l <= depth; ++l) {
-      const uint64_t mask = (l == 0) ? ~0ull : ((1ull << (2 * (depth - l))) - 1ull);
-      const int64_t end = (l == 0) ? n : upper_bound(k, i + 1, n, k[i] | mask);
-      if (end - i <= leaf) break;
+      const bool more = l == 0 ? n > leaf : i + leaf < n && ((ki ^ kl) >> (2 * (depth - l))) == 0;
+      if (!more) break;
       if (l == dcap) { if (!WRITE) atomicExch(deep_flag, 1); break; }
       if (WRITE) {
         unsigned long long pos = atomicAdd(&cursor[l], 1ull);
@@ -268,7 +271,33 @@ struct ListOut {
   const int64_t* oV; const int64_t* oX; const int64_t* oU; const int64_t* oW;  // offsets (pass 2)
   int* V; int* X; int* U; int* W;
   int64_t* ustars;  // per active index: stars in U (pass 1)
+  const int* nbr;   // per active index: 18 neighbour boxes (k_neighbours)
 };
+
+// The 18 neighbour lookups of each active box, one thread each: [0..8] the
+// boxes at level l-1 around its parent (V and X lists, levels >= 2), [9..17]
+// the boxes at level l around it (U and W lists, leaves), in the row-major
+// (dy, dx) order the list kernel walks them; -1 outside the root or unused.
+// A lookup is a binary search per level, so spreading them over threads
+// shortens the chains of dependent loads the list kernel would wait on.
+__global__ void k_neighbours(TreeView T, const int* __restrict__ active, int64_t nact,
+                             int* __restrict__ nbr) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nact * 18) return;
+  const int64_t a = t / 18;
+  const int q = (int)(t - a * 18), q9 = q % 9;
+  const int dx = q9 % 3 - 1, dy = q9 / 3 - 1;
+  const int B = active[a];
+  const int l = T.level[B];
+  const long long bx = T.ix[B], by = T.iy[B];
+  int r = -1;
+  if (q < 9) {
+    if (l >= 2) r = find_box(T, l - 1, (bx >> 1) + dx, (by >> 1) + dy);
+  } else if (T.child[B] < 0) {
+    r = find_box(T, l, bx + dx, by + dy);
+  }
+  nbr[t] = r;
+}
 
 template <bool WRITE>
 __global__ void k_lists(TreeView T, const int* __restrict__ active, int64_t nact, ListOut o) {
@@ -276,17 +305,15 @@ __global__ void k_lists(TreeView T, const int* __restrict__ active, int64_t nact
   if (a >= nact) return;
   const int B = active[a];
   const int l = T.level[B];
-  const long long bx = T.ix[B], by = T.iy[B];
   int64_t nV = 0, nX = 0, nU = 0, nW = 0, us = 0;
   int64_t pV = WRITE ? o.oV[a] : 0, pX = WRITE ? o.oX[a] : 0;
   int64_t pU = WRITE ? o.oU[a] : 0, pW = WRITE ? o.oW[a] : 0;
   if (l >= 2) {
     int seen[9];
     int nseen = 0;
-    const long long px = bx >> 1, py = by >> 1;
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
-        const int Q = find_box(T, l - 1, px + dx, py + dy);
+        const int Q = o.nbr[a * 18 + (dy + 1) * 3 + (dx + 1)];
         if (Q < 0) continue;
         if (T.level[Q] == l - 1 && T.child[Q] >= 0) {
           for (int q = 0; q < 4; ++q) {
@@ -312,7 +339,7 @@ __global__ void k_lists(TreeView T, const int* __restrict__ active, int64_t nact
     int stack[128];
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
-        const int C = find_box(T, l, bx + dx, by + dy);
+        const int C = o.nbr[a * 18 + 9 + (dy + 1) * 3 + (dx + 1)];
         if (C < 0) continue;
         if (T.level[C] < l) {
           bool dup = false;
@@ -539,6 +566,12 @@ void tree_build_lists(Plan& P, cudaStream_t s) {
   int64_t* c = cnt.as<int64_t>();
   ListOut o{};
   o.cV = c; o.cX = c + na; o.cU = c + 2 * na; o.cW = c + 3 * na; o.ustars = c + 4 * na;
+  Scratch nbr(&P.da, sizeof(int) * 18 * (size_t)std::max<int64_t>(na, 1));
+  if (na > 0) {
+    k_neighbours<<<grid_for(na * 18, 256), 256, 0, s>>>(T, P.active, na, nbr.as<int>());
+    LENS_LAUNCHED("k_neighbours");
+  }
+  o.nbr = nbr.as<int>();
   k_lists<false><<<grid_for(na, 128), 128, 0, s>>>(T, P.active, na, o);
   LENS_LAUNCHED("k_lists<count>");
   int64_t* offs[4];
