@@ -502,38 +502,77 @@ __global__ void k_prep_lists(const int* __restrict__ leaves, int64_t nl, const i
                              const int64_t* __restrict__ uoff, const int64_t* __restrict__ woff,
                              float4* __restrict__ ust, float* __restrict__ um,
                              int* __restrict__ wlist, float4* __restrict__ wgeo) {
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // One warp per active leaf.  Its candidate boxes (U leaves, then W boxes)
+  // are taken 32 at a time, one per lane; the stars of the staged ones (U
+  // leaves, W boxes of at most wmax stars) are then spread over the lanes,
+  // so the float64 offsets run on full lanes and the loads in parallel.
+  __shared__ int sh_incl[4][32], sh_st[4][32];
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, wb = (threadIdx.x >> 5) & 3;
   if (k >= nl) return;
   const int a = aidx[leaves[k]];
   const double cx = lp[k].cx, cy = lp[k].cy;
   int64_t os = uoff[k], ow = woff[k];
-  auto stage = [&](int C) {
-    for (int j = start[C]; j < start[C] + count[C]; ++j) {
-      const ff fx = ff_of(spos[j].x - cx), fy = ff_of(spos[j].y - cy);
-      ust[os] = make_float4(fx.hi, fy.hi, fx.lo, fy.lo);
-      um[os] = (float)smass[j];
-      ++os;
+  const int64_t u0 = U_off[a], nu = U_off[a + 1] - u0;
+  const int64_t w0 = W_off[a], ntot = nu + (W_off[a + 1] - w0);
+  for (int64_t e0 = 0; e0 < ntot; e0 += 32) {
+    const int64_t e = e0 + lane;
+    int C = -1, cnt = 0, st = 0;
+    bool far = false;
+    if (e < ntot) {
+      C = e < nu ? U_list[u0 + e] : W_list[w0 + (e - nu)];
+      const int c = count[C];
+      if (e < nu || c <= wmax) { cnt = c; st = start[C]; } else { far = true; }
     }
-  };
-  for (int64_t e = U_off[a]; e < U_off[a + 1]; ++e) stage(U_list[e]);
-  for (int64_t e = W_off[a]; e < W_off[a + 1]; ++e) {
-    const int C = W_list[e];
-    if (count[C] <= wmax) {
-      stage(C);
-    } else {
+    // far W boxes keep their order in wlist / wgeo
+    const unsigned fm = __ballot_sync(0xffffffffu, far);
+    if (far) {
+      const int64_t slot = ow + __popc(fm & ((1u << lane) - 1u));
       const double r = size / (double)(2ull << level[C]);
       const double wx = lo_x + (2.0 * ix[C] + 1.0) * r, wy = lo_y + (2.0 * iy[C] + 1.0) * r;
-      wlist[ow] = C;
-      wgeo[ow] = make_float4((float)(wx - cx), (float)(wy - cy), (float)r, 0.f);
-      ++ow;
+      wlist[slot] = C;
+      wgeo[slot] = make_float4((float)(wx - cx), (float)(wy - cy), (float)r, 0.f);
     }
+    ow += __popc(fm);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    sh_incl[wb][lane] = incl;
+    sh_st[wb][lane] = st;
+    __syncwarp();
+    for (int f0 = 0; f0 < total; f0 += 32) {
+      const int f = f0 + lane;
+      if (f < total) {
+        int L = 0;  // first lane whose inclusive count exceeds f
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (sh_incl[wb][L + step - 1] <= f) L += step;
+        const int j = sh_st[wb][L] + f - (L ? sh_incl[wb][L - 1] : 0);
+        const double2 z = spos[j];
+        const ff fx = ff_of(z.x - cx), fy = ff_of(z.y - cy);
+        ust[os + f] = make_float4(fx.hi, fy.hi, fx.lo, fy.lo);
+        um[os + f] = (float)smass[j];
+      }
+    }
+    os += total;
   }
 }
 
-__global__ void k_to_f32(const double2* __restrict__ in, int64_t n, float2* __restrict__ out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+// float32 copies of the multipoles the float32 evaluation reads: those of the
+// far W boxes (M2P), one thread per (list entry, coefficient); a box listed
+// by several leaves is written with the same values by each
+__global__ void k_to_f32(const int* __restrict__ wlist, int64_t nw, int P1,
+                         const double2* __restrict__ M, float2* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nw * P1) return;
+  const int64_t e = t / P1;
+  const int64_t i = (int64_t)wlist[e] * P1 + (t - e * P1);
+  out[i] = make_float2((float)M[i].x, (float)M[i].y);
 }
 
 // ---- per-call grid constants -------------------------------------------------
@@ -628,8 +667,9 @@ void eval32_prepare_tree(Plan& P, cudaStream_t s) {
   P.f_ust = P.dalloc_n<float4>(tot[0]);
   P.f_um = P.dalloc_n<float>(tot[0]);
   P.f_wlist = P.dalloc_n<int>(tot[1]);
+  P.f_nw = tot[1];
   P.f_wgeo = P.dalloc_n<float4>(tot[1]);
-  k_prep_lists<<<grid_for(nl, 128), 128, 0, s>>>(
+  k_prep_lists<<<grid_for(nl * 32, 128), 128, 0, s>>>(
       P.active_leaves, nl, P.box_aidx, P.f_leaf, P.U_off, P.U_list, P.W_off, P.W_list,
       P.box_start, P.box_count, P.box_level, P.box_ix, P.box_iy, P.root_lo[0], P.root_lo[1],
       P.root_size, P.spos, P.smass, wmax, P.f_uoff, P.f_woff, P.f_ust, P.f_um, P.f_wlist,
@@ -646,9 +686,10 @@ void eval32_prepare_expansions(Plan& P, cudaStream_t s) {
                                                       P.f_leaf, P.f_L);
     LENS_LAUNCHED("k_prep_leaf_exp");
   }
-  k_to_f32<<<grid_for((int64_t)P.nb * P1, 256, 152 * 16), 256, 0, s>>>(P.M, (int64_t)P.nb * P1,
-                                                                       P.f_M);
-  LENS_LAUNCHED("k_to_f32");
+  if (P.f_nw > 0) {
+    k_to_f32<<<grid_for(P.f_nw * P1, 256), 256, 0, s>>>(P.f_wlist, P.f_nw, P1, P.M, P.f_M);
+    LENS_LAUNCHED("k_to_f32");
+  }
 }
 
 void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int2* tile_leaf,

@@ -158,7 +158,7 @@ struct Plan {
   // float32-bulk evaluation data (eval32_prepare)
   LeafPlan* f_leaf = nullptr;   // per active leaf
   float2* f_L = nullptr;        // per active leaf, (p+1) local coefficients
-  float2* f_M = nullptr;        // per box, (p+1) multipole coefficients
+  float2* f_M = nullptr;        // per box, (p+1) multipole coefficients (far W boxes filled)
   // near field of every active leaf k (its U-list leaves plus the W boxes
   // small enough for P2P): the stars as float-float offsets from the leaf
   // centre (f_ust / f_um from f_uoff[k]); the far W boxes left to M2P
@@ -168,6 +168,7 @@ struct Plan {
   float* f_um = nullptr;
   int64_t* f_uoff = nullptr;
   int64_t* f_woff = nullptr; int* f_wlist = nullptr;
+  int64_t f_nw = 0;             // far W entries in f_wlist
   float4* f_wgeo = nullptr;     // per far W entry: centre offset from the leaf centre, radius
   int64_t* f_ncnt = nullptr; int64_t* f_wcnt = nullptr;
 
