@@ -16,7 +16,7 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kIPT = 16;  // keys per thread
+constexpr int kIPT = 8;   // keys per thread
 constexpr int kSortTile = kSortThreads * kIPT;
 
 __global__ void __launch_bounds__(kSortThreads)

@@ -123,32 +123,48 @@ __global__ void k_splits(const uint64_t* __restrict__ k, int64_t n, int depth, i
                          unsigned long long* __restrict__ counts, int* __restrict__ deep_flag,
                          unsigned long long* __restrict__ cursor, uint64_t* __restrict__ out) {
   __shared__ unsigned int sc[kMaxDepth + 1];
-  if (!WRITE) {
-    for (int q = threadIdx.x; q <= kMaxDepth; q += blockDim.x) sc[q] = 0;
-    __syncthreads();
-  }
+  __shared__ unsigned long long sbase[kMaxDepth + 1];
+  for (int q = threadIdx.x; q <= kMaxDepth; q += blockDim.x) sc[q] = 0;
+  __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  uint64_t ki = 0, kl = 0;
+  int l0 = depth + 1;
   if (i < n) {
-    const uint64_t ki = k[i];
+    ki = k[i];
     // star i + leaf shares the level-l prefix exactly when the box starting
     // at i holds more than leaf stars (the keys are sorted by prefix)
-    const uint64_t kl = i + leaf < n ? k[i + leaf] : ~ki;
-    for (int l = first_level(k, i, depth); l <= depth; ++l) {
-      const bool more = l == 0 ? n > leaf : i + leaf < n && ((ki ^ kl) >> (2 * (depth - l))) == 0;
-      if (!more) break;
-      if (l == dcap) { if (!WRITE) atomicExch(deep_flag, 1); break; }
-      if (WRITE) {
-        unsigned long long pos = atomicAdd(&cursor[l], 1ull);
-        out[pos] = ((uint64_t)l << 32) | (uint64_t)i;
-      } else {
-        atomicAdd(&sc[l], 1u);
+    kl = i + leaf < n ? k[i + leaf] : ~ki;
+    l0 = first_level(k, i, depth);
+  }
+  auto more = [&](int l) {
+    return l == 0 ? n > leaf : i + leaf < n && ((ki ^ kl) >> (2 * (depth - l))) == 0;
+  };
+  // the levels at which the box starting at star i splits: l0 .. l1-1
+  int l1 = l0;
+  if (i < n) {
+    for (; l1 <= depth && more(l1); ++l1) {
+      if (l1 == dcap) {
+        if (!WRITE) atomicExch(deep_flag, 1);
+        break;
       }
     }
   }
-  if (!WRITE) {
-    __syncthreads();
+  for (int l = l0; l < l1; ++l) atomicAdd(&sc[l], 1u);
+  __syncthreads();
+  if constexpr (!WRITE) {
     for (int q = threadIdx.x; q < kMaxDepth; q += blockDim.x)
       if (sc[q]) atomicAdd(&counts[q], (unsigned long long)sc[q]);
+  } else {
+    // one global reservation per level and block, then block-local slots
+    for (int q = threadIdx.x; q < kMaxDepth; q += blockDim.x) {
+      sbase[q] = sc[q] ? atomicAdd(&cursor[q], (unsigned long long)sc[q]) : 0ull;
+      sc[q] = 0;
+    }
+    __syncthreads();
+    for (int l = l0; l < l1; ++l) {
+      const unsigned int r = atomicAdd(&sc[l], 1u);
+      out[sbase[l] + r] = ((uint64_t)l << 32) | (uint64_t)i;
+    }
   }
 }
 
