@@ -58,6 +58,8 @@ struct E32Args {
   const float4* ust; const float* um; const int64_t* uoff; const float4* wgeo;
   int p;
   ff af, bf;
+  bool unit_mass;  // every star has mass m0 (near field summed without the mass)
+  float m0;
   double a, b;
   // grid source
   const int64_t* rect; const LeafGrid* lgrid; ff hf; int64_t gnx1, grow0;
@@ -67,7 +69,7 @@ struct E32Args {
   PixCorner* pix; ff iduf, idvf;
 };
 
-template <bool JAC, bool GRID, bool PIX>
+template <bool JAC, bool GRID, bool PIX, bool UM = false>
 __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   // staged stars, each value duplicated into both halves of a float2 (the
   // offsets negated, so that d = x + (-s) is the plain difference)
@@ -139,8 +141,10 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   // The leaf's near stars are contiguous: they are staged kChunk at a time
   // and summed in groups of kGroup (8) in plain float32, each group partial then
   // entering a two-sum (compensated) accumulator.  The staged chunk is padded
-  // with massless stars to whole groups, so every group loop has a fixed trip
-  // count and unrolls (a massless star adds exactly zero: w = 0 * finite).
+  // to whole groups, so every group loop has a fixed trip count and unrolls,
+  // with massless stars 1e18 away: they add exactly zero when the mass
+  // multiplies (w = 0 * finite) and ~1e-18 (far below float32 rounding of
+  // the sum) in the equal-mass form, which leaves the mass out.
   static_assert(kChunk % kGroup == 0, "chunks hold whole groups");
   const int64_t star0 = A.uoff[k], nstar = A.uoff[k + 1] - star0;
   for (int64_t f0 = 0; f0 < nstar; f0 += kChunk) {
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
     const int nfg = (nf + kGroup - 1) / kGroup * kGroup;
     __syncthreads();
     for (int f = tid; f < nfg; f += kT) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 v = make_float4(1e18f, 0.f, 0.f, 0.f);
       float mm = 0.f;
       if (f < nf) {
         const int64_t g = star0 + f0 + f;
@@ -179,13 +183,15 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
 #pragma unroll
         for (int jj = 0; jj < kGroup; ++jj) {
           const int j = lo + jj;
-          const float2 nsx = s_x[j], nsy = s_y[j], nsxl = s_xl[j], nsyl = s_yl[j], sm = s_m[j];
+          const float2 nsx = s_x[j], nsy = s_y[j], nsxl = s_xl[j], nsyl = s_yl[j];
 #pragma unroll
           for (int h = 0; h < kRpt / 2; ++h) {
             const float2 d1 = __fadd2_rn(__fadd2_rn(DX[h], nsx), __fadd2_rn(DXL[h], nsxl));
             const float2 d2 = __fadd2_rn(__fadd2_rn(DY[h], nsy), __fadd2_rn(DYL[h], nsyl));
             const float2 r2 = __ffma2_rn(d1, d1, __ffma2_rn(d2, d2, tiny));
-            const float2 w = __fmul2_rn(sm, make_float2(frcp_fast(r2.x), frcp_fast(r2.y)));
+            const float2 rr = make_float2(frcp_fast(r2.x), frcp_fast(r2.y));
+            // equal masses: the mass multiplies the sums once, after the loop
+            const float2 w = UM ? rr : __fmul2_rn(s_m[j], rr);
             P1[h] = __ffma2_rn(w, d1, P1[h]);
             P2[h] = __ffma2_rn(w, d2, P2[h]);
           }
@@ -226,6 +232,17 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
           n1[q].add(p1[q]); n2[q].add(p2[q]);
           nj1[q].add(pj1[q]); nj2[q].add(pj2[q]);
         }
+      }
+    }
+  }
+
+  if constexpr (!JAC && UM) {
+    if (A.m0 != 1.f) {
+      const float2 m2 = make_float2(A.m0, A.m0);
+#pragma unroll
+      for (int h = 0; h < kRpt / 2; ++h) {
+        N1[h].hi = __fmul2_rn(N1[h].hi, m2); N1[h].lo = __fmul2_rn(N1[h].lo, m2);
+        N2[h].hi = __fmul2_rn(N2[h].hi, m2); N2[h].lo = __fmul2_rn(N2[h].lo, m2);
       }
     }
   }
@@ -618,6 +635,9 @@ E32Args base_args32(Plan& P) {
   A.b = 1.0 - P.kappa_s + P.gamma;
   A.af = ff_of(A.a);
   A.bf = ff_of(A.b);
+  // a mass that float32 holds exactly (1, or any other with a short mantissa)
+  A.unit_mass = P.equal_mass && (double)(float)P.mass0 == P.mass0;
+  A.m0 = (float)P.mass0;
   return A;
 }
 
@@ -627,6 +647,7 @@ void launch32(E32Args& A, int64_t total, bool jac, cudaStream_t s) {
   if (total > (int64_t)INT32_MAX) fail(LENS_EINVAL, "too many ray tiles in one call");
   const unsigned g = (unsigned)total;
   if (jac) k_eval32<true, GRID, PIX><<<g, kT, 0, s>>>(A);
+  else if (A.unit_mass) k_eval32<false, GRID, PIX, true><<<g, kT, 0, s>>>(A);
   else k_eval32<false, GRID, PIX><<<g, kT, 0, s>>>(A);
   LENS_LAUNCHED("k_eval32");
 }

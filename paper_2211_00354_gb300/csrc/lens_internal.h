@@ -105,6 +105,8 @@ struct Plan {
 
   int64_t n = 0;
   int p = 0, leaf = 0, prec = 0, depth = kMaxDepth;
+  bool equal_mass = false;  // every star has mass mass0
+  double mass0 = 0.0;
   double kappa_s = 0, gamma = 0;
   double root_lo[2] = {0, 0}, root_size = 1;
   bool has_target = false;

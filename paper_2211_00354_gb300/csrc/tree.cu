@@ -38,19 +38,25 @@ struct LevelOffsets {
   int nlevels;
 };
 
+// per block: x min, x max, y min, y max, non-finite count, mass min, mass max
+constexpr int kBoundsParts = 7;
+
 __global__ void k_bounds(const double* __restrict__ stars, const double* __restrict__ m,
                          int64_t n, double* __restrict__ part) {
-  __shared__ double sh[5][256];
+  __shared__ double sh[kBoundsParts][256];
   double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY, bad = 0;
+  double mmin = INFINITY, mmax = -INFINITY;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double x = stars[2 * i], y = stars[2 * i + 1], w = m[i];
     if (!isfinite(x) || !isfinite(y) || !isfinite(w)) { bad += 1; continue; }
     xmin = fmin(xmin, x); xmax = fmax(xmax, x);
     ymin = fmin(ymin, y); ymax = fmax(ymax, y);
+    mmin = fmin(mmin, w); mmax = fmax(mmax, w);
   }
   sh[0][threadIdx.x] = xmin; sh[1][threadIdx.x] = xmax;
   sh[2][threadIdx.x] = ymin; sh[3][threadIdx.x] = ymax; sh[4][threadIdx.x] = bad;
+  sh[5][threadIdx.x] = mmin; sh[6][threadIdx.x] = mmax;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
@@ -59,10 +65,12 @@ __global__ void k_bounds(const double* __restrict__ stars, const double* __restr
       sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + o]);
       sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + o]);
       sh[4][threadIdx.x] += sh[4][threadIdx.x + o];
+      sh[5][threadIdx.x] = fmin(sh[5][threadIdx.x], sh[5][threadIdx.x + o]);
+      sh[6][threadIdx.x] = fmax(sh[6][threadIdx.x], sh[6][threadIdx.x + o]);
     }
     __syncthreads();
   }
-  if (threadIdx.x < 5) part[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x < kBoundsParts) part[blockIdx.x * kBoundsParts + threadIdx.x] = sh[threadIdx.x][0];
 }
 
 __global__ void k_keys(const double* __restrict__ stars, int64_t n, double lo_x, double lo_y,
@@ -399,22 +407,29 @@ void tree_build_boxes(Plan& P, const double* stars, const double* masses, cudaSt
   const int depth = P.depth;
   // ---- 1. bounds + finiteness -------------------------------------------
   const int nbb = (int)std::min<int64_t>(1024, (n + 255) / 256);
-  std::vector<double> part(5 * (size_t)nbb);
+  std::vector<double> part(kBoundsParts * (size_t)nbb);
   {
-    Scratch dpart(&P.da, sizeof(double) * 5 * nbb);
+    Scratch dpart(&P.da, sizeof(double) * kBoundsParts * nbb);
     k_bounds<<<nbb, 256, 0, s>>>(stars, masses, n, dpart.as<double>());
     LENS_LAUNCHED("k_bounds");
-    LENS_CUDA(cudaMemcpyAsync(part.data(), dpart.p, sizeof(double) * 5 * nbb,
+    LENS_CUDA(cudaMemcpyAsync(part.data(), dpart.p, sizeof(double) * kBoundsParts * nbb,
                               cudaMemcpyDeviceToHost, s));
     LENS_CUDA(cudaStreamSynchronize(s));
   }
   double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY, bad = 0;
+  double mmin = INFINITY, mmax = -INFINITY;
   for (int b = 0; b < nbb; ++b) {
-    xmin = std::min(xmin, part[5 * b]); xmax = std::max(xmax, part[5 * b + 1]);
-    ymin = std::min(ymin, part[5 * b + 2]); ymax = std::max(ymax, part[5 * b + 3]);
-    bad += part[5 * b + 4];
+    const double* q = &part[(size_t)kBoundsParts * b];
+    xmin = std::min(xmin, q[0]); xmax = std::max(xmax, q[1]);
+    ymin = std::min(ymin, q[2]); ymax = std::max(ymax, q[3]);
+    bad += q[4];
+    mmin = std::min(mmin, q[5]); mmax = std::max(mmax, q[6]);
   }
   if (bad > 0) fail(LENS_EINVAL, "non-finite star position or mass");
+  // all stars of one mass (a common microlensing field): the float32 near
+  // field then sums 1/|d|^2-weighted offsets and scales by the mass once
+  P.equal_mass = mmin == mmax;
+  P.mass0 = mmin;
   if (P.has_target) {
     xmin = std::min(xmin, P.target[0]); xmax = std::max(xmax, P.target[1]);
     ymin = std::min(ymin, P.target[2]); ymax = std::max(ymax, P.target[3]);

@@ -141,6 +141,20 @@ def test_tree_deeper_than_the_partial_sort():
     assert alpha_rel_err(y32, y_ref, x, f.kappa_s, f.gamma).max() < 2e-5
 
 
+@pytest.mark.parametrize("m0", [1.0, 0.5, 0.37])
+def test_equal_mass_fields(m0):
+    # equal masses: the float32 near field sums unweighted and scales once
+    # (1 and 0.5 are exact in float32; 0.37 is not and takes the general path)
+    f = synth.config_uniform(seed=9, n=3000, kappa_star=0.4, kappa_s=0.1, gamma=0.2)
+    f.masses = np.full(f.n, m0)
+    x = np.concatenate([synth.random_rays(10, 3000, (-8, -8), (8, 8)), f.stars[:200] + 1e-4])
+    x = x[np.all(np.abs(x) < 8, axis=1)]
+    y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x)
+    with plan_for(f, 24, 8, lens.FP32_BULK, (-8.5, 8.5, -8.5, 8.5)) as P:
+        y = P.deflect(T(x)).cpu().numpy()
+    assert alpha_rel_err(y, y_ref, x, f.kappa_s, f.gamma).max() < 2e-5
+
+
 @pytest.mark.parametrize("prec,tol", [(lens.FP64, 1e-8), (lens.FP32_BULK, 2e-4)])
 def test_jacobian(prec, tol):
     f = synth.config_uniform(seed=1, n=800, kappa_star=0.3, kappa_s=0.2, gamma=0.4)
