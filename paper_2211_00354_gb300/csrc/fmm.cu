@@ -164,11 +164,6 @@ k_m2m(const int* __restrict__ parent, int64_t c0, int64_t ngroups, int p,
   }
 }
 
-// per-level offsets into the active-box list, passed by value
-struct LevelOffsets64 {
-  int64_t off[kMaxDepth + 3];
-};
-
 // ---- downward pass ---------------------------------------------------------
 // The far-field part of each local expansion (M2L over the V list, P2L over
 // the X list) reads only multipole expansions and stars, so one launch forms
@@ -338,13 +333,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_far_local(DownArgs A) {
 // expansion is zero), one thread per (box, coefficient j):
 //   L_B[j] += sum_{l >= j} S_q[j][l] L_parent[l],  q = the box's quadrant.
 // The parent of an active box is active and its expansion is final.
-__device__ __forceinline__ void l2l_one(const int* __restrict__ active, int64_t a0, int64_t t,
-                                        const int* __restrict__ parent,
-                                        const int* __restrict__ child,
-                                        const double2* __restrict__ l2l, int p,
-                                        double2* __restrict__ L) {
+__global__ void k_l2l(const int* __restrict__ active, int64_t a0, int64_t a1,
+                      const int* __restrict__ parent, const int* __restrict__ child,
+                      const double2* __restrict__ l2l, int p, double2* __restrict__ L) {
   const int P1 = p + 1;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t a = a0 + t / P1;
+  if (a >= a1) return;
   const int j = (int)(t - (a - a0) * P1);
   const int B = active[a];
   const int par = parent[B];
@@ -355,27 +350,6 @@ __device__ __forceinline__ void l2l_one(const int* __restrict__ active, int64_t 
   for (int l = j; l <= p; ++l) v = cfma(ld2(S + l), ld2(Lp + l), v);
   double2* o = L + (int64_t)B * P1 + j;
   *o = *o + v;
-}
-
-__global__ void k_l2l(const int* __restrict__ active, int64_t a0, int64_t a1,
-                      const int* __restrict__ parent, const int* __restrict__ child,
-                      const double2* __restrict__ l2l, int p, double2* __restrict__ L) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t < (a1 - a0) * (p + 1)) l2l_one(active, a0, t, parent, child, l2l, p, L);
-}
-
-// The coarse levels, a few boxes each, in one block, level by level (a
-// launch per level would cost more than its work).
-constexpr int kL2LBlock = 1024;
-__global__ void __launch_bounds__(kL2LBlock)
-k_l2l_levels(const int* __restrict__ active, LevelOffsets64 lv, int l0, int l1,
-             const int* __restrict__ parent, const int* __restrict__ child,
-             const double2* __restrict__ l2l, int p, double2* __restrict__ L) {
-  for (int l = l0; l < l1; ++l) {
-    const int64_t a0 = lv.off[l], n = (lv.off[l + 1] - a0) * (p + 1);
-    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) l2l_one(active, a0, t, parent, child, l2l, p, L);
-    __syncthreads();  // the next level reads this one's expansions
-  }
 }
 
 }  // namespace
@@ -541,17 +515,7 @@ void fmm_downward(Plan& P, cudaStream_t s) {
     LENS_LAUNCHED("k_far_local");
   }
   const int P1 = P.p + 1;
-  // levels 2 .. lc-1 with at most 4 block-widths of work each in one block
-  LevelOffsets64 lv{};
-  for (int l = 0; l <= P.nlevels && l < kMaxDepth + 3; ++l) lv.off[l] = P.active_level_off[l];
-  int lc = 2;
-  while (lc < P.nlevels && (lv.off[lc + 1] - lv.off[lc]) * P1 <= 4 * kL2LBlock) ++lc;
-  if (lc > 2) {
-    k_l2l_levels<<<1, kL2LBlock, 0, s>>>(P.active, lv, 2, lc, P.box_parent, P.box_child, t.l2l,
-                                         P.p, P.L);
-    LENS_LAUNCHED("k_l2l_levels");
-  }
-  for (int l = lc; l < P.nlevels; ++l) {
+  for (int l = 2; l < P.nlevels; ++l) {
     const int64_t a0 = P.active_level_off[l], a1 = P.active_level_off[l + 1];
     if (a1 <= a0) continue;
     k_l2l<<<grid_for((a1 - a0) * P1, 128), 128, 0, s>>>(P.active, a0, a1, P.box_parent,
