@@ -72,17 +72,21 @@ struct fcomp {
 };
 
 // Two compensated accumulators side by side (one per ray of a pair) on
-// Blackwell's two-lane float32 instructions: the same two-sum as
-// fcomp::add, with a - b formed as fma(b, -1, a) (exactly a - b: the product
-// is exact and the sum rounds once).
+// Blackwell's two-lane float32 instructions.  The error of hi + x comes from
+// Dekker's fast two-sum with the operands ordered by magnitude (the ordering
+// runs on the integer/compare pipe, the three paired operations on the FMA
+// pipe, instead of six for Knuth's two-sum): the exact error of a rounded sum
+// is unique, so the result equals fcomp::add's.  a - b is formed as
+// fma(b, -1, a), exactly a - b (the product is exact, the sum rounds once).
 struct fcomp2 {
   float2 hi, lo;
   __device__ __forceinline__ void add(float2 x) {
     const float2 m1 = make_float2(-1.f, -1.f);
-    const float2 s = __fadd2_rn(hi, x);
-    const float2 bb = __ffma2_rn(hi, m1, s);  // s - hi
-    const float2 t = __ffma2_rn(bb, m1, s);   // s - bb
-    const float2 e = __fadd2_rn(__ffma2_rn(t, m1, hi), __ffma2_rn(bb, m1, x));  // (hi - t) + (x - bb)
+    const bool kx = fabsf(hi.x) >= fabsf(x.x), ky = fabsf(hi.y) >= fabsf(x.y);
+    const float2 a = make_float2(kx ? hi.x : x.x, ky ? hi.y : x.y);
+    const float2 b = make_float2(kx ? x.x : hi.x, ky ? x.y : hi.y);
+    const float2 s = __fadd2_rn(a, b);
+    const float2 e = __ffma2_rn(__ffma2_rn(a, m1, s), m1, b);  // b - (s - a)
     hi = s;
     lo = __fadd2_rn(lo, e);
   }
