@@ -65,6 +65,10 @@ def _load():
         lib.oracle_ipm_map.argtypes = [i64, i64, d, _dp, d, d, d, d, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int, _dp, _dp]
         lib.oracle_ipm_map.restype = None
+        lib.oracle_ipm_map_refined.argtypes = [i64, i64, d, d, d, _dp, i64, _dp, _dp, d, d, d, d,
+                                               d, d, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, _dp, _dp]
+        lib.oracle_ipm_map_refined.restype = None
         lib.oracle_adjoint.argtypes = [i64, _dp, _dp, i64, _dp, _dp, _dp, _dp, _dp]
         lib.oracle_adjoint.restype = None
         lib.oracle_light_curve.argtypes = [i64, _dp, d, i64, _dp, d, d, _dp]
@@ -138,6 +142,28 @@ def ipm_map(ycorn, h, box, npx, npy, bbox_cap=0):
     u0, u1, v0, v1 = (float(v) for v in box)
     lib.oracle_ipm_map(nx, ny, float(h), py_, u0, u1, v0, v1, int(npx), int(npy),
                        int(bbox_cap), mp.ctypes.data_as(_dp), st.ctypes.data_as(_dp))
+    return mp, dict(zip(IPM_STAT_KEYS, st.tolist()))
+
+
+def ipm_map_refined(ycorn, x0, y0, h, stars, masses, kappa_s, gamma, box, npx, npy, bbox_cap,
+                    levels):
+    """IPM with critical-cell refinement: cells whose pixel box exceeds
+    bbox_cap are split 2 x 2 (new corners by the direct sum) up to `levels`
+    times.  ycorn: (ny+1, nx+1, 2) deflected corners of the grid whose cell
+    (i, j) starts at (x0 + i h, y0 + j h).  Returns (map, stats dict)."""
+    lib = _load()
+    yc, py_ = _c(ycorn)
+    assert yc.ndim == 3 and yc.shape[2] == 2
+    ny, nx = yc.shape[0] - 1, yc.shape[1] - 1
+    st_, sp = _c(np.asarray(stars).reshape(-1, 2))
+    ms, mp_ = _c(np.asarray(masses).reshape(-1))
+    mp = np.empty((npy, npx))
+    st = np.empty(8)
+    u0, u1, v0, v1 = (float(v) for v in box)
+    lib.oracle_ipm_map_refined(nx, ny, float(x0), float(y0), float(h), py_, st_.shape[0], sp, mp_,
+                               float(kappa_s), float(gamma), u0, u1, v0, v1, int(npx), int(npy),
+                               int(bbox_cap), int(levels), mp.ctypes.data_as(_dp),
+                               st.ctypes.data_as(_dp))
     return mp, dict(zip(IPM_STAT_KEYS, st.tolist()))
 
 

@@ -20,6 +20,11 @@
  *                          image-plane cell is mapped to a source-plane
  *                          quadrilateral and its area is apportioned to the
  *                          pixels it overlaps, mu = sum(S_i)/S*.
+ *   oracle_ipm_map_refined -- the same with cells whose pixel box exceeds the
+ *                          cap split into 2 x 2 sub-cells (new corner rays by
+ *                          Eq. 1) up to a number of levels, instead of dropped
+ *                          (the critical-cell refinement that the first-order
+ *                          IPM of Sec. 2.3 leaves to a higher-order method).
  *   oracle_clip_area_sh -- polygon/pixel overlap by Sutherland-Hodgman
  *                          clipping + shoelace (used by oracle_ipm_map).
  *   oracle_clip_area_green -- the same overlap by an independent route: Green's
@@ -236,75 +241,148 @@ double oracle_clip_area_green(const double* poly, int n, double x0, double y0) {
  * stats (8 doubles): [0] cells, [1] area_total, [2] area_in_map,
  *   [3] area_outside, [4] area_dropped, [5] area_degenerate,
  *   [6] cells_dropped, [7] cells_degenerate. */
-void oracle_ipm_map(int64_t nx, int64_t ny, double h, const double* ycorn,
-                    double u0, double u1, double v0, double v1, int npx, int npy,
-                    int bbox_cap, double* map, double* stats) {
-  const double du = (u1 - u0) / npx, dv = (v1 - v0) / npy;
-  const double A_cell = h * h;
-  const double S_star = du * dv;
+/* The state one IPM pass accumulates into. */
+typedef struct {
+  double u0, v0, du, dv, S_star;
+  int npx, npy, bbox_cap;
+  double* map;
+  nsum in_map, outside, dropped, degen;
+  double n_dropped, n_degen;
+  /* refinement: the lens, the grid origin, the levels allowed */
+  int64_t n;
+  const double *stars, *masses;
+  double kappa_s, gamma;
+  int levels;
+} ipm_ctx;
+
+/* One (sub)cell of side hc whose deflected corners are P (c00, c10, c11,
+ * c01), lower-left image-plane corner (xl, yl), at refinement level `level`. */
+static void ipm_cell(ipm_ctx* c, const double P[8], double xl, double yl, double hc, int level) {
+  const double A_cell = hc * hc;
+  /* source-plane area of the mapped cell */
+  const double A_P = shoelace(P, 4);
+  if (!(fabs(A_P) > 1e-14 * A_cell)) {
+    nsum_add(&c->degen, A_cell); c->n_degen += 1; return;
+  }
+  /* pixel coordinates */
+  double Q[8];
+  for (int k = 0; k < 4; ++k) {
+    Q[2 * k] = (P[2 * k] - c->u0) / c->du;
+    Q[2 * k + 1] = (P[2 * k + 1] - c->v0) / c->dv;
+  }
+  double qmin0 = Q[0], qmax0 = Q[0], qmin1 = Q[1], qmax1 = Q[1];
+  for (int k = 1; k < 4; ++k) {
+    qmin0 = fmin(qmin0, Q[2 * k]); qmax0 = fmax(qmax0, Q[2 * k]);
+    qmin1 = fmin(qmin1, Q[2 * k + 1]); qmax1 = fmax(qmax1, Q[2 * k + 1]);
+  }
+  const double fx0 = floor(qmin0), fx1 = floor(qmax0);
+  const double fy0 = floor(qmin1), fy1 = floor(qmax1);
+  const int npx = c->npx, npy = c->npy;
+  if (fx1 < 0 || fy1 < 0 || fx0 > npx - 1 || fy0 > npy - 1) {
+    nsum_add(&c->outside, A_cell); return;
+  }
+  if (c->bbox_cap > 0 && (fx1 - fx0 + 1 > c->bbox_cap || fy1 - fy0 + 1 > c->bbox_cap)) {
+    if (level < c->levels) {
+      /* 2 x 2 sub-cells of half the side: the five new corner rays (edge
+       * midpoints and centre) through the lens equation */
+      const double g = 0.5 * hc;
+      const double X[10] = {xl + g, yl, xl + hc, yl + g, xl + g, yl + hc, xl, yl + g, xl + g, yl + g};
+      double Y[10];
+      oracle_deflect(c->n, c->stars, c->masses, c->kappa_s, c->gamma, 5, X, Y, NULL, NULL);
+      /* 3 x 3 corner grid G[row][col], rows along x2 */
+      const double* G[3][3] = {{P + 0, Y + 0, P + 2}, {Y + 6, Y + 8, Y + 2}, {P + 6, Y + 4, P + 4}};
+      for (int bq = 0; bq < 2; ++bq)
+        for (int aq = 0; aq < 2; ++aq) {
+          const double* k00 = G[bq][aq];
+          const double* k10 = G[bq][aq + 1];
+          const double* k11 = G[bq + 1][aq + 1];
+          const double* k01 = G[bq + 1][aq];
+          const double S[8] = {k00[0], k00[1], k10[0], k10[1], k11[0], k11[1], k01[0], k01[1]};
+          ipm_cell(c, S, xl + aq * g, yl + bq * g, g, level + 1);
+        }
+      return;
+    }
+    nsum_add(&c->dropped, A_cell); c->n_dropped += 1; return;
+  }
+  const double A_Pp = A_P / c->S_star; /* area in pixel units */
+  const int64_t ix0 = fx0 < 0 ? 0 : (int64_t)fx0;
+  const int64_t ix1 = fx1 > npx - 1 ? npx - 1 : (int64_t)fx1;
+  const int64_t iy0 = fy0 < 0 ? 0 : (int64_t)fy0;
+  const int64_t iy1 = fy1 > npy - 1 ? npy - 1 : (int64_t)fy1;
+  double frac_in = 0.0;
+  for (int64_t py = iy0; py <= iy1; ++py) {
+    for (int64_t px = ix0; px <= ix1; ++px) {
+      const double a = oracle_clip_area_sh(Q, 4, (double)px, (double)py);
+      if (a == 0.0) continue;
+      const double frac = a / A_Pp;
+      c->map[py * npx + px] += A_cell * frac;
+      frac_in += frac;
+    }
+  }
+  nsum_add(&c->in_map, A_cell * frac_in);
+  nsum_add(&c->outside, A_cell * (1.0 - frac_in));
+}
+
+static void ipm_run(ipm_ctx* c, int64_t nx, int64_t ny, double x0, double y0, double h,
+                    const double* ycorn, double* stats) {
   const int64_t W = nx + 1;
-  nsum in_map = {0, 0}, outside = {0, 0}, dropped = {0, 0}, degen = {0, 0};
-  double n_dropped = 0, n_degen = 0;
-  for (int64_t p = 0; p < (int64_t)npx * npy; ++p) map[p] = 0.0;
+  for (int64_t p = 0; p < (int64_t)c->npx * c->npy; ++p) c->map[p] = 0.0;
   for (int64_t j = 0; j < ny; ++j) {
     for (int64_t i = 0; i < nx; ++i) {
       const double* c00 = ycorn + 2 * (j * W + i);
       const double* c10 = ycorn + 2 * (j * W + i + 1);
       const double* c11 = ycorn + 2 * ((j + 1) * W + i + 1);
       const double* c01 = ycorn + 2 * ((j + 1) * W + i);
-      double P[8] = {c00[0], c00[1], c10[0], c10[1], c11[0], c11[1], c01[0], c01[1]};
-      /* source-plane area of the mapped cell */
-      const double A_P = shoelace(P, 4);
-      if (!(fabs(A_P) > 1e-14 * A_cell)) {
-        nsum_add(&degen, A_cell); n_degen += 1; continue;
-      }
-      /* pixel coordinates */
-      double Q[8];
-      for (int k = 0; k < 4; ++k) {
-        Q[2 * k] = (P[2 * k] - u0) / du;
-        Q[2 * k + 1] = (P[2 * k + 1] - v0) / dv;
-      }
-      double qmin0 = Q[0], qmax0 = Q[0], qmin1 = Q[1], qmax1 = Q[1];
-      for (int k = 1; k < 4; ++k) {
-        qmin0 = fmin(qmin0, Q[2 * k]); qmax0 = fmax(qmax0, Q[2 * k]);
-        qmin1 = fmin(qmin1, Q[2 * k + 1]); qmax1 = fmax(qmax1, Q[2 * k + 1]);
-      }
-      const double fx0 = floor(qmin0), fx1 = floor(qmax0);
-      const double fy0 = floor(qmin1), fy1 = floor(qmax1);
-      if (fx1 < 0 || fy1 < 0 || fx0 > npx - 1 || fy0 > npy - 1) {
-        nsum_add(&outside, A_cell); continue;
-      }
-      if (bbox_cap > 0 && (fx1 - fx0 + 1 > bbox_cap || fy1 - fy0 + 1 > bbox_cap)) {
-        nsum_add(&dropped, A_cell); n_dropped += 1; continue;
-      }
-      const double A_Pp = A_P / S_star; /* area in pixel units */
-      const int64_t ix0 = fx0 < 0 ? 0 : (int64_t)fx0;
-      const int64_t ix1 = fx1 > npx - 1 ? npx - 1 : (int64_t)fx1;
-      const int64_t iy0 = fy0 < 0 ? 0 : (int64_t)fy0;
-      const int64_t iy1 = fy1 > npy - 1 ? npy - 1 : (int64_t)fy1;
-      double frac_in = 0.0;
-      for (int64_t py = iy0; py <= iy1; ++py) {
-        for (int64_t px = ix0; px <= ix1; ++px) {
-          const double a = oracle_clip_area_sh(Q, 4, (double)px, (double)py);
-          if (a == 0.0) continue;
-          const double frac = a / A_Pp;
-          map[py * npx + px] += A_cell * frac;
-          frac_in += frac;
-        }
-      }
-      nsum_add(&in_map, A_cell * frac_in);
-      nsum_add(&outside, A_cell * (1.0 - frac_in));
+      const double P[8] = {c00[0], c00[1], c10[0], c10[1], c11[0], c11[1], c01[0], c01[1]};
+      ipm_cell(c, P, x0 + (double)i * h, y0 + (double)j * h, h, 0);
     }
   }
-  for (int64_t p = 0; p < (int64_t)npx * npy; ++p) map[p] /= S_star;
+  for (int64_t p = 0; p < (int64_t)c->npx * c->npy; ++p) c->map[p] /= c->S_star;
   stats[0] = (double)nx * (double)ny;
-  stats[1] = stats[0] * A_cell;
-  stats[2] = nsum_get(&in_map);
-  stats[3] = nsum_get(&outside);
-  stats[4] = nsum_get(&dropped);
-  stats[5] = nsum_get(&degen);
-  stats[6] = n_dropped;
-  stats[7] = n_degen;
+  stats[1] = stats[0] * h * h;
+  stats[2] = nsum_get(&c->in_map);
+  stats[3] = nsum_get(&c->outside);
+  stats[4] = nsum_get(&c->dropped);
+  stats[5] = nsum_get(&c->degen);
+  stats[6] = c->n_dropped;
+  stats[7] = c->n_degen;
+}
+
+void oracle_ipm_map(int64_t nx, int64_t ny, double h, const double* ycorn,
+                    double u0, double u1, double v0, double v1, int npx, int npy,
+                    int bbox_cap, double* map, double* stats) {
+  ipm_ctx c;
+  memset(&c, 0, sizeof(c));
+  c.u0 = u0; c.v0 = v0;
+  c.du = (u1 - u0) / npx; c.dv = (v1 - v0) / npy;
+  c.S_star = c.du * c.dv;
+  c.npx = npx; c.npy = npy; c.bbox_cap = bbox_cap;
+  c.map = map;
+  ipm_run(&c, nx, ny, 0.0, 0.0, h, ycorn, stats);
+}
+
+/* Refined IPM: as oracle_ipm_map, but a cell whose pixel box spans more
+ * than bbox_cap pixels on a side is split into 2 x 2 sub-cells of half the
+ * side, the five new corner rays deflected by Eq. 1 (direct sum), up to
+ * `levels` times; a sub-cell still too large at the last level is dropped.
+ * The grid's cell (i, j) has its lower-left corner at (x0 + i h, y0 + j h)
+ * and ycorn holds the deflected corners of the grid.  levels = 0 gives
+ * oracle_ipm_map. */
+void oracle_ipm_map_refined(int64_t nx, int64_t ny, double x0, double y0, double h,
+                            const double* ycorn, int64_t n, const double* stars,
+                            const double* masses, double kappa_s, double gamma, double u0,
+                            double u1, double v0, double v1, int npx, int npy, int bbox_cap,
+                            int levels, double* map, double* stats) {
+  ipm_ctx c;
+  memset(&c, 0, sizeof(c));
+  c.u0 = u0; c.v0 = v0;
+  c.du = (u1 - u0) / npx; c.dv = (v1 - v0) / npy;
+  c.S_star = c.du * c.dv;
+  c.npx = npx; c.npy = npy; c.bbox_cap = bbox_cap;
+  c.map = map;
+  c.n = n; c.stars = stars; c.masses = masses; c.kappa_s = kappa_s; c.gamma = gamma;
+  c.levels = levels;
+  ipm_run(&c, nx, ny, x0, y0, h, ycorn, stats);
 }
 
 /* ------------------------------------------------------------------------ */

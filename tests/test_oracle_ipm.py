@@ -184,3 +184,59 @@ def test_mean_magnification_of_random_field():
         led = st["area_in_map"] + st["area_outside"] + st["area_dropped"] + st["area_degenerate"]
         assert led == pytest.approx(st["area_total"], rel=1e-12)
     assert abs(np.mean(vals) - 1) < 0.10, vals
+
+
+# ---- refinement of cells larger than the cap (2 x 2 split, new corner rays) --
+
+def _corner_grid(stars, masses, ks, g, grid):
+    xc = grid.corners().reshape(-1, 2)
+    return oracle.deflect(stars, masses, ks, g, xc).reshape(grid.ny + 1, grid.nx + 1, 2)
+
+
+def test_refinement_with_no_levels_is_the_plain_map():
+    f = synth.config_uniform(seed=3, n=40, kappa_star=0.3, kappa_s=0.1, gamma=0.2)
+    grid = synth.Grid(x0=-3.0, y0=-3.0, h=0.25, nx=24, ny=24)
+    y = _corner_grid(f.stars, f.masses, f.kappa_s, f.gamma, grid)
+    box = (-2.0, 2.0, -2.0, 2.0)
+    mp, st = oracle.ipm_map(y, grid.h, box, 30, 30, bbox_cap=3)
+    mr, sr = oracle.ipm_map_refined(y, grid.x0, grid.y0, grid.h, f.stars, f.masses, f.kappa_s,
+                                    f.gamma, box, 30, 30, 3, 0)
+    assert np.array_equal(mp, mr) and st == sr
+    assert st["cells_dropped"] > 0
+
+
+def test_refined_affine_map_equals_the_uncapped_map():
+    # an affine lens (one massless star): the four sub-cells of a cell tile its
+    # image exactly, so splitting the cells a cap rejects gives the map every
+    # cell would give uncapped
+    star, m = np.array([[0.3, -0.2]]), np.array([0.0])
+    ks, g = -2.0, 0.5  # y = diag(2.5, 3.5) x: cells grow ~3x
+    grid = synth.Grid(x0=-0.5, y0=-0.4, h=0.1, nx=10, ny=8)
+    y = _corner_grid(star, m, ks, g, grid)
+    box = (-1.5, 1.5, -1.5, 1.5)
+    full, sf = oracle.ipm_map(y, grid.h, box, 30, 30, bbox_cap=0)
+    capped, sc = oracle.ipm_map(y, grid.h, box, 30, 30, bbox_cap=4)
+    ref, sr = oracle.ipm_map_refined(y, grid.x0, grid.y0, grid.h, star, m, ks, g, box, 30, 30, 4, 3)
+    assert sc["cells_dropped"] > 0 and sr["cells_dropped"] == 0
+    np.testing.assert_allclose(ref, full, rtol=1e-12, atol=1e-12)
+    assert sr["area_in_map"] == pytest.approx(sf["area_in_map"], rel=1e-12)
+    assert not np.allclose(capped, full)
+
+
+def test_refinement_recovers_flux_near_a_point_lens():
+    # cells next to the lens map to huge polygons: each level splits what the
+    # cap rejects, the dropped area falls and the ledger stays closed
+    box = (-2.0, 2.0, -2.0, 2.0)
+    h = 0.05
+    grid = synth.Grid(x0=-2.0 + 0.5 * h, y0=-2.0 + 0.3 * h, h=h, nx=80, ny=80)
+    star, m = np.zeros((1, 2)), np.array([1.0])
+    y = _corner_grid(star, m, 0.0, 0.0, grid)
+    dropped = []
+    for levels in (0, 1, 2, 3):
+        mp, st = oracle.ipm_map_refined(y, grid.x0, grid.y0, grid.h, star, m, 0.0, 0.0, box, 40,
+                                        40, 8, levels)
+        led = st["area_in_map"] + st["area_outside"] + st["area_dropped"] + st["area_degenerate"]
+        assert led == pytest.approx(st["area_total"], rel=1e-12)
+        dropped.append(st["area_dropped"])
+    assert dropped[0] > 0
+    assert all(b < a for a, b in zip(dropped, dropped[1:]))
