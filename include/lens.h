@@ -115,6 +115,7 @@ typedef struct {
   double ms_eval_kernel;
   double ms_ipm_kernel;
   int64_t launches;    /* kernels this call launched */
+  double cells_refined; /* (sub)cells over the cap split 2 x 2 (lens_ipm_map_refined) */
 } lens_ipm_stats;
 
 typedef struct {
@@ -188,6 +189,24 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid,
                          const lens_box* box, int npx, int npy,
                          int64_t max_cells_per_chunk, int bbox_cap_px,
                          double* map_out, lens_ipm_stats* stats, void* stream);
+
+/* lens_ipm_map with critical-cell refinement instead of the drop rule: a cell
+ * whose pixel box spans more than bbox_cap_px pixels on a side (or has a
+ * corner beyond 2^30 pixels) is split into 2 x 2 sub-cells of half the side,
+ * the new corner rays deflected through the plan like lens_deflect, each
+ * sub-cell carrying a quarter of the area; up to refine_levels times, after
+ * which a sub-cell still over the cap is dropped and booked as before.
+ * (Sec. 2.3 leaves such cells to the higher-order IPM; this is the adaptive
+ * step toward it.)  refine_levels 0..16 (0: lens_ipm_map); needs
+ * bbox_cap_px > 0.  stats->cells_refined counts the cells split.  The ledger
+ * keeps its areas in image-plane units (a sub-cell of level l counts 4^-l
+ * cells), the cell counts count sub-cells as cells.
+ * Errors: as lens_ipm_map; EDOMAIN if the grid leaves the target region. */
+lens_status lens_ipm_map_refined(lens_plan* plan, const lens_grid* grid,
+                                 const lens_box* box, int npx, int npy,
+                                 int64_t max_cells_per_chunk, int bbox_cap_px,
+                                 int refine_levels, double* map_out,
+                                 lens_ipm_stats* stats, void* stream);
 
 /* Adjoint of lens_deflect (not in the paper): given grad_y = dL/dy at the m
  * rays, the transposed FMM (L2P^T, L2L^T, M2L^T, M2M^T, P2M^T, P2P^T, M2P^T,

@@ -342,8 +342,18 @@ lens_status lens_deflect_grid(lens_plan* plan, const lens_grid* grid, int64_t ro
 lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box* box, int npx,
                          int npy, int64_t max_cells_per_chunk, int bbox_cap_px, double* map_out,
                          lens_ipm_stats* stats, void* stream) {
+  return lens_ipm_map_refined(plan, grid, box, npx, npy, max_cells_per_chunk, bbox_cap_px, 0,
+                              map_out, stats, stream);
+}
+
+lens_status lens_ipm_map_refined(lens_plan* plan, const lens_grid* grid, const lens_box* box,
+                                 int npx, int npy, int64_t max_cells_per_chunk, int bbox_cap_px,
+                                 int refine_levels, double* map_out, lens_ipm_stats* stats,
+                                 void* stream) {
   LENS_API_BEGIN
   need(plan != nullptr, "plan is NULL");
+  need(refine_levels >= 0 && refine_levels <= 16, "refine_levels must be in 0..16");
+  need(refine_levels == 0 || bbox_cap_px > 0, "refinement needs a cap (bbox_cap_px > 0)");
   Plan& P = plan->P;
   check_grid(P, grid);
   need(box != nullptr && map_out != nullptr, "box or map_out is NULL");
@@ -395,6 +405,10 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
   // in a per-row difference array, prefix-summed into the map at the end
   Scratch rowdiff(&P.da, sizeof(float) * ((size_t)npx + 1) * (size_t)npy);
   int* qcount = queue.as<int>() + (size_t)rows * (size_t)nx;
+  // refinement: the grid cells of a chunk over the cap, then per level
+  Scratch rq0(&P.da, refine_levels > 0 ? sizeof(int) * ((size_t)rows * (size_t)nx + 2) : 0);
+  int* rq0count = refine_levels > 0 ? rq0.as<int>() + (size_t)rows * (size_t)nx : nullptr;
+  int64_t refined = 0;
   LENS_CUDA(cudaMemsetAsync(map32.p, 0, map32.bytes, s));
   LENS_CUDA(cudaMemsetAsync(rowdiff.p, 0, rowdiff.bytes, s));
   LENS_CUDA(cudaMemsetAsync(sdev.p, 0, sdev.bytes, s));
@@ -426,10 +440,50 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     mark();
     evaluate_grid_pix(P, g, corners.as<PixCorner>(), ip, s);
     mark();
+    if (rq0count) LENS_CUDA(cudaMemsetAsync(rq0count, 0, sizeof(int), s));
     ipm_accumulate(corners.as<PixCorner>(), nx, nr, ip, map32.as<float>(), rowdiff.as<float>(),
-                   sdev.as<double>(), queue.as<int>(), qcount, s, &P.ev_ipm);
+                   sdev.as<double>(), queue.as<int>(), qcount, rq0.as<int>(), rq0count, s,
+                   &P.ev_ipm);
     pending += nr * nx;
     ++chunks;
+    if (refine_levels > 0) {
+      // split the cells over the cap 2 x 2, level by level; the sub-cell
+      // corner rays are not part of the grid's ray count
+      double* work = P.work;
+      P.work = nullptr;
+      int np = 0;
+      LENS_CUDA(cudaMemcpyAsync(&np, rq0count, sizeof(int), cudaMemcpyDeviceToHost, s));
+      LENS_CUDA(cudaStreamSynchronize(s));
+      Scratch parents_keep, org_keep;
+      const int* parents = rq0.as<int>();
+      const double2* org_in = nullptr;
+      double hc = grid->h;
+      for (int level = 1; level <= refine_levels && np > 0; ++level) {
+        const bool more = level < refine_levels;
+        Scratch org_out(&P.da, sizeof(double2) * 4 * (size_t)np);
+        Scratch rq(&P.da, more ? sizeof(int) * (4 * (size_t)np + 2) : 0);
+        int* rqc = more ? rq.as<int>() + 4 * (size_t)np : nullptr;
+        if (rqc) LENS_CUDA(cudaMemsetAsync(rqc, 0, sizeof(int), s));
+        ipm_refine(P, parents, np, org_in, grid->x0, grid->y0, r0, nx, hc, level, ip,
+                   map32.as<float>(), rowdiff.as<float>(), sdev.as<double>(),
+                   more ? rq.as<int>() : nullptr, rqc, org_out.as<double2>(), s, &P.ev_ipm);
+        refined += np;
+        pending += 4 * (int64_t)np;
+        int next = 0;
+        if (more) {
+          LENS_CUDA(cudaMemcpyAsync(&next, rqc, sizeof(int), cudaMemcpyDeviceToHost, s));
+          LENS_CUDA(cudaStreamSynchronize(s));
+        }
+        // this level's queue and corners feed the next one
+        parents_keep = std::move(rq);
+        org_keep = std::move(org_out);
+        parents = parents_keep.as<int>();
+        org_in = org_keep.as<double2>();
+        np = next;
+        hc *= 0.5;
+      }
+      P.work = work;
+    }
   }
   ipm_finish_map(map32.as<float>(), rowdiff.as<float>(), npx, npy, map_out, flushed, false, s);
   mark();
@@ -458,8 +512,8 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     stats->area_total = stats->cells * ip.a_cell;
     stats->area_in_map = ip.a_cell * hs[2];
     stats->area_outside = ip.a_cell * hs[3];
-    stats->area_dropped = ip.a_cell * hs[4];
-    stats->area_degenerate = ip.a_cell * hs[5];
+    stats->area_dropped = ip.a_cell * hs[6];
+    stats->area_degenerate = ip.a_cell * hs[7];
     stats->cells_dropped = hs[4];
     stats->cells_degenerate = hs[5];
     stats->chunks = chunks;
@@ -474,6 +528,7 @@ lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box*
     stats->ms_eval_kernel = mse;
     stats->ms_ipm_kernel = msk;
     stats->launches = launch_count() - l0;
+    stats->cells_refined = (double)refined;
   }
   LENS_API_END
 }

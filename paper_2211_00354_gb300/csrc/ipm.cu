@@ -66,7 +66,7 @@ __device__ __forceinline__ float pixel_area_f(const float* qx, const float* qy, 
 }
 
 struct IpmArgs {
-  const PixCorner* yc;  // (nrows+1) x (nx+1) corners of the chunk
+  const PixCorner* yc;  // (nrows+1) x (nx+1) corners of the chunk, or 4 per cell (quads)
   int64_t nx, ncells;
   float* map;           // float32 accumulation map (added to the float64 output at the end)
   float* D;             // per-row difference array, npy x (npx + 1): prefix-summed at the end
@@ -76,7 +76,9 @@ struct IpmArgs {
   IpmParams ip;
   float thr_area;       // fast-path lower bound on |A_P| in pixel units
   float thr_degen;      // |A_P| (pixel units) at or below which a cell is degenerate
-  float scale_f;        // ip.scale in float32
+  float scale_f;        // ip.scale x wcell in float32
+  float wcell;          // cell area in units of the grid's cell (1, or 4^-level for sub-cells)
+  int* rq; int* rqcount;  // refinement: cells over the cap are queued here (NULL: dropped)
 };
 
 // Ledger of one thread: fractions in float32, counts in integers (no
@@ -89,7 +91,10 @@ struct Ledger {
   unsigned ndrop = 0, ndeg = 0, nupd = 0, nq = 0, nff = 0;
 };
 
-__device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L) {
+// w: the cells' area in grid cells (uniform over a launch), applied to the
+// fractions here once instead of per update.  Slots [6], [7]: dropped and
+// degenerate area in grid cells (the counts [4], [5] times w).
+__device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L, float wcell) {
   __shared__ float shf[2][kIpmThreads / 32];
   __shared__ unsigned shu[5][kIpmThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -109,12 +114,14 @@ __device__ __forceinline__ void block_add_stats(double* stats, const Ledger& L) 
     shu[0][w] = u0; shu[1][w] = u1; shu[2][w] = u2; shu[3][w] = u3; shu[4][w] = u4;
   }
   __syncthreads();
-  if (threadIdx.x < 7) {
+  if (threadIdx.x < 9) {
+    // thread t: slots 2, 3 (fractions x w), 4, 5 (counts), 8, 9, 10, then 6, 7
+    const int src = threadIdx.x < 7 ? threadIdx.x : threadIdx.x - 5;
     double x = 0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
-      x += threadIdx.x < 2 ? (double)shf[threadIdx.x][q] : (double)shu[threadIdx.x - 2][q];
-    // slots 2, 3, 4, 5, 8, 9, 10
-    const int slot = threadIdx.x < 4 ? 2 + threadIdx.x : 4 + threadIdx.x;
+      x += src < 2 ? (double)shf[src][q] : (double)shu[src - 2][q];
+    if (src < 2 || threadIdx.x >= 7) x *= (double)wcell;
+    const int slot = threadIdx.x < 4 ? 2 + threadIdx.x : threadIdx.x < 7 ? 4 + threadIdx.x : threadIdx.x - 1;
     if (x != 0.0) atomicAdd(&stats[slot], x);
   }
 }
@@ -210,6 +217,7 @@ __device__ __forceinline__ void unpack4(float (&a)[4], const float4 v) {
 //     (the same Green's-theorem terms as pixel_area_f()), again spread over
 //     the lanes.  Work per large cell follows its perimeter in pixels, not
 //     its area.
+template <bool QUADS>
 __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
   __shared__ CellShared sh;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -233,14 +241,19 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
     int nsmall = 0, nrows = 0;
     bool f64 = false;
     if (c < A.ncells) {
-      // cell index < 2^30 and nx < 2^31: 32-bit division
-      const uint32_t j32 = (uint32_t)c / (uint32_t)A.nx;
-      const int64_t j = j32, i = c - j * A.nx;
       PixCorner q4[4];
-      q4[0] = A.yc[j * W + i];
-      q4[1] = A.yc[j * W + i + 1];
-      q4[2] = A.yc[(j + 1) * W + i + 1];
-      q4[3] = A.yc[(j + 1) * W + i];
+      if (QUADS) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q4[k] = A.yc[4 * c + k];
+      } else {
+        // cell index < 2^30 and nx < 2^31: 32-bit division
+        const uint32_t j32 = (uint32_t)c / (uint32_t)A.nx;
+        const int64_t j = j32, i = c - j * A.nx;
+        q4[0] = A.yc[j * W + i];
+        q4[1] = A.yc[j * W + i + 1];
+        q4[2] = A.yc[(j + 1) * W + i + 1];
+        q4[3] = A.yc[(j + 1) * W + i];
+      }
       bool far = false;
       int ix0 = kFar, ix1 = -kFar, iy0 = kFar, iy1 = -kFar;
 #pragma unroll
@@ -249,12 +262,13 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
         ix0 = min(ix0, q4[k].iu); ix1 = max(ix1, q4[k].iu);
         iy0 = min(iy0, q4[k].iv); iy1 = max(iy1, q4[k].iv);
       }
-      if (far) {
-        led.ndrop += 1;
-      } else if (ix1 < 0 || iy1 < 0 || ix0 > npx - 1 || iy0 > npy - 1) {
+      if (!far && (ix1 < 0 || iy1 < 0 || ix0 > npx - 1 || iy0 > npy - 1)) {
         led.fout += 1.f;
-      } else if (A.ip.cap > 0 && ((int64_t)ix1 - ix0 + 1 > A.ip.cap || (int64_t)iy1 - iy0 + 1 > A.ip.cap)) {
-        led.ndrop += 1;
+      } else if (far || (A.ip.cap > 0 && ((int64_t)ix1 - ix0 + 1 > A.ip.cap ||
+                                          (int64_t)iy1 - iy0 + 1 > A.ip.cap))) {
+        // over the cap (or a corner beyond 2^30 pixels): split further, or dropped
+        if (A.rq) A.rq[atomicAdd(A.rqcount, 1)] = (int)c;
+        else led.ndrop += 1;
       } else {
         float qx[4], qy[4];
         float xmn = 1e30f, xmx = -1e30f, ymn = 1e30f, ymx = -1e30f;
@@ -444,7 +458,7 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
       ch = (int64_t)__shfl_sync(0xffffffffu, g_u, 0) * kChunksPerGrab;
     }
   }
-  block_add_stats(A.stats, led);
+  block_add_stats(A.stats, led, A.wcell);
 }
 
 // ---- float-float (about 48-bit) arithmetic for ill-conditioned cells -------
@@ -496,6 +510,7 @@ __device__ __forceinline__ ff pixel_area_ff(const ff* qx, const ff* qy, const ff
 // edge cuts are collected in shared memory and their overlaps taken in
 // float-float (coordinates local to the box, exact from the corners' integer
 // and fractional parts) 32 at a time.
+template <bool QUADS>
 __global__ void __launch_bounds__(kIpmThreads) k_ipm_ext(IpmArgs A) {
   __shared__ int cut_x[kWarps][64], cut_y[kWarps][64];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -505,14 +520,19 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_ext(IpmArgs A) {
   Ledger led;
   for (int64_t t = wg; t < nq; t += nwarps) {
     const int64_t c = A.queue[t];
-    const uint32_t j32 = (uint32_t)c / (uint32_t)A.nx;
-    const int64_t j = j32, i = c - j * A.nx;
-    const int64_t W = A.nx + 1;
     PixCorner q4[4];
-    q4[0] = A.yc[j * W + i];
-    q4[1] = A.yc[j * W + i + 1];
-    q4[2] = A.yc[(j + 1) * W + i + 1];
-    q4[3] = A.yc[(j + 1) * W + i];
+    if (QUADS) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q4[k] = A.yc[4 * c + k];
+    } else {
+      const uint32_t j32 = (uint32_t)c / (uint32_t)A.nx;
+      const int64_t j = j32, i = c - j * A.nx;
+      const int64_t W = A.nx + 1;
+      q4[0] = A.yc[j * W + i];
+      q4[1] = A.yc[j * W + i + 1];
+      q4[2] = A.yc[(j + 1) * W + i + 1];
+      q4[3] = A.yc[(j + 1) * W + i];
+    }
     int ix0 = kFar, ix1 = -kFar, iy0 = kFar, iy1 = -kFar;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -610,7 +630,7 @@ __global__ void __launch_bounds__(kIpmThreads) k_ipm_ext(IpmArgs A) {
     for (int o = 16; o > 0; o >>= 1) fin += __shfl_xor_sync(0xffffffffu, fin, o);
     if (lane == 0) { led.fin += fin; led.fout += 1.f - fin; }
   }
-  block_add_stats(A.stats, led);
+  block_add_stats(A.stats, led, A.wcell);
 }
 
 }  // namespace
@@ -676,18 +696,12 @@ void ipm_finish_map(float* map32, float* rowdiff, int npx, int npy, double* map,
   LENS_LAUNCHED("k_map_finish");
 }
 
-void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const IpmParams& ip,
-                    float* map, float* rowdiff, double* stats_dev, int* queue, int* qcount,
-                    cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev) {
-  const int64_t ncells = nx * nrows_cells;
-  if (ncells <= 0) return;
-  IpmArgs A{};
-  A.yc = yc; A.nx = nx; A.ncells = ncells; A.map = map; A.stats = stats_dev;
-  A.D = rowdiff; A.ldd = (int64_t)ip.npx + 1;
-  A.queue = queue; A.qcount = qcount; A.ip = ip;
-  A.thr_area = (float)(1e-13 * ip.a_cell / ip.s_star);
-  A.thr_degen = (float)(1e-14 * ip.a_cell / ip.s_star);
-  A.scale_f = (float)ip.scale;
+namespace {
+void ipm_launch(IpmArgs& A, bool quads, int* qcount, cudaStream_t s,
+                std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev) {
+  A.thr_area = (float)(1e-13 * A.ip.a_cell / A.ip.s_star);
+  A.thr_degen = (float)(1e-14 * A.ip.a_cell / A.ip.s_star);
+  A.scale_f = (float)(A.ip.scale * A.wcell);
   // qcount[0]: float-float queue length; qcount[1]: chunk counter of k_ipm_cells
   LENS_CUDA(cudaMemsetAsync(qcount, 0, 2 * sizeof(int), s));
   std::pair<cudaEvent_t, cudaEvent_t> e;
@@ -695,15 +709,120 @@ void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const 
   int dev = 0, sms = 152;
   LENS_CUDA(cudaGetDevice(&dev));
   LENS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t chunk_blocks = (ncells + kIpmThreads - 1) / kIpmThreads;
-  k_ipm_cells<<<(unsigned)std::min<int64_t>(chunk_blocks, (int64_t)sms * 8), kIpmThreads, 0, s>>>(A);
+  const int64_t chunk_blocks = (A.ncells + kIpmThreads - 1) / kIpmThreads;
+  const unsigned g = (unsigned)std::min<int64_t>(chunk_blocks, (int64_t)sms * 8);
+  if (quads) k_ipm_cells<true><<<g, kIpmThreads, 0, s>>>(A);
+  else k_ipm_cells<false><<<g, kIpmThreads, 0, s>>>(A);
   LENS_LAUNCHED("k_ipm_cells");
-  k_ipm_ext<<<sms * 2, kIpmThreads, 0, s>>>(A);
+  if (quads) k_ipm_ext<true><<<sms * 2, kIpmThreads, 0, s>>>(A);
+  else k_ipm_ext<false><<<sms * 2, kIpmThreads, 0, s>>>(A);
   LENS_LAUNCHED("k_ipm_ext");
   if (ev) {
     event_pair_end(e, s);
     ev->push_back(e);
   }
+}
+
+// Refinement, step 1: for each queued cell, its 3 x 3 corner grid of half
+// spacing (the rays to deflect) and the lower-left corners of its 2 x 2
+// sub-cells.  A queued cell is a grid cell (origin from the grid) at the first
+// level, a sub-cell of the previous level (origin from org_in) after that.
+__global__ void k_refine_points(const int* __restrict__ parents, int64_t np,
+                                const double2* __restrict__ org_in, double gx0, double gy0,
+                                int64_t grow0, int64_t gnx, double h, double2* __restrict__ rays,
+                                double2* __restrict__ org_out) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  const int64_t c = parents[k];
+  double xl, yl;
+  if (org_in) {
+    xl = org_in[c].x; yl = org_in[c].y;
+  } else {
+    // the expression the grid's corners use: x0 + i h, y0 + j h
+    const int64_t j = c / gnx, i = c - j * gnx;
+    xl = gx0 + (double)i * h; yl = gy0 + (double)(grow0 + j) * h;
+  }
+  const double g = 0.5 * h;
+  const double xs[3] = {xl, xl + g, xl + h}, ys[3] = {yl, yl + g, yl + h};
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rays[9 * k + 3 * b + a] = make_double2(xs[a], ys[b]);
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) org_out[4 * k + 2 * b + a] = make_double2(xs[a], ys[b]);
+}
+
+// Refinement, step 2: the deflected 3 x 3 grids in pixel coordinates, four
+// corners (c00, c10, c11, c01) per sub-cell, sub-cell 4k + 2b + a.
+__global__ void k_refine_quads(const double2* __restrict__ y, int64_t np, IpmParams ip,
+                               PixCorner* __restrict__ quads) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= np * 16) return;
+  const int64_t k = t >> 4;
+  const int q = (int)(t & 15), sub = q >> 2, corner = q & 3;
+  const int a = sub & 1, b = sub >> 1;
+  // corner order c00, c10, c11, c01 of the sub-cell at (a, b)
+  const int ca = a + (corner == 1 || corner == 2), cb = b + (corner >= 2);
+  const double2 p = y[9 * k + 3 * cb + ca];
+  const double u = (p.x - ip.u0) * ip.inv_du, v = (p.y - ip.v0) * ip.inv_dv;
+  PixCorner pc;
+  if (!(fabs(u) < 5.0e8) || !(fabs(v) < 5.0e8)) {
+    pc.iu = kFar; pc.fu = 0.f; pc.iv = kFar; pc.fv = 0.f;
+  } else {
+    const double fu = floor(u), fv = floor(v);
+    pc.iu = (int)fu; pc.fu = (float)(u - fu);
+    pc.iv = (int)fv; pc.fv = (float)(v - fv);
+    // a fraction that rounds up to 1 moves to the next pixel
+    if (pc.fu >= 1.f) { pc.iu += 1; pc.fu = 0.f; }
+    if (pc.fv >= 1.f) { pc.iv += 1; pc.fv = 0.f; }
+  }
+  quads[4 * (4 * k + sub) + corner] = pc;
+}
+}  // namespace
+
+void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const IpmParams& ip,
+                    float* map, float* rowdiff, double* stats_dev, int* queue, int* qcount,
+                    int* rq, int* rqcount, cudaStream_t s,
+                    std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev) {
+  const int64_t ncells = nx * nrows_cells;
+  if (ncells <= 0) return;
+  IpmArgs A{};
+  A.yc = yc; A.nx = nx; A.ncells = ncells; A.map = map; A.stats = stats_dev;
+  A.D = rowdiff; A.ldd = (int64_t)ip.npx + 1;
+  A.queue = queue; A.qcount = qcount; A.ip = ip;
+  A.wcell = 1.f;
+  A.rq = rq; A.rqcount = rqcount;
+  ipm_launch(A, false, qcount, s, ev);
+}
+
+int64_t ipm_refine(Plan& P, const int* parents, int64_t np, const double2* org_in, double gx0,
+                   double gy0, int64_t grow0, int64_t gnx, double h, int level,
+                   const IpmParams& ip, float* map,
+                   float* rowdiff, double* stats_dev, int* rq_next, int* rqcount_next,
+                   double2* org_out, cudaStream_t s,
+                   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev) {
+  if (np <= 0) return 0;
+  Scratch rays(&P.da, sizeof(double2) * 9 * (size_t)np);
+  Scratch y(&P.da, sizeof(double2) * 9 * (size_t)np);
+  Scratch quads(&P.da, sizeof(PixCorner) * 16 * (size_t)np);
+  Scratch queue(&P.da, sizeof(int) * 4 * (size_t)np + sizeof(int) * 2);
+  k_refine_points<<<grid_for(np, 128), 128, 0, s>>>(parents, np, org_in, gx0, gy0, grow0, gnx,
+                                                     h, rays.as<double2>(), org_out);
+  LENS_LAUNCHED("k_refine_points");
+  evaluate_rays(P, rays.as<double>(), 9 * np, y.as<double>(), nullptr, s);
+  k_refine_quads<<<grid_for(16 * np, 256), 256, 0, s>>>(y.as<double2>(), np, ip,
+                                                         quads.as<PixCorner>());
+  LENS_LAUNCHED("k_refine_quads");
+  IpmArgs A{};
+  A.yc = quads.as<PixCorner>(); A.nx = 0; A.ncells = 4 * np; A.map = map; A.stats = stats_dev;
+  A.D = rowdiff; A.ldd = (int64_t)ip.npx + 1;
+  A.queue = queue.as<int>(); A.qcount = queue.as<int>() + 4 * np; A.ip = ip;
+  A.wcell = (float)std::ldexp(1.0, -2 * level);
+  A.rq = rq_next; A.rqcount = rqcount_next;
+  ipm_launch(A, true, A.qcount, s, ev);
+  return 4 * np;
 }
 
 }  // namespace lens

@@ -270,9 +270,24 @@ void evaluate_grid_pix(Plan& P, const GridRows& g, PixCorner* out, const IpmPara
                        cudaStream_t s);
 // map32: float32 accumulation map (npy x npx); rowdiff: float32 per-row
 // difference array (npy x (npx + 1)) for whole-pixel runs of large cells.
+// rq / rqcount: with refinement, the cells over the cap are queued there
+// instead of dropped (NULL: dropped).
 void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const IpmParams& ip,
                     float* map32, float* rowdiff, double* stats_dev, int* queue, int* qcount,
-                    cudaStream_t s, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev);
+                    int* rq, int* rqcount, cudaStream_t s,
+                    std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev);
+// One refinement level: each of the np queued cells (cells of the chunk
+// starting at grid row grow0 when org_in is NULL, else sub-cells with
+// lower-left corners org_in[]) of side h is split into 2 x 2 sub-cells of
+// side h/2, whose corners are deflected (the plan's ray path) and mapped with
+// weight 4^-level.  Sub-cells over the cap go to rq_next (NULL: dropped);
+// org_out receives the 4 np sub-cell corners.  Returns the sub-cells mapped.
+int64_t ipm_refine(Plan& P, const int* parents, int64_t np, const double2* org_in, double gx0,
+                   double gy0, int64_t grow0, int64_t gnx, double h, int level,
+                   const IpmParams& ip, float* map,
+                   float* rowdiff, double* stats_dev, int* rq_next, int* rqcount_next,
+                   double2* org_out, cudaStream_t s,
+                   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev);
 // float32 evaluation data that needs only the tree (leaf geometry, staged
 // near-field stars, far W boxes), and the part that needs the expansions
 // (constants of the lens equation per leaf, float32 copies of L and M);

@@ -35,6 +35,7 @@ FP32_BULK = 1
 
 # Every symbol include/lens.h declares (checked by the ABI tests).
 EXPORTED = ("lens_fmm_build", "lens_deflect", "lens_deflect_grid", "lens_ipm_map",
+            "lens_ipm_map_refined",
             "lens_deflect_adjoint", "lens_plan_info_get", "lens_plan_destroy",
             "lens_direct_deflect", "lens_direct_deflect_noalloc", "lens_light_curve",
             "lens_light_curve_grad",
@@ -74,7 +75,8 @@ class lens_ipm_stats(ctypes.Structure):
                 ("ipm_updates", ctypes.c_double), ("cells_queued", ctypes.c_double),
                 ("cells_ext", ctypes.c_double),
                 ("ms_eval_kernel", ctypes.c_double),
-                ("ms_ipm_kernel", ctypes.c_double), ("launches", ctypes.c_int64)]
+                ("ms_ipm_kernel", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("cells_refined", ctypes.c_double)]
 
 
 class lens_plan_info(ctypes.Structure):
@@ -127,6 +129,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lens_ipm_map.argtypes = [vp, ctypes.POINTER(lens_grid), ctypes.POINTER(lens_box), i, i,
                                  i64, i, vp, ctypes.POINTER(lens_ipm_stats), vp]
     lib.lens_ipm_map.restype = st
+    lib.lens_ipm_map_refined.argtypes = [vp, ctypes.POINTER(lens_grid), ctypes.POINTER(lens_box),
+                                         i, i, i64, i, i, vp, ctypes.POINTER(lens_ipm_stats), vp]
+    lib.lens_ipm_map_refined.restype = st
     lib.lens_deflect_adjoint.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
     lib.lens_deflect_adjoint.restype = st
     lib.lens_plan_info_get.argtypes = [vp, ctypes.POINTER(lens_plan_info)]
@@ -283,15 +288,24 @@ class LensFMM:
         return (y, jac) if jacobian else y
 
     def ipm_map(self, grid, box, npx: int, npy: int, max_cells_per_chunk: int = 0,
-                bbox_cap: int = 0, out: Optional[torch.Tensor] = None, stream=None):
+                bbox_cap: int = 0, out: Optional[torch.Tensor] = None, stream=None,
+                refine_levels: int = 0):
+        """Magnification map (lens_ipm_map; lens_ipm_map_refined when
+        refine_levels > 0: cells over bbox_cap split 2 x 2 instead of dropped)."""
         g = grid_struct(grid)
         b = lens_box(*(float(v) for v in box))
         dev = torch.device("cuda", torch.cuda.current_device())
         mp = out if out is not None else torch.empty((npy, npx), dtype=torch.float64, device=dev)
         st = lens_ipm_stats()
-        _check(_lib.lens_ipm_map(self._handle, ctypes.byref(g), ctypes.byref(b), int(npx),
-                                 int(npy), int(max_cells_per_chunk), int(bbox_cap),
-                                 mp.data_ptr(), ctypes.byref(st), _stream_ptr(stream)))
+        if refine_levels:
+            _check(_lib.lens_ipm_map_refined(self._handle, ctypes.byref(g), ctypes.byref(b),
+                                             int(npx), int(npy), int(max_cells_per_chunk),
+                                             int(bbox_cap), int(refine_levels), mp.data_ptr(),
+                                             ctypes.byref(st), _stream_ptr(stream)))
+        else:
+            _check(_lib.lens_ipm_map(self._handle, ctypes.byref(g), ctypes.byref(b), int(npx),
+                                     int(npy), int(max_cells_per_chunk), int(bbox_cap),
+                                     mp.data_ptr(), ctypes.byref(st), _stream_ptr(stream)))
         stats = {name: getattr(st, name) for name, _ in lens_ipm_stats._fields_}
         return mp, stats
 
