@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--half-map", type=float, default=100.0)
     ap.add_argument("--h", type=float, default=0.063)
     ap.add_argument("--cap", type=int, default=64)
+    ap.add_argument("--refine", type=int, default=0,
+                    help="levels of 2x2 refinement of cells over the cap (0: they are dropped)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--shard", default="independent", choices=["independent", "strips"],
                     help="N>1: independent maps per rank (weak scaling) or one map split in "
@@ -237,7 +239,8 @@ def main():
     def step():
         P = lens.LensFMM(stars, masses, f.kappa_s, f.gamma, p=args.p, leaf_size=args.leaf,
                          prec=prec, target_box=target)
-        _, st = P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp)
+        _, st = P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp,
+                          refine_levels=args.refine)
         if strips:
             ldist.allreduce_map(mp)  # the path's one exchange: sum of the strip maps
         info = P.info()
@@ -388,7 +391,8 @@ def main():
             d_masses.copy_(h_masses, non_blocking=True)
             P = lens.LensFMM(d_stars, d_masses, f.kappa_s, f.gamma, p=args.p, leaf_size=args.leaf,
                              prec=prec, target_box=target)
-            P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp)
+            P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp,
+                      refine_levels=args.refine)
             if strips:
                 ldist.allreduce_map(mp)
             h_map.copy_(mp, non_blocking=True)
@@ -422,6 +426,7 @@ def main():
             "config": {"workload": workload_name(args), "n_stars": f.n, "cells": g.n_cells,
                        "grid": [g.nx, g.ny], "npix": [f.npx, f.npy], "p": args.p,
                        "leaf_size": args.leaf, "bbox_cap_px": args.cap,
+                       "refine_levels": args.refine,
                        "l2": "flushed between steps (256 MiB write)" if not args.no_flush else "not flushed",
                        "parallelism": ("one map in %d row strips + map all-reduce" % world if strips
                                        else "independent map per GPU" if world > 1 else "1 GPU")},
@@ -437,7 +442,8 @@ def main():
             "tree": {k: info[k] for k in ("n_boxes", "n_active_boxes", "n_active_leaves", "n_v",
                                           "n_x", "n_u", "n_w", "levels")},
             "ledger": {k: st[k] for k in ("area_total", "area_in_map", "area_outside",
-                                           "area_dropped", "area_degenerate", "cells_dropped")},
+                                           "area_dropped", "area_degenerate", "cells_dropped",
+                                           "cells_refined")},
             "mean_mu_interior": mu_mean,
             "roofline": roof,
             "ipm_roofline": {"bound": "hbm", "achieved": ipm_gbs, "peak": hbm_peak,
