@@ -69,6 +69,13 @@ def _load():
                                                d, d, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_int, _dp, _dp]
         lib.oracle_ipm_map_refined.restype = None
+        ci = ctypes.c_int
+        lib.oracle_map_convolve_gaussian.argtypes = [ci, ci, _dp, d, d, _dp]
+        lib.oracle_map_convolve_gaussian.restype = None
+        lib.oracle_histogram.argtypes = [i64, _dp, d, d, ci, ci, ctypes.POINTER(i64)]
+        lib.oracle_histogram.restype = None
+        lib.oracle_map_track.argtypes = [ci, ci, _dp, d, d, d, d, i64, _dp, _dp]
+        lib.oracle_map_track.restype = None
         lib.oracle_adjoint.argtypes = [i64, _dp, _dp, i64, _dp, _dp, _dp, _dp, _dp]
         lib.oracle_adjoint.restype = None
         lib.oracle_light_curve.argtypes = [i64, _dp, d, i64, _dp, d, d, _dp]
@@ -165,6 +172,39 @@ def ipm_map_refined(ycorn, x0, y0, h, stars, masses, kappa_s, gamma, box, npx, n
                                int(bbox_cap), int(levels), mp.ctypes.data_as(_dp),
                                st.ctypes.data_as(_dp))
     return mp, dict(zip(IPM_STAT_KEYS, st.tolist()))
+
+
+def map_convolve_gaussian(mp, sigma_px, trunc=6.0):
+    """The map seen by a Gaussian source of sigma_px pixels (truncated at trunc
+    sigma, renormalised at the map's edges)."""
+    lib = _load()
+    m, mp_ = _c(mp)
+    out = np.empty_like(m)
+    lib.oracle_map_convolve_gaussian(m.shape[1], m.shape[0], mp_, float(sigma_px), float(trunc),
+                                     out.ctypes.data_as(_dp))
+    return out
+
+
+def histogram(v, lo, hi, nbins, log_bins=False):
+    """counts[0] below lo, counts[1..nbins] the bins, counts[nbins+1] above."""
+    lib = _load()
+    a, ap = _c(np.asarray(v).reshape(-1))
+    counts = np.zeros(nbins + 2, dtype=np.int64)
+    lib.oracle_histogram(a.shape[0], ap, float(lo), float(hi), int(nbins), int(bool(log_bins)),
+                         counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return counts
+
+
+def map_track(mp, box, s):
+    """The map at source positions s (k x 2), bilinear between pixel centres."""
+    lib = _load()
+    m, mp_ = _c(mp)
+    ss, sp = _c(np.asarray(s).reshape(-1, 2))
+    out = np.empty(ss.shape[0])
+    u0, u1, v0, v1 = (float(x) for x in box)
+    lib.oracle_map_track(m.shape[1], m.shape[0], mp_, u0, u1, v0, v1, ss.shape[0], sp,
+                         out.ctypes.data_as(_dp))
+    return out
 
 
 def adjoint(stars, masses, rays, grad_y):

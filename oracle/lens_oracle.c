@@ -34,6 +34,10 @@
  *                          star positions, masses, kappa_s and gamma, from the
  *                          real-variable derivatives of Eq. 1 (no complex
  *                          form, no FMM).
+ *   oracle_map_convolve_gaussian, oracle_histogram, oracle_map_track --
+ *                          consumers of a map (Sec. 3): a Gaussian finite
+ *                          source (direct 2D sum), magnification histograms,
+ *                          light curves sampled along a source track.
  *   oracle_light_curve(_grad) -- light curve of a finite source (Sec. 3.3
  *                          derives light curves for Earendel; the source
  *                          profile is a Gaussian, as for the background source
@@ -477,5 +481,83 @@ void oracle_light_curve_grad(int64_t m, const double* y, double w_ray, int64_t n
     }
     gy[2 * r] = nsum_get(&g1);
     gy[2 * r + 1] = nsum_get(&g2);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Consumers of a magnification map (Sec. 3: histograms of the magnification
+ * of finite sources, light curves along source tracks).  The map is npy x npx,
+ * row-major, pixel (px, py) centred at (px + 1/2, py + 1/2) in pixel units.
+ *
+ * Finite source: the map convolved with a Gaussian of sigma_px pixels,
+ * truncated at trunc sigma and renormalised to the part of the kernel inside
+ * the map:
+ *   out[p] = sum_q w(q - p) map[q] / sum_q w(q - p),  w(d) = exp(-|d|^2 / 2 s^2),
+ * q over the map pixels with |q - p| <= trunc s.  Plain 2D sum. */
+void oracle_map_convolve_gaussian(int npx, int npy, const double* map, double sigma_px,
+                                  double trunc, double* out) {
+  const int R = (int)floor(trunc * sigma_px);
+  const double inv2s2 = 1.0 / (2.0 * sigma_px * sigma_px);
+  const double cut2 = trunc * trunc * sigma_px * sigma_px;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int py = 0; py < npy; ++py) {
+    for (int px = 0; px < npx; ++px) {
+      nsum num = {0, 0}, den = {0, 0};
+      for (int dy = -R; dy <= R; ++dy) {
+        const int qy = py + dy;
+        if (qy < 0 || qy >= npy) continue;
+        for (int dx = -R; dx <= R; ++dx) {
+          const int qx = px + dx;
+          if (qx < 0 || qx >= npx) continue;
+          const double d2 = (double)dx * dx + (double)dy * dy;
+          if (d2 > cut2) continue;
+          const double w = exp(-d2 * inv2s2);
+          nsum_add(&num, w * map[(int64_t)qy * npx + qx]);
+          nsum_add(&den, w);
+        }
+      }
+      out[(int64_t)py * npx + px] = nsum_get(&num) / nsum_get(&den);
+    }
+  }
+}
+
+/* Histogram of n values into nbins equal bins of [lo, hi) (of log10(value)
+ * when log_bins, values <= 0 counting as below): counts[0] below lo,
+ * counts[1 .. nbins] the bins, counts[nbins + 1] at or above hi. */
+void oracle_histogram(int64_t n, const double* v, double lo, double hi, int nbins, int log_bins,
+                      int64_t* counts) {
+  for (int b = 0; b < nbins + 2; ++b) counts[b] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    double x = v[i];
+    if (log_bins) {
+      if (!(x > 0.0)) { counts[0] += 1; continue; }
+      x = log10(x);
+    }
+    if (x < lo) { counts[0] += 1; continue; }
+    if (x >= hi) { counts[nbins + 1] += 1; continue; }
+    int b = (int)floor((x - lo) / (hi - lo) * nbins);
+    if (b >= nbins) b = nbins - 1;
+    counts[1 + b] += 1;
+  }
+}
+
+/* The map at ns source positions s (source-plane coordinates, the map
+ * covering [u0, u1) x [v0, v1)), bilinear between pixel centres, clamped to
+ * the outermost centres: a light curve along a track of the source. */
+void oracle_map_track(int npx, int npy, const double* map, double u0, double u1, double v0,
+                      double v1, int64_t ns, const double* s, double* out) {
+  const double du = (u1 - u0) / npx, dv = (v1 - v0) / npy;
+  for (int64_t k = 0; k < ns; ++k) {
+    double x = (s[2 * k] - u0) / du - 0.5, y = (s[2 * k + 1] - v0) / dv - 0.5;
+    x = fmin(fmax(x, 0.0), (double)(npx - 1));
+    y = fmin(fmax(y, 0.0), (double)(npy - 1));
+    int ix = (int)floor(x), iy = (int)floor(y);
+    if (ix > npx - 2) ix = npx > 1 ? npx - 2 : 0;
+    if (iy > npy - 2) iy = npy > 1 ? npy - 2 : 0;
+    const double fx = npx > 1 ? x - ix : 0.0, fy = npy > 1 ? y - iy : 0.0;
+    const int ix1 = npx > 1 ? ix + 1 : ix, iy1 = npy > 1 ? iy + 1 : iy;
+    const double m00 = map[(int64_t)iy * npx + ix], m10 = map[(int64_t)iy * npx + ix1];
+    const double m01 = map[(int64_t)iy1 * npx + ix], m11 = map[(int64_t)iy1 * npx + ix1];
+    out[k] = (1 - fy) * ((1 - fx) * m00 + fx * m10) + fy * ((1 - fx) * m01 + fx * m11);
   }
 }
