@@ -277,6 +277,34 @@ lens_status lens_light_curve_grad(const double* y, int64_t m, double w_ray,
                                   const double* T, double* grad_y_out,
                                   void* stream);
 
+/* ---- consumers of a magnification map (Sec. 3: magnification histograms of
+ * finite sources, light curves along source tracks).  map: dev npy x npx,
+ * row-major as lens_ipm_map writes it. */
+
+/* The map seen by a Gaussian source of sigma_px pixels: the map convolved with
+ * exp(-|d|^2 / 2 sigma^2), truncated at R = floor(trunc sigma_px) pixels along
+ * each axis (R <= 1024) and renormalised to the part of the kernel inside the
+ * map.  out: dev npy x npx (may not alias map).  Scratch from allocator (may
+ * be NULL: the library's pool).  Synchronises `stream`. */
+lens_status lens_map_source(const double* map, int npx, int npy, double sigma_px,
+                            double trunc, double* out,
+                            const lens_allocator* allocator, void* stream);
+
+/* Histogram of n values (dev) into nbins equal bins of [lo, hi), of
+ * log10(value) when log_bins != 0 (values <= 0 then count as below).
+ * counts: dev int64[nbins + 2]: [0] below lo, [1..nbins] the bins,
+ * [nbins + 1] at or above hi.  nbins 1..8192. */
+lens_status lens_map_histogram(const double* values, int64_t n, double lo,
+                               double hi, int nbins, int log_bins,
+                               int64_t* counts, void* stream);
+
+/* The map at ns source positions (dev ns x 2, source-plane coordinates of
+ * the map window box): bilinear between pixel centres, clamped to the
+ * outermost centres.  out: dev ns. */
+lens_status lens_map_track(const double* map, int npx, int npy,
+                           const lens_box* box, const double* positions,
+                           int64_t ns, double* out, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* lens_last_error(void);
 

@@ -587,4 +587,44 @@ lens_status lens_light_curve_grad(const double* y, int64_t m, double w_ray, cons
   LENS_API_END
 }
 
+lens_status lens_map_source(const double* map, int npx, int npy, double sigma_px, double trunc,
+                            double* out, const lens_allocator* allocator, void* stream) {
+  LENS_API_BEGIN
+  need(map && out, "NULL buffer");
+  need(map != out, "out may not alias map");
+  need(npx >= 1 && npy >= 1 && (int64_t)npx * npy < (1ll << 31), "npx, npy must be >= 1 with npx*npy < 2^31");
+  need(sigma_px > 0 && trunc > 0 && std::isfinite(sigma_px) && std::isfinite(trunc),
+       "sigma_px, trunc must be finite and > 0");
+  DeviceAlloc da;
+  if (allocator) { da.a = *allocator; da.custom = true; }
+  da.stream = S(stream);
+  map_source(map, npx, npy, sigma_px, trunc, out, da, S(stream));
+  LENS_API_END
+}
+
+lens_status lens_map_histogram(const double* values, int64_t n, double lo, double hi, int nbins,
+                               int log_bins, int64_t* counts, void* stream) {
+  LENS_API_BEGIN
+  need(n >= 0, "n must be >= 0");
+  need(counts && (n == 0 || values), "NULL buffer");
+  need(nbins >= 1 && nbins <= 8192, "nbins must be in 1..8192");
+  need(std::isfinite(lo) && std::isfinite(hi) && hi > lo, "need finite lo < hi");
+  map_histogram(values, n, lo, hi, nbins, log_bins ? 1 : 0, counts, S(stream));
+  LENS_API_END
+}
+
+lens_status lens_map_track(const double* map, int npx, int npy, const lens_box* box,
+                           const double* positions, int64_t ns, double* out, void* stream) {
+  LENS_API_BEGIN
+  need(ns >= 0, "ns must be >= 0");
+  need(box && map && (ns == 0 || (positions && out)), "NULL buffer");
+  need(npx >= 1 && npy >= 1 && (int64_t)npx * npy < (1ll << 31), "npx, npy must be >= 1 with npx*npy < 2^31");
+  need(std::isfinite(box->u0) && std::isfinite(box->u1) && std::isfinite(box->v0) &&
+           std::isfinite(box->v1) && box->u1 > box->u0 && box->v1 > box->v0,
+       "map window must be finite with u1 > u0, v1 > v0");
+  const double b[4] = {box->u0, box->u1, box->v0, box->v1};
+  map_track(map, npx, npy, b, positions, ns, out, S(stream));
+  LENS_API_END
+}
+
 }  // extern "C"

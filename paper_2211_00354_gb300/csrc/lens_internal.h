@@ -308,6 +308,13 @@ void eval32_rays(Plan& P, const double* rays, const int64_t* off, const int* per
 // `accumulate`; `clear` zeroes map32 and rowdiff behind the read
 void ipm_finish_map(float* map32, float* rowdiff, int npx, int npy, double* map, bool accumulate,
                     bool clear, cudaStream_t s);
+// map consumers (mapops.cu): Gaussian finite source, histogram, track
+void map_source(const double* map, int npx, int npy, double sigma_px, double trunc, double* out,
+                DeviceAlloc& da, cudaStream_t s);
+void map_histogram(const double* v, int64_t n, double lo, double hi, int nbins, int log_bins,
+                   int64_t* counts, cudaStream_t s);
+void map_track(const double* map, int npx, int npy, const double box[4], const double* pos,
+               int64_t ns, double* out, cudaStream_t s);
 // a pair of recorded events bracketing work on a stream
 std::pair<cudaEvent_t, cudaEvent_t> event_pair_begin(cudaStream_t s);
 void event_pair_end(std::pair<cudaEvent_t, cudaEvent_t>& e, cudaStream_t s);

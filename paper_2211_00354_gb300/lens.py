@@ -38,7 +38,7 @@ EXPORTED = ("lens_fmm_build", "lens_deflect", "lens_deflect_grid", "lens_ipm_map
             "lens_ipm_map_refined",
             "lens_deflect_adjoint", "lens_plan_info_get", "lens_plan_destroy",
             "lens_direct_deflect", "lens_direct_deflect_noalloc", "lens_light_curve",
-            "lens_light_curve_grad",
+            "lens_light_curve_grad", "lens_map_source", "lens_map_histogram", "lens_map_track",
             "lens_last_error", "lens_version")
 
 
@@ -143,6 +143,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lens_direct_deflect.restype = st
     lib.lens_direct_deflect_noalloc.argtypes = [vp, vp, i64, d, d, vp, i64, vp, vp, vp]
     lib.lens_direct_deflect_noalloc.restype = st
+    lib.lens_map_source.argtypes = [vp, i, i, d, d, vp, ctypes.POINTER(lens_allocator), vp]
+    lib.lens_map_source.restype = st
+    lib.lens_map_histogram.argtypes = [vp, i64, d, d, i, i, vp, vp]
+    lib.lens_map_histogram.restype = st
+    lib.lens_map_track.argtypes = [vp, i, i, ctypes.POINTER(lens_box), vp, i64, vp, vp]
+    lib.lens_map_track.restype = st
     lib.lens_light_curve.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp]
     lib.lens_light_curve.restype = st
     lib.lens_light_curve_grad.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp, vp, vp]
@@ -357,6 +363,39 @@ def direct_deflect_noalloc(stars, masses, kappa_s, gamma, rays, jacobian=False, 
                                            jac.data_ptr() if jacobian else None,
                                            _stream_ptr(stream)))
     return (y, jac) if jacobian else y
+
+
+def map_source(mp, sigma_px, trunc=6.0, stream=None):
+    """The map seen by a Gaussian source of sigma_px pixels (lens_map_source)."""
+    lib = load()
+    mp = _dev(mp, "map")
+    out = torch.empty_like(mp)
+    _check(lib.lens_map_source(mp.data_ptr(), mp.shape[1], mp.shape[0], float(sigma_px),
+                               float(trunc), out.data_ptr(), None, _stream_ptr(stream)))
+    return out
+
+
+def map_histogram(values, lo, hi, nbins, log_bins=False, stream=None):
+    """counts[0] below lo, counts[1..nbins] the bins, counts[nbins+1] above
+    (lens_map_histogram)."""
+    lib = load()
+    v = _dev(values, "values").reshape(-1)
+    counts = torch.empty((nbins + 2,), dtype=torch.int64, device=v.device)
+    _check(lib.lens_map_histogram(v.data_ptr(), v.shape[0], float(lo), float(hi), int(nbins),
+                                  int(bool(log_bins)), counts.data_ptr(), _stream_ptr(stream)))
+    return counts
+
+
+def map_track(mp, box, positions, stream=None):
+    """The map at source positions (k x 2), bilinear (lens_map_track)."""
+    lib = load()
+    mp = _dev(mp, "map")
+    pos = _dev(positions, "positions", 2)
+    out = torch.empty((pos.shape[0],), dtype=torch.float64, device=mp.device)
+    b = lens_box(*(float(v) for v in box))
+    _check(lib.lens_map_track(mp.data_ptr(), mp.shape[1], mp.shape[0], ctypes.byref(b),
+                              pos.data_ptr(), pos.shape[0], out.data_ptr(), _stream_ptr(stream)))
+    return out
 
 
 def light_curve(y, w_ray, samples, sigma, trunc=6.0, stream=None):
