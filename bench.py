@@ -34,7 +34,7 @@ sys.path.insert(0, HERE)
 METRIC = "FMM rays deflected/s at stated error vs GPU direct sum; IPM map time (1xGB300)"
 UNIT = "rays/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-FP64_PEAK_TFLOPS = 1.18                           # measured DFMA probe
+FP64_PEAK_TFLOPS = 1.18                           # measured DFMA micro-benchmark on this GPU
 
 
 def parse():
