@@ -75,13 +75,21 @@ __global__ void k_bin_offsets(const int* __restrict__ bins, int leaf_size, int* 
   offs[0] = acc;
 }
 
+// P2M: a_k = sum_j m_j w_j^k, w_j = (z_j - c)/r, into shared-memory
+// accumulators [(p+1)][blockDim.x].  V = double2, or float2 for a float32-bulk
+// plan: there the multipoles only feed far-field terms evaluated to float32
+// accuracy, P2M is not one of the translations kept in float64, and the
+// float64 pipe (~60x slower) would otherwise hold the upward pass on the
+// build's critical path; w_j is formed in float64 and rounded once.
+template <typename V>
 __global__ void k_p2m(const double2* __restrict__ spos, const double* __restrict__ smass,
                       const int* __restrict__ start, const int* __restrict__ count,
                       const int* __restrict__ level, const int* __restrict__ ix,
                       const int* __restrict__ iy, const int* __restrict__ list,
                       const int* __restrict__ total, double lo_x, double lo_y, double root_size,
                       int p, double2* __restrict__ M) {
-  extern __shared__ double2 acc[];  // [(p+1)][blockDim.x]
+  extern __shared__ unsigned char acc_raw[];
+  V* acc = reinterpret_cast<V*>(acc_raw);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= *total) return;
   const int64_t b = list[i];
@@ -90,21 +98,24 @@ __global__ void k_p2m(const double2* __restrict__ spos, const double* __restrict
   const double r = root_size / (double)(2ull << level[b]);
   const double cx = lo_x + (2.0 * ix[b] + 1.0) * r, cy = lo_y + (2.0 * iy[b] + 1.0) * r;
   const double ir = 1.0 / r;
-  double2* a = acc + threadIdx.x;
+  V* a = acc + threadIdx.x;
   const int st = blockDim.x;
-  for (int k = 0; k <= p; ++k) a[k * st] = make_double2(0.0, 0.0);
+  V zero;
+  zero.x = 0; zero.y = 0;
+  for (int k = 0; k <= p; ++k) a[k * st] = zero;
   const int s0 = start[b];
   for (int j = 0; j < nst; ++j) {
     const double2 z = spos[s0 + j];
     const double m = smass[s0 + j];
-    const double2 w = make_double2((z.x - cx) * ir, (z.y - cy) * ir);
-    double2 pw = make_double2(m, 0.0);
+    V w, pw;
+    w.x = (z.x - cx) * ir; w.y = (z.y - cy) * ir;
+    pw.x = m; pw.y = 0;
     for (int k = 0; k <= p; ++k) {
       a[k * st] = a[k * st] + pw;
       pw = cmul(pw, w);
     }
   }
-  for (int k = 0; k <= p; ++k) out[k] = a[k * st];
+  for (int k = 0; k <= p; ++k) out[k] = make_double2(a[k * st].x, a[k * st].y);
 }
 
 // ---- M2M: one thread per (internal box, coefficient) of a level -------------
@@ -468,13 +479,23 @@ void fmm_p2m(Plan& P, cudaStream_t s) {
                                                       list, P.M);
   LENS_LAUNCHED("k_leaf_bins<place>");
   const int tpb = 32;
-  const size_t smem = sizeof(double2) * (size_t)P1 * tpb;
-  if (smem > 48 * 1024)
-    LENS_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_p2m<<<grid_for(P.nb, tpb), tpb, smem, s>>>(P.spos, P.smass, P.box_start, P.box_count,
-                                                P.box_level, P.box_ix, P.box_iy, list,
-                                                offs, P.root_lo[0], P.root_lo[1], P.root_size,
-                                                p, P.M);
+  if (P.prec == LENS_FP32_BULK) {
+    const size_t smem = sizeof(float2) * (size_t)P1 * tpb;
+    if (smem > 48 * 1024)
+      LENS_CUDA(cudaFuncSetAttribute(k_p2m<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    k_p2m<float2><<<grid_for(P.nb, tpb), tpb, smem, s>>>(
+        P.spos, P.smass, P.box_start, P.box_count, P.box_level, P.box_ix, P.box_iy, list, offs,
+        P.root_lo[0], P.root_lo[1], P.root_size, p, P.M);
+  } else {
+    const size_t smem = sizeof(double2) * (size_t)P1 * tpb;
+    if (smem > 48 * 1024)
+      LENS_CUDA(cudaFuncSetAttribute(k_p2m<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    k_p2m<double2><<<grid_for(P.nb, tpb), tpb, smem, s>>>(
+        P.spos, P.smass, P.box_start, P.box_count, P.box_level, P.box_ix, P.box_iy, list, offs,
+        P.root_lo[0], P.root_lo[1], P.root_size, p, P.M);
+  }
   LENS_LAUNCHED("k_p2m");
 }
 
