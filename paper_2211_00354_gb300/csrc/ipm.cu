@@ -32,17 +32,24 @@ constexpr int kIpmThreads = 256;
 constexpr int kChunksPerGrab = 8;  // 32-cell chunks per fetch of the chunk counter
 constexpr int kFar = 0x7fffffff;
 
-// Mean of clamp(g, 0, 1) for g running linearly from a to b, without
-// branches (the lanes of a warp take different cases): the integral of the
-// clamp over [lo, hi] divided by the length; a vanishing length (a vertical
-// edge) takes the clamped midpoint.  All-below-0 gives exactly 0; the other
-// pure cases are within an ulp.
-__device__ __forceinline__ float mean_clamp01f(float a, float b) {
-  const float lo = fminf(a, b), hi = fmaxf(a, b);
-  const float l0 = fmaxf(lo, 0.f), h1 = fminf(hi, 1.f);
-  const float I = 0.5f * fmaxf(h1 - l0, 0.f) * (h1 + l0) + fmaxf(hi - fmaxf(lo, 1.f), 0.f);
-  const float d = hi - lo;
-  return d > 1e-30f ? I * frcp_fast(d) : fminf(fmaxf(0.5f * (lo + hi), 0.f), 1.f);
+// Twice the mean of clamp(g, 0, 1) for g running linearly from a to b,
+// without branches or ordering (the lanes of a warp take different cases):
+// 2 (F(b) - F(a)) / (b - a) with F(t) = c^2 / 2 + max(t - 1, 0), c = clamp(t,
+// 0, 1), the antiderivative of the clamp.  The difference of squares is
+// taken as (c_b - c_a)(c_b + c_a), which keeps its relative precision when
+// a and b are close, and max(t - 1, 0) as 2^31 clamp((t - 1) 2^-31, 0, 1),
+// exact for t - 1 < 2^31 (pixel-local coordinates are below 2^31): every
+// clamp is then a saturating add or fma.  A vanishing b - a (a vertical
+// edge) takes twice the clamped midpoint.  All-below-0 gives exactly 0; the
+// other pure cases are within an ulp or two.
+__device__ __forceinline__ float mean2_clamp01f(float a, float b) {
+  constexpr float kS = 4.656612873077393e-10f;  // 2^-31
+  const float ca = __saturatef(a), cb = __saturatef(b);
+  const float sa = __saturatef(fmaf(a, kS, -kS)), sb = __saturatef(fmaf(b, kS, -kS));
+  const float sc = ca + cb;
+  const float num = fmaf(cb - ca, sc, (sb - sa) * 4294967296.0f);
+  const float d = b - a;
+  return fabsf(d) > 1e-30f ? num * frcp_fast(d) : sc;
 }
 
 // Signed (winding-weighted) area of the quadrilateral q inside the unit pixel
@@ -52,17 +59,27 @@ __device__ __forceinline__ float mean_clamp01f(float a, float b) {
 // giving (y_b - y_a) * mean(g) over the edge's part inside the band.  The
 // edge slopes dx/dy are given (0 for a horizontal edge, whose clipped part
 // then has ya == yb and adds nothing).
+//
+// In band-local heights w = y - Y and v = clamp(w, 0, 1) (the clipped
+// height), an edge from vertex e to f runs inside the band from v_e to v_f,
+// at x - X = (x_e - X) + (v - w_e) dx/dy.
 __device__ __forceinline__ float pixel_area_f(const float* qx, const float* qy, const float* sl,
                                               float X, float Y) {
+  float w[4], v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    w[k] = qy[k] - Y;
+    v[k] = __saturatef(w[k]);
+  }
   float s = 0.f;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    const float x0 = qx[e], y0 = qy[e], y1 = qy[(e + 1) & 3];
-    const float ya = fminf(fmaxf(y0, Y), Y + 1.f), yb = fminf(fmaxf(y1, Y), Y + 1.f);
-    const float xa = x0 + (ya - y0) * sl[e], xb = x0 + (yb - y0) * sl[e];
-    s += (yb - ya) * mean_clamp01f(xa - X, xb - X);
+    const int f = (e + 1) & 3;
+    const float x0 = qx[e] - X;
+    const float ta = fmaf(v[e] - w[e], sl[e], x0), tb = fmaf(v[f] - w[e], sl[e], x0);
+    s = fmaf(v[f] - v[e], mean2_clamp01f(ta, tb), s);
   }
-  return s;
+  return 0.5f * s;
 }
 
 struct IpmArgs {
@@ -190,11 +207,12 @@ struct CellShared {
   float4 qx[kWarps][32], qy[kWarps][32];  // polygon, pixel units local to (ix0, iy0)
   float4 sl[kWarps][32];                  // edge slopes dx/dy (0 if horizontal)
   int4 box[kWarps][32];                   // ix0, iy0, cx0, cy0 (box clipped to the map at cx0, cy0)
-  int2 ext[kWarps][32];                   // clipped box width, 1 / A_P (float bits)
+  int2 ext[kWarps][32];                   // clipped box width (+ whole-box flag and height
+                                          // of a small cell), 1 / A_P (float bits)
   int cum[kWarps][32], cum2[kWarps][32];
   // owner lane of each (cell, pixel) task of the small cells (<= 32 x 16)
   unsigned char own[kWarps][32 * kSmallBox * kSmallBox];
-  float4 seg[kWarps][128];                // crossing segments: xa, xb, dy, first pixel (int bits)
+  float4 seg[kWarps][128];                // crossing segments: xa, xb, dy / 2, first pixel (int bits)
   int4 sst[kWarps][32];                   // starts of a row task's segments 1..3 in its pixel list
   int2 rbi[kWarps][32];                   // row task: map offset of (row, box x0), 1 / A_P (float bits)
 };
@@ -208,7 +226,8 @@ __device__ __forceinline__ void unpack4(float (&a)[4], const float4 v) {
 //     dropped or outside, single-pixel cells (fraction 1), hand-off of
 //     ill-conditioned cells to the float-float queue;
 //  B. small cells (box <= 4 x 4): the warp's (cell, pixel) pairs spread over
-//     the lanes, one Green's-theorem overlap each;
+//     the lanes, one Green's-theorem overlap each (a box inside the map skips
+//     its last pixel, which takes the remainder of the cell);
 //  C. large cells: the warp's (cell, row) pairs spread over the lanes; in the
 //     band Y <= y <= Y+1 an edge whose clipped part runs (xa,ya)->(xb,yb)
 //     adds dy = yb - ya to each pixel X with X + 1 <= min(xa, xb): that
@@ -304,12 +323,26 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
           sh.qy[w][lane] = make_float4(qy[0], qy[1], qy[2], qy[3]);
           sh.sl[w][lane] = make_float4(slk[0], slk[1], slk[2], slk[3]);
           sh.box[w][lane] = make_int4(ix0, iy0, cx0, cy0);
+          const bool smallc = ix1 - ix0 < kSmallBox && iy1 - iy0 < kSmallBox;
+          // A small cell whose pixel box lies inside the map puts all of its
+          // area there: its fractions sum to 1 (winding-weighted areas add up
+          // to the signed area), so the last pixel of the box is not
+          // evaluated and takes 1 minus the others (added whole here, each
+          // other pixel's fraction subtracted from it in B).
+          const bool whole = smallc && cx0 == ix0 && cy0 == iy0 && cx1 == ix1 && cy1 == iy1;
           // |A_loc| > 0: the cell is well conditioned
-          sh.ext[w][lane] = make_int2(cx1 - cx0 + 1, __float_as_int(frcp_fast(A_loc)));
-          // every fraction that lands in the map is moved from fout to fin
-          led.fout += 1.f;
-          if (ix1 - ix0 < kSmallBox && iy1 - iy0 < kSmallBox) {
-            nsmall = (cx1 - cx0 + 1) * (cy1 - cy0 + 1);
+          sh.ext[w][lane] = make_int2((cx1 - cx0 + 1) | (whole ? (cy1 - cy0 + 1) << 3 : 0),
+                                      __float_as_int(frcp_fast(A_loc)));
+          if (whole) {
+            atomicAdd(&A.map[(int64_t)cy1 * npx + cx1], A.scale_f);
+            led.fin += 1.f;
+            led.nupd += 1;
+          } else {
+            // every fraction that lands in the map is moved from fout to fin
+            led.fout += 1.f;
+          }
+          if (smallc) {
+            nsmall = (cx1 - cx0 + 1) * (cy1 - cy0 + 1) - (whole ? 1 : 0);
           } else {
             nrows = cy1 - cy0 + 1;
             led.nq += 1;
@@ -341,7 +374,7 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
         const int off = f - (L ? sh.cum[w][L - 1] : 0);
         const int4 bx = sh.box[w][L];
         const int2 ex = sh.ext[w][L];
-        const int wd = ex.x;
+        const int wd = ex.x & 7, hg = ex.x >> 3;  // hg > 0: a whole-box cell of hg rows
         // off < 16 and wd <= 4: off / wd without a division
         const int r = wd == 3 ? (off * 21846) >> 16 : off >> (wd >> 1);
         const int px = bx.z + off - r * wd, py = bx.w + r;
@@ -353,9 +386,15 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
         if (a != 0.0f) {
           const float fr = a * __int_as_float(ex.y);
           atomicAdd(&A.map[(int64_t)py * npx + px], A.scale_f * fr);
-          led.fin += fr;
-          led.fout -= fr;
           led.nupd += 1;
+          if (hg) {
+            // inside the map: npx * npy < 2^31, the offset fits an int
+            atomicAdd(&A.map[(bx.w + hg - 1) * npx + bx.z + wd - 1], -A.scale_f * fr);
+            led.nupd += 1;
+          } else {
+            led.fin += fr;
+            led.fout -= fr;
+          }
         }
       }
     }
@@ -409,7 +448,7 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
             const int pa = max(Xa, lx0), pb = min(Xb, lx1);
             if (pb >= pa) {
               n = pb - pa + 1;
-              sh.seg[w][t] = make_float4(xa, xb, dy, __int_as_float(pa));
+              sh.seg[w][t] = make_float4(xa, xb, 0.5f * dy, __int_as_float(pa));
             }
           }
           cnt += n;
@@ -437,7 +476,7 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
           off -= k == 0 ? 0 : k == 1 ? ss.x : k == 2 ? ss.y : ss.z;
           const float4 sg = sh.seg[w][L * 4 + k];
           const int X = __float_as_int(sg.w) + off;
-          const float a = sg.z * mean_clamp01f(sg.x - (float)X, sg.y - (float)X);
+          const float a = sg.z * mean2_clamp01f(sg.x - (float)X, sg.y - (float)X);
           if (a != 0.0f) {
             const int2 rb = sh.rbi[w][L];
             const float fr = a * __int_as_float(rb.y);
