@@ -388,9 +388,9 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
           atomicAdd(&A.map[(int64_t)py * npx + px], A.scale_f * fr);
           led.nupd += 1;
           if (hg) {
-            // inside the map: npx * npy < 2^31, the offset fits an int
+            // inside the map: npx * npy < 2^31, the offset fits an int (the
+            // remainder's correction, not counted as a map increment)
             atomicAdd(&A.map[(bx.w + hg - 1) * npx + bx.z + wd - 1], -A.scale_f * fr);
-            led.nupd += 1;
           } else {
             led.fin += fr;
             led.fout -= fr;
