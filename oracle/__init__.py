@@ -16,6 +16,10 @@ Routines (all plain definitions; see the header of ``lens_oracle.c``):
 * :func:`adjoint` -- gradient through Eq. 1 from its real-variable derivatives.
 * :func:`light_curve`, :func:`light_curve_grad` -- Gaussian-source light
   curve as a ray sum (light curves: Sec. 3.3; Gaussian source: Sec. 2.5).
+* :func:`find_images`, :func:`source_image` (``images.py``) -- images of a
+  point source as the grid cells whose deflected quadrilateral winds around
+  it, located by inverting the cell's bilinear map, and the lensed image of
+  a Gaussian source (Sec. 2.5).
 
 Parity unpinned: none -- every routine has closed-form or brute-force pins in
 ``tests/test_oracle_*.py``.
@@ -27,6 +31,8 @@ import os
 import subprocess
 
 import numpy as np
+
+from .images import find_images, source_image, winding_numbers  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lens_oracle.c")
