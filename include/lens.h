@@ -305,6 +305,41 @@ lens_status lens_map_track(const double* map, int npx, int npy,
                            const lens_box* box, const double* positions,
                            int64_t ns, double* out, void* stream);
 
+/* ---- images on a deflected ray grid (Sec. 2.5: the images of a background
+ * Gaussian source behind a simulated halo, from a regular grid of deflected
+ * rays).  y: dev (ny+1) x (nx+1) x 2, the corner positions in the source
+ * plane as lens_deflect_grid writes them for `grid`. */
+
+/* Images of the point source (beta1, beta2).  Cell (i, j) is an image cell
+ * when beta lies in the bounding box of its deflected corners and their
+ * closed polygon (i,j) -> (i+1,j) -> (i+1,j+1) -> (i,j+1) winds around it:
+ * an edge a -> b adds +1 when a_2 <= beta_2 < b_2 and beta is left of it, -1
+ * when b_2 <= beta_2 < a_2 and beta is right of it, the orientation
+ * (b - a) x (beta - a) taken in rounded float64 without contraction (a
+ * source on an edge shared by two cells is claimed by one of them, the same
+ * one on any machine).  In an image cell the bilinear interpolation of the
+ * corners is inverted by 20 Newton steps from the cell centre (cell
+ * coordinates kept within [-1, 2]): the image is that point, its signed
+ * magnification h^2 / det J of the bilinear map there (INFINITY if det J
+ * is 0).  A cell holding a point mass reports that mass's infinitely
+ * demagnified image (|mu| ~ 0).
+ * out: dev max_out x 3 (x1, x2, mu); cells: dev int64 max_out (j * nx + i);
+ * both in no particular order and may be NULL when max_out is 0.
+ * n_found: host, the number of image cells; entries past max_out are not
+ * written (call again with a larger buffer).  Scratch from the library's
+ * pool.  Synchronises `stream`. */
+lens_status lens_find_images(const double* y, const lens_grid* grid,
+                             double beta1, double beta2, int64_t max_out,
+                             double* out, int64_t* cells, int64_t* n_found,
+                             void* stream);
+
+/* The lensed image of a Gaussian source: out[r] = exp(-|y_r - beta|^2 /
+ * (2 sigma^2)), the source's peak-normalised surface brightness at each of m
+ * rays (dev m x 2); out: dev m. */
+lens_status lens_source_image(const double* y, int64_t m, double beta1,
+                              double beta2, double sigma, double* out,
+                              void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* lens_last_error(void);
 

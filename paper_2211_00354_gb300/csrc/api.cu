@@ -627,4 +627,33 @@ lens_status lens_map_track(const double* map, int npx, int npy, const lens_box* 
   LENS_API_END
 }
 
+lens_status lens_find_images(const double* y, const lens_grid* grid, double beta1, double beta2,
+                             int64_t max_out, double* out, int64_t* cells, int64_t* n_found,
+                             void* stream) {
+  LENS_API_BEGIN
+  need(y && grid && n_found, "NULL buffer");
+  need(max_out >= 0 && (max_out == 0 || (out && cells)), "max_out must be >= 0 with buffers");
+  need(grid->nx >= 1 && grid->ny >= 1 && grid->nx < (1ll << 31) && grid->ny < (1ll << 31),
+       "grid must have 1 <= nx, ny < 2^31");
+  need(std::isfinite(grid->x0) && std::isfinite(grid->y0) && std::isfinite(grid->h) && grid->h > 0,
+       "grid origin and spacing must be finite with h > 0");
+  need(std::isfinite(beta1) && std::isfinite(beta2), "beta must be finite");
+  DeviceAlloc da;
+  da.stream = S(stream);
+  *n_found = find_images(y, grid->nx, grid->ny, grid->x0, grid->y0, grid->h, beta1, beta2, max_out,
+                         out, cells, da, S(stream));
+  LENS_API_END
+}
+
+lens_status lens_source_image(const double* y, int64_t m, double beta1, double beta2, double sigma,
+                              double* out, void* stream) {
+  LENS_API_BEGIN
+  need(m >= 0, "m must be >= 0");
+  need(m == 0 || (y && out), "NULL buffer");
+  need(std::isfinite(beta1) && std::isfinite(beta2), "beta must be finite");
+  need(std::isfinite(sigma) && sigma > 0, "sigma must be finite and > 0");
+  source_image(y, m, beta1, beta2, sigma, out, S(stream));
+  LENS_API_END
+}
+
 }  // extern "C"

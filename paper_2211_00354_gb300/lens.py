@@ -39,6 +39,7 @@ EXPORTED = ("lens_fmm_build", "lens_deflect", "lens_deflect_grid", "lens_ipm_map
             "lens_deflect_adjoint", "lens_plan_info_get", "lens_plan_destroy",
             "lens_direct_deflect", "lens_direct_deflect_noalloc", "lens_light_curve",
             "lens_light_curve_grad", "lens_map_source", "lens_map_histogram", "lens_map_track",
+            "lens_find_images", "lens_source_image",
             "lens_last_error", "lens_version")
 
 
@@ -149,6 +150,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lens_map_histogram.restype = st
     lib.lens_map_track.argtypes = [vp, i, i, ctypes.POINTER(lens_box), vp, i64, vp, vp]
     lib.lens_map_track.restype = st
+    lib.lens_find_images.argtypes = [vp, ctypes.POINTER(lens_grid), d, d, i64, vp, vp,
+                                     ctypes.POINTER(ctypes.c_int64), vp]
+    lib.lens_find_images.restype = st
+    lib.lens_source_image.argtypes = [vp, i64, d, d, d, vp, vp]
+    lib.lens_source_image.restype = st
     lib.lens_light_curve.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp]
     lib.lens_light_curve.restype = st
     lib.lens_light_curve_grad.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp, vp, vp]
@@ -396,6 +402,41 @@ def map_track(mp, box, positions, stream=None):
     _check(lib.lens_map_track(mp.data_ptr(), mp.shape[1], mp.shape[0], ctypes.byref(b),
                               pos.data_ptr(), pos.shape[0], out.data_ptr(), _stream_ptr(stream)))
     return out
+
+
+def find_images(y, grid, beta, max_out=64, stream=None):
+    """Images of the point source beta on a deflected grid (lens_find_images):
+    y (ny+1, nx+1, 2) as deflect_grid returns it.  Returns (cells int64 [k],
+    images float64 [k, 3] = x1, x2, signed magnification), sorted by cell."""
+    lib = load()
+    y = _dev(y.reshape(-1, 2), "y", 2)
+    if y.shape[0] != (grid.nx + 1) * (grid.ny + 1):
+        raise ValueError("y must hold the (nx+1) x (ny+1) corners of the grid")
+    g = grid_struct(grid)
+    while True:
+        out = torch.empty((max(max_out, 1), 3), dtype=torch.float64, device=y.device)
+        cells = torch.empty((max(max_out, 1),), dtype=torch.int64, device=y.device)
+        n = ctypes.c_int64(0)
+        _check(lib.lens_find_images(y.data_ptr(), ctypes.byref(g), float(beta[0]), float(beta[1]),
+                                    max_out, out.data_ptr(), cells.data_ptr(), ctypes.byref(n),
+                                    _stream_ptr(stream)))
+        if n.value <= max_out:
+            break
+        max_out = n.value
+    cells, out = cells[:n.value], out[:n.value]
+    order = torch.argsort(cells)
+    return cells[order], out[order]
+
+
+def source_image(y, beta, sigma, stream=None):
+    """exp(-|y - beta|^2 / 2 sigma^2) at every ray (lens_source_image)."""
+    lib = load()
+    shape = y.shape[:-1]
+    y = _dev(y.reshape(-1, 2), "y", 2)
+    out = torch.empty((y.shape[0],), dtype=torch.float64, device=y.device)
+    _check(lib.lens_source_image(y.data_ptr(), y.shape[0], float(beta[0]), float(beta[1]),
+                                 float(sigma), out.data_ptr(), _stream_ptr(stream)))
+    return out.reshape(shape)
 
 
 def light_curve(y, w_ray, samples, sigma, trunc=6.0, stream=None):
