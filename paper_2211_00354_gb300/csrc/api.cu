@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "lens_internal.h"
+#include "images.h"
 
 namespace lens {
 

@@ -16,7 +16,7 @@
 //  * source_image: exp(-|y - beta|^2 / 2 sigma^2) per ray (lensing keeps
 //    surface brightness).
 #include "cx.cuh"
-#include "lens_internal.h"
+#include "images.h"
 
 namespace lens {
 namespace {

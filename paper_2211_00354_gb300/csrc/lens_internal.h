@@ -315,12 +315,6 @@ void map_histogram(const double* v, int64_t n, double lo, double hi, int nbins, 
                    int64_t* counts, cudaStream_t s);
 void map_track(const double* map, int npx, int npy, const double box[4], const double* pos,
                int64_t ns, double* out, cudaStream_t s);
-// images of a point source, lensed Gaussian source (images.cu)
-int64_t find_images(const double* y, int64_t nx, int64_t ny, double x0, double y0, double h,
-                    double b1, double b2, int64_t max_out, double* out, int64_t* cells,
-                    DeviceAlloc& da, cudaStream_t s);
-void source_image(const double* y, int64_t m, double b1, double b2, double sigma, double* out,
-                  cudaStream_t s);
 // a pair of recorded events bracketing work on a stream
 std::pair<cudaEvent_t, cudaEvent_t> event_pair_begin(cudaStream_t s);
 void event_pair_end(std::pair<cudaEvent_t, cudaEvent_t>& e, cudaStream_t s);
