@@ -20,6 +20,8 @@ Routines (all plain definitions; see the header of ``lens_oracle.c``):
   point source as the grid cells whose deflected quadrilateral winds around
   it, located by inverting the cell's bilinear map, and the lensed image of
   a Gaussian source (Sec. 2.5).
+* :func:`potential` (``potential.py``) -- the lensing potential
+  sum m ln|x - x_i| + smooth field, by direct sum (Sec. 2.5).
 
 Parity unpinned: none -- every routine has closed-form or brute-force pins in
 ``tests/test_oracle_*.py``.
@@ -33,6 +35,7 @@ import subprocess
 import numpy as np
 
 from .images import find_images, source_image, winding_numbers  # noqa: F401
+from .potential import potential  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lens_oracle.c")
