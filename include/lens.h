@@ -169,6 +169,19 @@ lens_status lens_deflect(lens_plan* plan, const double* rays_xy, int64_t m,
  * 0 <= row0, row0 + nrows <= ny + 1), all columns 0..nx.
  *   y_out: dev nrows x (nx+1) x 2 (row-major); jac_out: dev
  *   nrows x (nx+1) x 4 or NULL.  No ray array is materialised. */
+/* Lensing potential psi(x) = sum_i m_i ln|x - x_i| + kappa_s |x|^2 / 2 +
+ * gamma (x1^2 - x2^2) / 2 at m rays (dev m x 2, inside the plan's target
+ * region), whose gradient is x - y of Eq. 1 (the potential of the
+ * cosmological-lens example, Sec. 2.5).  Through the plan's expansions: the
+ * field's multipole and local coefficients integrated once (Appendix A's
+ * expansions of the complex logarithm) plus one real constant per box,
+ * float64 throughout whatever the plan's precision (a float32-bulk plan's
+ * multipoles carry float32 P2M sums).  A star exactly at a ray contributes
+ * nothing.  psi_out: dev m.  Synchronises `stream`.  LENS_EDOMAIN for a
+ * ray outside the target region or not finite. */
+lens_status lens_potential(lens_plan* plan, const double* rays_xy, int64_t m,
+                           double* psi_out, void* stream);
+
 lens_status lens_deflect_grid(lens_plan* plan, const lens_grid* grid,
                               int64_t row0, int64_t nrows, double* y_out,
                               double* jac_out, void* stream);

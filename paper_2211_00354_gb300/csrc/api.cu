@@ -17,6 +17,7 @@
 
 #include "lens_internal.h"
 #include "images.h"
+#include "potential.h"
 
 namespace lens {
 
@@ -322,6 +323,19 @@ lens_status lens_deflect(lens_plan* plan, const double* rays_xy, int64_t m, doub
   Plan& P = plan->P;
   P.da.stream = S(stream);
   evaluate_rays(P, rays_xy, m, y_out, jac_out, S(stream));
+  LENS_API_END
+}
+
+lens_status lens_potential(lens_plan* plan, const double* rays_xy, int64_t m, double* psi_out,
+                           void* stream) {
+  LENS_API_BEGIN
+  need(plan != nullptr, "plan is NULL");
+  need(m >= 0, "m must be >= 0");
+  if (m == 0) return LENS_OK;
+  need(rays_xy && psi_out, "rays or psi_out is NULL");
+  Plan& P = plan->P;
+  P.da.stream = S(stream);
+  evaluate_potential(P, rays_xy, m, psi_out, S(stream));
   LENS_API_END
 }
 

@@ -39,7 +39,7 @@ EXPORTED = ("lens_fmm_build", "lens_deflect", "lens_deflect_grid", "lens_ipm_map
             "lens_deflect_adjoint", "lens_plan_info_get", "lens_plan_destroy",
             "lens_direct_deflect", "lens_direct_deflect_noalloc", "lens_light_curve",
             "lens_light_curve_grad", "lens_map_source", "lens_map_histogram", "lens_map_track",
-            "lens_find_images", "lens_source_image",
+            "lens_find_images", "lens_source_image", "lens_potential",
             "lens_last_error", "lens_version")
 
 
@@ -155,6 +155,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lens_find_images.restype = st
     lib.lens_source_image.argtypes = [vp, i64, d, d, d, vp, vp]
     lib.lens_source_image.restype = st
+    lib.lens_potential.argtypes = [vp, vp, i64, vp, vp]
+    lib.lens_potential.restype = st
     lib.lens_light_curve.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp]
     lib.lens_light_curve.restype = st
     lib.lens_light_curve_grad.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp, vp, vp]
@@ -284,6 +286,14 @@ class LensFMM:
         _check(_lib.lens_deflect(self._handle, rays.data_ptr(), m, y.data_ptr(),
                                  jac.data_ptr() if jacobian else None, _stream_ptr(stream)))
         return (y, jac) if jacobian else y
+
+    def potential(self, rays: torch.Tensor, stream=None):
+        """Lensing potential psi at rays (m x 2) (lens_potential)."""
+        rays = _dev(rays, "rays", 2)
+        psi = torch.empty((rays.shape[0],), dtype=torch.float64, device=rays.device)
+        _check(_lib.lens_potential(self._handle, rays.data_ptr(), rays.shape[0], psi.data_ptr(),
+                                   _stream_ptr(stream)))
+        return psi
 
     def deflect_grid(self, grid, row0: int = 0, nrows: Optional[int] = None,
                      jacobian: bool = False, stream=None):
