@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--next-rows", action="store_true",
+                    help="also time image finding, the lensed Gaussian source, the lensing "
+                         "potential and the map consumers on this workload")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -197,6 +200,61 @@ def measured_traffic(kernel, src, rays_per_launch):
         with open(os.path.join(HERE, "paper_2211_00354_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return per * rays_per_launch if h.hexdigest() == sha else None
+
+
+def next_rows(args, f, g, stars, masses, prec, target, mp, hbm_peak):
+    """Device times (CUDA events on the current stream, after one warm-up
+    call) of the calls built on top of the map path, on the same workload:
+    image finding and the lensed Gaussian source on the whole deflected
+    grid (float64 corners, (nx+1)(ny+1) x 16 B read), the lensing potential
+    at 2^20 rays of the target region, the finite-source map and a
+    log-binned histogram of the map."""
+    import torch
+
+    from paper_2211_00354_gb300 import lens
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    P = lens.LensFMM(stars, masses, f.kappa_s, f.gamma, p=args.p, leaf_size=args.leaf,
+                     prec=prec, target_box=target)
+    y = P.deflect_grid(g)
+    nray = y.shape[0] * y.shape[1]
+    beta = (0.5 * (f.box[0] + f.box[1]) + 0.37, 0.5 * (f.box[2] + f.box[3]) - 0.21)
+    t = timed(lambda: lens.find_images(y, g, beta, max_out=1 << 16))
+    cells, _ = lens.find_images(y, g, beta, max_out=1 << 16)
+    gbs = 16.0 * nray / t / 1e6
+    out["find_images"] = {"ms": t, "cells": g.n_cells, "image_cells": int(cells.shape[0]),
+                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+                                       "unit": "GB/s", "frac": gbs / hbm_peak}}
+    t = timed(lambda: lens.source_image(y, beta, 0.05))
+    gbs = 24.0 * nray / t / 1e6
+    out["source_image"] = {"ms": t, "rays": nray,
+                           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+                                        "unit": "GB/s", "frac": gbs / hbm_peak}}
+    del y
+    gen = torch.Generator().manual_seed(args.seed + 11)
+    u = torch.rand((1 << 20, 2), generator=gen, dtype=torch.float64)
+    xr = torch.stack([target[0] + (target[1] - target[0]) * u[:, 0],
+                      target[2] + (target[3] - target[2]) * u[:, 1]], dim=1).to(stars.device)
+    t = timed(lambda: P.potential(xr), reps=3)
+    out["potential"] = {"ms": t, "rays": 1 << 20, "rays_per_s": (1 << 20) / (t / 1e3)}
+    P.close()
+    t = timed(lambda: lens.map_source(mp, 5.0), reps=3)
+    out["map_source"] = {"ms": t, "sigma_px": 5.0, "npix": [f.npx, f.npy]}
+    t = timed(lambda: lens.map_histogram(mp.reshape(-1), 1e-2, 1e3, 256, log_bins=True))
+    out["map_histogram"] = {"ms": t, "bins": 256, "values": f.npx * f.npy}
+    return out
 
 
 def main():
@@ -415,6 +473,8 @@ def main():
                          "stars, %.1f s" % (m, f.n, dt)}
 
     if rank == 0:
+        if args.next_rows:
+            extra["next_rows"] = next_rows(args, f, g, stars, masses, prec, target, mp, hbm_peak)
         info = infos[-1]
         st = stats[-1]
         mu_mean = float(mp[int(0.05 * f.npy):int(0.95 * f.npy), int(0.05 * f.npx):int(0.95 * f.npx)].mean())

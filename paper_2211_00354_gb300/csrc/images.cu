@@ -12,7 +12,11 @@
 //    corners' bilinear interpolation is inverted by 20 Newton steps from the
 //    cell centre (cell coordinates kept within [-1, 2]); the image is that
 //    point, its signed magnification h^2 / det J of the bilinear map there.
-//    Image cells are few: each takes a slot from one counter.
+//    Image cells are few: each takes a slot from one counter.  The float64
+//    pipe is GB300's slowest, so every cell first passes an integer test on
+//    the high words of its corner coordinates (a key that never decreases
+//    with the value, one unit of slack for -0/+0): only the cells whose
+//    coarse bounding box can hold beta reach the float64 test above.
 //  * source_image: exp(-|y - beta|^2 / 2 sigma^2) per ray (lensing keeps
 //    surface brightness).
 #include "cx.cuh"
@@ -25,6 +29,13 @@ constexpr int kNewtonSteps = 20;
 
 __device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
+// sign, exponent and top 20 mantissa bits of v as an int that never
+// decreases when v increases (-0 sits one below +0)
+__device__ __forceinline__ int okey(double v) {
+  const int h = __double2hiint(v);
+  return h ^ ((h >> 31) & 0x7fffffff);
+}
+
 // (b - a) x (p - a), each product and difference rounded once
 __device__ __forceinline__ double orient(double2 a, double2 b, double px, double py) {
   return __dsub_rn(__dmul_rn(__dsub_rn(b.x, a.x), __dsub_rn(py, a.y)),
@@ -36,10 +47,21 @@ __global__ void k_find_images(const double2* __restrict__ y, int64_t nx, int64_t
                               unsigned long long* __restrict__ count, double* __restrict__ out,
                               int64_t* __restrict__ cells) {
   const int64_t n = nx * ny, W = nx + 1;
+  const bool small = n < (1ll << 32);
+  const int kb1 = okey(b1), kb2 = okey(b2);  // beta finite: no overflow below
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = c / nx, i = c - j * nx;
+    const int64_t j = small ? (int64_t)((uint32_t)c / (uint32_t)nx) : c / nx, i = c - j * nx;
     const double2 q[4] = {y[j * W + i], y[j * W + i + 1], y[(j + 1) * W + i + 1], y[(j + 1) * W + i]};
+    int kx0 = okey(q[0].x), kx1 = kx0, ky0 = okey(q[0].y), ky1 = ky0;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+      const int kx = okey(q[k].x), ky = okey(q[k].y);
+      kx0 = min(kx0, kx); kx1 = max(kx1, kx);
+      ky0 = min(ky0, ky); ky1 = max(ky1, ky);
+    }
+    // necessary for the exact test: x <= b implies okey(x) <= okey(b) + 1
+    if (kx0 > kb1 + 1 || kx1 < kb1 - 1 || ky0 > kb2 + 1 || ky1 < kb2 - 1) continue;
     double xmn = q[0].x, xmx = q[0].x, ymn = q[0].y, ymx = q[0].y;
 #pragma unroll
     for (int k = 1; k < 4; ++k) {
