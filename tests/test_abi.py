@@ -71,6 +71,30 @@ def test_invalid_arguments_rejected_without_gpu(lib):
                                  None) == lens.LENS_EINVAL
 
 
+
+def test_image_and_potential_arguments_rejected_without_gpu(lib):
+    from paper_2211_00354_gb300 import lens
+    L = lens.load()
+    fake = ctypes.c_void_p(0x1000)
+    n = ctypes.c_int64(-1)
+    g = lens.lens_grid(0.0, 0.0, 0.1, 10, 10)
+    assert L.lens_find_images(None, ctypes.byref(g), 0.0, 0.0, 4, fake, fake, ctypes.byref(n),
+                              None) == lens.LENS_EINVAL
+    assert L.lens_find_images(fake, ctypes.byref(g), 0.0, 0.0, -1, fake, fake, ctypes.byref(n),
+                              None) == lens.LENS_EINVAL
+    assert L.lens_find_images(fake, ctypes.byref(g), float("nan"), 0.0, 4, fake, fake,
+                              ctypes.byref(n), None) == lens.LENS_EINVAL
+    bad = lens.lens_grid(0.0, 0.0, 0.0, 10, 10)
+    assert L.lens_find_images(fake, ctypes.byref(bad), 0.0, 0.0, 4, fake, fake, ctypes.byref(n),
+                              None) == lens.LENS_EINVAL
+    assert b"h > 0" in L.lens_last_error()
+    assert n.value == -1  # untouched on failure
+    assert L.lens_source_image(fake, 4, 0.0, 0.0, 0.0, fake, None) == lens.LENS_EINVAL
+    assert L.lens_source_image(fake, -1, 0.0, 0.0, 0.1, fake, None) == lens.LENS_EINVAL
+    assert L.lens_source_image(None, 0, 0.0, 0.0, 0.1, None, None) == lens.LENS_OK  # empty
+    assert L.lens_potential(None, fake, 4, fake, None) == lens.LENS_EINVAL
+
+
 FAULT_CHILD = r"""
 import ctypes, sys
 sys.path.insert(0, %r)
