@@ -184,8 +184,9 @@ def ipm_map_refined(ycorn, x0, y0, h, stars, masses, kappa_s, gamma, box, npx, n
 
 
 def map_convolve_gaussian(mp, sigma_px, trunc=6.0):
-    """The map seen by a Gaussian source of sigma_px pixels (truncated at trunc
-    sigma, renormalised at the map's edges)."""
+    """The map seen by a circular Gaussian source of sigma_px pixels (the
+    profile cut at the isophote |d| = trunc sigma, renormalised to its part
+    inside the map)."""
     lib = _load()
     m, mp_ = _c(mp)
     out = np.empty_like(m)

@@ -53,7 +53,10 @@
  *     |A_P| <= 1e-14 * A_cell are "degenerate" and skipped; cells whose pixel
  *     bounding box lies entirely outside the map go to "outside"; cells whose
  *     pixel bounding box spans more than bbox_cap pixels on a side (cap > 0)
- *     are "dropped"; every category is booked in a flux ledger.
+ *     are "dropped"; every category is booked in a flux ledger;
+ *   - finite source (Sec. 3 histograms of sources of given size): a circular
+ *     Gaussian profile of sigma pixels cut at the isophote |d| = trunc sigma,
+ *     renormalised to its part inside the map.
  *
  * Parity pins for every routine live in tests/test_oracle_*.py.
  */
@@ -489,16 +492,17 @@ void oracle_light_curve_grad(int64_t m, const double* y, double w_ray, int64_t n
  * of finite sources, light curves along source tracks).  The map is npy x npx,
  * row-major, pixel (px, py) centred at (px + 1/2, py + 1/2) in pixel units.
  *
- * Finite source: the map convolved with a Gaussian of sigma_px pixels,
- * truncated at R = floor(trunc sigma) pixels along each axis and renormalised
- * to the part of the kernel inside the map:
+ * Finite source: the map seen by a circular Gaussian source of sigma_px
+ * pixels, the source's profile cut at the isophote |d| = trunc sigma (where
+ * its brightness has fallen to exp(-trunc^2 / 2) of the peak) and
+ * renormalised to the part of the profile that lies inside the map:
  *   out[p] = sum_q w(q - p) map[q] / sum_q w(q - p),  w(d) = exp(-|d|^2 / 2 s^2),
- * q over the map pixels with |qx - px| <= R and |qy - py| <= R.  Plain 2D
- * sum. */
+ * q over the map pixels with |q - p|^2 <= (trunc s)^2.  Plain 2D sum. */
 void oracle_map_convolve_gaussian(int npx, int npy, const double* map, double sigma_px,
                                   double trunc, double* out) {
   const int R = (int)floor(trunc * sigma_px);
   const double inv2s2 = 1.0 / (2.0 * sigma_px * sigma_px);
+  const double cut2 = trunc * trunc * sigma_px * sigma_px;
 #pragma omp parallel for schedule(dynamic, 4)
   for (int py = 0; py < npy; ++py) {
     for (int px = 0; px < npx; ++px) {
@@ -510,6 +514,7 @@ void oracle_map_convolve_gaussian(int npx, int npy, const double* map, double si
           const int qx = px + dx;
           if (qx < 0 || qx >= npx) continue;
           const double d2 = (double)dx * dx + (double)dy * dy;
+          if (d2 > cut2) continue;
           const double w = exp(-d2 * inv2s2);
           nsum_add(&num, w * map[(int64_t)qy * npx + qx]);
           nsum_add(&den, w);
