@@ -67,8 +67,16 @@ typedef struct {
 
 typedef enum {
   LENS_FP64 = 0,      /* every step in float64 */
-  LENS_FP32_BULK = 1  /* P2P / L2P / M2P in float32 with compensated sums;
-                         P2M, M2M, M2L, L2L, P2L and y = x - alpha in float64 */
+  LENS_FP32_BULK = 1  /* P2P / L2P / M2P in float32 with compensated sums,
+                         near-field offsets as float-float (pairs of float32)
+                         from each leaf's centre; P2M accumulated in float32
+                         (each star's scaled offset formed in float64);
+                         M2M, M2L, L2L and P2L in float64.  The lens
+                         equation is the float64 value at the leaf centre
+                         (a c1 - Re b0, b c2 + Im b0) plus the ray's part
+                         a dx - Re f - near formed in float-float (~48-bit
+                         significand): within a few float32 ulps of the
+                         deflection, not float64 */
 } lens_precision;
 
 typedef struct {
@@ -165,10 +173,6 @@ lens_status lens_fmm_build(const double* stars_xy, const double* masses,
 lens_status lens_deflect(lens_plan* plan, const double* rays_xy, int64_t m,
                          double* y_out, double* jac_out, void* stream);
 
-/* Eq. 1 at the corner rays of grid rows row0 .. row0+nrows-1 (corner rows,
- * 0 <= row0, row0 + nrows <= ny + 1), all columns 0..nx.
- *   y_out: dev nrows x (nx+1) x 2 (row-major); jac_out: dev
- *   nrows x (nx+1) x 4 or NULL.  No ray array is materialised. */
 /* Lensing potential psi(x) = sum_i m_i ln|x - x_i| + kappa_s |x|^2 / 2 +
  * gamma (x1^2 - x2^2) / 2 at m rays (dev m x 2, inside the plan's target
  * region), whose gradient is x - y of Eq. 1 (the potential of the
@@ -182,6 +186,10 @@ lens_status lens_deflect(lens_plan* plan, const double* rays_xy, int64_t m,
 lens_status lens_potential(lens_plan* plan, const double* rays_xy, int64_t m,
                            double* psi_out, void* stream);
 
+/* Eq. 1 at the corner rays of grid rows row0 .. row0+nrows-1 (corner rows,
+ * 0 <= row0, row0 + nrows <= ny + 1), all columns 0..nx.
+ *   y_out: dev nrows x (nx+1) x 2 (row-major); jac_out: dev
+ *   nrows x (nx+1) x 4 or NULL.  No ray array is materialised. */
 lens_status lens_deflect_grid(lens_plan* plan, const lens_grid* grid,
                               int64_t row0, int64_t nrows, double* y_out,
                               double* jac_out, void* stream);
@@ -294,11 +302,13 @@ lens_status lens_light_curve_grad(const double* y, int64_t m, double w_ray,
  * finite sources, light curves along source tracks).  map: dev npy x npx,
  * row-major as lens_ipm_map writes it. */
 
-/* The map seen by a Gaussian source of sigma_px pixels: the map convolved with
- * exp(-|d|^2 / 2 sigma^2), truncated at R = floor(trunc sigma_px) pixels along
- * each axis (R <= 1024) and renormalised to the part of the kernel inside the
- * map.  out: dev npy x npx (may not alias map).  Scratch from allocator (may
- * be NULL: the library's pool).  Synchronises `stream`. */
+/* The map seen by a circular Gaussian source of sigma_px pixels (Sec. 3:
+ * magnification of sources of a given size): the map convolved with
+ * exp(-|d|^2 / 2 sigma^2) over the pixel offsets d with |d| <= trunc sigma_px
+ * (the profile cut at an isophote; floor(trunc sigma_px) <= 1024), each output
+ * pixel renormalised to the part of that disk inside the map.  out: dev
+ * npy x npx (may not alias map).  Scratch from allocator (may be NULL: the
+ * library's pool).  Synchronises `stream`. */
 lens_status lens_map_source(const double* map, int npx, int npy, double sigma_px,
                             double trunc, double* out,
                             const lens_allocator* allocator, void* stream);

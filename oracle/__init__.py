@@ -79,6 +79,8 @@ def _load():
                                                ctypes.c_int, _dp, _dp]
         lib.oracle_ipm_map_refined.restype = None
         ci = ctypes.c_int
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = ci
         lib.oracle_map_convolve_gaussian.argtypes = [ci, ci, _dp, d, d, _dp]
         lib.oracle_map_convolve_gaussian.restype = None
         lib.oracle_histogram.argtypes = [i64, _dp, d, d, ci, ci, ctypes.POINTER(i64)]
@@ -93,6 +95,11 @@ def _load():
         lib.oracle_light_curve_grad.restype = None
         _lib = lib
     return _lib
+
+
+def threads() -> int:
+    """Threads the oracle's OpenMP loops run on."""
+    return int(_load().oracle_threads())
 
 
 def _c(a):

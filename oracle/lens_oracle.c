@@ -61,11 +61,24 @@
  * Parity pins for every routine live in tests/test_oracle_*.py.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
 /* ------------------------------------------------------------------------ */
+/* Threads the OpenMP loops of this file use (reported with the timings of
+ * the CPU baseline). */
+int oracle_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* Neumaier-compensated running sum (so the oracle itself is ~1e-15 exact). */
 typedef struct { double s, c; } nsum;
 static inline void nsum_add(nsum* a, double x) {
@@ -86,7 +99,9 @@ void oracle_deflect(int64_t n, const double* stars, const double* masses,
                     double* y_out, double* alpha_out, double* jac_out) {
   const double a = 1.0 - kappa_s - gamma;
   const double b = 1.0 - kappa_s + gamma;
-#pragma omp parallel for schedule(dynamic, 64)
+  /* one ray per scheduling unit: with a million stars a ray is milliseconds
+   * of work, and small samples still spread over every core */
+#pragma omp parallel for schedule(dynamic, 1)
   for (int64_t r = 0; r < m; ++r) {
     const double x1 = rays[2 * r], x2 = rays[2 * r + 1];
     nsum s1 = {0, 0}, s2 = {0, 0};

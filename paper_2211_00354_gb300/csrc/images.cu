@@ -62,13 +62,18 @@ __global__ void k_find_images(const double2* __restrict__ y, int64_t nx, int64_t
     }
     // necessary for the exact test: x <= b implies okey(x) <= okey(b) + 1
     if (kx0 > kb1 + 1 || kx1 < kb1 - 1 || ky0 > kb2 + 1 || ky1 < kb2 - 1) continue;
+    // a NaN corner leaves the bounding box undefined: no image (fmin and
+    // fmax would drop the NaN operand and build the box from the others)
+    bool nan = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) nan |= isnan(q[k].x) | isnan(q[k].y);
+    if (nan) continue;
     double xmn = q[0].x, xmx = q[0].x, ymn = q[0].y, ymx = q[0].y;
 #pragma unroll
     for (int k = 1; k < 4; ++k) {
       xmn = fmin(xmn, q[k].x); xmx = fmax(xmx, q[k].x);
       ymn = fmin(ymn, q[k].y); ymx = fmax(ymx, q[k].y);
     }
-    // NaN corners fail every comparison: no image
     if (!(xmn <= b1 && b1 <= xmx && ymn <= b2 && b2 <= ymx)) continue;
     int w = 0;
 #pragma unroll

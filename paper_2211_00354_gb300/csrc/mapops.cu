@@ -1,10 +1,14 @@
 // mapops.cu -- consumers of a magnification map (Sec. 3: magnification
 // histograms of finite sources, light curves along source tracks).
-//  * finite Gaussian source: the map convolved with a Gaussian truncated at R
-//    pixels along each axis and renormalised to the part of the kernel inside
-//    the map; the window is a rectangle, so numerator and normalisation are
-//    both separable: one pass along rows, one along columns, thread per
-//    output pixel, float64;
+//  * finite Gaussian source: the map seen by a circular Gaussian source of
+//    sigma pixels whose profile is cut at the isophote |d| = trunc sigma,
+//    renormalised to the part of the profile inside the map.  The disk is a
+//    stack of row segments |dx| <= r(dy); the weight exp(-|d|^2 / 2 s^2) is
+//    g(dx) g(dy), so each output pixel sums, per dy >= 0, the two map rows
+//    y + dy and y - dy (added once into shared memory) against g(dx) over
+//    |dx| <= r(dy), folded as g(0) T[x] + sum_k g(k) (T[x+k] + T[x-k]); the
+//    normalisation is the same stack of segments over the all-ones map, a
+//    prefix sum of g per segment.  Block per 256 pixels of a row, float64;
 //  * histogram: equal bins of the value or of log10(value), counts kept per
 //    block in shared memory, then one atomic per bin and block;
 //  * track: the map bilinear between pixel centres at source positions.
@@ -15,38 +19,55 @@ namespace lens {
 namespace {
 
 constexpr int kMaxSourceRadius = 1024;  // pixels
+constexpr int kSourceThreads = 256;
 
-// pass along x: t[p] = sum_{|dx| <= R, in map} w[|dx|] map[p + dx]
-__global__ void k_source_rows(const double* __restrict__ map, int npx, int npy, int R,
-                              const double* __restrict__ w, double* __restrict__ t) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= (int64_t)npx * npy) return;
-  const int py = (int)(i / npx), px = (int)(i - (int64_t)py * npx);
-  const double* row = map + (int64_t)py * npx;
-  const int a = max(px - R, 0), b = min(px + R, npx - 1);
-  double s = 0.0;
-  for (int q = a; q <= b; ++q) s = fma(w[abs(q - px)], row[q], s);
-  t[i] = s;
-}
-
-// pass along y, divided by the in-map kernel weight (a product of the two
-// axes' in-map sums)
-__global__ void k_source_cols(const double* __restrict__ t, int npx, int npy, int R,
-                              const double* __restrict__ w, double* __restrict__ out) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= (int64_t)npx * npy) return;
-  const int py = (int)(i / npx), px = (int)(i - (int64_t)py * npx);
-  const int a = max(py - R, 0), b = min(py + R, npy - 1);
-  double s = 0.0, wy = 0.0;
-  for (int q = a; q <= b; ++q) {
-    const double wq = w[abs(q - py)];
-    s = fma(wq, t[(int64_t)q * npx + px], s);
-    wy += wq;
+// tab: g[0..R] (g[k] = exp(-k^2 / 2 s^2)), G[0..R] (G[k] = g[0] + .. + g[k]),
+// then r[0..R] as ints (r[dy]: largest |dx| with dx^2 + dy^2 <= (trunc s)^2,
+// -1 if none).  Shared memory: g, then the folded row T (256 + 2 R values).
+__global__ void __launch_bounds__(kSourceThreads)
+k_source_disk(const double* __restrict__ map, int npx, int npy, int R,
+              const double* __restrict__ tab, double* __restrict__ out) {
+  extern __shared__ double sm[];
+  double* g = sm;
+  double* T = sm + (R + 1);
+  const double* G = tab + (R + 1);
+  const int* rt = reinterpret_cast<const int*>(tab + 2 * (R + 1));
+  const int t = threadIdx.x;
+  const int blocks_x = (npx + kSourceThreads - 1) / kSourceThreads;
+  const int py = blockIdx.x / blocks_x;
+  const int x0 = (blockIdx.x - py * blocks_x) * kSourceThreads;
+  const int px = x0 + t;
+  for (int k = t; k <= R; k += kSourceThreads) g[k] = tab[k];
+  double num = 0.0, den = 0.0;
+  for (int dy = 0; dy <= R; ++dy) {
+    const int r = rt[dy];
+    const int ya = py + dy, yb = py - dy;
+    const bool ina = ya < npy, inb = dy > 0 && yb >= 0;
+    if (r < 0 || !(ina || inb)) continue;  // uniform over the block
+    __syncthreads();  // the previous segment's readers of T are done
+    const int nt = kSourceThreads + 2 * r;
+    for (int i = t; i < nt; i += kSourceThreads) {
+      const int x = x0 - r + i;
+      double v = 0.0;
+      if (x >= 0 && x < npx) {
+        if (ina) v = map[(int64_t)ya * npx + x];
+        if (inb) v += map[(int64_t)yb * npx + x];
+      }
+      T[i] = v;
+    }
+    __syncthreads();
+    if (px < npx) {
+      const int c = t + r;
+      double acc = g[0] * T[c];
+      for (int k = 1; k <= r; ++k) acc = fma(g[k], T[c + k] + T[c - k], acc);
+      const double gy = g[dy];
+      num = fma(gy, acc, num);
+      // in-map weight of this segment: columns px - min(r, px) .. px + min(r, npx-1-px)
+      const double seg = G[min(r, px)] + G[min(r, npx - 1 - px)] - g[0];
+      den = fma(gy * ((ina ? 1.0 : 0.0) + (inb ? 1.0 : 0.0)), seg, den);
+    }
   }
-  const int ax = max(px - R, 0), bx = min(px + R, npx - 1);
-  double wx = 0.0;
-  for (int q = ax; q <= bx; ++q) wx += w[abs(q - px)];
-  out[i] = s / (wx * wy);
+  if (px < npx) out[(int64_t)py * npx + px] = num / den;
 }
 
 __global__ void k_histogram(const double* __restrict__ v, int64_t n, double lo, double hi,
@@ -97,18 +118,38 @@ void map_source(const double* map, int npx, int npy, double sigma_px, double tru
                 DeviceAlloc& da, cudaStream_t s) {
   const int R = (int)std::floor(trunc * sigma_px);
   if (R > kMaxSourceRadius) fail(LENS_EINVAL, "source radius above 1024 pixels");
-  std::vector<double> w((size_t)R + 1);
+  // the disk: integer offsets with dx^2 + dy^2 <= (trunc sigma)^2 (the same
+  // products in the same order as the definition, so the same offsets)
+  const double cut2 = trunc * trunc * sigma_px * sigma_px;
   const double inv2s2 = 1.0 / (2.0 * sigma_px * sigma_px);
-  for (int d = 0; d <= R; ++d) w[(size_t)d] = std::exp(-(double)d * d * inv2s2);
-  Scratch dw(&da, sizeof(double) * w.size());
-  Scratch t(&da, sizeof(double) * (size_t)npx * (size_t)npy);
-  LENS_CUDA(cudaMemcpyAsync(dw.p, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, s));
-  const int64_t n = (int64_t)npx * npy;
-  k_source_rows<<<grid_for(n, 256), 256, 0, s>>>(map, npx, npy, R, dw.as<double>(), t.as<double>());
-  LENS_LAUNCHED("k_source_rows");
-  k_source_cols<<<grid_for(n, 256), 256, 0, s>>>(t.as<double>(), npx, npy, R, dw.as<double>(), out);
-  LENS_LAUNCHED("k_source_cols");
-  // the host weights must outlive the copy
+  const size_t n1 = (size_t)R + 1;
+  std::vector<double> tab(3 * n1, 0.0);
+  double acc = 0.0;
+  for (int d = 0; d <= R; ++d) {
+    tab[(size_t)d] = std::exp(-(double)d * d * inv2s2);
+    acc += tab[(size_t)d];
+    tab[n1 + (size_t)d] = acc;
+  }
+  int* rt = reinterpret_cast<int*>(tab.data() + 2 * n1);
+  for (int dy = 0; dy <= R; ++dy) {
+    int r = -1;
+    while (r < R && (double)(r + 1) * (r + 1) + (double)dy * dy <= cut2) ++r;
+    rt[dy] = r;
+  }
+  Scratch dt(&da, sizeof(double) * tab.size());
+  LENS_CUDA(cudaMemcpyAsync(dt.p, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice,
+                            s));
+  const int blocks_x = (npx + kSourceThreads - 1) / kSourceThreads;
+  const int64_t blocks = (int64_t)blocks_x * npy;
+  if (blocks > INT32_MAX) fail(LENS_EINVAL, "map too large");
+  const size_t smem = sizeof(double) * (n1 + kSourceThreads + 2 * (size_t)R);
+  if (smem > 48 * 1024)
+    LENS_CUDA(cudaFuncSetAttribute(k_source_disk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  k_source_disk<<<(unsigned)blocks, kSourceThreads, smem, s>>>(map, npx, npy, R, dt.as<double>(),
+                                                               out);
+  LENS_LAUNCHED("k_source_disk");
+  // the host table must outlive the copy
   LENS_CUDA(cudaStreamSynchronize(s));
 }
 

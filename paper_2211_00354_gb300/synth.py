@@ -145,6 +145,23 @@ def c2_high_mag(seed: int = 0, n: int = 1_500_000, npix: int = 2000,
     return f
 
 
+def c2_window(seed: int = 0, npix: int = 200, h: float = 0.063) -> Field:
+    """A window of the high-magnification map: npix^2 pixels of 0.1 ER
+    (kappa_*=0.45, kappa_s=0, gamma=0.45, cells of side h), its shooting
+    region alone, equal-mass stars uniform in a disk that circumscribes that
+    region with a quarter of its radius to spare (star density kappa_*, as in
+    the full map)."""
+    half = 0.05 * npix
+    grid = shooting_grid(0.45, 0.45, half, h, margin_frac=0.03, margin_min=max(10.0 * h, 0.1 * half))
+    rc = math.hypot(0.5 * grid.nx * h, 0.5 * grid.ny * h)
+    n = int(math.ceil(0.45 * (1.25 * rc) ** 2))
+    f = config_uniform(seed, n, 0.45, 0.0, 0.45, name="c2-window")
+    f.grid = grid
+    f.box = (-half, half, -half, half)
+    f.npx = f.npy = npix
+    return f
+
+
 def c3_clustered(seed: int = 0, n_clusters: int = 1000, per_cluster: int = 1000,
                  a: float = 0.5, npix: int = 4096, half_map: float = 50.0,
                  h: float = 0.0244, trunc: float = 20.0) -> Field:

@@ -49,55 +49,68 @@ def test_version_and_error_string(lib):
     assert isinstance(lib.lens_last_error(), bytes)
 
 
-def test_invalid_arguments_rejected_without_gpu(lib):
-    from paper_2211_00354_gb300 import lens
-    L = lens.load()
-    opts = lens.lens_build_opts()
-    opts.p, opts.leaf_size, opts.prec = 0, 16, 1
-    h = ctypes.c_void_p()
-    fake = ctypes.c_void_p(0x1000)
-    st = L.lens_fmm_build(fake, fake, 10, 0.0, 0.0, ctypes.byref(opts), None, None, ctypes.byref(h))
-    assert st == lens.LENS_EINVAL
-    assert b"p must be" in L.lens_last_error()
-    opts.p, opts.leaf_size = 8, 0
-    assert L.lens_fmm_build(fake, fake, 10, 0.0, 0.0, ctypes.byref(opts), None, None,
-                            ctypes.byref(h)) == lens.LENS_EINVAL
-    opts.leaf_size = 16
-    assert L.lens_fmm_build(fake, fake, 0, 0.0, 0.0, ctypes.byref(opts), None, None,
-                            ctypes.byref(h)) == lens.LENS_EINVAL
-    assert L.lens_fmm_build(fake, fake, 5, float("nan"), 0.0, ctypes.byref(opts), None, None,
-                            ctypes.byref(h)) == lens.LENS_EINVAL
-    assert L.lens_direct_deflect(fake, fake, 4, 0.0, 0.0, fake, 4, 7, fake, None, None,
-                                 None) == lens.LENS_EINVAL
+# The argument checks below pass a made-up device address.  They run in a
+# child process that sees no CUDA device (CUDA_VISIBLE_DEVICES=""), so even a
+# check that regressed could reach no GPU: the call would fail on the missing
+# device instead of launching a kernel on that address.
+def run_without_device(body, **extra_env):
+    code = "import ctypes, sys\nsys.path.insert(0, %r)\n" % ROOT + body
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="", **extra_env)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=120)
+    assert out.returncode == 0, out.stdout + out.stderr
+    return out.stdout
 
 
+ARGS_CHILD = r"""
+from paper_2211_00354_gb300 import lens
+L = lens.load()
+opts = lens.lens_build_opts()
+opts.p, opts.leaf_size, opts.prec = 0, 16, 1
+h = ctypes.c_void_p()
+fake = ctypes.c_void_p(0x1000)
+st = L.lens_fmm_build(fake, fake, 10, 0.0, 0.0, ctypes.byref(opts), None, None, ctypes.byref(h))
+assert st == lens.LENS_EINVAL, st
+assert b"p must be" in L.lens_last_error()
+opts.p, opts.leaf_size = 8, 0
+assert L.lens_fmm_build(fake, fake, 10, 0.0, 0.0, ctypes.byref(opts), None, None,
+                        ctypes.byref(h)) == lens.LENS_EINVAL
+opts.leaf_size = 16
+assert L.lens_fmm_build(fake, fake, 0, 0.0, 0.0, ctypes.byref(opts), None, None,
+                        ctypes.byref(h)) == lens.LENS_EINVAL
+assert L.lens_fmm_build(fake, fake, 5, float("nan"), 0.0, ctypes.byref(opts), None, None,
+                        ctypes.byref(h)) == lens.LENS_EINVAL
+assert L.lens_direct_deflect(fake, fake, 4, 0.0, 0.0, fake, 4, 7, fake, None, None,
+                             None) == lens.LENS_EINVAL
+assert L.lens_direct_deflect_noalloc(fake, fake, 262145, 0.0, 0.0, fake, 4, fake, None,
+                                     None) == lens.LENS_EINVAL
+assert b"262144" in L.lens_last_error()
+n = ctypes.c_int64(-1)
+g = lens.lens_grid(0.0, 0.0, 0.1, 10, 10)
+assert L.lens_find_images(None, ctypes.byref(g), 0.0, 0.0, 4, fake, fake, ctypes.byref(n),
+                          None) == lens.LENS_EINVAL
+assert L.lens_find_images(fake, ctypes.byref(g), 0.0, 0.0, -1, fake, fake, ctypes.byref(n),
+                          None) == lens.LENS_EINVAL
+assert L.lens_find_images(fake, ctypes.byref(g), float("nan"), 0.0, 4, fake, fake,
+                          ctypes.byref(n), None) == lens.LENS_EINVAL
+bad = lens.lens_grid(0.0, 0.0, 0.0, 10, 10)
+assert L.lens_find_images(fake, ctypes.byref(bad), 0.0, 0.0, 4, fake, fake, ctypes.byref(n),
+                          None) == lens.LENS_EINVAL
+assert b"h > 0" in L.lens_last_error()
+assert n.value == -1  # untouched on failure
+assert L.lens_source_image(fake, 4, 0.0, 0.0, 0.0, fake, None) == lens.LENS_EINVAL
+assert L.lens_source_image(fake, -1, 0.0, 0.0, 0.1, fake, None) == lens.LENS_EINVAL
+assert L.lens_source_image(None, 0, 0.0, 0.0, 0.1, None, None) == lens.LENS_OK  # empty
+assert L.lens_potential(None, fake, 4, fake, None) == lens.LENS_EINVAL
+print("ok")
+"""
 
-def test_image_and_potential_arguments_rejected_without_gpu(lib):
-    from paper_2211_00354_gb300 import lens
-    L = lens.load()
-    fake = ctypes.c_void_p(0x1000)
-    n = ctypes.c_int64(-1)
-    g = lens.lens_grid(0.0, 0.0, 0.1, 10, 10)
-    assert L.lens_find_images(None, ctypes.byref(g), 0.0, 0.0, 4, fake, fake, ctypes.byref(n),
-                              None) == lens.LENS_EINVAL
-    assert L.lens_find_images(fake, ctypes.byref(g), 0.0, 0.0, -1, fake, fake, ctypes.byref(n),
-                              None) == lens.LENS_EINVAL
-    assert L.lens_find_images(fake, ctypes.byref(g), float("nan"), 0.0, 4, fake, fake,
-                              ctypes.byref(n), None) == lens.LENS_EINVAL
-    bad = lens.lens_grid(0.0, 0.0, 0.0, 10, 10)
-    assert L.lens_find_images(fake, ctypes.byref(bad), 0.0, 0.0, 4, fake, fake, ctypes.byref(n),
-                              None) == lens.LENS_EINVAL
-    assert b"h > 0" in L.lens_last_error()
-    assert n.value == -1  # untouched on failure
-    assert L.lens_source_image(fake, 4, 0.0, 0.0, 0.0, fake, None) == lens.LENS_EINVAL
-    assert L.lens_source_image(fake, -1, 0.0, 0.0, 0.1, fake, None) == lens.LENS_EINVAL
-    assert L.lens_source_image(None, 0, 0.0, 0.0, 0.1, None, None) == lens.LENS_OK  # empty
-    assert L.lens_potential(None, fake, 4, fake, None) == lens.LENS_EINVAL
+
+def test_invalid_arguments_rejected_before_any_device_work(lib):
+    assert run_without_device(ARGS_CHILD).strip() == "ok"
 
 
 FAULT_CHILD = r"""
-import ctypes, sys
-sys.path.insert(0, %r)
 from paper_2211_00354_gb300 import lens
 L = lens.load()
 fake = ctypes.c_void_p(0x1000)
@@ -106,10 +119,7 @@ print(st, L.lens_last_error().decode())
 """
 
 
-def test_allocation_fault_injection_on_host():
-    env = dict(os.environ, LENS_FAULT="alloc@1")
-    out = subprocess.run([sys.executable, "-c", FAULT_CHILD % ROOT], env=env,
-                         capture_output=True, text=True, timeout=120)
-    assert out.returncode == 0, out.stderr
-    st, msg = out.stdout.strip().split(" ", 1)
+def test_allocation_fault_injection_on_host(lib):
+    out = run_without_device(FAULT_CHILD, LENS_FAULT="alloc@1")
+    st, msg = out.strip().split(" ", 1)
     assert int(st) == 7 and "injected" in msg

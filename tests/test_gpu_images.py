@@ -112,3 +112,20 @@ def test_no_image_far_away_and_source_image():
     # the exponent reaches ~745 before underflow: one rounding of it moves the
     # value by up to ~745 * 2^-53 = 8e-14 relative
     np.testing.assert_allclose(img.cpu().numpy(), ref, rtol=5e-13, atol=1e-300)
+
+
+def test_nan_corner_matches_oracle():
+    # identity lens on a 6 x 6 corner grid, the source inside cell (2, 2);
+    # with that cell's top-left corner undefined the oracle finds no image
+    # there, and neither may the kernel (which must not build the bounding
+    # box from the three finite corners)
+    g = synth.Grid(x0=0.0, y0=0.0, h=1.0, nx=5, ny=5)
+    y = g.corners().copy()
+    beta = (2.5, 2.5)
+    assert [r[0] for r in oracle.find_images(y, g.x0, g.y0, g.h, beta)] == [12]
+    y[3, 2] = (np.nan, 3.0)
+    ref, _ = check_parity(y, g, beta)
+    assert ref == []
+    y[3, 2] = (2.0, np.nan)
+    ref, _ = check_parity(y, g, beta)
+    assert ref == []

@@ -99,6 +99,16 @@ def test_winding_and_bounding_box():
     assert int(np.abs(w).sum()) == 1
 
 
+def test_a_nan_corner_holds_no_image():
+    # an undefined corner leaves the cell's bounding box undefined: no image,
+    # even where the remaining edges would wind around the source (here the
+    # right edge, upward with beta on its left, alone would give +1)
+    y = np.array([[[0.0, 0.0], [1.0, 0.0]], [[np.nan, 1.0], [1.0, 1.0]]])
+    assert oracle.winding_numbers(y, (0.5, 0.5))[0, 0] == 0
+    y[1, 0] = (0.0, 1.0)
+    assert oracle.winding_numbers(y, (0.5, 0.5))[0, 0] == 1
+
+
 def test_source_image_closed_form():
     beta, sig = (0.3, -0.2), 0.05
     y = np.array([[0.3, -0.2], [0.35, -0.2], [0.3, -0.1], [10.0, 10.0]])
