@@ -79,6 +79,10 @@ def _load():
                                                ctypes.c_int, _dp, _dp]
         lib.oracle_ipm_map_refined.restype = None
         ci = ctypes.c_int
+        lib.oracle_multiplane_deflect.argtypes = [ci, ctypes.POINTER(i64),
+                                                  ctypes.POINTER(_dp), ctypes.POINTER(_dp),
+                                                  _dp, _dp, _dp, i64, _dp, _dp, _dp]
+        lib.oracle_multiplane_deflect.restype = None
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = ci
         lib.oracle_map_convolve_gaussian.argtypes = [ci, ci, _dp, d, d, _dp]
@@ -128,6 +132,38 @@ def deflect(stars, masses, kappa_s, gamma, rays, *, alpha=False, jacobian=False)
     if jacobian:
         out.append(jac)
     return out[0] if len(out) == 1 else tuple(out)
+
+
+def multiplane_deflect(planes, beta, rays, *, planes_out=False):
+    """Rays through K thin lens planes.  planes: K tuples (stars (n, 2),
+    masses (n,), kappa_s, gamma); beta: (K, K), beta[i, j] for i < j the
+    distance ratio of planes i and j.  Returns y (m, 2) [, x_planes (K, m, 2)]."""
+    lib = _load()
+    K = len(planes)
+    keep = []
+    ns = (ctypes.c_int64 * K)()
+    sp = (_dp * K)()
+    mp = (_dp * K)()
+    kap = np.empty(K)
+    gam = np.empty(K)
+    for i, (st, ms, ks, g) in enumerate(planes):
+        st, pst = _c(np.asarray(st, dtype=np.float64).reshape(-1, 2))
+        ms, pms = _c(np.asarray(ms, dtype=np.float64).reshape(-1))
+        assert ms.shape[0] == st.shape[0]
+        keep += [st, ms]
+        ns[i] = st.shape[0]
+        sp[i] = pst
+        mp[i] = pms
+        kap[i], gam[i] = float(ks), float(g)
+    b, pb = _c(np.asarray(beta, dtype=np.float64).reshape(K, K))
+    rays, pr = _c(np.asarray(rays).reshape(-1, 2))
+    m = rays.shape[0]
+    y = np.empty((m, 2))
+    xp = np.empty((K, m, 2)) if planes_out else None
+    lib.oracle_multiplane_deflect(K, ns, sp, mp, kap.ctypes.data_as(_dp), gam.ctypes.data_as(_dp),
+                                  pb, m, pr, y.ctypes.data_as(_dp),
+                                  xp.ctypes.data_as(_dp) if planes_out else None)
+    return (y, xp) if planes_out else y
 
 
 def clip_area_sh(poly, x0, y0):

@@ -34,6 +34,9 @@
  *                          star positions, masses, kappa_s and gamma, from the
  *                          real-variable derivatives of Eq. 1 (no complex
  *                          form, no FMM).
+ *   oracle_multiplane_deflect -- rays through several thin lens planes (Sec.
+ *                          1 and the footnote to the thin-lens approximation):
+ *                          the multi-plane recursion, Eq. 1 at each plane.
  *   oracle_map_convolve_gaussian, oracle_histogram, oracle_map_track --
  *                          consumers of a map (Sec. 3): a Gaussian finite
  *                          source (direct 2D sum), magnification histograms,
@@ -500,6 +503,59 @@ void oracle_light_curve_grad(int64_t m, const double* y, double w_ray, int64_t n
     gy[2 * r] = nsum_get(&g1);
     gy[2 * r + 1] = nsum_get(&g2);
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Several thin lens planes (Sec. 1: thick lenses and cosmological ray tracing
+ * take several lens planes, the mapping repeated plane by plane; footnote to
+ * the thin-lens approximation: a 3D lens as a collection of thin planes).
+ * K planes in order of distance from the observer; plane i holds n[i] point
+ * lenses (stars[i]: n[i] x 2, masses[i]: n[i]) and a smooth field (kappa[i],
+ * gamma[i]), each deflection scaled to the source plane as in Eq. 1:
+ *   alpha_i(x) = sum_k m_ik (x - x_ik) / |x - x_ik|^2
+ *                + diag(kappa_i + gamma_i, kappa_i - gamma_i) x.
+ * A ray enters plane 1 at x_1 = x, reaches plane j at
+ *   x_j = x_1 - sum_{i<j} beta[i K + j] alpha_i(x_i)      (j = 2 .. K)
+ * and the source plane at
+ *   y = x_1 - sum_{i<=K} alpha_i(x_i),
+ * beta[i K + j] (i < j, 0-based) being the distance ratio D_ij D_s / (D_j D_is)
+ * of the pair (entries with i >= j are not read).  With K = 1 this is Eq. 1.
+ * y_out: m x 2; xplanes_out: K x m x 2 (x_i per plane) or NULL. */
+void oracle_multiplane_deflect(int K, const int64_t* n, const double* const* stars,
+                               const double* const* masses, const double* kappa,
+                               const double* gamma, const double* beta, int64_t m,
+                               const double* rays, double* y_out, double* xplanes_out) {
+  double* x = (double*)malloc(sizeof(double) * 2 * (size_t)(m > 0 ? m : 1));
+  double* al = (double*)malloc(sizeof(double) * 2 * (size_t)(m > 0 ? m : 1));
+  double* yt = (double*)malloc(sizeof(double) * 2 * (size_t)(m > 0 ? m : 1));
+  /* sum over the planes seen so far of beta_ij alpha_i, for every later plane j
+   * (acc[j] for j < K) and for the source plane (acc[K], beta = 1) */
+  double* acc = (double*)calloc((size_t)(K + 1) * 2 * (size_t)(m > 0 ? m : 1), sizeof(double));
+  for (int i = 0; i < K; ++i) {
+    /* x_i = x_1 - (sum of the earlier planes' deflections weighted for plane i) */
+    for (int64_t r = 0; r < 2 * m; ++r) x[r] = rays[r] - acc[(size_t)i * 2 * m + r];
+    if (xplanes_out)
+      for (int64_t r = 0; r < 2 * m; ++r) xplanes_out[(size_t)i * 2 * m + r] = x[r];
+    if (n[i] > 0) {
+      oracle_deflect(n[i], stars[i], masses[i], 0.0, 0.0, m, x, yt, al, NULL);
+    } else {
+      for (int64_t r = 0; r < 2 * m; ++r) al[r] = 0.0;
+    }
+    for (int64_t r = 0; r < m; ++r) {
+      al[2 * r] += (kappa[i] + gamma[i]) * x[2 * r];
+      al[2 * r + 1] += (kappa[i] - gamma[i]) * x[2 * r + 1];
+    }
+    for (int j = i + 1; j <= K; ++j) {
+      const double bij = j < K ? beta[(size_t)i * K + j] : 1.0;
+      double* aj = acc + (size_t)j * 2 * m;
+      for (int64_t r = 0; r < 2 * m; ++r) aj[r] += bij * al[r];
+    }
+  }
+  for (int64_t r = 0; r < 2 * m; ++r) y_out[r] = rays[r] - acc[(size_t)K * 2 * m + r];
+  free(x);
+  free(al);
+  free(yt);
+  free(acc);
 }
 
 /* ------------------------------------------------------------------------ */
