@@ -229,6 +229,63 @@ lens_status lens_ipm_map_refined(lens_plan* plan, const lens_grid* grid,
                                  int refine_levels, double* map_out,
                                  lens_ipm_stats* stats, void* stream);
 
+/* ---- several lens planes (Sec. 1: ray tracing through several lens planes
+ * repeats the mapping plane by plane; footnote to the thin-lens
+ * approximation: a 3D lens as a collection of thin planes) ---------------
+ * Plane i (in order of distance from the observer) holds n point lenses and
+ * a smooth field, each deflection scaled to the source plane as in Eq. 1:
+ *     alpha_i(x) = sum_k m_ik (x - x_ik) / |x - x_ik|^2
+ *                  + diag(kappa_s + gamma, kappa_s - gamma) x.
+ * A ray entering at x_1 reaches plane j at
+ *     x_j = x_1 - sum_{i<j} beta[i K + j] alpha_i(x_i)
+ * and the source plane at y = x_1 - sum_i alpha_i(x_i); beta[i K + j]
+ * (i < j) is the distance ratio D_ij D_s / (D_j D_is) of the pair (other
+ * entries are not read).  With one plane this is Eq. 1. */
+typedef struct {
+  const double* stars_xy;  /* dev n x 2 (may be NULL when n = 0) */
+  const double* masses;    /* dev n */
+  int64_t n;               /* >= 0 */
+  double kappa_s, gamma;   /* the plane's smooth field */
+} lens_plane;
+
+/* y at m rays (dev m x 2) through nplanes planes (1..64, host array of
+ * lens_plane; beta: host nplanes x nplanes, row-major).  Per plane an FMM
+ * plan is built over its stars (opts: p, leaf_size, prec, max_depth; the
+ * target region is the bounding box of the rays' positions on that plane),
+ * the rays are deflected through it as by lens_deflect, and one kernel moves
+ * them on to the next plane.  y_out: dev m x 2; x_planes_out: dev
+ * nplanes x m x 2 (the positions x_i at each plane) or NULL.  Scratch and
+ * plans from allocator (may be NULL: the library's pool).  Synchronises
+ * `stream` once per plane.  Errors: EINVAL (bad sizes, NULL buffers,
+ * non-finite kappa_s, gamma or beta), EDOMAIN (a position that is not
+ * finite), and those of lens_fmm_build. */
+lens_status lens_multiplane_deflect(const lens_plane* planes, int nplanes,
+                                    const double* beta,
+                                    const lens_build_opts* opts,
+                                    const double* rays_xy, int64_t m,
+                                    double* y_out, double* x_planes_out,
+                                    const lens_allocator* allocator,
+                                    void* stream);
+
+/* FMM-IPM magnification map through several planes: the chunk loop of
+ * lens_ipm_map (Sec. 2.4 steps 2-4) with each chunk's corner rays traced
+ * through every plane as by lens_multiplane_deflect (plans built per chunk
+ * and plane), then apportioned to the map by the same first-order IPM.
+ * Arguments as lens_ipm_map (map_out overwritten; stats: host or NULL, its
+ * rays counting corner rays deflected by planes with stars) plus the planes,
+ * beta, opts and allocator of lens_multiplane_deflect.  Synchronises
+ * `stream`. */
+lens_status lens_multiplane_ipm_map(const lens_plane* planes, int nplanes,
+                                    const double* beta,
+                                    const lens_build_opts* opts,
+                                    const lens_grid* grid, const lens_box* box,
+                                    int npx, int npy,
+                                    int64_t max_cells_per_chunk,
+                                    int bbox_cap_px, double* map_out,
+                                    lens_ipm_stats* stats,
+                                    const lens_allocator* allocator,
+                                    void* stream);
+
 /* Adjoint of lens_deflect (not in the paper): given grad_y = dL/dy at the m
  * rays, the transposed FMM (L2P^T, L2L^T, M2L^T, M2M^T, P2M^T, P2P^T, M2P^T,
  * P2L^T on the same tree) gives

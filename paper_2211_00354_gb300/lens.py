@@ -40,6 +40,7 @@ EXPORTED = ("lens_fmm_build", "lens_deflect", "lens_deflect_grid", "lens_ipm_map
             "lens_direct_deflect", "lens_direct_deflect_noalloc", "lens_light_curve",
             "lens_light_curve_grad", "lens_map_source", "lens_map_histogram", "lens_map_track",
             "lens_find_images", "lens_source_image", "lens_potential",
+            "lens_multiplane_deflect", "lens_multiplane_ipm_map",
             "lens_last_error", "lens_version")
 
 
@@ -94,6 +95,11 @@ class lens_plan_info(ctypes.Structure):
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class lens_plane(ctypes.Structure):
+    _fields_ = [("stars_xy", ctypes.c_void_p), ("masses", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("kappa_s", ctypes.c_double), ("gamma", ctypes.c_double)]
 
 
 class lens_allocator(ctypes.Structure):
@@ -157,6 +163,16 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lens_source_image.restype = st
     lib.lens_potential.argtypes = [vp, vp, i64, vp, vp]
     lib.lens_potential.restype = st
+    lib.lens_multiplane_deflect.argtypes = [ctypes.POINTER(lens_plane), i, vp,
+                                            ctypes.POINTER(lens_build_opts), vp, i64, vp, vp,
+                                            ctypes.POINTER(lens_allocator), vp]
+    lib.lens_multiplane_deflect.restype = st
+    lib.lens_multiplane_ipm_map.argtypes = [ctypes.POINTER(lens_plane), i, vp,
+                                            ctypes.POINTER(lens_build_opts),
+                                            ctypes.POINTER(lens_grid), ctypes.POINTER(lens_box),
+                                            i, i, i64, i, vp, ctypes.POINTER(lens_ipm_stats),
+                                            ctypes.POINTER(lens_allocator), vp]
+    lib.lens_multiplane_ipm_map.restype = st
     lib.lens_light_curve.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp]
     lib.lens_light_curve.restype = st
     lib.lens_light_curve_grad.argtypes = [vp, i64, d, vp, i64, d, d, vp, vp, vp, vp]
@@ -342,6 +358,76 @@ class LensFMM:
                                          grad_y.data_ptr(), gxy.data_ptr(), gm.data_ptr(),
                                          gkg.data_ptr(), _stream_ptr(stream)))
         return gxy, gm, gkg
+
+
+def _planes(planes, beta):
+    """(lens_plane array, kept tensors, beta as a contiguous host buffer)."""
+    K = len(planes)
+    arr = (lens_plane * K)()
+    keep = []
+    for k, (st, ms, ks, g) in enumerate(planes):
+        st = _dev(st, "stars", 2)
+        ms = _dev(ms, "masses").reshape(-1)
+        if ms.shape[0] != st.shape[0]:
+            raise ValueError("a plane's stars and masses disagree in length")
+        keep += [st, ms]
+        arr[k] = lens_plane(st.data_ptr() if st.shape[0] else None,
+                            ms.data_ptr() if ms.shape[0] else None, int(st.shape[0]),
+                            float(ks), float(g))
+    b = (ctypes.c_double * (K * K))()
+    rows = [list(map(float, r)) for r in beta]
+    if len(rows) != K or any(len(r) != K for r in rows):
+        raise ValueError("beta must be nplanes x nplanes")
+    for i in range(K):
+        for j in range(K):
+            b[i * K + j] = rows[i][j]
+    return arr, keep, b
+
+
+def _mp_opts(p, leaf_size, prec, max_depth=0):
+    o = lens_build_opts()
+    o.p, o.leaf_size, o.prec, o.max_depth = int(p), int(leaf_size), int(prec), int(max_depth)
+    return o
+
+
+def multiplane_deflect(planes, beta, rays, p=16, leaf_size=16, prec=FP32_BULK,
+                       planes_out=False, stream=None):
+    """Rays through several lens planes (lens_multiplane_deflect).  planes: a
+    list of (stars (n, 2), masses (n,), kappa_s, gamma) CUDA float64 tensors
+    and floats, nearest first; beta: nplanes x nplanes distance ratios.
+    Returns y (m, 2) [, x_planes (nplanes, m, 2)]."""
+    lib = load()
+    rays = _dev(rays, "rays", 2)
+    arr, keep, b = _planes(planes, beta)
+    K = len(planes)
+    y = torch.empty_like(rays)
+    xp = (torch.empty((K, rays.shape[0], 2), dtype=torch.float64, device=rays.device)
+          if planes_out else None)
+    o = _mp_opts(p, leaf_size, prec)
+    _check(lib.lens_multiplane_deflect(arr, K, ctypes.cast(b, ctypes.c_void_p), ctypes.byref(o),
+                                       rays.data_ptr(), rays.shape[0], y.data_ptr(),
+                                       xp.data_ptr() if planes_out else None, None,
+                                       _stream_ptr(stream)))
+    return (y, xp) if planes_out else y
+
+
+def multiplane_ipm_map(planes, beta, grid, box, npx, npy, p=16, leaf_size=16, prec=FP32_BULK,
+                       max_cells_per_chunk=0, bbox_cap=0, out=None, stream=None):
+    """Magnification map through several lens planes (lens_multiplane_ipm_map)."""
+    lib = load()
+    arr, keep, b = _planes(planes, beta)
+    g = grid_struct(grid)
+    bx = lens_box(*(float(v) for v in box))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mp = out if out is not None else torch.empty((npy, npx), dtype=torch.float64, device=dev)
+    st = lens_ipm_stats()
+    o = _mp_opts(p, leaf_size, prec)
+    _check(lib.lens_multiplane_ipm_map(arr, len(planes), ctypes.cast(b, ctypes.c_void_p),
+                                       ctypes.byref(o), ctypes.byref(g), ctypes.byref(bx),
+                                       int(npx), int(npy), int(max_cells_per_chunk),
+                                       int(bbox_cap), mp.data_ptr(), ctypes.byref(st), None,
+                                       _stream_ptr(stream)))
+    return mp, {name: getattr(st, name) for name, _ in lens_ipm_stats._fields_}
 
 
 def direct_deflect(stars, masses, kappa_s, gamma, rays, prec=FP64, jacobian=False, stream=None):
