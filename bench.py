@@ -34,8 +34,31 @@ sys.path.insert(0, HERE)
 
 METRIC = "FMM rays deflected/s at stated error vs GPU direct sum; IPM map time (1xGB300)"
 UNIT = "rays/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-FP64_PEAK_TFLOPS = 1.18                           # measured DFMA micro-benchmark on this GPU
+# Fallbacks when the pipe micro-benchmark cannot run: unit counts x the
+# maximum SM clock (float32: 152 SMs x 128 lanes x 2 flops; float64: the
+# ratio the micro-benchmark measured on this GPU in development, 1/62)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 62.0
+
+
+def measure_pipe_peaks():
+    """Run the pipe micro-benchmark (paper_2211_00354_gb300/pipe_peaks.cu,
+    built by build()): float32 FMA, paired float32 FMA, float64 FMA and MUFU
+    reciprocal rates on this GPU.  None if it is not built or fails."""
+    from paper_2211_00354_gb300 import _build
+    path = _build.PEAKS_BIN
+    if not os.path.exists(path):
+        try:
+            path = _build.build_peaks()
+        except Exception:
+            return None
+    try:
+        out = subprocess.run([path], capture_output=True, text=True, timeout=120)
+        if out.returncode != 0:
+            return None
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
 
 
 def parse():
@@ -68,6 +91,15 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--accuracy-rays", type=int, default=100_000,
                     help="corner rays compared with the CPU oracle (0: skip)")
+    ap.add_argument("--workload", default="high_mag",
+                    choices=["high_mag", "clustered", "critical", "nfw", "differentiation"],
+                    help="high_mag: the high-magnification map (the default line); clustered: "
+                         "1e6 lenses in Plummer clusters, 4096^2 map; critical: mu ~ 286 near a "
+                         "critical curve, 8192^2 map in chunks; nfw: deflection of a 4096^2 grid "
+                         "by a 1e7-particle elliptical NFW halo; differentiation: forward + "
+                         "adjoint of a Gaussian-source light-curve loss (1e5 stars, 3e6 rays)")
+    ap.add_argument("--p-arms", default="8,24",
+                    help="high_mag: also time whole maps at these orders (comma list, '' = none)")
     return ap.parse_args()
 
 
@@ -308,10 +340,164 @@ def next_rows(args, f, g, stars, masses, prec, target, mp, hbm_peak):
     return out
 
 
+def config_line(args):
+    """One JSON line for a workload other than the high-magnification map:
+    W untimed warm-up steps, then K steps timed with CUDA events (L2 flushed
+    before each), clocks sampled meanwhile.  Map workloads: a step is the
+    plan build plus the whole map (value = corner rays/s); nfw: the plan
+    build plus the deflection of the whole 4096^2 ray grid (rays/s);
+    differentiation: the forward pass (plan build, deflection of 3e6 rays,
+    2048-sample light curve) and the backward pass (light-curve gradient,
+    adjoint FMM) of the squared light-curve loss (rays/s through both)."""
+    import torch
+    from paper_2211_00354_gb300 import autograd, lens, synth
+    pipes = measure_pipe_peaks()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(HERE, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    fp32_peak = max(pipes["ffma_tflops"], pipes["ffma2_tflops"]) if pipes else FP32_PEAK_TFLOPS
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    w = args.workload
+    if w == "clustered":
+        f, p, leaf, cap = synth.c3_clustered(seed=args.seed), 16, 64, 64
+        desc = ("clustered PBH field: 1e6 lenses in 1e3 Plummer clusters (a = 0.5 ER), log-normal "
+                "masses, kappa*=0.2, kappa_s=0.3, gamma=0.3, 4096^2 map over 100 ER, n0 = 1, "
+                "p=16, leaf=64, FP32-bulk, cap 64 px")
+    elif w == "critical":
+        f, p, leaf, cap = synth.c4_critical(seed=args.seed), 16, 8, 64
+        desc = ("critical curve: 2e5 stars m ~ U[0.1,1], kappa_s=0.81, kappa*=0.01, gamma=0.17 "
+                "(mu ~ 286), 8192^2 map over 2 ER, h = 2.44e-4 ER, p=16, leaf=8, FP32-bulk, cap 64 px")
+    elif w == "nfw":
+        f, p, leaf, cap = synth.nfw_halo(seed=args.seed), 16, 16, 0
+        desc = ("elliptical NFW halo (q = 0.7): 1e7 equal-mass particles, 4096^2 ray grid over "
+                "+-2 r_s, p=16, leaf=16, FP32-bulk, deflection only")
+    else:
+        f, p, leaf, cap = synth.c5_differentiable(seed=args.seed), 32, 16, 0
+        desc = ("differentiation: 1e5 stars m ~ U[0.5,1.5], kappa*=0.3, kappa_s=0.2, gamma=0.4, "
+                "6000 x 500 cells of h = 0.01 ER (3e6 rays), 2048-sample Gaussian light curve "
+                "(sigma 0.05 ER), p=32, leaf=16, FP64 forward and adjoint")
+    g = f.grid
+    box = (g.x0, g.x0 + g.nx * g.h, g.y0, g.y0 + g.ny * g.h)
+    stars, masses = T(f.stars), T(f.masses)
+    extra = {}
+    if w in ("clustered", "critical"):
+        mp = torch.empty((f.npy, f.npx), dtype=torch.float64, device=dev)
+
+        def step():
+            P = lens.LensFMM(stars, masses, f.kappa_s, f.gamma, p=p, leaf_size=leaf,
+                             prec=lens.FP32_BULK, target_box=box)
+            _, st = P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=cap, out=mp)
+            info = P.info()
+            P.close()
+            return st, info
+    elif w == "nfw":
+        # the work counters and the evaluation kernel's time come from one map
+        # call over the same grid (the grid kernel with pixel output)
+        P = lens.LensFMM(stars, masses, 0.0, 0.0, p=p, leaf_size=leaf, prec=lens.FP32_BULK,
+                         target_box=box)
+        _, st_w = P.ipm_map(g, (-1.0, 1.0, -1.0, 1.0), 16, 16)
+        P.close()
+
+        def step():
+            P = lens.LensFMM(stars, masses, 0.0, 0.0, p=p, leaf_size=leaf, prec=lens.FP32_BULK,
+                             target_box=box)
+            P.deflect_grid(g)
+            info = P.info()
+            P.close()
+            return st_w, info
+    else:
+        rays = T(g.corners().reshape(-1, 2))
+        smp = T(synth.light_curve_track(2048, length=5.0))
+        sig, wr = 0.05, g.h ** 2
+        ft = synth.perturbed(f, seed=args.seed + 1, sd=0.01)
+        with torch.no_grad():
+            yt = autograd.deflect(T(ft.stars), T(ft.masses), ft.kappa_s, ft.gamma, rays, p=p,
+                                  leaf_size=leaf, target_box=box)
+            Tk = lens.light_curve(yt, wr, smp, sig)
+
+        def step():
+            st_ = stars.detach().clone().requires_grad_(True)
+            ms_ = masses.detach().clone().requires_grad_(True)
+            y = autograd.deflect(st_, ms_, f.kappa_s, f.gamma, rays, p=p, leaf_size=leaf,
+                                 prec=lens.FP64, target_box=box)
+            loss = ((autograd.light_curve(y, wr, smp, sig) - Tk) ** 2).sum()
+            loss.backward()
+            return {"rays": float(rays.shape[0])}, None
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    tot, stats, infos = 0.0, [], []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+        stats.append(st); infos.append(info)
+    clk = clocks.stop()
+    ms = tot / args.steps
+    rays = stats[-1]["rays"] if w != "nfw" else float((g.nx + 1) * (g.ny + 1))
+    line = {"metric": METRIC, "value": rays / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if w != "differentiation" else "f64", "data": "synthetic",
+            "config": {"workload": desc, "n_stars": f.n, "grid": [g.nx, g.ny],
+                       "l2": "flushed between steps (256 MiB write)"},
+            "clocks": clk, "pipe_peaks": pipes}
+    if w != "differentiation":
+        st, info = stats[-1], infos[-1]
+        K = args.steps
+        ms_eval = sum(s_["ms_eval_kernel"] for s_ in stats) / K
+        eval_flops = 10.0 * st["p2p_pairs"] + 8.0 * (p + 1) * (st["rays"] + st["m2p_evals"])
+        tf = eval_flops / (ms_eval / 1e3) / 1e12
+        line["eval_roofline"] = {"bound": "alu", "achieved": tf, "peak": fp32_peak,
+                                 "unit": "TFLOP/s", "frac": tf / fp32_peak, "ms": ms_eval}
+        line["roofline"] = dict(line["eval_roofline"], kernel="k_eval32 (fused L2P+P2P+M2P)",
+                                traffic=None)
+        line["phase_ms"] = {"build": sum(i_["ms_build"] for i_ in infos) / K,
+                            "tree": sum(i_["ms_tree"] for i_ in infos) / K}
+        line["work"] = {"rays": st["rays"], "p2p_pairs": st["p2p_pairs"],
+                        "pairs_per_ray": st["p2p_pairs"] / max(st["rays"], 1.0)}
+        line["tree"] = {k: info[k] for k in ("n_boxes", "n_active_leaves", "n_v", "n_x", "n_u",
+                                             "n_w", "levels")}
+        if w != "nfw":
+            ms_ipm = sum(s_["ms_ipm_kernel"] for s_ in stats) / K
+            ipm_bytes = 16.0 * st["rays"] + 8.0 * st["ipm_updates"]
+            gbs = ipm_bytes / (ms_ipm / 1e3) / 1e9
+            line["ipm_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+                                    "unit": "GB/s", "frac": gbs / hbm_peak, "ms": ms_ipm}
+            if ms_ipm > ms_eval:
+                line["roofline"] = dict(line["ipm_roofline"], kernel="k_ipm_cells+k_ipm_ext",
+                                        traffic=None)
+            line["map_ms"] = ms
+            line["phase_ms"].update({"deflect": st["ms_deflect"], "ipm": st["ms_ipm"],
+                                     "eval_kernel": ms_eval, "ipm_kernels": ms_ipm})
+            line["ledger"] = {k: st[k] for k in ("area_total", "area_in_map", "area_outside",
+                                                 "area_dropped", "cells_dropped", "chunks")}
+    else:
+        line["config"]["parts"] = "forward (build + deflect + light curve) + backward (light-curve gradient + adjoint FMM)"
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "high_mag":
+        config_line(args)
         return
     import torch
     import torch.distributed as dist
@@ -320,6 +506,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the pipe peaks first, in a process of their own (before this one
+    # creates its CUDA context)
+    pipes = measure_pipe_peaks() if local == 0 else None
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -399,6 +588,19 @@ def main():
     eval_flops = 10.0 * pairs + 8.0 * (args.p + 1) * (rays_step + m2p)
     launches = stats[-1]["chunks"]
     eval_tflops = eval_flops / (ms_eval / 1e3) / 1e12
+    if pipes:
+        fp32_peak = max(pipes["ffma_tflops"], pipes["ffma2_tflops"])
+        fp32_src = "measured: pipe_peaks.cu, max of FFMA and paired FFMA2 (%.1f / %.1f TFLOP/s)" % (
+            pipes["ffma_tflops"], pipes["ffma2_tflops"])
+        fp64_peak = pipes["dfma_tflops"]
+        fp64_src = "measured: pipe_peaks.cu DFMA"
+    else:
+        fp32_peak, fp32_src = FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+        fp64_peak, fp64_src = FP64_PEAK_TFLOPS, "derived: float32 peak / 62"
+    # far field (M2L over the V lists): 2 (p+1)^2 float64 FMAs per V pair
+    ms_far = sum(i_.get("ms_far_local", 0.0) for i_ in infos) / K
+    far_flops = 4.0 * (args.p + 1) ** 2 * infos[-1]["n_v"]
+    far_tflops = far_flops / (ms_far / 1e3) / 1e12 if ms_far > 0 else 0.0
     # IPM algorithmic bytes: the 16 B pixel-coordinate corner read per grid
     # ray plus 8 B (read + write of a float) per atomic map or difference
     # array update
@@ -414,10 +616,9 @@ def main():
     eval_traffic = measured_traffic("k_eval32", "eval32.cu", rays_step / launches)
     if ms_eval >= ms_ipm:
         roof = {"bound": "alu", "kernel": "k_eval (fused L2P+P2P+M2P)",
-                "achieved": eval_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": eval_tflops / FP32_PEAK_TFLOPS, "traffic": eval_traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "ms_per_launch": ms_eval / launches}
+                "achieved": eval_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": eval_tflops / fp32_peak, "traffic": eval_traffic,
+                "peak_source": fp32_src, "ms_per_launch": ms_eval / launches}
     else:
         roof = {"bound": "hbm", "kernel": "k_ipm_cells+k_ipm_ext", "achieved": ipm_gbs,
                 "peak": hbm_peak, "unit": "GB/s", "frac": ipm_gbs / hbm_peak, "traffic": ipm_traffic,
@@ -491,6 +692,35 @@ def main():
         extra["fmm_fp64"] = {"p": 32, "deflect_rays_per_s": band.n_rays / (t0.elapsed_time(t1) / 1e3),
                              "rays": band.n_rays, "build_ms": build64,
                              "error_vs_gpu_direct_fp64_max": rel_err(y64)}
+        # the same map at other expansion orders: whole maps timed (one warm-up,
+        # three timed), their error on the same 4096 corners
+        arms = {}
+        for pa in [int(t) for t in args.p_arms.split(",") if t.strip()]:
+            if pa == args.p:
+                continue
+            msa, sta = [], None
+            for it in range(4):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                PA = lens.LensFMM(stars, masses, f.kappa_s, f.gamma, p=pa, leaf_size=args.leaf,
+                                  prec=prec, target_box=target)
+                _, sta = PA.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                if it > 0:
+                    msa.append(a0.elapsed_time(a1))
+                ya = PA.deflect(xs_t) if it == 3 else None
+                PA.close()
+            ea = sum(msa) / len(msa)
+            fl = 10.0 * sta["p2p_pairs"] + 8.0 * (pa + 1) * (sta["rays"] + sta["m2p_evals"])
+            arms[str(pa)] = {"map_ms": ea, "rays_per_s": sta["rays"] / (ea / 1e3),
+                             "error_vs_gpu_direct_fp64_max": rel_err(ya),
+                             "eval_kernel_ms": sta["ms_eval_kernel"],
+                             "ipm_kernels_ms": sta["ms_ipm_kernel"],
+                             "eval_tflops": fl / (sta["ms_eval_kernel"] / 1e3) / 1e12}
+        extra["order_arms"] = arms
         # GPU direct-sum throughput on the same workload (FP32 and FP64 forms)
         _, xd = synth.subsample_grid_rays(args.seed + 8, g, 1 << 19)
         xd_t = torch.tensor(xd, device=dev)
@@ -587,8 +817,15 @@ def main():
             "roofline": roof,
             "ipm_roofline": {"bound": "hbm", "achieved": ipm_gbs, "peak": hbm_peak,
                              "unit": "GB/s", "frac": ipm_gbs / hbm_peak},
-            "eval_roofline": {"bound": "alu", "achieved": eval_tflops, "peak": FP32_PEAK_TFLOPS,
-                              "unit": "TFLOP/s", "frac": eval_tflops / FP32_PEAK_TFLOPS},
+            "eval_roofline": {"bound": "alu", "achieved": eval_tflops, "peak": fp32_peak,
+                              "unit": "TFLOP/s", "frac": eval_tflops / fp32_peak,
+                              "peak_source": fp32_src},
+            "far_field_roofline": {"bound": "fp64", "kernel": "k_far_local (M2L over V, P2L over X)",
+                                   "achieved": far_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                                   "frac": far_tflops / fp64_peak if fp64_peak else None,
+                                   "ms": ms_far, "peak_source": fp64_src,
+                                   "work": "4 (p+1)^2 flops per V pair (P2L over X not counted)"},
+            "pipe_peaks": pipes,
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -124,6 +124,10 @@ typedef struct {
   double ms_ipm_kernel;
   int64_t launches;    /* kernels this call launched */
   double cells_refined; /* (sub)cells over the cap split 2 x 2 (lens_ipm_map_refined) */
+  int64_t fused;        /* 1: the fused deflection + IPM kernel ran (lens_ipm_map_ex) */
+  double ms_fused_kernel; /* device time of the fused kernel (all chunks) */
+  double rays_evaluated;  /* corner evaluations, including the corners that the
+                             fused kernel's overlapping work items share */
 } lens_ipm_stats;
 
 typedef struct {
@@ -136,6 +140,8 @@ typedef struct {
   double ms_build;             /* device time of the build, tree to expansions */
   int64_t build_launches;      /* kernels the build launched */
   double ms_tree;              /* of ms_build: tree, lists and near-field staging */
+  double ms_far_local;         /* device time of the far-field launch (M2L over the
+                                  V lists and P2L over the X lists, all levels) */
 } lens_plan_info;
 
 /* ---- FMM plan ------------------------------------------------------------
@@ -285,6 +291,29 @@ lens_status lens_multiplane_ipm_map(const lens_plane* planes, int nplanes,
                                     lens_ipm_stats* stats,
                                     const lens_allocator* allocator,
                                     void* stream);
+
+/* lens_ipm_map_refined with a choice of kernels (flags):
+ *   LENS_MAP_SEPARATE -- the deflection kernel writes every corner of a chunk
+ *     to device memory as pixel coordinates, then the IPM kernels read them;
+ *   LENS_MAP_FUSED -- float32-bulk plans only: one kernel deflects the
+ *     corners of a rectangle of one leaf's grid rays (the leaf's expansions
+ *     and near stars staged once) into shared memory and apportions every
+ *     cell whose four corners lie in the rectangle (Sec. 2.4 steps 3 and 4
+ *     with no corner round trip); rectangles of one leaf overlap by one row or
+ *     column of corners, which both evaluate from the same leaf data to the
+ *     same bits, so each cell's polygon is the one the separate path forms;
+ *     only corners on leaf boundaries are written out, for the cells that
+ *     straddle two leaves, mapped afterwards;
+ *   0 -- the library's default for the plan.
+ * The two paths give the same map up to the order of the float32 additions.
+ * stats->fused tells which ran. */
+#define LENS_MAP_FUSED 1u
+#define LENS_MAP_SEPARATE 2u
+lens_status lens_ipm_map_ex(lens_plan* plan, const lens_grid* grid,
+                            const lens_box* box, int npx, int npy,
+                            int64_t max_cells_per_chunk, int bbox_cap_px,
+                            int refine_levels, unsigned flags, double* map_out,
+                            lens_ipm_stats* stats, void* stream);
 
 /* Adjoint of lens_deflect (not in the paper): given grad_y = dL/dy at the m
  * rays, the transposed FMM (L2P^T, L2L^T, M2L^T, M2M^T, P2M^T, P2P^T, M2P^T,

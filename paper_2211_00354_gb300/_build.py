@@ -78,6 +78,25 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     return LIB
 
 
+PEAKS_SRC = os.path.join(HERE, "pipe_peaks.cu")
+PEAKS_BIN = os.path.join(OUT, "pipe_peaks")
+
+
+def build_peaks(force: bool = False) -> str:
+    """The pipe-peak micro-benchmark (pipe_peaks.cu) as a standalone program."""
+    os.makedirs(OUT, exist_ok=True)
+    if (not force and os.path.exists(PEAKS_BIN)
+            and os.path.getmtime(PEAKS_BIN) >= os.path.getmtime(PEAKS_SRC)):
+        return PEAKS_BIN
+    tmp = PEAKS_BIN + ".tmp%d" % os.getpid()
+    cmd = [nvcc(), "-O3", "-std=c++17", "-o", tmp, PEAKS_SRC] + ARCH
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for pipe_peaks.cu:\n%s\n%s" % (r.stdout, r.stderr))
+    os.replace(tmp, PEAKS_BIN)
+    return PEAKS_BIN
+
+
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose=True))

@@ -143,6 +143,9 @@ struct lens_plan {
   return LENS_OK;
 
 namespace {
+// lens_ipm_map with a float32-bulk plan and no flag: the fused path or not
+constexpr bool kFusedDefault = false;
+
 void need(bool ok, const char* msg) {
   if (!ok) fail(LENS_EINVAL, msg);
 }
@@ -224,6 +227,8 @@ lens_status lens_fmm_build(const double* stars_xy, const double* masses, int64_t
   LENS_CUDA(cudaEventCreate(&P.ev_tree));
   LENS_CUDA(cudaEventCreateWithFlags(&P.ev_boxes, cudaEventDisableTiming));
   LENS_CUDA(cudaEventCreate(&P.ev_fmm));
+  LENS_CUDA(cudaEventCreate(&P.ev_far0));
+  LENS_CUDA(cudaEventCreate(&P.ev_far1));
   LENS_CUDA(cudaEventRecord(P.ev_start, S(stream)));
   const long long l0 = launch_count();
   // The tree on the caller's stream.  The upward pass (P2M, M2M) needs only
@@ -277,7 +282,7 @@ void lens_plan_destroy(lens_plan* plan) {
   cudaStreamSynchronize(P.da.stream);
   P.ev_clear();
   if (P.fmm_stream) cudaStreamDestroy(P.fmm_stream);
-  for (cudaEvent_t e : {P.ev_start, P.ev_boxes, P.ev_tree, P.ev_fmm})
+  for (cudaEvent_t e : {P.ev_start, P.ev_boxes, P.ev_tree, P.ev_fmm, P.ev_far0, P.ev_far1})
     if (e) cudaEventDestroy(e);
   delete plan;
 }
@@ -307,6 +312,12 @@ lens_status lens_plan_info_get(const lens_plan* plan, lens_plan_info* info) {
   }
   info->ms_build = ms;
   info->ms_tree = ms_tree;
+  info->ms_far_local = 0.0;
+  if (P.ev_fmm && P.n_active > 0) {
+    float mf = 0.f;
+    LENS_CUDA(cudaEventElapsedTime(&mf, P.ev_far0, P.ev_far1));
+    info->ms_far_local = mf;
+  }
   info->build_launches = P.build_launches;
   info->n_leaves = -1;  // not tracked separately (n_active_leaves is)
   LENS_API_END
@@ -357,20 +368,35 @@ lens_status lens_deflect_grid(lens_plan* plan, const lens_grid* grid, int64_t ro
 lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid, const lens_box* box, int npx,
                          int npy, int64_t max_cells_per_chunk, int bbox_cap_px, double* map_out,
                          lens_ipm_stats* stats, void* stream) {
-  return lens_ipm_map_refined(plan, grid, box, npx, npy, max_cells_per_chunk, bbox_cap_px, 0,
-                              map_out, stats, stream);
+  return lens_ipm_map_ex(plan, grid, box, npx, npy, max_cells_per_chunk, bbox_cap_px, 0, 0,
+                         map_out, stats, stream);
 }
 
 lens_status lens_ipm_map_refined(lens_plan* plan, const lens_grid* grid, const lens_box* box,
                                  int npx, int npy, int64_t max_cells_per_chunk, int bbox_cap_px,
                                  int refine_levels, double* map_out, lens_ipm_stats* stats,
                                  void* stream) {
+  return lens_ipm_map_ex(plan, grid, box, npx, npy, max_cells_per_chunk, bbox_cap_px,
+                         refine_levels, 0, map_out, stats, stream);
+}
+
+lens_status lens_ipm_map_ex(lens_plan* plan, const lens_grid* grid, const lens_box* box, int npx,
+                            int npy, int64_t max_cells_per_chunk, int bbox_cap_px,
+                            int refine_levels, unsigned flags, double* map_out,
+                            lens_ipm_stats* stats, void* stream) {
   LENS_API_BEGIN
   need(plan != nullptr, "plan is NULL");
+  need((flags & ~(unsigned)(LENS_MAP_FUSED | LENS_MAP_SEPARATE)) == 0 &&
+           flags != (LENS_MAP_FUSED | LENS_MAP_SEPARATE),
+       "flags: LENS_MAP_FUSED or LENS_MAP_SEPARATE (or 0)");
   need(refine_levels >= 0 && refine_levels <= 16, "refine_levels must be in 0..16");
   need(refine_levels == 0 || bbox_cap_px > 0, "refinement needs a cap (bbox_cap_px > 0)");
   Plan& P = plan->P;
   check_grid(P, grid);
+  need(!(flags & LENS_MAP_FUSED) || P.prec == LENS_FP32_BULK,
+       "the fused map path needs a float32-bulk plan");
+  const bool fused = (flags & LENS_MAP_FUSED) ||
+                     (!(flags & LENS_MAP_SEPARATE) && P.prec == LENS_FP32_BULK && kFusedDefault);
   need(box != nullptr && map_out != nullptr, "box or map_out is NULL");
   need(npx >= 1 && npy >= 1 && (int64_t)npx * npy < (1ll << 31), "npx, npy must be >= 1 with npx*npy < 2^31");
   need(grid->nx < (1ll << 30), "grid nx must be below 2^30");
@@ -452,13 +478,22 @@ lens_status lens_ipm_map_refined(lens_plan* plan, const lens_grid* grid, const l
       pending = 0;
     }
     GridRows g{grid->x0, grid->y0, grid->h, nx, ny, r0, nr + 1};
-    mark();
-    evaluate_grid_pix(P, g, corners.as<PixCorner>(), ip, s);
-    mark();
     if (rq0count) LENS_CUDA(cudaMemsetAsync(rq0count, 0, sizeof(int), s));
-    ipm_accumulate(corners.as<PixCorner>(), nx, nr, ip, map32.as<float>(), rowdiff.as<float>(),
-                   sdev.as<double>(), queue.as<int>(), qcount, rq0.as<int>(), rq0count, s,
-                   &P.ev_ipm);
+    if (fused) {
+      // deflection and IPM in one kernel; only leaf-boundary corners reach
+      // `corners`, for the seam cells mapped after it
+      mark();
+      evaluate_grid_fused(P, g, corners.as<PixCorner>(), ip, map32.as<float>(), rowdiff.as<float>(),
+                          sdev.as<double>(), queue.as<int>(), qcount, rq0.as<int>(), rq0count, s);
+      mark();
+    } else {
+      mark();
+      evaluate_grid_pix(P, g, corners.as<PixCorner>(), ip, s);
+      mark();
+      ipm_accumulate(corners.as<PixCorner>(), nx, nr, ip, map32.as<float>(), rowdiff.as<float>(),
+                     sdev.as<double>(), queue.as<int>(), qcount, rq0.as<int>(), rq0count, s,
+                     &P.ev_ipm);
+    }
     pending += nr * nx;
     ++chunks;
     if (refine_levels > 0) {
@@ -522,6 +557,8 @@ lens_status lens_ipm_map_refined(lens_plan* plan, const lens_grid* grid, const l
   double mse = 0, msk = 0;
   for (auto& e : P.ev_eval) { float ms = 0; cudaEventElapsedTime(&ms, e.first, e.second); mse += ms; }
   for (auto& e : P.ev_ipm) { float ms = 0; cudaEventElapsedTime(&ms, e.first, e.second); msk += ms; }
+  double msf = 0;
+  for (auto& e : P.ev_fused) { float ms = 0; cudaEventElapsedTime(&ms, e.first, e.second); msf += ms; }
   if (stats) {
     stats->cells = (double)nx * (double)ny;
     stats->area_total = stats->cells * ip.a_cell;
@@ -544,6 +581,9 @@ lens_status lens_ipm_map_refined(lens_plan* plan, const lens_grid* grid, const l
     stats->ms_ipm_kernel = msk;
     stats->launches = launch_count() - l0;
     stats->cells_refined = (double)refined;
+    stats->fused = fused ? 1 : 0;
+    stats->ms_fused_kernel = msf;
+    stats->rays_evaluated = fused ? hs[15] : hs[12];
   }
   LENS_API_END
 }

@@ -505,6 +505,34 @@ void grid_impl(Plan& P, const GridRows& g, double* y, double* jac, PixCorner* pi
 }
 }  // namespace
 
+void evaluate_grid_fused(Plan& P, const GridRows& g, PixCorner* edge, const IpmParams& ip,
+                         float* map32, float* rowdiff, double* stats_dev, int* queue, int* qcount,
+                         int* rq, int* rqcount, cudaStream_t s) {
+  const int64_t nl = P.n_active_leaves;
+  if (nl == 0 || g.nrows <= 0) return;
+  if (P.prec != LENS_FP32_BULK) fail(LENS_EINVAL, "the fused map path needs a float32-bulk plan");
+  Scratch rect(&P.da, sizeof(int64_t) * 4 * nl);
+  Scratch tiles(&P.da, sizeof(int64_t) * (nl + 1));
+  k_grid_rects<<<grid_for(nl, 128), 128, 0, s>>>(P.active_leaves, nl, P.box_level, P.box_ix,
+                                                 P.box_iy, P.root_lo[0], P.root_lo[1],
+                                                 P.root_size, g.x0, g.y0, g.h, g.nx, g.row0,
+                                                 g.nrows, tile_rays(P), rect.as<int64_t>(),
+                                                 tiles.as<int64_t>());
+  LENS_LAUNCHED("k_grid_rects");
+  if (P.work) {
+    k_work_count<<<grid_for(nl, 128, 1024), 128, 0, s>>>(P.active_leaves, nl, P.box_aidx,
+                                                        rect.as<int64_t>(), P.ustar_cnt,
+                                                        P.W_off, P.f_ncnt, P.f_wcnt, P.work);
+    LENS_LAUNCHED("k_work_count");
+  }
+  int64_t nseam = 0;
+  Scratch seam = eval32_fused(P, g, rect.as<int64_t>(), edge, ip, map32, rowdiff, stats_dev, rq,
+                              rqcount, nseam, s);
+  // the cells on leaves' last corner rows and columns, from the boundary corners
+  ipm_accumulate_list(edge, g.nx, seam.as<int>(), nseam, ip, map32, rowdiff, stats_dev, queue,
+                      qcount, rq, rqcount, s, P.timing ? &P.ev_ipm : nullptr);
+}
+
 void evaluate_grid(Plan& P, const GridRows& g, double* y, double* jac, cudaStream_t s) {
   grid_impl<false>(P, g, y, jac, nullptr, nullptr, s);
 }

@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "cx.cuh"
+#include "ipm_warp.cuh"
 #include "lens_internal.h"
 
 namespace lens {
@@ -69,27 +70,233 @@ struct E32Args {
   PixCorner* pix; ff iduf, idvf;
 };
 
+// Shared memory of the float32 evaluation: the staged near stars, each value
+// duplicated into both halves of a float2 (the offsets negated, so that
+// d = x + (-s) is the plain difference), and the expansion coefficients with
+// each real / imaginary part duplicated (operands of the paired-ray
+// arithmetic).
+struct E32Smem {
+  float2 s_x[kChunk], s_y[kChunk], s_xl[kChunk], s_yl[kChunk], s_m[kChunk];
+  float2 s_Lx[kMaxOrder + 1], s_Ly[kMaxOrder + 1];
+  float2 s_Wx[kWChunk][kMaxOrder + 1], s_Wy[kWChunk][kMaxOrder + 1];
+  float4 s_wg[kWChunk];
+};
+
+// The leaf's float32 local coefficients (block-cooperative; a barrier must
+// follow before they are read).
+__device__ __forceinline__ void stage_local(E32Smem& sm, const E32Args& A, int64_t k, int tid) {
+  const int p = A.p;
+  for (int l = tid; l <= p; l += kT) {
+    const float2 c = A.fL[k * (int64_t)(p + 1) + l];
+    sm.s_Lx[l] = make_float2(c.x, c.x);
+    sm.s_Ly[l] = make_float2(c.y, c.y);
+  }
+}
+
+// Near stars g0 .. g0 + nf - 1 of a leaf into the staging arrays, padded to nfg
+// (whole groups of kGroup) with massless stars 1e18 away: they add exactly
+// zero when the mass multiplies (w = 0 * finite) and ~1e-18 (far below
+// float32 rounding of the sum) in the equal-mass form, which leaves the mass
+// out.  Block-cooperative, between barriers.
+__device__ __forceinline__ void stage_stars(E32Smem& sm, const E32Args& A, int64_t g0, int nf,
+                                            int nfg, int tid) {
+  for (int f = tid; f < nfg; f += kT) {
+    float4 v = make_float4(1e18f, 0.f, 0.f, 0.f);
+    float mm = 0.f;
+    if (f < nf) {
+      v = A.ust[g0 + f];
+      mm = A.um[g0 + f];
+    }
+    sm.s_x[f] = make_float2(-v.x, -v.x); sm.s_y[f] = make_float2(-v.y, -v.y);
+    sm.s_xl[f] = make_float2(-v.z, -v.z); sm.s_yl[f] = make_float2(-v.w, -v.w);
+    sm.s_m[f] = make_float2(mm, mm);
+  }
+}
+
+// P2P of a thread's rays against the nfg staged stars, rays (2h, 2h+1) side
+// by side in float2 pair arithmetic (Blackwell's two-lane FP32 instructions,
+// IEEE round-to-nearest per lane): summed in groups of kGroup stars in plain
+// float32, each group partial entering the two-sum accumulators N1, N2.  A
+// star exactly on the ray contributes nothing: the floor on r2 keeps w
+// finite and w * d = 0.
+template <bool UM>
+__device__ __forceinline__ void p2p_paired(const E32Smem& sm, int nfg, const float (&dx)[kRpt],
+                                           const float (&dy)[kRpt], const float (&dxl)[kRpt],
+                                           const float (&dyl)[kRpt], fcomp2 (&N1)[kRpt / 2],
+                                           fcomp2 (&N2)[kRpt / 2]) {
+  for (int lo = 0; lo < nfg; lo += kGroup) {
+    float2 P1[kRpt / 2], P2[kRpt / 2], DX[kRpt / 2], DY[kRpt / 2], DXL[kRpt / 2], DYL[kRpt / 2];
+#pragma unroll
+    for (int h = 0; h < kRpt / 2; ++h) {
+      P1[h] = make_float2(0.f, 0.f); P2[h] = make_float2(0.f, 0.f);
+      DX[h] = make_float2(dx[2 * h], dx[2 * h + 1]); DY[h] = make_float2(dy[2 * h], dy[2 * h + 1]);
+      DXL[h] = make_float2(dxl[2 * h], dxl[2 * h + 1]); DYL[h] = make_float2(dyl[2 * h], dyl[2 * h + 1]);
+    }
+    const float2 tiny = make_float2(1e-30f, 1e-30f);
+#pragma unroll
+    for (int jj = 0; jj < kGroup; ++jj) {
+      const int j = lo + jj;
+      const float2 nsx = sm.s_x[j], nsy = sm.s_y[j], nsxl = sm.s_xl[j], nsyl = sm.s_yl[j];
+#pragma unroll
+      for (int h = 0; h < kRpt / 2; ++h) {
+        const float2 d1 = __fadd2_rn(__fadd2_rn(DX[h], nsx), __fadd2_rn(DXL[h], nsxl));
+        const float2 d2 = __fadd2_rn(__fadd2_rn(DY[h], nsy), __fadd2_rn(DYL[h], nsyl));
+        const float2 r2 = __ffma2_rn(d1, d1, __ffma2_rn(d2, d2, tiny));
+        const float2 rr = make_float2(frcp_fast(r2.x), frcp_fast(r2.y));
+        // equal masses: the mass multiplies the sums once, after the loop
+        const float2 w = UM ? rr : __fmul2_rn(sm.s_m[j], rr);
+        P1[h] = __ffma2_rn(w, d1, P1[h]);
+        P2[h] = __ffma2_rn(w, d2, P2[h]);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < kRpt / 2; ++h) {
+      N1[h].add(P1[h]);
+      N2[h].add(P2[h]);
+    }
+  }
+}
+
+// far W boxes e0 .. e0 + nw - 1 of a leaf (their float32 multipoles and
+// geometry) into shared memory; block-cooperative, between barriers
+__device__ __forceinline__ void stage_w(E32Smem& sm, const E32Args& A, int64_t e0, int nw, int tid) {
+  const int p = A.p;
+  for (int t = tid; t < nw * (p + 1); t += kT) {
+    const int w = t / (p + 1), kk = t - w * (p + 1);
+    const float2 c = A.fM[(int64_t)A.wlist[e0 + w] * (p + 1) + kk];
+    sm.s_Wx[w][kk] = make_float2(c.x, c.x);
+    sm.s_Wy[w][kk] = make_float2(c.y, c.y);
+  }
+  if (tid < nw) sm.s_wg[tid] = A.wgeo[e0 + tid];
+}
+
+// M2P of the nw staged W boxes, rays (2h, 2h+1) side by side: Horner's rule
+// for f(z) = (1/z) sum_k A_k (r/z)^k, 4 paired multiply-adds per order.
+__device__ __forceinline__ void m2p_paired(const E32Smem& sm, int nw, int p, const float (&dx)[kRpt],
+                                           const float (&dy)[kRpt], float2 (&FX)[kRpt / 2],
+                                           float2 (&FY)[kRpt / 2]) {
+  for (int w = 0; w < nw; ++w) {
+    const float4 gw = sm.s_wg[w];
+    const float2 ngx = make_float2(-gw.x, -gw.x), ngy = make_float2(-gw.y, -gw.y);
+    const float2 gr = make_float2(gw.z, gw.z), ngr = make_float2(-gw.z, -gw.z);
+#pragma unroll
+    for (int h = 0; h < kRpt / 2; ++h) {
+      const float2 zx = __fadd2_rn(make_float2(dx[2 * h], dx[2 * h + 1]), ngx);
+      const float2 zy = __fadd2_rn(make_float2(dy[2 * h], dy[2 * h + 1]), ngy);
+      const float2 n2 = __ffma2_rn(zx, zx, __fmul2_rn(zy, zy));
+      const float2 d = make_float2(frcp_fast(n2.x), frcp_fast(n2.y));
+      const float2 ix = __fmul2_rn(zx, d);   // 1/z = (zx d, -zy d)
+      const float2 niy = __fmul2_rn(zy, d);  // -Im(1/z)
+      const float2 iy = make_float2(-niy.x, -niy.y);
+      const float2 qx = __fmul2_rn(ix, gr), qy = __fmul2_rn(iy, gr);
+      const float2 nqy = __fmul2_rn(iy, ngr);
+      float2 sx = sm.s_Wx[w][p], sy = sm.s_Wy[w][p];
+      for (int kk = p - 1; kk >= 0; --kk) {
+        const float2 tx = __ffma2_rn(sy, nqy, sm.s_Wx[w][kk]);
+        const float2 ty = __ffma2_rn(sy, qx, sm.s_Wy[w][kk]);
+        const float2 nsx = __ffma2_rn(sx, qx, tx);
+        sy = __ffma2_rn(sx, qy, ty);
+        sx = nsx;
+      }
+      FX[h] = __ffma2_rn(sx, ix, __ffma2_rn(sy, niy, FX[h]));
+      FY[h] = __ffma2_rn(sx, iy, __ffma2_rn(sy, ix, FY[h]));
+    }
+  }
+}
+
+// L2P by Horner's rule and the float-float lens equation for rays (2h, 2h+1)
+// side by side: T1 = a dx - Re f - near1, T2 = b dy + Im f - near2 (y minus
+// the leaf's float64 constant; alpha = conj(b0 + f + near)).
+__device__ __forceinline__ void l2p_lens_pair(const E32Smem& sm, const E32Args& A, float ir, int h,
+                                              const float (&dx)[kRpt], const float (&dy)[kRpt],
+                                              const float (&dxl)[kRpt], const float (&dyl)[kRpt],
+                                              const fcomp2& N1h, const fcomp2& N2h, float2 FXh,
+                                              float2 FYh, ff2& T1, ff2& T2) {
+  const int p = A.p;
+  const float2 irr = make_float2(ir, ir), nirr = make_float2(-ir, -ir);
+  const float2 DXh = make_float2(dx[2 * h], dx[2 * h + 1]);
+  const float2 DYh = make_float2(dy[2 * h], dy[2 * h + 1]);
+  const float2 wx = __fmul2_rn(DXh, irr);
+  const float2 wy = __fmul2_rn(DYh, irr);
+  const float2 nwy = __fmul2_rn(DYh, nirr);
+  float2 fx = make_float2(0.f, 0.f), fy = make_float2(0.f, 0.f);
+  if (p >= 1) {
+    float2 sx = sm.s_Lx[p], sy = sm.s_Ly[p];
+    for (int l = p - 1; l >= 1; --l) {
+      const float2 tx = __ffma2_rn(sy, nwy, sm.s_Lx[l]);
+      const float2 ty = __ffma2_rn(sy, wx, sm.s_Ly[l]);
+      const float2 nsx = __ffma2_rn(sx, wx, tx);
+      sy = __ffma2_rn(sx, wy, ty);
+      sx = nsx;
+    }
+    fx = __ffma2_rn(sx, wx, __fmul2_rn(sy, nwy));
+    fy = __ffma2_rn(sx, wy, __fmul2_rn(sy, wx));
+  }
+  // f = L2P + M2P (the far W boxes)
+  fx = __fadd2_rn(fx, FXh);
+  fy = __fadd2_rn(fy, FYh);
+  // y1 = a x1 - Re f - near1, y2 = b x2 + Im f - near2 (alpha = conj f)
+  T1 = ff2_mul(A.af, ff2{DXh, make_float2(dxl[2 * h], dxl[2 * h + 1])});
+  T1 = ff2_sub(T1, fx);
+  T1 = ff2_sub(T1, ff2{N1h.hi, N1h.lo});
+  T2 = ff2_mul(A.bf, ff2{DYh, make_float2(dyl[2 * h], dyl[2 * h + 1])});
+  T2 = ff2_add(T2, fy);
+  T2 = ff2_sub(T2, ff2{N2h.hi, N2h.lo});
+}
+
+// The two rays' source-plane positions in map-pixel coordinates: u = U1 +
+// T1 / du (U1 the leaf centre's reference), split into an integer pixel and a
+// float32 fraction in [0, 1); corners beyond 2^30 pixels are marked far.
+__device__ __forceinline__ void pix_pair(const E32Args& A, const LeafGrid& lg, const ff2& T1,
+                                         const ff2& T2, PixCorner (&pc)[2]) {
+  const ff2 U = ff2_add(lg.U1f, ff2_mul(A.iduf, T1));
+  const ff2 V = ff2_add(lg.V1f, ff2_mul(A.idvf, T2));
+  const float2 ku2 = make_float2(floorf(U.hi.x), floorf(U.hi.y));
+  const float2 kv2 = make_float2(floorf(V.hi.x), floorf(V.hi.y));
+  const float2 fu2 = __fadd2_rn(fsub2(U.hi, ku2), U.lo);
+  const float2 fv2 = __fadd2_rn(fsub2(V.hi, kv2), V.lo);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const float uh = c ? U.hi.y : U.hi.x, vh = c ? V.hi.y : V.hi.x;
+    float ku = c ? ku2.y : ku2.x, kv = c ? kv2.y : kv2.x;
+    float fu = c ? fu2.y : fu2.x, fv = c ? fv2.y : fv2.x;
+    bool far = lg.far || !(fabsf(uh) < 5.0e8f) || !(fabsf(vh) < 5.0e8f);
+    if (fu < 0.f) { ku -= 1.f; fu += 1.f; } else if (fu >= 1.f) { ku += 1.f; fu -= 1.f; }
+    if (fv < 0.f) { kv -= 1.f; fv += 1.f; } else if (fv >= 1.f) { kv += 1.f; fv -= 1.f; }
+    // float -> int32 (|k| < 5e8); integer adds only afterwards
+    const int64_t iu = (int64_t)lg.U1i + (int)ku, iv = (int64_t)lg.V1i + (int)kv;
+    far = far || !(iu > -1073741824ll && iu < 1073741824ll && iv > -1073741824ll &&
+                   iv < 1073741824ll);
+    if (!far) {
+      pc[c].iu = (int)iu; pc[c].fu = fu; pc[c].iv = (int)iv; pc[c].fv = fv;
+    } else {
+      pc[c].iu = 0x7fffffff; pc[c].fu = 0.f; pc[c].iv = 0x7fffffff; pc[c].fv = 0.f;
+    }
+  }
+}
+
+// The offset of grid ray (di, dj) of a leaf (counted from the leaf's first
+// ray) from the leaf centre, float-float; int32 -> float only (64-bit forms
+// run on the float64 pipe).
+__device__ __forceinline__ void grid_offset(const E32Args& A, const LeafGrid& lg, uint32_t di,
+                                            uint32_t dj, float& dx, float& dxl, float& dy,
+                                            float& dyl) {
+  const ff ox = ff_add(lg.bx, ff_mul(A.hf, (float)(int)di));
+  const ff oy = ff_add(lg.by, ff_mul(A.hf, (float)(int)dj));
+  dx = ox.hi; dxl = ox.lo;
+  dy = oy.hi; dyl = oy.lo;
+}
+
 template <bool JAC, bool GRID, bool PIX, bool UM = false>
 __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
-  // staged stars, each value duplicated into both halves of a float2 (the
-  // offsets negated, so that d = x + (-s) is the plain difference)
-  __shared__ float2 s_x[kChunk], s_y[kChunk], s_xl[kChunk], s_yl[kChunk], s_m[kChunk];
-  // expansion coefficients with each real / imaginary part duplicated into
-  // both halves of a float2 (operands of the paired-ray arithmetic)
-  __shared__ float2 s_Lx[kMaxOrder + 1], s_Ly[kMaxOrder + 1];
-  __shared__ float2 s_Wx[kWChunk][kMaxOrder + 1], s_Wy[kWChunk][kMaxOrder + 1];
-  __shared__ float4 s_wg[kWChunk];
+  __shared__ E32Smem sm;
   const int tid = threadIdx.x;
   const int p = A.p;
   const int2 kt = A.tile_leaf[blockIdx.x];
   const int64_t k = kt.x;
   const int64_t tile = kt.y;
   const LeafPlan lp = A.leaf[k];
-  for (int l = tid; l <= p; l += kT) {
-    const float2 c = A.fL[k * (int64_t)(p + 1) + l];
-    s_Lx[l] = make_float2(c.x, c.x);
-    s_Ly[l] = make_float2(c.y, c.y);
-  }
+  stage_local(sm, A, k, tid);
 
   // ---- rays of this tile -------------------------------------------------
   int64_t nr_leaf, i0 = 0, ni = 1, j0 = 0;
@@ -120,14 +327,11 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
     n1[q] = {0.f, 0.f}; n2[q] = {0.f, 0.f}; nj1[q] = {0.f, 0.f}; nj2[q] = {0.f, 0.f};
     if (!ok[q]) continue;
     if (GRID) {
-      // 32-bit division and int32 -> float (64-bit forms run on the float64 pipe)
+      // 32-bit division
       const uint32_t l32 = (uint32_t)loc, n32 = (uint32_t)ni;
       const uint32_t dj = l32 / n32, di = l32 - dj * n32;
       oidx[q] = (j0 + (int64_t)dj - A.grow0) * A.gnx1 + i0 + (int64_t)di;
-      const ff ox = ff_add(lg.bx, ff_mul(A.hf, (float)(int)di));
-      const ff oy = ff_add(lg.by, ff_mul(A.hf, (float)(int)dj));
-      dx[q] = ox.hi; dxl[q] = ox.lo;
-      dy[q] = oy.hi; dyl[q] = oy.lo;
+      grid_offset(A, lg, di, dj, dx[q], dxl[q], dy[q], dyl[q]);
     } else {
       const int64_t ridx = A.perm[A.ray_off[k] + loc];
       oidx[q] = ridx;
@@ -141,74 +345,27 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   // The leaf's near stars are contiguous: they are staged kChunk at a time
   // and summed in groups of kGroup (8) in plain float32, each group partial then
   // entering a two-sum (compensated) accumulator.  The staged chunk is padded
-  // to whole groups, so every group loop has a fixed trip count and unrolls,
-  // with massless stars 1e18 away: they add exactly zero when the mass
-  // multiplies (w = 0 * finite) and ~1e-18 (far below float32 rounding of
-  // the sum) in the equal-mass form, which leaves the mass out.
+  // to whole groups, so every group loop has a fixed trip count and unrolls.
   static_assert(kChunk % kGroup == 0, "chunks hold whole groups");
   const int64_t star0 = A.uoff[k], nstar = A.uoff[k + 1] - star0;
   for (int64_t f0 = 0; f0 < nstar; f0 += kChunk) {
     const int nf = (int)min64(kChunk, nstar - f0);
     const int nfg = (nf + kGroup - 1) / kGroup * kGroup;
     __syncthreads();
-    for (int f = tid; f < nfg; f += kT) {
-      float4 v = make_float4(1e18f, 0.f, 0.f, 0.f);
-      float mm = 0.f;
-      if (f < nf) {
-        const int64_t g = star0 + f0 + f;
-        v = A.ust[g];
-        mm = A.um[g];
-      }
-      s_x[f] = make_float2(-v.x, -v.x); s_y[f] = make_float2(-v.y, -v.y);
-      s_xl[f] = make_float2(-v.z, -v.z); s_yl[f] = make_float2(-v.w, -v.w);
-      s_m[f] = make_float2(mm, mm);
-    }
+    stage_stars(sm, A, star0 + f0, nf, nfg, tid);
     __syncthreads();
-    for (int lo = 0; lo < nfg; lo += kGroup) {
-      float p1[kRpt], p2[kRpt], pj1[kRpt], pj2[kRpt];
-      if (!JAC) {
-        // rays (2h, 2h+1) side by side in float2 pair arithmetic
-        // (Blackwell's two-lane FP32 instructions, IEEE round-to-nearest
-        // per lane): the same operations as the scalar loop below in half
-        // the issue slots.  A star exactly on the ray contributes nothing:
-        // the floor on r2 keeps w finite and w * d = 0.
-        float2 P1[kRpt / 2], P2[kRpt / 2], DX[kRpt / 2], DY[kRpt / 2], DXL[kRpt / 2], DYL[kRpt / 2];
-#pragma unroll
-        for (int h = 0; h < kRpt / 2; ++h) {
-          P1[h] = make_float2(0.f, 0.f); P2[h] = make_float2(0.f, 0.f);
-          DX[h] = make_float2(dx[2 * h], dx[2 * h + 1]); DY[h] = make_float2(dy[2 * h], dy[2 * h + 1]);
-          DXL[h] = make_float2(dxl[2 * h], dxl[2 * h + 1]); DYL[h] = make_float2(dyl[2 * h], dyl[2 * h + 1]);
-        }
-        const float2 tiny = make_float2(1e-30f, 1e-30f);
-#pragma unroll
-        for (int jj = 0; jj < kGroup; ++jj) {
-          const int j = lo + jj;
-          const float2 nsx = s_x[j], nsy = s_y[j], nsxl = s_xl[j], nsyl = s_yl[j];
-#pragma unroll
-          for (int h = 0; h < kRpt / 2; ++h) {
-            const float2 d1 = __fadd2_rn(__fadd2_rn(DX[h], nsx), __fadd2_rn(DXL[h], nsxl));
-            const float2 d2 = __fadd2_rn(__fadd2_rn(DY[h], nsy), __fadd2_rn(DYL[h], nsyl));
-            const float2 r2 = __ffma2_rn(d1, d1, __ffma2_rn(d2, d2, tiny));
-            const float2 rr = make_float2(frcp_fast(r2.x), frcp_fast(r2.y));
-            // equal masses: the mass multiplies the sums once, after the loop
-            const float2 w = UM ? rr : __fmul2_rn(s_m[j], rr);
-            P1[h] = __ffma2_rn(w, d1, P1[h]);
-            P2[h] = __ffma2_rn(w, d2, P2[h]);
-          }
-        }
-#pragma unroll
-        for (int h = 0; h < kRpt / 2; ++h) {
-          N1[h].add(P1[h]);
-          N2[h].add(P2[h]);
-        }
-      } else {
+    if (!JAC) {
+      p2p_paired<UM>(sm, nfg, dx, dy, dxl, dyl, N1, N2);
+    } else {
+      for (int lo = 0; lo < nfg; lo += kGroup) {
+        float p1[kRpt], p2[kRpt], pj1[kRpt], pj2[kRpt];
 #pragma unroll
         for (int q = 0; q < kRpt; ++q) { p1[q] = 0.f; p2[q] = 0.f; pj1[q] = 0.f; pj2[q] = 0.f; }
 #pragma unroll
         for (int jj = 0; jj < kGroup; ++jj) {
           const int j = lo + jj;
-          const float sx = -s_x[j].x, sy = -s_y[j].x, sxl = -s_xl[j].x, syl = -s_yl[j].x;
-          const float sm = s_m[j].x;
+          const float sx = -sm.s_x[j].x, sy = -sm.s_y[j].x, sxl = -sm.s_xl[j].x, syl = -sm.s_yl[j].x;
+          const float smm = sm.s_m[j].x;
 #pragma unroll
           for (int q = 0; q < kRpt; ++q) {
             const float d1 = (dx[q] - sx) + (dxl[q] - sxl);
@@ -217,7 +374,7 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
             // overflow with a floor on r2, hence the select)
             const float r2 = fmaf(d1, d1, d2 * d2);
             const float inv = r2 > 0.f ? frcp_fast(r2) : 0.f;
-            const float w = sm * inv;
+            const float w = smm * inv;
             p1[q] = fmaf(w, d1, p1[q]);
             p2[q] = fmaf(w, d2, p2[q]);
             const float w2 = w * inv;
@@ -225,8 +382,6 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
             pj2[q] = fmaf(w2, 2.f * d1 * d2, pj2[q]);
           }
         }
-      }
-      if (JAC) {
 #pragma unroll
         for (int q = 0; q < kRpt; ++q) {
           n1[q].add(p1[q]); n2[q].add(p2[q]);
@@ -248,9 +403,6 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   }
 
   // ---- M2P over the far W boxes --------------------------------------------
-  // Without the Jacobian, rays (2h, 2h+1) run side by side in paired float32
-  // arithmetic: Horner's rule for f(z) = (1/z) sum_k A_k (r/z)^k takes 4
-  // paired multiply-adds per order for two rays.
   float2 fw[kRpt], dfw[kRpt];
 #pragma unroll
   for (int q = 0; q < kRpt; ++q) { fw[q] = make_float2(0.f, 0.f); dfw[q] = make_float2(0.f, 0.f); }
@@ -261,53 +413,24 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   for (int64_t e0 = w_beg; e0 < w_end; e0 += kWChunk) {
     const int nw = (int)min64(kWChunk, w_end - e0);
     __syncthreads();
-    for (int t = tid; t < nw * (p + 1); t += kT) {
-      const int w = t / (p + 1), kk = t - w * (p + 1);
-      const float2 c = A.fM[(int64_t)A.wlist[e0 + w] * (p + 1) + kk];
-      s_Wx[w][kk] = make_float2(c.x, c.x);
-      s_Wy[w][kk] = make_float2(c.y, c.y);
-    }
-    if (tid < nw) s_wg[tid] = A.wgeo[e0 + tid];
+    stage_w(sm, A, e0, nw, tid);
     __syncthreads();
-    for (int w = 0; w < nw; ++w) {
-      const float4 gw = s_wg[w];
-      if (!JAC) {
-        const float2 ngx = make_float2(-gw.x, -gw.x), ngy = make_float2(-gw.y, -gw.y);
-        const float2 gr = make_float2(gw.z, gw.z), ngr = make_float2(-gw.z, -gw.z);
-#pragma unroll
-        for (int h = 0; h < kRpt / 2; ++h) {
-          const float2 zx = __fadd2_rn(make_float2(dx[2 * h], dx[2 * h + 1]), ngx);
-          const float2 zy = __fadd2_rn(make_float2(dy[2 * h], dy[2 * h + 1]), ngy);
-          const float2 n2 = __ffma2_rn(zx, zx, __fmul2_rn(zy, zy));
-          const float2 d = make_float2(frcp_fast(n2.x), frcp_fast(n2.y));
-          const float2 ix = __fmul2_rn(zx, d);   // 1/z = (zx d, -zy d)
-          const float2 niy = __fmul2_rn(zy, d);  // -Im(1/z)
-          const float2 iy = make_float2(-niy.x, -niy.y);
-          const float2 qx = __fmul2_rn(ix, gr), qy = __fmul2_rn(iy, gr);
-          const float2 nqy = __fmul2_rn(iy, ngr);
-          float2 sx = s_Wx[w][p], sy = s_Wy[w][p];
-          for (int kk = p - 1; kk >= 0; --kk) {
-            const float2 tx = __ffma2_rn(sy, nqy, s_Wx[w][kk]);
-            const float2 ty = __ffma2_rn(sy, qx, s_Wy[w][kk]);
-            const float2 nsx = __ffma2_rn(sx, qx, tx);
-            sy = __ffma2_rn(sx, qy, ty);
-            sx = nsx;
-          }
-          FX[h] = __ffma2_rn(sx, ix, __ffma2_rn(sy, niy, FX[h]));
-          FY[h] = __ffma2_rn(sx, iy, __ffma2_rn(sy, ix, FY[h]));
-        }
-      } else {
+    if (!JAC) {
+      m2p_paired(sm, nw, p, dx, dy, FX, FY);
+    } else {
+      for (int w = 0; w < nw; ++w) {
+        const float4 gw = sm.s_wg[w];
 #pragma unroll
         for (int q = 0; q < kRpt; ++q) {
           const float2 z = make_float2(dx[q] - gw.x, dy[q] - gw.y);
           const float2 inv = cinv(z);
           const float2 qq = make_float2(inv.x * gw.z, inv.y * gw.z);
-          float2 s = make_float2(s_Wx[w][p].x, s_Wy[w][p].x);
-          for (int kk = p - 1; kk >= 0; --kk) s = cfma(s, qq, make_float2(s_Wx[w][kk].x, s_Wy[w][kk].x));
+          float2 s = make_float2(sm.s_Wx[w][p].x, sm.s_Wy[w][p].x);
+          for (int kk = p - 1; kk >= 0; --kk) s = cfma(s, qq, make_float2(sm.s_Wx[w][kk].x, sm.s_Wy[w][kk].x));
           fw[q] = cfma(s, inv, fw[q]);
-          float2 t = make_float2((float)(p + 1) * s_Wx[w][p].x, (float)(p + 1) * s_Wy[w][p].x);
+          float2 t = make_float2((float)(p + 1) * sm.s_Wx[w][p].x, (float)(p + 1) * sm.s_Wy[w][p].x);
           for (int kk = p - 1; kk >= 0; --kk)
-            t = cfma(t, qq, make_float2((float)(kk + 1) * s_Wx[w][kk].x, (float)(kk + 1) * s_Wy[w][kk].x));
+            t = cfma(t, qq, make_float2((float)(kk + 1) * sm.s_Wx[w][kk].x, (float)(kk + 1) * sm.s_Wy[w][kk].x));
           const float2 dd = cmul(t, cmul(inv, inv));
           dfw[q] = make_float2(dfw[q].x - dd.x, dfw[q].y - dd.y);
         }
@@ -319,68 +442,15 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   __syncthreads();
   const float ir = lp.ir;
   if constexpr (!JAC) {
-    // L2P by Horner's rule and the float-float lens equation for rays
-    // (2h, 2h+1) side by side in the two-lane float32 instructions
-    const float2 irr = make_float2(ir, ir), nirr = make_float2(-ir, -ir);
 #pragma unroll
     for (int h = 0; h < kRpt / 2; ++h) {
-      const float2 DXh = make_float2(dx[2 * h], dx[2 * h + 1]);
-      const float2 DYh = make_float2(dy[2 * h], dy[2 * h + 1]);
-      const float2 wx = __fmul2_rn(DXh, irr);
-      const float2 wy = __fmul2_rn(DYh, irr);
-      const float2 nwy = __fmul2_rn(DYh, nirr);
-      float2 fx = make_float2(0.f, 0.f), fy = make_float2(0.f, 0.f);
-      if (p >= 1) {
-        float2 sx = s_Lx[p], sy = s_Ly[p];
-        for (int l = p - 1; l >= 1; --l) {
-          const float2 tx = __ffma2_rn(sy, nwy, s_Lx[l]);
-          const float2 ty = __ffma2_rn(sy, wx, s_Ly[l]);
-          const float2 nsx = __ffma2_rn(sx, wx, tx);
-          sy = __ffma2_rn(sx, wy, ty);
-          sx = nsx;
-        }
-        fx = __ffma2_rn(sx, wx, __fmul2_rn(sy, nwy));
-        fy = __ffma2_rn(sx, wy, __fmul2_rn(sy, wx));
-      }
-      // f = L2P + M2P (the far W boxes)
-      fx = __fadd2_rn(fx, FX[h]);
-      fy = __fadd2_rn(fy, FY[h]);
-      // y1 = a x1 - Re f - near1, y2 = b x2 + Im f - near2 (alpha = conj f)
-      ff2 T1 = ff2_mul(A.af, ff2{DXh, make_float2(dxl[2 * h], dxl[2 * h + 1])});
-      T1 = ff2_sub(T1, fx);
-      T1 = ff2_sub(T1, ff2{N1[h].hi, N1[h].lo});
-      ff2 T2 = ff2_mul(A.bf, ff2{DYh, make_float2(dyl[2 * h], dyl[2 * h + 1])});
-      T2 = ff2_add(T2, fy);
-      T2 = ff2_sub(T2, ff2{N2[h].hi, N2[h].lo});
+      ff2 T1, T2;
+      l2p_lens_pair(sm, A, ir, h, dx, dy, dxl, dyl, N1[h], N2[h], FX[h], FY[h], T1, T2);
       if (PIX) {
-        const ff2 U = ff2_add(lg.U1f, ff2_mul(A.iduf, T1));
-        const ff2 V = ff2_add(lg.V1f, ff2_mul(A.idvf, T2));
-        const float2 ku2 = make_float2(floorf(U.hi.x), floorf(U.hi.y));
-        const float2 kv2 = make_float2(floorf(V.hi.x), floorf(V.hi.y));
-        const float2 fu2 = __fadd2_rn(fsub2(U.hi, ku2), U.lo);
-        const float2 fv2 = __fadd2_rn(fsub2(V.hi, kv2), V.lo);
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int q = 2 * h + c;
-          if (!ok[q]) continue;
-          const float uh = c ? U.hi.y : U.hi.x, vh = c ? V.hi.y : V.hi.x;
-          float ku = c ? ku2.y : ku2.x, kv = c ? kv2.y : kv2.x;
-          float fu = c ? fu2.y : fu2.x, fv = c ? fv2.y : fv2.x;
-          bool far = lg.far || !(fabsf(uh) < 5.0e8f) || !(fabsf(vh) < 5.0e8f);
-          if (fu < 0.f) { ku -= 1.f; fu += 1.f; } else if (fu >= 1.f) { ku += 1.f; fu -= 1.f; }
-          if (fv < 0.f) { kv -= 1.f; fv += 1.f; } else if (fv >= 1.f) { kv += 1.f; fv -= 1.f; }
-          // float -> int32 (|k| < 5e8); integer adds only afterwards
-          const int64_t iu = (int64_t)lg.U1i + (int)ku, iv = (int64_t)lg.V1i + (int)kv;
-          far = far || !(iu > -1073741824ll && iu < 1073741824ll && iv > -1073741824ll &&
-                         iv < 1073741824ll);
-          PixCorner pc;
-          if (!far) {
-            pc.iu = (int)iu; pc.fu = fu; pc.iv = (int)iv; pc.fv = fv;
-          } else {
-            pc.iu = 0x7fffffff; pc.fu = 0.f; pc.iv = 0x7fffffff; pc.fv = 0.f;
-          }
-          A.pix[oidx[q]] = pc;
-        }
+        PixCorner pc[2];
+        pix_pair(A, lg, T1, T2, pc);
+        if (ok[2 * h]) A.pix[oidx[2 * h]] = pc[0];
+        if (ok[2 * h + 1]) A.pix[oidx[2 * h + 1]] = pc[1];
       } else {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -401,12 +471,12 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
       float2 f = make_float2(0.f, 0.f), df = make_float2(0.f, 0.f);
       if (p >= 1) {
         const float2 w = make_float2(dx[q] * ir, dy[q] * ir);
-        float2 s = make_float2(s_Lx[p].x, s_Ly[p].x);
-        for (int l = p - 1; l >= 1; --l) s = cfma(s, w, make_float2(s_Lx[l].x, s_Ly[l].x));
+        float2 s = make_float2(sm.s_Lx[p].x, sm.s_Ly[p].x);
+        for (int l = p - 1; l >= 1; --l) s = cfma(s, w, make_float2(sm.s_Lx[l].x, sm.s_Ly[l].x));
         f = cmul(s, w);
-        float2 t = make_float2((float)p * s_Lx[p].x, (float)p * s_Ly[p].x);
+        float2 t = make_float2((float)p * sm.s_Lx[p].x, (float)p * sm.s_Ly[p].x);
         for (int l = p - 1; l >= 1; --l)
-          t = cfma(t, w, make_float2((float)l * s_Lx[l].x, (float)l * s_Ly[l].x));
+          t = cfma(t, w, make_float2((float)l * sm.s_Lx[l].x, (float)l * sm.s_Ly[l].x));
         df = make_float2(t.x * ir, t.y * ir);
       }
       f = f + fw[q];
@@ -448,6 +518,193 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
         A.jac[4 * oidx[q] + 3] = A.b + dre;
       }
     }
+  }
+}
+
+// ---- fused deflection + IPM (Sec. 2.4 steps 3-4 without a corner array) --
+// A block takes one work item (FuseItem: a rectangle of one leaf's grid
+// corners).  It evaluates the item's corners exactly as k_eval32 does (the
+// same leaf data, the same operations: a corner that two items of the leaf
+// share gets the same bits from both), keeps them in shared memory as pixel
+// coordinates, writes only those on the leaf's first or last corner row or
+// column to `edge`, and then maps every cell whose four corners lie in the
+// item with the warp IPM of k_ipm_cells (ill-conditioned cells by the whole
+// warp on the spot).  Cells on the leaf's last corner row or column are left
+// to the seam pass.
+constexpr int kFuseCorners = 1024;  // corners per item: two groups of kT x kRpt rays
+constexpr int kFuseSeg = 128;       // corner columns per item at most
+constexpr int kFuseWarps = kT / 32;
+
+template <bool UM>
+__global__ void __launch_bounds__(kT, 4) k_eval32_map(E32Args A, IpmArgs I, const FuseItem* items,
+                                                   PixCorner* edge) {
+  // the evaluation's staging and the IPM's per-warp staging are used one
+  // after the other
+  __shared__ union Stage {
+    E32Smem e;
+    struct {
+      WarpCells c[kFuseWarps];
+      int cut[kFuseWarps][128];  // cut pixels of the warp's float-float cell
+    } m;
+  } sm;
+  __shared__ PixCorner cs[kFuseCorners];
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const FuseItem it = items[blockIdx.x];
+  const int64_t k = it.leaf;
+  const LeafGrid lg = A.lgrid[k];
+  const int64_t i0 = A.rect[4 * k], ni = A.rect[4 * k + 1];
+  const int64_t j0 = A.rect[4 * k + 2], nj = A.rect[4 * k + 3];
+  const float ir = A.leaf[k].ir;
+  stage_local(sm.e, A, k, tid);
+  const int ncorn = it.w * it.h;
+  const int ngroups = (ncorn + kT * kRpt - 1) / (kT * kRpt);
+  const int64_t star0 = A.uoff[k], nstar = A.uoff[k + 1] - star0;
+  const int64_t w_beg = A.woff[k], w_end = A.woff[k + 1];
+  // a leaf whose near stars (W boxes) fill one staging chunk stages them once
+  const bool restage_stars = nstar > kChunk, restage_w = w_end - w_beg > kWChunk;
+  for (int g = 0; g < ngroups; ++g) {
+    float dx[kRpt], dy[kRpt], dxl[kRpt], dyl[kRpt];
+    int t[kRpt];
+    bool ok[kRpt];
+    uint32_t di[kRpt], dj[kRpt];
+    fcomp2 N1[kRpt / 2], N2[kRpt / 2];
+#pragma unroll
+    for (int h = 0; h < kRpt / 2; ++h) {
+      N1[h] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      N2[h] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    }
+#pragma unroll
+    for (int q = 0; q < kRpt; ++q) {
+      t[q] = g * (kT * kRpt) + q * kT + tid;
+      ok[q] = t[q] < ncorn;
+      dx[q] = dy[q] = dxl[q] = dyl[q] = 0.f;
+      di[q] = dj[q] = 0;
+      if (!ok[q]) continue;
+      const uint32_t r = (uint32_t)t[q] / (uint32_t)it.w, c = (uint32_t)t[q] - r * (uint32_t)it.w;
+      di[q] = (uint32_t)it.ci + c;
+      dj[q] = (uint32_t)it.cj + r;
+      grid_offset(A, lg, di[q], dj[q], dx[q], dxl[q], dy[q], dyl[q]);
+    }
+    for (int64_t f0 = 0; f0 < nstar; f0 += kChunk) {
+      const int nf = (int)min64(kChunk, nstar - f0);
+      const int nfg = (nf + kGroup - 1) / kGroup * kGroup;
+      if (g == 0 || restage_stars) {
+        __syncthreads();
+        stage_stars(sm.e, A, star0 + f0, nf, nfg, tid);
+        __syncthreads();
+      }
+      p2p_paired<UM>(sm.e, nfg, dx, dy, dxl, dyl, N1, N2);
+    }
+    if (UM && A.m0 != 1.f) {
+      const float2 m2 = make_float2(A.m0, A.m0);
+#pragma unroll
+      for (int h = 0; h < kRpt / 2; ++h) {
+        N1[h].hi = __fmul2_rn(N1[h].hi, m2); N1[h].lo = __fmul2_rn(N1[h].lo, m2);
+        N2[h].hi = __fmul2_rn(N2[h].hi, m2); N2[h].lo = __fmul2_rn(N2[h].lo, m2);
+      }
+    }
+    float2 FX[kRpt / 2], FY[kRpt / 2];
+#pragma unroll
+    for (int h = 0; h < kRpt / 2; ++h) { FX[h] = make_float2(0.f, 0.f); FY[h] = make_float2(0.f, 0.f); }
+    for (int64_t e0 = w_beg; e0 < w_end; e0 += kWChunk) {
+      const int nw = (int)min64(kWChunk, w_end - e0);
+      if (g == 0 || restage_w) {
+        __syncthreads();
+        stage_w(sm.e, A, e0, nw, tid);
+        __syncthreads();
+      }
+      m2p_paired(sm.e, nw, A.p, dx, dy, FX, FY);
+    }
+    if (g == 0) __syncthreads();  // the local coefficients, with no star or W chunk staged
+#pragma unroll
+    for (int h = 0; h < kRpt / 2; ++h) {
+      ff2 T1, T2;
+      l2p_lens_pair(sm.e, A, ir, h, dx, dy, dxl, dyl, N1[h], N2[h], FX[h], FY[h], T1, T2);
+      PixCorner pc[2];
+      pix_pair(A, lg, T1, T2, pc);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int q = 2 * h + c;
+        if (!ok[q]) continue;
+        cs[t[q]] = pc[c];
+        // corners on the leaf's boundary rows and columns: the seam cells'
+        if (di[q] == 0 || di[q] == (uint32_t)(ni - 1) || dj[q] == 0 || dj[q] == (uint32_t)(nj - 1))
+          edge[(j0 + (int64_t)dj[q] - A.grow0) * A.gnx1 + i0 + (int64_t)di[q]] = pc[c];
+      }
+    }
+  }
+  if (tid == 0) atomicAdd(&I.stats[15], (double)ncorn);
+  __syncthreads();  // every corner in cs; the evaluation's staging becomes the IPM's
+  // ---- IPM of the item's interior cells: 32 cells a round, rounds over the warps
+  const int cw = it.w - 1, nc = cw > 0 && it.h > 1 ? cw * (it.h - 1) : 0;
+  const int64_t crow0 = j0 + it.cj - A.grow0, ccol0 = i0 + it.ci;
+  Ledger led;
+  for (int rd = wp; rd * 32 < nc; rd += kFuseWarps) {
+    const int idx = rd * 32 + lane;
+    const bool has = idx < nc;
+    int64_t cid = 0;
+    PixCorner q4[4];
+    if (has) {
+      const int r = idx / cw, c = idx - r * cw;
+      const int b = r * it.w + c;
+      q4[0] = cs[b]; q4[1] = cs[b + 1]; q4[2] = cs[b + it.w + 1]; q4[3] = cs[b + it.w];
+      cid = (crow0 + r) * I.nx + ccol0 + c;
+    }
+    ipm_round<true>(I, sm.m.c[wp], lane, has, cid, q4, led, sm.m.cut[wp]);
+    __syncwarp();
+  }
+  block_add_stats<kFuseWarps>(I.stats, led, I.wcell);
+}
+
+// Per active leaf: its work items and its seam cells (the chunk's cells on
+// the leaf's last corner column or row).  jlast: the chunk's last cell row.
+__global__ void k_fuse_count(const int64_t* __restrict__ rect, int64_t nl, int64_t nx, int64_t jlast,
+                             int64_t* __restrict__ nitem, int64_t* __restrict__ nseam) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nl) return;
+  const int64_t i0 = rect[4 * k], ni = rect[4 * k + 1], j0 = rect[4 * k + 2], nj = rect[4 * k + 3];
+  if (ni <= 0 || nj <= 0) { nitem[k] = 0; nseam[k] = 0; return; }
+  const int64_t sw = ni < kFuseSeg ? ni : kFuseSeg;
+  const int64_t nseg = ni <= kFuseSeg ? 1 : (ni - 1 + kFuseSeg - 2) / (kFuseSeg - 1);
+  const int64_t bh = min64(nj, max64(2, kFuseCorners / sw));
+  const int64_t nband = nj <= bh ? 1 : (nj - 1 + bh - 2) / (bh - 1);
+  nitem[k] = nseg * nband;
+  const int64_t right = i0 + ni - 1 <= nx - 1 ? max64(0, min64(j0 + nj - 1, jlast) - j0 + 1) : 0;
+  const int64_t top = j0 + nj - 1 <= jlast ? ni - 1 : 0;
+  nseam[k] = right + top;
+}
+
+// One warp per active leaf: its items (segments x bands) and seam cell ids.
+__global__ void k_fuse_fill(const int64_t* __restrict__ rect, int64_t nl, int64_t nx, int64_t jlast,
+                            int64_t grow0, const int64_t* __restrict__ ioff,
+                            const int64_t* __restrict__ soff, FuseItem* __restrict__ items,
+                            int* __restrict__ seam) {
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= nl) return;
+  const int64_t i0 = rect[4 * k], ni = rect[4 * k + 1], j0 = rect[4 * k + 2], nj = rect[4 * k + 3];
+  if (ni <= 0 || nj <= 0) return;
+  const int64_t sw = ni < kFuseSeg ? ni : kFuseSeg;
+  const int64_t nseg = ni <= kFuseSeg ? 1 : (ni - 1 + kFuseSeg - 2) / (kFuseSeg - 1);
+  const int64_t bh = min64(nj, max64(2, kFuseCorners / sw));
+  const int64_t nitems = ioff[k + 1] - ioff[k];
+  for (int64_t e = lane; e < nitems; e += 32) {
+    const int64_t b = e / nseg, sg = e - b * nseg;
+    FuseItem it;
+    it.leaf = (int)k;
+    it.ci = (int)(sg * (kFuseSeg - 1));
+    it.w = (int)min64(sw, ni - it.ci);
+    it.cj = (int)(b * (bh - 1));
+    it.h = (int)min64(bh, nj - it.cj);
+    items[ioff[k] + e] = it;
+  }
+  const int64_t right = i0 + ni - 1 <= nx - 1 ? max64(0, min64(j0 + nj - 1, jlast) - j0 + 1) : 0;
+  const int64_t ns = soff[k + 1] - soff[k];
+  for (int64_t e = lane; e < ns; e += 32) {
+    int64_t i, j;
+    if (e < right) { i = i0 + ni - 1; j = j0 + e; }
+    else { i = i0 + (e - right); j = j0 + nj - 1; }
+    seam[soff[k] + e] = (int)((j - grow0) * nx + i);
   }
 }
 
@@ -735,16 +992,75 @@ void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int2* ti
   A.grow0 = g.row0;
   A.y = y; A.jac = jac; A.pix = pix;
   if (px) { A.iduf = ff_of(ip->inv_du); A.idvf = ff_of(ip->inv_dv); }
-  std::pair<cudaEvent_t, cudaEvent_t> e;
-  if (P.timing) e = event_pair_begin(s);
   wait_expansions(P, s);
   leaf_grid(px ? 3 : 1);
+  // kernel time only: the events follow the wait for the plan's expansions
+  std::pair<cudaEvent_t, cudaEvent_t> e;
+  if (P.timing) e = event_pair_begin(s);
   if (px) launch32<true, true>(A, total, false, s);
   else launch32<true, false>(A, total, jac != nullptr, s);
   if (P.timing) {
     event_pair_end(e, s);
     P.ev_eval.push_back(e);
   }
+}
+
+Scratch eval32_fused(Plan& P, const GridRows& g, const int64_t* rect, PixCorner* edge,
+                     const IpmParams& ip, float* map32, float* rowdiff, double* stats_dev, int* rq,
+                     int* rqcount, int64_t& nseam, cudaStream_t s) {
+  const int64_t nl = P.n_active_leaves;
+  const int64_t jlast = g.row0 + g.nrows - 2;  // the chunk's last cell row
+  Scratch cnt(&P.da, sizeof(int64_t) * (nl + 1)), scnt(&P.da, sizeof(int64_t) * (nl + 1));
+  Scratch ioff(&P.da, sizeof(int64_t) * (nl + 1)), soff(&P.da, sizeof(int64_t) * (nl + 1));
+  LENS_CUDA(cudaMemsetAsync(cnt.as<int64_t>() + nl, 0, sizeof(int64_t), s));
+  LENS_CUDA(cudaMemsetAsync(scnt.as<int64_t>() + nl, 0, sizeof(int64_t), s));
+  k_fuse_count<<<grid_for(nl, 128), 128, 0, s>>>(rect, nl, g.nx, jlast, cnt.as<int64_t>(),
+                                                 scnt.as<int64_t>());
+  LENS_LAUNCHED("k_fuse_count");
+  exclusive_scan_i64(cnt.as<int64_t>(), ioff.as<int64_t>(), nl + 1, P.da, s);
+  exclusive_scan_i64(scnt.as<int64_t>(), soff.as<int64_t>(), nl + 1, P.da, s);
+  int64_t tot[2] = {0, 0};
+  const int64_t* addr[2] = {ioff.as<int64_t>() + nl, soff.as<int64_t>() + nl};
+  read_i64(addr, 2, tot, P.da, s);
+  const int64_t nitems = tot[0];
+  nseam = tot[1];
+  if (nitems > (int64_t)INT32_MAX) fail(LENS_EINVAL, "too many work items in one chunk");
+  Scratch items(&P.da, sizeof(FuseItem) * (size_t)std::max<int64_t>(nitems, 1));
+  Scratch seam(&P.da, sizeof(int) * (size_t)std::max<int64_t>(nseam, 1));
+  k_fuse_fill<<<grid_for(nl * 32, 128), 128, 0, s>>>(rect, nl, g.nx, jlast, g.row0,
+                                                    ioff.as<int64_t>(), soff.as<int64_t>(),
+                                                    items.as<FuseItem>(), seam.as<int>());
+  LENS_LAUNCHED("k_fuse_fill");
+  Scratch lg(&P.da, sizeof(LeafGrid) * (nl + 1));
+  E32Args A = base_args32(P);
+  A.rect = rect;
+  A.lgrid = lg.as<LeafGrid>();
+  A.hf = ff_of(g.h);
+  A.gnx1 = g.nx + 1;
+  A.grow0 = g.row0;
+  A.iduf = ff_of(ip.inv_du);
+  A.idvf = ff_of(ip.inv_dv);
+  IpmArgs I{};
+  I.nx = g.nx; I.map = map32; I.D = rowdiff; I.ldd = (int64_t)ip.npx + 1; I.stats = stats_dev;
+  I.ip = ip; I.wcell = 1.f; I.rq = rq; I.rqcount = rqcount;
+  ipm_prepare(I);
+  wait_expansions(P, s);
+  k_leaf_grid<<<grid_for(nl, 128), 128, 0, s>>>(nl, P.f_leaf, rect, g.x0, g.y0, g.h, 3, ip.inv_du,
+                                                -ip.u0 * ip.inv_du, ip.inv_dv, -ip.v0 * ip.inv_dv,
+                                                lg.as<LeafGrid>());
+  LENS_LAUNCHED("k_leaf_grid");
+  std::pair<cudaEvent_t, cudaEvent_t> e;
+  if (P.timing) e = event_pair_begin(s);
+  if (nitems > 0) {
+    if (A.unit_mass) k_eval32_map<true><<<(unsigned)nitems, kT, 0, s>>>(A, I, items.as<FuseItem>(), edge);
+    else k_eval32_map<false><<<(unsigned)nitems, kT, 0, s>>>(A, I, items.as<FuseItem>(), edge);
+    LENS_LAUNCHED("k_eval32_map");
+  }
+  if (P.timing) {
+    event_pair_end(e, s);
+    P.ev_fused.push_back(e);
+  }
+  return seam;
 }
 
 void eval32_rays(Plan& P, const double* rays, const int64_t* off, const int* perm,

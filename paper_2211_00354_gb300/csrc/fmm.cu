@@ -532,8 +532,10 @@ void fmm_downward(Plan& P, cudaStream_t s) {
   A.a0 = 0;
   A.a1 = P.n_active;
   if (A.a1 > 0) {
+    if (P.ev_far0) LENS_CUDA(cudaEventRecord(P.ev_far0, s));
     k_far_local<<<grid_for(A.a1 * 32, 32 * kWarpsPerBlock), 32 * kWarpsPerBlock, smem, s>>>(A);
     LENS_LAUNCHED("k_far_local");
+    if (P.ev_far1) LENS_CUDA(cudaEventRecord(P.ev_far1, s));
   }
   const int P1 = P.p + 1;
   for (int l = 2; l < P.nlevels; ++l) {

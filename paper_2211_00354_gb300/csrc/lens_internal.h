@@ -184,19 +184,23 @@ struct Plan {
   // waits on ev_tree.
   cudaStream_t fmm_stream = nullptr;
   cudaEvent_t ev_start = nullptr, ev_boxes = nullptr, ev_tree = nullptr, ev_fmm = nullptr;
+  // around the far-field launch (M2L over V, P2L over X) on the plan's stream
+  cudaEvent_t ev_far0 = nullptr, ev_far1 = nullptr;
   bool build_timed = false;
 
   // per-active-index count of stars in the U list (work accounting)
   int64_t* ustar_cnt = nullptr;
   // optional kernel timing and work counters (lens_ipm_map turns them on)
   bool timing = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_eval, ev_ipm;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_eval, ev_ipm, ev_fused;
   double* work = nullptr;  // device [4]: rays, p2p pairs, m2p evals, spare
   void ev_clear() {
     for (auto& e : ev_eval) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     for (auto& e : ev_ipm) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    for (auto& e : ev_fused) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     ev_eval.clear();
     ev_ipm.clear();
+    ev_fused.clear();
   }
 
   void* dalloc(size_t bytes) {
@@ -276,6 +280,11 @@ void ipm_accumulate(const PixCorner* yc, int64_t nx, int64_t nrows_cells, const 
                     float* map32, float* rowdiff, double* stats_dev, int* queue, int* qcount,
                     int* rq, int* rqcount, cudaStream_t s,
                     std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev);
+// ipm_accumulate over a list of n cells (ids j * nx + i into yc's grid)
+void ipm_accumulate_list(const PixCorner* yc, int64_t nx, const int* list, int64_t n,
+                         const IpmParams& ip, float* map32, float* rowdiff, double* stats_dev,
+                         int* queue, int* qcount, int* rq, int* rqcount, cudaStream_t s,
+                         std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev);
 // One refinement level: each of the np queued cells (cells of the chunk
 // starting at grid row grow0 when org_in is NULL, else sub-cells with
 // lower-left corners org_in[]) of side h is split into 2 x 2 sub-cells of
@@ -304,6 +313,29 @@ void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int2* ti
                  cudaStream_t s);
 void eval32_rays(Plan& P, const double* rays, const int64_t* off, const int* perm,
                  const int2* tile_leaf, int64_t total, double* y, double* jac, cudaStream_t s);
+// The fused deflection + IPM path (eval32.cu, float32-bulk plans).  A work
+// item is a rectangle of one leaf's grid corners: w x h corners from corner
+// (ci, cj) counted from the leaf's first ray; the items of a leaf overlap by
+// one corner row / column, which both evaluate from the leaf's data to the
+// same bits.  The kernel maps every cell whose four corners lie in its item;
+// the cells on a leaf's last corner row or column (their other corners
+// belong to neighbouring leaves) are mapped afterwards from the corners on
+// leaf boundaries, the only ones written to device memory (`edge`, in the
+// chunk's grid layout).  Returns the seam cells (ids j * nx + i in the chunk)
+// and their count.
+struct FuseItem {
+  int leaf;    // active-leaf index
+  int ci, cj;  // first corner of the item, relative to the leaf's first ray
+  int w, h;    // corners in the item
+};
+struct IpmArgs;
+void ipm_prepare(IpmArgs& A);
+Scratch eval32_fused(Plan& P, const GridRows& g, const int64_t* rect, PixCorner* edge,
+                     const IpmParams& ip, float* map32, float* rowdiff, double* stats_dev, int* rq,
+                     int* rqcount, int64_t& nseam, cudaStream_t s);
+void evaluate_grid_fused(Plan& P, const GridRows& g, PixCorner* edge, const IpmParams& ip,
+                         float* map32, float* rowdiff, double* stats_dev, int* queue, int* qcount,
+                         int* rq, int* rqcount, cudaStream_t s);
 // map (float64 output) = map32 + row-wise prefix sums of rowdiff, or += with
 // `accumulate`; `clear` zeroes map32 and rowdiff behind the read
 void ipm_finish_map(float* map32, float* rowdiff, int npx, int npy, double* map, bool accumulate,

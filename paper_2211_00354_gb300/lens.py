@@ -32,10 +32,12 @@ STATUS_NAMES = {0: "LENS_OK", 1: "LENS_EINVAL", 2: "LENS_ENOMEM", 3: "LENS_ECUDA
 
 FP64 = 0
 FP32_BULK = 1
+MAP_FUSED = 1
+MAP_SEPARATE = 2
 
 # Every symbol include/lens.h declares (checked by the ABI tests).
 EXPORTED = ("lens_fmm_build", "lens_deflect", "lens_deflect_grid", "lens_ipm_map",
-            "lens_ipm_map_refined",
+            "lens_ipm_map_refined", "lens_ipm_map_ex",
             "lens_deflect_adjoint", "lens_plan_info_get", "lens_plan_destroy",
             "lens_direct_deflect", "lens_direct_deflect_noalloc", "lens_light_curve",
             "lens_light_curve_grad", "lens_map_source", "lens_map_histogram", "lens_map_track",
@@ -78,7 +80,8 @@ class lens_ipm_stats(ctypes.Structure):
                 ("cells_ext", ctypes.c_double),
                 ("ms_eval_kernel", ctypes.c_double),
                 ("ms_ipm_kernel", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("cells_refined", ctypes.c_double)]
+                ("cells_refined", ctypes.c_double), ("fused", ctypes.c_int64),
+                ("ms_fused_kernel", ctypes.c_double), ("rays_evaluated", ctypes.c_double)]
 
 
 class lens_plan_info(ctypes.Structure):
@@ -90,7 +93,8 @@ class lens_plan_info(ctypes.Structure):
                 ("leaf_size", ctypes.c_int), ("prec", ctypes.c_int),
                 ("root_lo", ctypes.c_double * 2), ("root_size", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("ms_build", ctypes.c_double),
-                ("build_launches", ctypes.c_int64), ("ms_tree", ctypes.c_double)]
+                ("build_launches", ctypes.c_int64), ("ms_tree", ctypes.c_double),
+                ("ms_far_local", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -139,6 +143,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lens_ipm_map_refined.argtypes = [vp, ctypes.POINTER(lens_grid), ctypes.POINTER(lens_box),
                                          i, i, i64, i, i, vp, ctypes.POINTER(lens_ipm_stats), vp]
     lib.lens_ipm_map_refined.restype = st
+    lib.lens_ipm_map_ex.argtypes = [vp, ctypes.POINTER(lens_grid), ctypes.POINTER(lens_box),
+                                    i, i, i64, i, i, ctypes.c_uint, vp,
+                                    ctypes.POINTER(lens_ipm_stats), vp]
+    lib.lens_ipm_map_ex.restype = st
     lib.lens_deflect_adjoint.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
     lib.lens_deflect_adjoint.restype = st
     lib.lens_plan_info_get.argtypes = [vp, ctypes.POINTER(lens_plan_info)]
@@ -327,23 +335,21 @@ class LensFMM:
 
     def ipm_map(self, grid, box, npx: int, npy: int, max_cells_per_chunk: int = 0,
                 bbox_cap: int = 0, out: Optional[torch.Tensor] = None, stream=None,
-                refine_levels: int = 0):
-        """Magnification map (lens_ipm_map; lens_ipm_map_refined when
-        refine_levels > 0: cells over bbox_cap split 2 x 2 instead of dropped)."""
+                refine_levels: int = 0, fused: Optional[bool] = None):
+        """Magnification map (lens_ipm_map_ex: refine_levels > 0 splits cells
+        over bbox_cap 2 x 2 instead of dropping them; fused True / False picks
+        the fused deflection + IPM kernel or the separate kernels, None the
+        library's default)."""
         g = grid_struct(grid)
         b = lens_box(*(float(v) for v in box))
         dev = torch.device("cuda", torch.cuda.current_device())
         mp = out if out is not None else torch.empty((npy, npx), dtype=torch.float64, device=dev)
         st = lens_ipm_stats()
-        if refine_levels:
-            _check(_lib.lens_ipm_map_refined(self._handle, ctypes.byref(g), ctypes.byref(b),
-                                             int(npx), int(npy), int(max_cells_per_chunk),
-                                             int(bbox_cap), int(refine_levels), mp.data_ptr(),
-                                             ctypes.byref(st), _stream_ptr(stream)))
-        else:
-            _check(_lib.lens_ipm_map(self._handle, ctypes.byref(g), ctypes.byref(b), int(npx),
-                                     int(npy), int(max_cells_per_chunk), int(bbox_cap),
-                                     mp.data_ptr(), ctypes.byref(st), _stream_ptr(stream)))
+        flags = 0 if fused is None else (MAP_FUSED if fused else MAP_SEPARATE)
+        _check(_lib.lens_ipm_map_ex(self._handle, ctypes.byref(g), ctypes.byref(b), int(npx),
+                                    int(npy), int(max_cells_per_chunk), int(bbox_cap),
+                                    int(refine_levels), flags, mp.data_ptr(), ctypes.byref(st),
+                                    _stream_ptr(stream)))
         stats = {name: getattr(st, name) for name, _ in lens_ipm_stats._fields_}
         return mp, stats
 
