@@ -33,6 +33,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
 METRIC = "FMM rays deflected/s at stated error vs GPU direct sum; IPM map time (1xGB300)"
+FUSED = {"default": None, "fused": True, "separate": False}
 UNIT = "rays/s"
 # Fallbacks when the pipe micro-benchmark cannot run: unit counts x the
 # maximum SM clock (float32: 152 SMs x 128 lanes x 2 flops; float64: the
@@ -98,6 +99,9 @@ def parse():
                          "critical curve, 8192^2 map in chunks; nfw: deflection of a 4096^2 grid "
                          "by a 1e7-particle elliptical NFW halo; differentiation: forward + "
                          "adjoint of a Gaussian-source light-curve loss (1e5 stars, 3e6 rays)")
+    ap.add_argument("--map-path", default="default", choices=["default", "fused", "separate"],
+                    help="the fused deflection + IPM kernel, the separate kernels, or the "
+                         "library's default")
     ap.add_argument("--p-arms", default="8,24",
                     help="high_mag: also time whole maps at these orders (comma list, '' = none)")
     return ap.parse_args()
@@ -538,7 +542,7 @@ def main():
         P = lens.LensFMM(stars, masses, f.kappa_s, f.gamma, p=args.p, leaf_size=args.leaf,
                          prec=prec, target_box=target)
         _, st = P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp,
-                          refine_levels=args.refine)
+                          refine_levels=args.refine, fused=FUSED[args.map_path])
         if strips:
             ldist.allreduce_map(mp)  # the path's one exchange: sum of the strip maps
         info = P.info()
@@ -587,7 +591,7 @@ def main():
     m2p = stats[-1]["m2p_evals"]
     eval_flops = 10.0 * pairs + 8.0 * (args.p + 1) * (rays_step + m2p)
     launches = stats[-1]["chunks"]
-    eval_tflops = eval_flops / (ms_eval / 1e3) / 1e12
+    eval_tflops = eval_flops / (ms_eval / 1e3) / 1e12 if ms_eval > 0 else 0.0
     if pipes:
         fp32_peak = max(pipes["ffma_tflops"], pipes["ffma2_tflops"])
         fp32_src = "measured: pipe_peaks.cu, max of FFMA and paired FFMA2 (%.1f / %.1f TFLOP/s)" % (
@@ -605,7 +609,7 @@ def main():
     # ray plus 8 B (read + write of a float) per atomic map or difference
     # array update
     ipm_bytes = 16.0 * rays_step + 8.0 * stats[-1]["ipm_updates"]
-    ipm_gbs = ipm_bytes / (ms_ipm / 1e3) / 1e9
+    ipm_gbs = ipm_bytes / (ms_ipm / 1e3) / 1e9 if ms_ipm > 0 else 0.0
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(HERE, "MEASURED_PEAKS.json")))
@@ -614,7 +618,21 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     ipm_traffic = measured_traffic("k_ipm_cells", "ipm.cu", rays_step / launches)
     eval_traffic = measured_traffic("k_eval32", "eval32.cu", rays_step / launches)
-    if ms_eval >= ms_ipm:
+    fused_on = bool(stats[-1].get("fused", 0))
+    ms_fused = sum(s_["ms_fused_kernel"] for s_ in stats) / K
+    if fused_on:
+        # one kernel deflects and maps (the seam cells' pass is ms_ipm): its
+        # float32 work against the FP32 peak, and its map updates (8 B each,
+        # the only algorithmic traffic once no corner array exists) against HBM
+        f_tflops = eval_flops / (ms_fused / 1e3) / 1e12
+        f_gbs = 8.0 * stats[-1]["ipm_updates"] / (ms_fused / 1e3) / 1e9
+        roof = {"bound": "alu", "kernel": "k_eval32_map (fused deflection + IPM)",
+                "achieved": f_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": f_tflops / fp32_peak, "traffic": None, "peak_source": fp32_src,
+                "ms_per_launch": ms_fused / launches,
+                "map_updates_gbs": f_gbs, "map_updates_frac_of_hbm": f_gbs / hbm_peak,
+                "seam_pass_ms": ms_ipm}
+    elif ms_eval >= ms_ipm:
         roof = {"bound": "alu", "kernel": "k_eval (fused L2P+P2P+M2P)",
                 "achieved": eval_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": eval_tflops / fp32_peak, "traffic": eval_traffic,
@@ -706,7 +724,8 @@ def main():
                 a0.record(stream)
                 PA = lens.LensFMM(stars, masses, f.kappa_s, f.gamma, p=pa, leaf_size=args.leaf,
                                   prec=prec, target_box=target)
-                _, sta = PA.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp)
+                _, sta = PA.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp,
+                                    fused=FUSED[args.map_path])
                 a1.record(stream)
                 torch.cuda.synchronize()
                 if it > 0:
@@ -755,7 +774,7 @@ def main():
             P = lens.LensFMM(d_stars, d_masses, f.kappa_s, f.gamma, p=args.p, leaf_size=args.leaf,
                              prec=prec, target_box=target)
             P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=args.cap, out=mp,
-                      refine_levels=args.refine)
+                      refine_levels=args.refine, fused=FUSED[args.map_path])
             if strips:
                 ldist.allreduce_map(mp)
             h_map.copy_(mp, non_blocking=True)
@@ -803,10 +822,12 @@ def main():
             "omega_per_s": 10.0 * f.npx * f.npy * f.n * (1 if strips else world) / (ms / 1e3),
             "phase_ms": {"build": info["ms_build"], "tree": info["ms_tree"],
                          "deflect": st["ms_deflect"],
-                         "ipm": st["ms_ipm"], "eval_kernel": ms_eval, "ipm_kernels": ms_ipm},
+                         "ipm": st["ms_ipm"], "eval_kernel": ms_eval, "ipm_kernels": ms_ipm,
+                         "fused_kernel": ms_fused},
+            "map_path": "fused" if fused_on else "separate",
             "work": {"rays": rays_step, "p2p_pairs": pairs, "m2p_evals": m2p,
                      "ipm_updates": st["ipm_updates"], "cells_queued": st["cells_queued"],
-                     "cells_ext": st["cells_ext"],
+                     "cells_ext": st["cells_ext"], "rays_evaluated": st["rays_evaluated"],
                      "pairs_per_ray": pairs / rays_step},
             "tree": {k: info[k] for k in ("n_boxes", "n_active_boxes", "n_active_leaves", "n_v",
                                           "n_x", "n_u", "n_w", "levels")},

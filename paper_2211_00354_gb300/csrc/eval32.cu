@@ -633,13 +633,18 @@ __global__ void __launch_bounds__(kT, 4) k_eval32_map(E32Args A, IpmArgs I, cons
       }
     }
   }
-  if (tid == 0) atomicAdd(&I.stats[15], (double)ncorn);
+  __shared__ int next_round;
+  if (tid == 0) {
+    atomicAdd(&I.stats[15], (double)ncorn);
+    next_round = kFuseWarps;
+  }
   __syncthreads();  // every corner in cs; the evaluation's staging becomes the IPM's
-  // ---- IPM of the item's interior cells: 32 cells a round, rounds over the warps
+  // ---- IPM of the item's interior cells: 32 cells a round, each warp taking
+  // the next round from a counter (cells near a star cost many times more)
   const int cw = it.w - 1, nc = cw > 0 && it.h > 1 ? cw * (it.h - 1) : 0;
   const int64_t crow0 = j0 + it.cj - A.grow0, ccol0 = i0 + it.ci;
   Ledger led;
-  for (int rd = wp; rd * 32 < nc; rd += kFuseWarps) {
+  for (int rd = wp; rd * 32 < nc;) {
     const int idx = rd * 32 + lane;
     const bool has = idx < nc;
     int64_t cid = 0;
@@ -652,6 +657,9 @@ __global__ void __launch_bounds__(kT, 4) k_eval32_map(E32Args A, IpmArgs I, cons
     }
     ipm_round<true>(I, sm.m.c[wp], lane, has, cid, q4, led, sm.m.cut[wp]);
     __syncwarp();
+    int nxt = 0;
+    if (lane == 0) nxt = atomicAdd(&next_round, 1);
+    rd = __shfl_sync(0xffffffffu, nxt, 0);
   }
   block_add_stats<kFuseWarps>(I.stats, led, I.wcell);
 }
