@@ -17,7 +17,9 @@
 // where Phi_j, Psi_j give dL/dm_j = Re Phi_j and dL/dz_j = Psi_j, i.e.
 // dL/dx_j = Re Psi_j, dL/dy_j = -Im Psi_j.  The smooth field adds
 // dL/dkappa_s = -sum_r (g1 x1 + g2 x2), dL/dgamma = sum_r (-g1 x1 + g2 x2).
-// Everything here is float64 and deterministic up to the order of atomic adds.
+// For float64 plans everything here is float64; float32-bulk plans run the
+// per-ray and per-pair operators in float32 (below).  Deterministic up to the
+// order of atomic adds.
 #include <cmath>
 
 #include "cx.cuh"
@@ -166,6 +168,126 @@ __global__ void __launch_bounds__(128) k_adj_p2p(AdjArgs A) {
       atomic_add2(A.Psi + sj, make_double2(mj * G.x, mj * G.y));
     }
     base += ns;
+  }
+}
+
+// ---- float32 bulk (plans of precision LENS_FP32_BULK) ------------------------
+// The per-ray and per-pair parts of the adjoint in float32, as the forward
+// pass evaluates them: P2P^T on float-float offsets from the leaf centre
+// (each pair's difference exact to float32 rounding however close a ray is
+// to a star), partial sums compensated; L2P^T / M2P^T moments with the
+// scaled offsets w rounded once to float32 (|w| <= ~1.5: no cancellation),
+// summed per lane in float32 and across lanes in float64.  The transposed
+// translations (L2L^T, M2L^T, P2L^T, M2M^T, P2M^T) stay float64.
+
+// P2P^T: block per (leaf, tile of rays), threads over the U-list stars; the
+// tile's rays staged as float-float offsets from the leaf centre with their
+// float32 charges.
+__global__ void __launch_bounds__(128) k_adj_p2p32(AdjArgs A) {
+  __shared__ float4 sz[kAdjTile];  // x_hi, y_hi, x_lo, y_lo
+  __shared__ float2 sc[kAdjTile];
+  const int64_t k = leaf_of_tile(A.tile_off, A.nleaf, blockIdx.x);
+  const int B = A.leaves[k];
+  const int a = A.aidx[B];
+  const int64_t tile = (int64_t)blockIdx.x - A.tile_off[k];
+  const int64_t n = A.ray_off[k + 1] - A.ray_off[k];
+  const int64_t r0 = tile * kAdjTile;
+  const int nr = (int)min64(kAdjTile, n - r0);
+  const double rB = box_r(A, B);
+  const double2 cB = box_c(A, B, rB);
+  for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+    const int64_t ridx = A.perm[A.ray_off[k] + r0 + t];
+    const ff ox = ff_of(A.rays[2 * ridx] - cB.x), oy = ff_of(A.rays[2 * ridx + 1] - cB.y);
+    sz[t] = make_float4(ox.hi, oy.hi, ox.lo, oy.lo);
+    sc[t] = make_float2((float)-A.gy[2 * ridx], (float)-A.gy[2 * ridx + 1]);
+  }
+  __syncthreads();
+  for (int64_t e = A.U_off[a]; e < A.U_off[a + 1]; ++e) {
+    const int C = A.U_list[e];
+    const int s0 = A.start[C], ns = A.count[C];
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+      const int sj = s0 + j;
+      const double2 zj = A.spos[sj];
+      const ff sx = ff_of(zj.x - cB.x), sy = ff_of(zj.y - cB.y);
+      fcomp F1{0.f, 0.f}, F2{0.f, 0.f}, G1{0.f, 0.f}, G2{0.f, 0.f};
+      for (int t = 0; t < nr; ++t) {
+        const float4 z = sz[t];
+        const float2 c = sc[t];
+        // d = z_r - z_j; 1/d = conj(d) / |d|^2 (a star exactly at the ray adds
+        // nothing: d = 0 makes both terms 0 under the floor on |d|^2)
+        const float d1 = (z.x - sx.hi) + (z.z - sx.lo), d2 = (z.y - sy.hi) + (z.w - sy.lo);
+        const float w = frcp_fast(fmaf(d1, d1, fmaf(d2, d2, 1e-30f)));
+        const float i1 = d1 * w, i2 = -d2 * w;
+        const float c1 = c.x * i1 - c.y * i2, c2 = c.x * i2 + c.y * i1;  // c / d
+        F1.add(c1); F2.add(c2);
+        G1.add(c1 * i1 - c2 * i2); G2.add(c1 * i2 + c2 * i1);             // c / d^2
+      }
+      const double mj = A.smass[sj];
+      atomic_add2(A.Phi + sj, make_double2(F1.value(), F2.value()));
+      atomic_add2(A.Psi + sj, make_double2(mj * G1.value(), mj * G2.value()));
+    }
+  }
+}
+
+// L2P^T and M2P^T moments in float32: one warp per (leaf, tile), as
+// k_adj_leaf_moments.
+__global__ void __launch_bounds__(32) k_adj_leaf_moments32(AdjArgs A) {
+  extern __shared__ float2 acc32[];  // [(p+1)][32]
+  const int lane = threadIdx.x;
+  const int64_t k = leaf_of_tile(A.tile_off, A.nleaf, blockIdx.x);
+  const int B = A.leaves[k];
+  const int a = A.aidx[B];
+  const int64_t tile = (int64_t)blockIdx.x - A.tile_off[k];
+  const int64_t n = A.ray_off[k + 1] - A.ray_off[k];
+  const int64_t r0 = tile * kAdjTile;
+  const int64_t r1 = min64(n, r0 + kAdjTile);
+  const int p = A.p;
+  const double rB = box_r(A, B);
+  const double2 cB = box_c(A, B, rB);
+  const double irB = 1.0 / rB;
+  const int64_t nW = A.W_off[a + 1] - A.W_off[a];
+  for (int64_t pass = 0; pass <= nW; ++pass) {
+    for (int l = 0; l <= p; ++l) acc32[l * 32 + lane] = make_float2(0.f, 0.f);
+    int C = -1;
+    double rC = 0;
+    double2 cC = make_double2(0, 0);
+    if (pass > 0) {
+      C = A.W_list[A.W_off[a] + pass - 1];
+      rC = box_r(A, C);
+      cC = box_c(A, C, rC);
+    }
+    for (int64_t t = r0 + lane; t < r1; t += 32) {
+      const int64_t ridx = A.perm[A.ray_off[k] + t];
+      const float2 c = make_float2((float)-A.gy[2 * ridx], (float)-A.gy[2 * ridx + 1]);
+      float2 pw, w;
+      if (pass == 0) {
+        w = make_float2((float)((A.rays[2 * ridx] - cB.x) * irB),
+                        (float)((A.rays[2 * ridx + 1] - cB.y) * irB));
+        pw = c;
+      } else {
+        const float2 inv = cinv(make_float2((float)(A.rays[2 * ridx] - cC.x),
+                                            (float)(A.rays[2 * ridx + 1] - cC.y)));
+        w = make_float2(inv.x * (float)rC, inv.y * (float)rC);
+        pw = cmul(c, inv);
+      }
+      for (int l = 0; l <= p; ++l) {
+        acc32[l * 32 + lane] = acc32[l * 32 + lane] + pw;
+        pw = cmul(pw, w);
+      }
+    }
+    __syncwarp();
+    double2* dst = pass == 0 ? A.Lh + (int64_t)B * (p + 1) : A.Mh + (int64_t)C * (p + 1);
+    for (int l = 0; l <= p; ++l) {
+      const float2 vf = acc32[l * 32 + lane];
+      double2 v = make_double2(vf.x, vf.y);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      if (lane == 0 && (v.x != 0.0 || v.y != 0.0)) atomic_add2(dst + l, v);
+    }
+    __syncwarp();
   }
 }
 
@@ -359,7 +481,13 @@ void adjoint(Plan& P, const double* rays, int64_t m, const double* gy, double* g
   A.Lh = Lh.as<double2>(); A.Mh = Mh.as<double2>();
   A.Phi = Phi.as<double2>(); A.Psi = Psi.as<double2>();
   if (RB.total > (int64_t)INT32_MAX) fail(LENS_EINVAL, "too many rays in one adjoint call");
-  if (RB.total > 0) {
+  if (RB.total > 0 && P.prec == LENS_FP32_BULK) {
+    const size_t smem = sizeof(float2) * (size_t)P1 * 32;
+    k_adj_leaf_moments32<<<(unsigned)RB.total, 32, smem, s>>>(A);
+    LENS_LAUNCHED("k_adj_leaf_moments32");
+    k_adj_p2p32<<<(unsigned)RB.total, 128, 0, s>>>(A);
+    LENS_LAUNCHED("k_adj_p2p32");
+  } else if (RB.total > 0) {
     const size_t smem = sizeof(double2) * (size_t)P1 * 32;
     if (smem > 48 * 1024)
       LENS_CUDA(cudaFuncSetAttribute(k_adj_leaf_moments, cudaFuncAttributeMaxDynamicSharedMemorySize,

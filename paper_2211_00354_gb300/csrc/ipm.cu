@@ -36,7 +36,7 @@ constexpr int kWarps = kIpmThreads / 32;
 
 // One warp per round of 32 cells of a grid chunk (or of a cell list, or of
 // sub-cells given as four corners each), rounds handed out by a counter.
-template <bool QUADS>
+template <bool QUADS, bool LIST = false>
 __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
   __shared__ WarpCells sh[kWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kIpmThreads, 4) k_ipm_cells(IpmArgs A) {
     int64_t c = idx;
     PixCorner q4[4];
     if (has) {
-      if (A.cell_list) c = A.cell_list[idx];
+      if (LIST) c = A.cell_list[idx];
       if (QUADS) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) q4[k] = A.yc[4 * c + k];
@@ -198,6 +198,7 @@ void ipm_launch(IpmArgs& A, bool quads, int* qcount, cudaStream_t s,
   const int64_t chunk_blocks = (A.ncells + kIpmThreads - 1) / kIpmThreads;
   const unsigned g = (unsigned)std::min<int64_t>(chunk_blocks, (int64_t)sms * 8);
   if (quads) k_ipm_cells<true><<<g, kIpmThreads, 0, s>>>(A);
+  else if (A.cell_list) k_ipm_cells<false, true><<<g, kIpmThreads, 0, s>>>(A);
   else k_ipm_cells<false><<<g, kIpmThreads, 0, s>>>(A);
   LENS_LAUNCHED("k_ipm_cells");
   if (quads) k_ipm_ext<true><<<sms * 2, kIpmThreads, 0, s>>>(A);
