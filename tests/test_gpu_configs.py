@@ -45,8 +45,11 @@ def band_check(f, P, row0, nrows, cap=64):
     e = np.mean(np.abs(mp[good] - ref[good]) / np.abs(ref[good]))
     assert e < 1e-3, e
     assert st["cells_dropped"] == pytest.approx(st_ref["cells_dropped"], rel=1e-3, abs=5)
+    # total flux to 1e-6, up to the cells the two sides drop differently at
+    # the cap (each moves at most one cell area h^2)
+    slack = 1e-6 * st_ref["area_total"] + abs(st["cells_dropped"] - st_ref["cells_dropped"]) * band.h ** 2
     for k in ("area_in_map", "area_outside"):
-        assert st[k] == pytest.approx(st_ref[k], rel=1e-5, abs=1e-9 * st_ref["area_total"])
+        assert abs(st[k] - st_ref[k]) <= slack, (k, st[k], st_ref[k], slack)
     return e, int(good.sum())
 
 
@@ -188,26 +191,41 @@ def test_differentiation_workload_gradients():
     inside = np.nonzero((np.abs(f.stars[:, 0]) < 28) & (np.abs(f.stars[:, 1]) < 2.3))[0]
     gs = stars.grad.cpu().numpy()
     assert np.linalg.norm(st32.grad.cpu().numpy()[inside] - gs[inside]) <= 1e-3 * np.linalg.norm(gs[inside])
+    # central differences at h and 2h combined by Richardson extrapolation,
+    # (4 D(h) - D(2h)) / 3, which cancels the O(h^2) term: a change of kappa_s
+    # or gamma moves every ray by h |x| (|x| up to 30 ER) against a source of
+    # 0.05 ER, where the plain central difference is off by ~(h x / sigma)^2 / 6
     h = 1e-5
+
+    def richardson(ev):
+        d1 = (ev(h) - ev(-h)) / (2 * h)
+        d2 = (ev(2 * h) - ev(-2 * h)) / (4 * h)
+        return (4 * d1 - d2) / 3
+
+    def check(name, g_adj, fd):
+        rel = abs(g_adj - fd) / max(abs(fd), 1e-300)
+        print("C5 %s: adjoint %.12g central %.12g rel %.2e" % (name, g_adj, fd, rel))
+        assert g_adj == pytest.approx(fd, rel=1e-6, abs=1e-7 * np.abs(gs).max())
+
     rng = np.random.default_rng(3)
     with torch.no_grad():
+        M0 = masses.detach()
         for j in rng.choice(inside, 4, replace=False):
             for c in range(2):
-                sp = stars.detach().clone(); sp[j, c] += h
-                sm = stars.detach().clone(); sm[j, c] -= h
-                fd = (loss(sp, masses.detach(), f.kappa_s, f.gamma) -
-                      loss(sm, masses.detach(), f.kappa_s, f.gamma)).item() / (2 * h)
-                assert gs[j, c] == pytest.approx(fd, rel=1e-5, abs=1e-6 * np.abs(gs).max())
-            mp = masses.detach().clone(); mp[j] += h
-            mm = masses.detach().clone(); mm[j] -= h
-            fd = (loss(stars.detach(), mp, f.kappa_s, f.gamma) -
-                  loss(stars.detach(), mm, f.kappa_s, f.gamma)).item() / (2 * h)
-            assert masses.grad[j].item() == pytest.approx(fd, rel=1e-5, abs=1e-6 * np.abs(gs).max())
+                def ev(d, j=j, c=c):
+                    sp = stars.detach().clone()
+                    sp[j, c] += d
+                    return loss(sp, M0, f.kappa_s, f.gamma).item()
+                check("dL/dx[%d,%d]" % (j, c), gs[j, c], richardson(ev))
+
+            def evm(d, j=j):
+                mp = M0.clone()
+                mp[j] += d
+                return loss(stars.detach(), mp, f.kappa_s, f.gamma).item()
+            check("dL/dm[%d]" % j, masses.grad[j].item(), richardson(evm))
         for var, grad in ((0, ks.grad), (1, gm.grad)):
-            kp = [f.kappa_s, f.gamma]
-            km = list(kp)
-            kp[var] += h
-            km[var] -= h
-            fd = (loss(stars.detach(), masses.detach(), kp[0], kp[1]) -
-                  loss(stars.detach(), masses.detach(), km[0], km[1])).item() / (2 * h)
-            assert grad.item() == pytest.approx(fd, rel=1e-5)
+            def evk(d, var=var):
+                kg = [f.kappa_s, f.gamma]
+                kg[var] += d
+                return loss(stars.detach(), M0, kg[0], kg[1]).item()
+            check("dL/d%s" % ("kappa_s", "gamma")[var], grad.item(), richardson(evk))

@@ -62,8 +62,13 @@ def test_ipm_on_a_full_width_band_matches_oracle(c2):
     print("C2 band map: mean rel err %.2e over %d pixels" % (e, good.sum()))
     assert e < 1e-3
     assert st["cells_dropped"] == pytest.approx(st_ref["cells_dropped"], rel=1e-3, abs=5)
+    # total flux to 1e-6, up to the cells the two sides drop differently
+    # (float32 against float64 pixel coordinates at the 64-pixel cap): each
+    # moves at most one cell area h^2 between the ledger's categories
+    slack = 1e-6 * st_ref["area_total"] + abs(st["cells_dropped"] - st_ref["cells_dropped"]) * band.h ** 2
     for k in ("area_in_map", "area_outside"):
-        assert st[k] == pytest.approx(st_ref[k], rel=1e-5)
+        print("C2 band %s: %.9g vs %.9g (slack %.3g)" % (k, st[k], st_ref[k], slack))
+        assert abs(st[k] - st_ref[k]) <= slack
 
 
 def test_full_map_invariants(c2):
