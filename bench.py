@@ -270,23 +270,42 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def measured_traffic(kernel, src, rays_per_launch):
-    """DRAM bytes (read + write) per launch of `kernel`, scaled from the ncu
-    figure per corner ray in profiles/<kernel>_c2_reduced_dram.md; None when
-    the kernel source has changed since that capture."""
+# Sources whose code a kernel's ncu figures depend on (a figure recorded
+# under profiles/ counts only while these files are unchanged).
+PROFILE_SOURCES = {
+    "k_ipm_cells": ("ipm.cu", "ipm_warp.cuh", "cx.cuh", "lens_internal.h"),
+    "k_eval32": ("eval32.cu", "ipm_warp.cuh", "cx.cuh", "lens_internal.h"),
+}
+
+
+def sources_sha(kernel):
     import hashlib
+    h = hashlib.sha256()
+    for fn in PROFILE_SOURCES[kernel]:
+        with open(os.path.join(HERE, "paper_2211_00354_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profile_figures(kernel):
+    """The machine-readable figures ('name: value' lines) of
+    profiles/<kernel>_c2_reduced.md, or {} when the kernel's sources have
+    changed since that capture (its 'source-sha256' line)."""
     import re
     try:
-        txt = open(os.path.join(HERE, "profiles", kernel + "_c2_reduced_dram.md")).read()
-        sha = re.search(r"traffic-source-sha256: ([0-9a-f]{64})", txt).group(1)
-        per = float(re.search(r"dram-bytes-per-corner-ray: ([0-9.]+)", txt).group(1))
-    except (OSError, AttributeError):
-        return None
-    h = hashlib.sha256()
-    for f in (src, "cx.cuh", "lens_internal.h"):
-        with open(os.path.join(HERE, "paper_2211_00354_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return per * rays_per_launch if h.hexdigest() == sha else None
+        txt = open(os.path.join(HERE, "profiles", kernel + "_c2_reduced.md")).read()
+    except OSError:
+        return {}
+    m = re.search(r"source-sha256: ([0-9a-f]{64})", txt)
+    if not m or m.group(1) != sources_sha(kernel):
+        return {}
+    out = {}
+    for key in ("dram-bytes-per-corner-ray", "warp-instructions-per-update",
+                "warp-instructions-per-ray", "issue-active-pct"):
+        mm = re.search(re.escape(key) + r": ([0-9.eE+-]+)", txt)
+        if mm:
+            out[key] = float(mm.group(1))
+    return out
 
 
 def next_rows(args, f, g, stars, masses, prec, target, mp, hbm_peak):
@@ -386,7 +405,8 @@ def config_line(args):
         f, p, leaf, cap = synth.c5_differentiable(seed=args.seed), 32, 16, 0
         desc = ("differentiation: 1e5 stars m ~ U[0.5,1.5], kappa*=0.3, kappa_s=0.2, gamma=0.4, "
                 "6000 x 500 cells of h = 0.01 ER (3e6 rays), 2048-sample Gaussian light curve "
-                "(sigma 0.05 ER), p=32, leaf=16, FP64 forward and adjoint")
+                "(sigma 0.05 ER), p=32, leaf=16, FP32-bulk forward and adjoint (float64 "
+                "translations)")
     g = f.grid
     box = (g.x0, g.x0 + g.nx * g.h, g.y0, g.y0 + g.ny * g.h)
     stars, masses = T(f.stars), T(f.masses)
@@ -426,13 +446,24 @@ def config_line(args):
                                   leaf_size=leaf, target_box=box)
             Tk = lens.light_curve(yt, wr, smp, sig)
 
-        def step():
+        split = {"fwd": [], "bwd": []}
+
+        def step(prec=lens.FP32_BULK, record=True):
             st_ = stars.detach().clone().requires_grad_(True)
             ms_ = masses.detach().clone().requires_grad_(True)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
             y = autograd.deflect(st_, ms_, f.kappa_s, f.gamma, rays, p=p, leaf_size=leaf,
-                                 prec=lens.FP64, target_box=box)
+                                 prec=prec, target_box=box)
             loss = ((autograd.light_curve(y, wr, smp, sig) - Tk) ** 2).sum()
+            e1.record(stream)
             loss.backward()
+            e2.record(stream)
+            if record:
+                torch.cuda.synchronize()
+                split["fwd"].append(e0.elapsed_time(e1))
+                split["bwd"].append(e1.elapsed_time(e2))
             return {"rays": float(rays.shape[0])}, None
     for _ in range(args.warmup):
         step()
@@ -452,11 +483,11 @@ def config_line(args):
         stats.append(st); infos.append(info)
     clk = clocks.stop()
     ms = tot / args.steps
-    rays = stats[-1]["rays"] if w != "nfw" else float((g.nx + 1) * (g.ny + 1))
-    line = {"metric": METRIC, "value": rays / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+    nrays = stats[-1]["rays"] if w != "nfw" else float((g.nx + 1) * (g.ny + 1))
+    line = {"metric": METRIC, "value": nrays / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if w != "differentiation" else "f64", "data": "synthetic",
+            "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": desc, "n_stars": f.n, "grid": [g.nx, g.ny],
                        "l2": "flushed between steps (256 MiB write)"},
             "clocks": clk, "pipe_peaks": pipes}
@@ -492,6 +523,17 @@ def config_line(args):
                                                  "area_dropped", "cells_dropped", "chunks")}
     else:
         line["config"]["parts"] = "forward (build + deflect + light curve) + backward (light-curve gradient + adjoint FMM)"
+        n = args.steps
+        line["phase_ms"] = {"forward": sum(split["fwd"][-n:]) / n, "backward": sum(split["bwd"][-n:]) / n}
+        # the float64 form of the same step (forward and adjoint in float64)
+        for _ in range(2):
+            step(lens.FP64, record=False)
+        torch.cuda.synchronize()
+        split["fwd"].clear(); split["bwd"].clear()
+        for _ in range(args.steps):
+            step(lens.FP64)
+        line["fp64_arm"] = {"ms_per_step": (sum(split["fwd"]) + sum(split["bwd"])) / n,
+                            "forward_ms": sum(split["fwd"]) / n, "backward_ms": sum(split["bwd"]) / n}
     print(json.dumps(line))
 
 
@@ -616,8 +658,27 @@ def main():
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    ipm_traffic = measured_traffic("k_ipm_cells", "ipm.cu", rays_step / launches)
-    eval_traffic = measured_traffic("k_eval32", "eval32.cu", rays_step / launches)
+    # DRAM bytes per launch from the ncu figure per corner ray of the reduced
+    # case (the traffic is the corner array, in proportion to the rays)
+    pf_ipm, pf_eval = profile_figures("k_ipm_cells"), profile_figures("k_eval32")
+    ipm_traffic = (pf_ipm["dram-bytes-per-corner-ray"] * rays_step / launches
+                   if "dram-bytes-per-corner-ray" in pf_ipm else None)
+    eval_traffic = (pf_eval["dram-bytes-per-corner-ray"] * rays_step / launches
+                    if "dram-bytes-per-corner-ray" in pf_eval else None)
+    # issue slots: warp instructions per map update (ncu, reduced case) x the
+    # updates of this map, over the kernels' live time, against one warp
+    # instruction per clock per SM sub-partition at the maximum SM clock
+    issue_peak = 152 * 4 * 2.070e9
+    ipm_issue = None
+    if "warp-instructions-per-update" in pf_ipm and ms_ipm > 0:
+        wi = pf_ipm["warp-instructions-per-update"] * stats[-1]["ipm_updates"]
+        ipm_issue = {"bound": "issue", "kernel": "k_ipm_cells+k_ipm_ext",
+                     "achieved": wi / (ms_ipm / 1e3), "peak": issue_peak, "unit": "warp-inst/s",
+                     "frac": wi / (ms_ipm / 1e3) / issue_peak,
+                     "warp_inst_per_update": pf_ipm["warp-instructions-per-update"],
+                     "thread_inst_per_update": pf_ipm["warp-instructions-per-update"] * 32,
+                     "issue_active_pct_ncu": pf_ipm.get("issue-active-pct"),
+                     "peak_source": "152 SMs x 4 sub-partitions x 1 warp instruction/clock x 2.07 GHz"}
     fused_on = bool(stats[-1].get("fused", 0))
     ms_fused = sum(s_["ms_fused_kernel"] for s_ in stats) / K
     if fused_on:
@@ -838,6 +899,7 @@ def main():
             "roofline": roof,
             "ipm_roofline": {"bound": "hbm", "achieved": ipm_gbs, "peak": hbm_peak,
                              "unit": "GB/s", "frac": ipm_gbs / hbm_peak},
+            "ipm_issue_roofline": ipm_issue,
             "eval_roofline": {"bound": "alu", "achieved": eval_tflops, "peak": fp32_peak,
                               "unit": "TFLOP/s", "frac": eval_tflops / fp32_peak,
                               "peak_source": fp32_src},

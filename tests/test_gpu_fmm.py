@@ -205,7 +205,11 @@ def test_evaluation_on_another_stream_waits_for_the_build():
                 g2 = P.adjoint(xs, gy, stream=s2)[0]
             s2.synchronize()
             np.testing.assert_array_equal(y2.cpu().numpy(), ref[prec][0])
-            np.testing.assert_allclose(g2.cpu().numpy(), ref[prec][1], rtol=1e-12, atol=1e-12)
+            # the adjoint's sums regroup with the order rays reach their leaves
+            # (an atomic cursor): ~1e-16 in float64, ~1e-7 in float32 partials
+            tol = 1e-12 if prec == lens.FP64 else 1e-5
+            g2n, gr = g2.cpu().numpy(), ref[prec][1]
+            assert np.linalg.norm(g2n - gr) <= tol * np.linalg.norm(gr)
             assert P.info()["ms_build"] > 0
 
 
