@@ -381,7 +381,11 @@ __global__ void k_ray_leaf(const double* __restrict__ rays, int64_t m, const int
     return;
   }
   slot[r] = li;
-  atomicAdd((unsigned long long*)&counts[li], 1ull);
+  // rays of a warp mostly share a leaf (grid rays, sorted rays): one atomic
+  // per group of lanes with the same leaf
+  const unsigned grp = __match_any_sync(__activemask(), li);
+  if ((threadIdx.x & 31) == __ffs(grp) - 1)
+    atomicAdd((unsigned long long*)&counts[li], (unsigned long long)__popc(grp));
 }
 
 __global__ void k_ray_scatter(const int* __restrict__ slot, int64_t m, const int64_t* __restrict__ off,
@@ -390,8 +394,14 @@ __global__ void k_ray_scatter(const int* __restrict__ slot, int64_t m, const int
   if (r >= m) return;
   const int li = slot[r];
   if (li < 0) return;
-  const int64_t pos = off[li] + (int64_t)atomicAdd((unsigned long long*)&cursor[li], 1ull);
-  perm[pos] = (int)r;
+  // one cursor fetch per group of lanes with the same leaf; each lane takes
+  // the place of its rank in the group
+  const unsigned grp = __match_any_sync(__activemask(), li);
+  const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd((unsigned long long*)&cursor[li], (unsigned long long)__popc(grp));
+  base = __shfl_sync(grp, base, leader);
+  perm[off[li] + (int64_t)base + __popc(grp & ((1u << lane) - 1u))] = (int)r;
 }
 
 __global__ void k_tiles_from_counts(const int64_t* __restrict__ counts, int64_t n, int tile,
