@@ -64,6 +64,7 @@ struct E32Args {
   double a, b;
   // grid source
   const int64_t* rect; const LeafGrid* lgrid; ff hf; int64_t gnx1, grow0;
+  ff ihf;  // 1 / h: the grid path's near field runs in grid units
   // ray source
   const double* rays; const int64_t* ray_off; const int* perm;
   double* y; double* jac;
@@ -98,14 +99,27 @@ __device__ __forceinline__ void stage_local(E32Smem& sm, const E32Args& A, int64
 // zero when the mass multiplies (w = 0 * finite) and ~1e-18 (far below
 // float32 rounding of the sum) in the equal-mass form, which leaves the mass
 // out.  Block-cooperative, between barriers.
+//
+// On the grid path (GU) the stars are staged in grid units relative to the
+// leaf's grid origin instead: sigma = (s - x_o) / h as float-float (bx, by:
+// the origin's offset from the leaf centre), so that a ray's own coordinates
+// are integers and a difference is (i - sigma_hi) - sigma_lo, two roundings
+// like the float-float form.
+template <bool GU>
 __device__ __forceinline__ void stage_stars(E32Smem& sm, const E32Args& A, int64_t g0, int nf,
-                                            int nfg, int tid) {
+                                            int nfg, int tid, ff bx = ff{0.f, 0.f},
+                                            ff by = ff{0.f, 0.f}) {
   for (int f = tid; f < nfg; f += kT) {
     float4 v = make_float4(1e18f, 0.f, 0.f, 0.f);
     float mm = 0.f;
     if (f < nf) {
       v = A.ust[g0 + f];
       mm = A.um[g0 + f];
+    }
+    if (GU) {
+      const ff gx = ff_mul(ff_add(ff{v.x, v.z}, ff_neg(bx)), A.ihf);
+      const ff gy = ff_mul(ff_add(ff{v.y, v.w}, ff_neg(by)), A.ihf);
+      v = make_float4(gx.hi, gy.hi, gx.lo, gy.lo);
     }
     sm.s_x[f] = make_float2(-v.x, -v.x); sm.s_y[f] = make_float2(-v.y, -v.y);
     sm.s_xl[f] = make_float2(-v.z, -v.z); sm.s_yl[f] = make_float2(-v.w, -v.w);
@@ -119,7 +133,11 @@ __device__ __forceinline__ void stage_stars(E32Smem& sm, const E32Args& A, int64
 // float32, each group partial entering the two-sum accumulators N1, N2.  A
 // star exactly on the ray contributes nothing: the floor on r2 keeps w
 // finite and w * d = 0.
-template <bool UM>
+// GU: grid units, the rays' coordinates exact integers in dx, dy (dxl, dyl
+// unused): d = (x - s_hi) - s_lo, one paired add fewer per coordinate.  A
+// padding star then lies ~1e18 / h away: its |d|^2 may overflow to infinity,
+// whose reciprocal 0 still makes its term exactly zero.
+template <bool UM, bool GU = false>
 __device__ __forceinline__ void p2p_paired(const E32Smem& sm, int nfg, const float (&dx)[kRpt],
                                            const float (&dy)[kRpt], const float (&dxl)[kRpt],
                                            const float (&dyl)[kRpt], fcomp2 (&N1)[kRpt / 2],
@@ -139,8 +157,10 @@ __device__ __forceinline__ void p2p_paired(const E32Smem& sm, int nfg, const flo
       const float2 nsx = sm.s_x[j], nsy = sm.s_y[j], nsxl = sm.s_xl[j], nsyl = sm.s_yl[j];
 #pragma unroll
       for (int h = 0; h < kRpt / 2; ++h) {
-        const float2 d1 = __fadd2_rn(__fadd2_rn(DX[h], nsx), __fadd2_rn(DXL[h], nsxl));
-        const float2 d2 = __fadd2_rn(__fadd2_rn(DY[h], nsy), __fadd2_rn(DYL[h], nsyl));
+        const float2 d1 = GU ? __fadd2_rn(__fadd2_rn(DX[h], nsx), nsxl)
+                             : __fadd2_rn(__fadd2_rn(DX[h], nsx), __fadd2_rn(DXL[h], nsxl));
+        const float2 d2 = GU ? __fadd2_rn(__fadd2_rn(DY[h], nsy), nsyl)
+                             : __fadd2_rn(__fadd2_rn(DY[h], nsy), __fadd2_rn(DYL[h], nsyl));
         const float2 r2 = __ffma2_rn(d1, d1, __ffma2_rn(d2, d2, tiny));
         const float2 rr = make_float2(frcp_fast(r2.x), frcp_fast(r2.y));
         // equal masses: the mass multiplies the sums once, after the loop
@@ -207,6 +227,8 @@ __device__ __forceinline__ void m2p_paired(const E32Smem& sm, int nw, int p, con
 // L2P by Horner's rule and the float-float lens equation for rays (2h, 2h+1)
 // side by side: T1 = a dx - Re f - near1, T2 = b dy + Im f - near2 (y minus
 // the leaf's float64 constant; alpha = conj(b0 + f + near)).
+// (GU: the near-field sums are in grid units and take the factor 1/h here.)
+template <bool GU = false>
 __device__ __forceinline__ void l2p_lens_pair(const E32Smem& sm, const E32Args& A, float ir, int h,
                                               const float (&dx)[kRpt], const float (&dy)[kRpt],
                                               const float (&dxl)[kRpt], const float (&dyl)[kRpt],
@@ -236,12 +258,14 @@ __device__ __forceinline__ void l2p_lens_pair(const E32Smem& sm, const E32Args& 
   fx = __fadd2_rn(fx, FXh);
   fy = __fadd2_rn(fy, FYh);
   // y1 = a x1 - Re f - near1, y2 = b x2 + Im f - near2 (alpha = conj f)
+  const ff2 n1 = GU ? ff2_mul(A.ihf, ff2{N1h.hi, N1h.lo}) : ff2{N1h.hi, N1h.lo};
+  const ff2 n2 = GU ? ff2_mul(A.ihf, ff2{N2h.hi, N2h.lo}) : ff2{N2h.hi, N2h.lo};
   T1 = ff2_mul(A.af, ff2{DXh, make_float2(dxl[2 * h], dxl[2 * h + 1])});
   T1 = ff2_sub(T1, fx);
-  T1 = ff2_sub(T1, ff2{N1h.hi, N1h.lo});
+  T1 = ff2_sub(T1, n1);
   T2 = ff2_mul(A.bf, ff2{DYh, make_float2(dyl[2 * h], dyl[2 * h + 1])});
   T2 = ff2_add(T2, fy);
-  T2 = ff2_sub(T2, ff2{N2h.hi, N2h.lo});
+  T2 = ff2_sub(T2, n2);
 }
 
 // The two rays' source-plane positions in map-pixel coordinates: u = U1 +
@@ -308,7 +332,10 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
   } else {
     nr_leaf = A.ray_off[k + 1] - A.ray_off[k];
   }
+  // the grid path without the Jacobian sums its near field in grid units
+  constexpr bool GU = GRID && !JAC;
   float dx[kRpt], dy[kRpt], dxl[kRpt], dyl[kRpt];
+  float gxr[kRpt], gyr[kRpt];  // GU: the rays' integer grid coordinates from the leaf's origin
   int64_t oidx[kRpt];
   bool ok[kRpt];
   fcomp n1[kRpt], n2[kRpt], nj1[kRpt], nj2[kRpt];
@@ -323,6 +350,7 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
     const int64_t loc = tile * (kT * kRpt) + (int64_t)q * kT + tid;
     ok[q] = loc < nr_leaf;
     dx[q] = dy[q] = dxl[q] = dyl[q] = 0.f;
+    gxr[q] = gyr[q] = 0.f;
     oidx[q] = 0;
     n1[q] = {0.f, 0.f}; n2[q] = {0.f, 0.f}; nj1[q] = {0.f, 0.f}; nj2[q] = {0.f, 0.f};
     if (!ok[q]) continue;
@@ -332,6 +360,8 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
       const uint32_t dj = l32 / n32, di = l32 - dj * n32;
       oidx[q] = (j0 + (int64_t)dj - A.grow0) * A.gnx1 + i0 + (int64_t)di;
       grid_offset(A, lg, di, dj, dx[q], dxl[q], dy[q], dyl[q]);
+      gxr[q] = (float)(lg.ri + (int)di);
+      gyr[q] = (float)(lg.rj + (int)dj);
     } else {
       const int64_t ridx = A.perm[A.ray_off[k] + loc];
       oidx[q] = ridx;
@@ -352,9 +382,11 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
     const int nf = (int)min64(kChunk, nstar - f0);
     const int nfg = (nf + kGroup - 1) / kGroup * kGroup;
     __syncthreads();
-    stage_stars(sm, A, star0 + f0, nf, nfg, tid);
+    stage_stars<GU>(sm, A, star0 + f0, nf, nfg, tid, lg.rx, lg.ry);
     __syncthreads();
-    if (!JAC) {
+    if constexpr (GU) {
+      p2p_paired<UM, true>(sm, nfg, gxr, gyr, dxl, dyl, N1, N2);
+    } else if (!JAC) {
       p2p_paired<UM>(sm, nfg, dx, dy, dxl, dyl, N1, N2);
     } else {
       for (int lo = 0; lo < nfg; lo += kGroup) {
@@ -445,7 +477,7 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
 #pragma unroll
     for (int h = 0; h < kRpt / 2; ++h) {
       ff2 T1, T2;
-      l2p_lens_pair(sm, A, ir, h, dx, dy, dxl, dyl, N1[h], N2[h], FX[h], FY[h], T1, T2);
+      l2p_lens_pair<GU>(sm, A, ir, h, dx, dy, dxl, dyl, N1[h], N2[h], FX[h], FY[h], T1, T2);
       if (PIX) {
         PixCorner pc[2];
         pix_pair(A, lg, T1, T2, pc);
@@ -564,6 +596,7 @@ __global__ void __launch_bounds__(kT, 4) k_eval32_map(E32Args A, IpmArgs I, cons
   const bool restage_stars = nstar > kChunk, restage_w = w_end - w_beg > kWChunk;
   for (int g = 0; g < ngroups; ++g) {
     float dx[kRpt], dy[kRpt], dxl[kRpt], dyl[kRpt];
+    float gxr[kRpt], gyr[kRpt];  // the rays' integer grid coordinates from the leaf's origin
     int t[kRpt];
     bool ok[kRpt];
     uint32_t di[kRpt], dj[kRpt];
@@ -578,22 +611,25 @@ __global__ void __launch_bounds__(kT, 4) k_eval32_map(E32Args A, IpmArgs I, cons
       t[q] = g * (kT * kRpt) + q * kT + tid;
       ok[q] = t[q] < ncorn;
       dx[q] = dy[q] = dxl[q] = dyl[q] = 0.f;
+      gxr[q] = gyr[q] = 0.f;
       di[q] = dj[q] = 0;
       if (!ok[q]) continue;
       const uint32_t r = (uint32_t)t[q] / (uint32_t)it.w, c = (uint32_t)t[q] - r * (uint32_t)it.w;
       di[q] = (uint32_t)it.ci + c;
       dj[q] = (uint32_t)it.cj + r;
       grid_offset(A, lg, di[q], dj[q], dx[q], dxl[q], dy[q], dyl[q]);
+      gxr[q] = (float)(lg.ri + (int)di[q]);
+      gyr[q] = (float)(lg.rj + (int)dj[q]);
     }
     for (int64_t f0 = 0; f0 < nstar; f0 += kChunk) {
       const int nf = (int)min64(kChunk, nstar - f0);
       const int nfg = (nf + kGroup - 1) / kGroup * kGroup;
       if (g == 0 || restage_stars) {
         __syncthreads();
-        stage_stars(sm.e, A, star0 + f0, nf, nfg, tid);
+        stage_stars<true>(sm.e, A, star0 + f0, nf, nfg, tid, lg.rx, lg.ry);
         __syncthreads();
       }
-      p2p_paired<UM>(sm.e, nfg, dx, dy, dxl, dyl, N1, N2);
+      p2p_paired<UM, true>(sm.e, nfg, gxr, gyr, dxl, dyl, N1, N2);
     }
     if (UM && A.m0 != 1.f) {
       const float2 m2 = make_float2(A.m0, A.m0);
@@ -619,7 +655,7 @@ __global__ void __launch_bounds__(kT, 4) k_eval32_map(E32Args A, IpmArgs I, cons
 #pragma unroll
     for (int h = 0; h < kRpt / 2; ++h) {
       ff2 T1, T2;
-      l2p_lens_pair(sm.e, A, ir, h, dx, dy, dxl, dyl, N1[h], N2[h], FX[h], FY[h], T1, T2);
+      l2p_lens_pair<true>(sm.e, A, ir, h, dx, dy, dxl, dyl, N1[h], N2[h], FX[h], FY[h], T1, T2);
       PixCorner pc[2];
       pix_pair(A, lg, T1, T2, pc);
 #pragma unroll
@@ -862,8 +898,9 @@ __global__ void k_to_f32(const int* __restrict__ wlist, int64_t nw, int P1,
 // leaf's first grid ray from its centre (the tree alone); parts & 2: the
 // pixel reference of the centre on the map path (needs the expansions).
 __global__ void k_leaf_grid(int64_t nl, const LeafPlan* __restrict__ lp, const int64_t* __restrict__ rect,
-                            double x0, double y0, double h, int parts, double inv_du, double u_off,
-                            double inv_dv, double v_off, LeafGrid* __restrict__ out) {
+                            double x0, double y0, double h, int64_t nx, int64_t ny, int parts,
+                            double inv_du, double u_off, double inv_dv, double v_off,
+                            LeafGrid* __restrict__ out) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nl) return;
   const LeafPlan L = lp[k];
@@ -872,6 +909,15 @@ __global__ void k_leaf_grid(int64_t nl, const LeafPlan* __restrict__ lp, const i
     const double yj = __dadd_rn(y0, __dmul_rn((double)rect[4 * k + 2], h));
     out[k].bx = ff_of(xi - L.cx);
     out[k].by = ff_of(yj - L.cy);
+    // the grid-unit origin: fixed by the leaf and the whole grid alone, so a
+    // corner gets the same bits in every band; clamped into the grid, it lies
+    // no farther from any of the leaf's rays than the leaf's rectangle spans
+    const double gi = fmin(fmax(rint((L.cx - x0) / h), 0.0), (double)nx);
+    const double gj = fmin(fmax(rint((L.cy - y0) / h), 0.0), (double)ny);
+    out[k].rx = ff_of(__dadd_rn(x0, __dmul_rn(gi, h)) - L.cx);
+    out[k].ry = ff_of(__dadd_rn(y0, __dmul_rn(gj, h)) - L.cy);
+    out[k].ri = (int)(rect[4 * k] - (int64_t)gi);
+    out[k].rj = (int)(rect[4 * k + 2] - (int64_t)gj);
   }
   if (parts & 2) {
     const double U1 = fma(L.K1, inv_du, u_off), V1 = fma(L.K2, inv_dv, v_off);
@@ -986,7 +1032,7 @@ void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int2* ti
   const bool px = pix != nullptr;
   auto leaf_grid = [&](int parts) {
     k_leaf_grid<<<grid_for(nl, 128), 128, 0, s>>>(
-        nl, P.f_leaf, rect, g.x0, g.y0, g.h, parts, px ? ip->inv_du : 0.0,
+        nl, P.f_leaf, rect, g.x0, g.y0, g.h, g.nx, g.ny, parts, px ? ip->inv_du : 0.0,
         px ? -ip->u0 * ip->inv_du : 0.0, px ? ip->inv_dv : 0.0, px ? -ip->v0 * ip->inv_dv : 0.0,
         lg.as<LeafGrid>());
     LENS_LAUNCHED("k_leaf_grid");
@@ -996,6 +1042,7 @@ void eval32_grid(Plan& P, const GridRows& g, const int64_t* rect, const int2* ti
   A.rect = rect;
   A.lgrid = lg.as<LeafGrid>();
   A.hf = ff_of(g.h);
+  A.ihf = ff_of(1.0 / g.h);
   A.gnx1 = g.nx + 1;
   A.grow0 = g.row0;
   A.y = y; A.jac = jac; A.pix = pix;
@@ -1044,6 +1091,7 @@ Scratch eval32_fused(Plan& P, const GridRows& g, const int64_t* rect, PixCorner*
   A.rect = rect;
   A.lgrid = lg.as<LeafGrid>();
   A.hf = ff_of(g.h);
+  A.ihf = ff_of(1.0 / g.h);
   A.gnx1 = g.nx + 1;
   A.grow0 = g.row0;
   A.iduf = ff_of(ip.inv_du);
@@ -1053,7 +1101,8 @@ Scratch eval32_fused(Plan& P, const GridRows& g, const int64_t* rect, PixCorner*
   I.ip = ip; I.wcell = 1.f; I.rq = rq; I.rqcount = rqcount;
   ipm_prepare(I);
   wait_expansions(P, s);
-  k_leaf_grid<<<grid_for(nl, 128), 128, 0, s>>>(nl, P.f_leaf, rect, g.x0, g.y0, g.h, 3, ip.inv_du,
+  k_leaf_grid<<<grid_for(nl, 128), 128, 0, s>>>(nl, P.f_leaf, rect, g.x0, g.y0, g.h, g.nx, g.ny, 3,
+                                                ip.inv_du,
                                                 -ip.u0 * ip.inv_du, ip.inv_dv, -ip.v0 * ip.inv_dv,
                                                 lg.as<LeafGrid>());
   LENS_LAUNCHED("k_leaf_grid");

@@ -85,6 +85,10 @@ struct LeafGrid {
   int U1i, V1i;   // integer part
   int far;        // the reference lies beyond 2^30 pixels
   int pad;
+  // grid units: the grid point nearest the centre (clamped into the grid) is
+  // the leaf's origin, the same for every band of rows the grid is cut into
+  ff rx, ry;      // its offset from the centre
+  int ri, rj;     // the first grid ray's index minus its index
 };
 
 // Host-built float64 tables for one order p (device copies owned by the plan).
