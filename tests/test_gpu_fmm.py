@@ -84,10 +84,19 @@ def test_full_grid_fp32_bulk_matches_oracle():
         with plan_for(f, 24, leaf, lens.FP32_BULK, (-6.0, 6.0, -5.0, 5.0)) as P:
             yg = P.deflect_grid(grid).cpu().numpy().reshape(-1, 2)
             yr = P.deflect(T(xc)).cpu().numpy()
+            bands = [P.deflect_grid(grid, row0=r0, nrows=n).cpu().numpy()
+                     for r0, n in ((0, 1), (7, 8), (100, 33), (250, 8))]
         eg = alpha_rel_err(yg, y_ref, xc, f.kappa_s, f.gamma)
         er = alpha_rel_err(yr, y_ref, xc, f.kappa_s, f.gamma)
         print("leaf %d: grid %.2e ray %.2e" % (leaf, eg.max(), er.max()))
         assert eg.max() < 2e-5 and er.max() < 2e-5, leaf
+        # a band of rows evaluates its corners like the whole grid: the
+        # near field's grid-unit origin of a leaf does not move with the
+        # band, so only the float-float rounding of the leaf-centre offset
+        # (~1e-14 ER) may differ
+        full = yg.reshape(grid.ny + 1, grid.nx + 1, 2)
+        for (r0, n), b in zip(((0, 1), (7, 8), (100, 33), (250, 8)), bands):
+            assert np.abs(b - full[r0:r0 + n]).max() < 1e-12, (leaf, r0)
 
 
 def clustered(seed=0, nc=30, per=80):
