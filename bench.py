@@ -394,13 +394,18 @@ def config_line(args):
                 "masses, kappa*=0.2, kappa_s=0.3, gamma=0.3, 4096^2 map over 100 ER, n0 = 1, "
                 "p=16, leaf=64, FP32-bulk, cap 64 px")
     elif w == "critical":
-        f, p, leaf, cap = synth.c4_critical(seed=args.seed), 16, 8, 64
+        # leaf 4: 29.5 near pairs per ray instead of 36.5 at leaf 8 (936 against
+        # 993 ms a map); p 16 keeps the 2e-5 bound (p 12: 7.6e-5)
+        f, p, leaf, cap = synth.c4_critical(seed=args.seed), 16, 4, 64
         desc = ("critical curve: 2e5 stars m ~ U[0.1,1], kappa_s=0.81, kappa*=0.01, gamma=0.17 "
-                "(mu ~ 286), 8192^2 map over 2 ER, h = 2.44e-4 ER, p=16, leaf=8, FP32-bulk, cap 64 px")
+                "(mu ~ 286), 8192^2 map over 2 ER, h = 2.44e-4 ER, p=16, leaf=4, FP32-bulk, cap 64 px")
     elif w == "nfw":
-        f, p, leaf, cap = synth.nfw_halo(seed=args.seed), 16, 16, 0
+        # leaf 128, p 12: 2.3e5 boxes and 2.9e6 V-list pairs instead of 1.8e6
+        # and 2.1e7 at leaf 16, ~120 rays per leaf instead of ~31 (15.7 against
+        # 54.9 ms a step; max error 4.8e-7 on sampled rays, p 10: 1.9e-6)
+        f, p, leaf, cap = synth.nfw_halo(seed=args.seed), 12, 128, 0
         desc = ("elliptical NFW halo (q = 0.7): 1e7 equal-mass particles, 4096^2 ray grid over "
-                "+-2 r_s, p=16, leaf=16, FP32-bulk, deflection only")
+                "+-2 r_s, p=12, leaf=128, FP32-bulk, deflection only")
     else:
         f, p, leaf, cap = synth.c5_differentiable(seed=args.seed), 32, 16, 0
         desc = ("differentiation: 1e5 stars m ~ U[0.5,1.5], kappa*=0.3, kappa_s=0.2, gamma=0.4, "
@@ -423,10 +428,12 @@ def config_line(args):
             return st, info
     elif w == "nfw":
         # the work counters and the evaluation kernel's time come from one map
-        # call over the same grid (the grid kernel with pixel output)
+        # call over the same grid (the grid kernel with pixel output); a 1024^2
+        # map keeps the grid in one chunk (chunks hold at most 64 cells per pixel)
         P = lens.LensFMM(stars, masses, 0.0, 0.0, p=p, leaf_size=leaf, prec=lens.FP32_BULK,
                          target_box=box)
-        _, st_w = P.ipm_map(g, (-1.0, 1.0, -1.0, 1.0), 16, 16)
+        _, st_w = P.ipm_map(g, box, 1024, 1024)
+        assert st_w["chunks"] == 1
         P.close()
 
         def step():
@@ -507,13 +514,24 @@ def config_line(args):
                         "pairs_per_ray": st["p2p_pairs"] / max(st["rays"], 1.0)}
         line["tree"] = {k: info[k] for k in ("n_boxes", "n_active_leaves", "n_v", "n_x", "n_u",
                                              "n_w", "levels")}
+        # the float64 far field (M2L over the V lists, P2L over X) of the build
+        ms_far = sum(i_["ms_far_local"] for i_ in infos) / K
+        if ms_far > 0 and pipes:
+            ftf = 4.0 * (p + 1) ** 2 * info["n_v"] / (ms_far / 1e3) / 1e12
+            line["far_field_roofline"] = {
+                "bound": "fp64", "kernel": "k_far_local (M2L over V, P2L over X)", "achieved": ftf,
+                "peak": pipes["dfma_tflops"], "unit": "TFLOP/s", "frac": ftf / pipes["dfma_tflops"],
+                "ms": ms_far, "peak_source": "measured: pipe_peaks.cu DFMA",
+                "work": "4 (p+1)^2 flops per V pair (P2L over X not counted)"}
+            if ms_far > ms_eval:
+                line["roofline"] = dict(line["far_field_roofline"], traffic=None)
         if w != "nfw":
             ms_ipm = sum(s_["ms_ipm_kernel"] for s_ in stats) / K
             ipm_bytes = 16.0 * st["rays"] + 8.0 * st["ipm_updates"]
             gbs = ipm_bytes / (ms_ipm / 1e3) / 1e9
             line["ipm_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak,
                                     "unit": "GB/s", "frac": gbs / hbm_peak, "ms": ms_ipm}
-            if ms_ipm > ms_eval:
+            if ms_ipm > max(ms_eval, ms_far):
                 line["roofline"] = dict(line["ipm_roofline"], kernel="k_ipm_cells+k_ipm_ext",
                                         traffic=None)
             line["map_ms"] = ms

@@ -98,7 +98,8 @@ def test_critical_curve_deflections_and_band(c4):
     f = c4
     idx, x = synth.subsample_grid_rays(12, f.grid, 2048)
     y_ref = oracle.deflect(f.stars, f.masses, f.kappa_s, f.gamma, x)
-    with lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=16, leaf_size=8,
+    # the configuration bench.py times (leaf 4, p 16)
+    with lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=16, leaf_size=4,
                       prec=lens.FP32_BULK, target_box=grid_box(f.grid)) as P:
         y = P.deflect(T(x)).cpu().numpy()
         e = alpha_rel_err(y, y_ref, x, f.kappa_s, f.gamma)
@@ -111,7 +112,7 @@ def test_critical_curve_deflections_and_band(c4):
 def test_critical_curve_full_map(c4):
     # ~2.2e10 cells, split into chunks by free device memory
     f = c4
-    with lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=16, leaf_size=8,
+    with lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=16, leaf_size=4,
                       prec=lens.FP32_BULK, target_box=grid_box(f.grid)) as P:
         mp, st = P.ipm_map(f.grid, f.box, f.npx, f.npy, bbox_cap=64)
     assert st["chunks"] >= 2
@@ -147,7 +148,8 @@ def test_nfw_halo_deflections():
     g = f.grid
     idx, x = synth.subsample_grid_rays(13, g, 384)
     y_ref = oracle.deflect(f.stars, f.masses, 0.0, 0.0, x)
-    with lens.LensFMM(T(f.stars), T(f.masses), 0.0, 0.0, p=16, leaf_size=16,
+    # the configuration bench.py times (leaf 128, p 12)
+    with lens.LensFMM(T(f.stars), T(f.masses), 0.0, 0.0, p=12, leaf_size=128,
                       prec=lens.FP32_BULK, target_box=grid_box(g)) as P:
         yg = P.deflect_grid(g)
         y = yg.cpu().numpy()[idx[:, 1], idx[:, 0]]
