@@ -264,7 +264,7 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -276,6 +276,31 @@ PROFILE_SOURCES = {
     "k_ipm_cells": ("ipm.cu", "ipm_warp.cuh", "cx.cuh", "lens_internal.h"),
     "k_eval32": ("eval32.cu", "ipm_warp.cuh", "cx.cuh", "lens_internal.h"),
 }
+
+
+def host_cpu():
+    """The host's machine type and CPU model (lscpu's "Model name", else
+    /proc/cpuinfo's "model name"), for the CPU baseline."""
+    import platform
+    import subprocess
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for l in out.splitlines():
+            if l.strip().startswith("Model name:"):
+                model = l.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for l in open("/proc/cpuinfo"):
+                if l.lower().startswith("model name"):
+                    model = l.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"machine": platform.machine(), "model": model, "logical_cpus": os.cpu_count()}
 
 
 def sources_sha(kernel):
@@ -875,7 +900,7 @@ def main():
                "sample": "best of %d samples of %d random corner rays of the workload grid (%d "
                          "per thread), FP64 direct sum over all %d stars, %.1f s in all"
                          % (reps, m, m // cores, f.n, dt),
-               "ipm": cpu_oracle_ipm(args.seed)}
+               "ipm": cpu_oracle_ipm(args.seed), "host": host_cpu()}
         if acc_oracle is not None:
             cpu["accuracy_sample_rays_per_s"] = acc_oracle
 
