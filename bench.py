@@ -426,7 +426,7 @@ def config_line(args):
                 "(mu ~ 286), 8192^2 map over 2 ER, h = 2.44e-4 ER, p=16, leaf=4, FP32-bulk, cap 64 px")
     elif w == "nfw":
         # leaf 128, p 12: 2.3e5 boxes and 2.9e6 V-list pairs instead of 1.8e6
-        # and 2.1e7 at leaf 16, ~120 rays per leaf instead of ~31 (15.7 against
+        # and 2.1e7 at leaf 16, ~200 rays per leaf instead of ~31 (13.3 against
         # 54.9 ms a step; max error 4.8e-7 on sampled rays, p 10: 1.9e-6)
         f, p, leaf, cap = synth.nfw_halo(seed=args.seed), 12, 128, 0
         desc = ("elliptical NFW halo (q = 0.7): 1e7 equal-mass particles, 4096^2 ray grid over "

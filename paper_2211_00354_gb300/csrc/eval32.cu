@@ -345,10 +345,18 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
     N1[h] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     N2[h] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   }
+  // A tile holds up to kT kRpt rays; a partial one (a leaf's last tile, or a
+  // leaf of few rays) lays them out with stride S, a multiple of 32, so that
+  // they fill whole warps: slot q of thread t is ray q S + t of the tile, and a
+  // warp with no ray (t >= S) joins the block's staging but skips the sums.
+  const int64_t tbase = tile * (int64_t)(kT * kRpt);
+  const int nt = (int)min64(kT * kRpt, nr_leaf - tbase);
+  const int S = min(kT, ((nt + kRpt - 1) / kRpt + 31) & ~31);
+  const bool live = (tid & ~31) < S;
 #pragma unroll
   for (int q = 0; q < kRpt; ++q) {
-    const int64_t loc = tile * (kT * kRpt) + (int64_t)q * kT + tid;
-    ok[q] = loc < nr_leaf;
+    const int64_t loc = tbase + (int64_t)q * S + tid;
+    ok[q] = tid < S && loc < nr_leaf;
     dx[q] = dy[q] = dxl[q] = dyl[q] = 0.f;
     gxr[q] = gyr[q] = 0.f;
     oidx[q] = 0;
@@ -384,6 +392,7 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
     __syncthreads();
     stage_stars<GU>(sm, A, star0 + f0, nf, nfg, tid, lg.rx, lg.ry);
     __syncthreads();
+    if (!live) continue;  // uniform over the warp; the barriers are above
     if constexpr (GU) {
       p2p_paired<UM, true>(sm, nfg, gxr, gyr, dxl, dyl, N1, N2);
     } else if (!JAC) {
@@ -447,6 +456,7 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
     __syncthreads();
     stage_w(sm, A, e0, nw, tid);
     __syncthreads();
+    if (!live) continue;
     if (!JAC) {
       m2p_paired(sm, nw, p, dx, dy, FX, FY);
     } else {
@@ -472,6 +482,7 @@ __global__ void __launch_bounds__(kT) k_eval32(E32Args A) {
 
   // ---- L2P + epilogue --------------------------------------------------------
   __syncthreads();
+  if (!live) return;  // no barrier follows
   const float ir = lp.ir;
   if constexpr (!JAC) {
 #pragma unroll
