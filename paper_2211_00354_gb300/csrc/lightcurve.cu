@@ -83,8 +83,8 @@ __device__ __forceinline__ ff ff_exp_neg(ff x, const ExpTab& T) {
 
 __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 
-// Positions are kept as a cell of the sample grid (power-of-two side, origin a
-// multiple of it) and the offset from that cell's origin, exact in float64
+// Positions are kept as a cell of the sample grid (a side of three significant
+// bits, origin a multiple of it) and the offset from that cell's origin, exact in float64
 // (|offset| < 2 cells) and then float-float: the difference of two points is
 // (a - b) + (cell_a - cell_b) * side, to ~2^-48 of a cell whatever the
 // coordinates' size.
@@ -308,11 +308,13 @@ void build_sample_grid(const double* smp, int64_t ns, double sigma, double trunc
   LENS_CUDA(cudaStreamSynchronize(s));
   if (!(std::isfinite(hb[0]) && std::isfinite(hb[1]) && std::isfinite(hb[2]) && std::isfinite(hb[3])))
     fail(LENS_EINVAL, "non-finite light-curve sample");
-  // side: the power of two at or above trunc sigma; origin: a multiple of it
-  // (so a cell's origin x0 + i side is exact in float64)
+  // side: the least k 2^e (k = 4 .. 8, three significant bits) at or above
+  // trunc sigma; origin: a multiple of it.  Then a cell's origin x0 + i side
+  // is exact in float64, and so is a point's offset from it.
   int ex = 0;
-  const double fr = std::frexp(trunc * sigma, &ex);
-  double cell = std::ldexp(1.0, fr == 0.5 ? ex - 1 : ex);
+  std::frexp(trunc * sigma, &ex);  // trunc sigma in [2^(ex-1), 2^ex)
+  const double unit = std::ldexp(1.0, ex - 3);
+  double cell = std::ceil(trunc * sigma / unit) * unit;
   double x0 = 0, y0 = 0;
   int nx = 0, ny = 0;
   for (;;) {
