@@ -113,12 +113,17 @@ __global__ void k_find_images(const double2* __restrict__ y, int64_t nx, int64_t
   }
 }
 
+// exp(-q / 2 sigma^2) per ray; beyond q = 746 * 2 sigma^2 the float64 value
+// is 0 (e^-746 is below half the least subnormal), so the division and the
+// exponential run only for the rays near the source -- on a whole map a
+// small share, and each costs some 30 operations of GB300's slow float64 pipe
 __global__ void k_source_image(const double2* __restrict__ y, int64_t m, double b1, double b2,
-                               double two_s2, double* __restrict__ out) {
+                               double two_s2, double qmax, double* __restrict__ out) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= m) return;
   const double dx = y[r].x - b1, dy = y[r].y - b2;
-  out[r] = exp(-(dx * dx + dy * dy) / two_s2);
+  const double q = dx * dx + dy * dy;
+  out[r] = q > qmax ? 0.0 : exp(-q / two_s2);
 }
 
 }  // namespace
@@ -143,7 +148,8 @@ void source_image(const double* y, int64_t m, double b1, double b2, double sigma
                   cudaStream_t s) {
   if (m == 0) return;
   k_source_image<<<grid_for(m, 256), 256, 0, s>>>(reinterpret_cast<const double2*>(y), m, b1, b2,
-                                                  2.0 * sigma * sigma, out);
+                                                  2.0 * sigma * sigma, 746.0 * 2.0 * sigma * sigma,
+                                                  out);
   LENS_LAUNCHED("k_source_image");
 }
 
