@@ -20,7 +20,13 @@
 //   P2P  over U (the leaf itself included): sum_j m_j ln|z - z_j| (a star
 //        exactly at the ray contributes nothing)
 //   M2P  over W:  a_0 ln|z - c_C| - Re sum_{k>=1} (A_k / k) (r_C / (z - c_C))^k
-// All float64; a thread per ray descends the tree to its leaf.
+// All float64; a thread per ray descends the tree to its leaf, the rays taken
+// in leaf order (bucketed as the deflection's ray path does), so that the
+// lanes of a warp share their leaf's lists and stars.  Divisions by
+// the small integers k take a per-block table of 1/k, and with equal masses
+// the near field's logarithms are taken of products of up to 8 squared
+// distances (flushed early outside [1e-200, 1e200]): one float64 log where
+// there were eight, on GB300's slow float64 pipe.
 #include "cx.cuh"
 #include "potential.h"
 
@@ -39,6 +45,8 @@ struct PotArgs {
   const int64_t* U_off; const int* U_list; const int64_t* W_off; const int* W_list;
   double* c0;  // per active box
   double ks, g;
+  int um;        // all masses equal to m0
+  double m0;
 };
 
 __device__ __forceinline__ double half_side(const PotArgs& A, int level) {
@@ -47,19 +55,28 @@ __device__ __forceinline__ double half_side(const PotArgs& A, int level) {
 __device__ __forceinline__ double2 centre(const PotArgs& A, int b, double r) {
   return make_double2(A.lo_x + (2.0 * A.ix[b] + 1.0) * r, A.lo_y + (2.0 * A.iy[b] + 1.0) * r);
 }
-// -Re sum_{k=1..p} (A_k / k) v^k
-__device__ __forceinline__ double tail(const double2* Ak, int p, double2 v) {
+// -Re sum_{k=1..p} (A_k / k) v^k, inv[k] = 1/k
+__device__ __forceinline__ double tail(const double2* Ak, int p, double2 v, const double* inv) {
   double s = 0.0;
   double2 pw = v;
   for (int k = 1; k <= p; ++k) {
-    s -= (Ak[k].x * pw.x - Ak[k].y * pw.y) / (double)k;
+    s -= (Ak[k].x * pw.x - Ak[k].y * pw.y) * inv[k];
     pw = cmul(pw, v);
   }
   return s;
 }
 
+// 1/k for k = 0 .. n-1 in shared memory (1/0 unused); block-cooperative
+constexpr int kPotInv = kMaxOrder + 2;
+__device__ __forceinline__ void fill_inv(double* inv, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) inv[k] = k ? 1.0 / (double)k : 0.0;
+  __syncthreads();
+}
+
 // own constant of every active box: M2L over V and P2L over X (warp per box)
 __global__ void k_pot_own(PotArgs A, int64_t nact) {
+  __shared__ double inv[kPotInv];
+  fill_inv(inv, A.p + 2);
   const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (a >= nact) return;
@@ -74,7 +91,8 @@ __global__ void k_pot_own(PotArgs A, int64_t nact) {
     const double2 t = make_double2(cB.x - cC.x, cB.y - cC.y);
     const double2* Ak = A.M + (int64_t)C * P1;
     const double2 it = cinv(t);
-    acc += Ak[0].x * 0.5 * log(t.x * t.x + t.y * t.y) + tail(Ak, A.p, make_double2(r * it.x, r * it.y));
+    acc += Ak[0].x * 0.5 * log(t.x * t.x + t.y * t.y) +
+           tail(Ak, A.p, make_double2(r * it.x, r * it.y), inv);
   }
   for (int64_t e = A.X_off[a]; e < A.X_off[a + 1]; ++e) {
     const int C = A.X_list[e];
@@ -114,9 +132,13 @@ __global__ void k_pot_down(PotArgs A, int64_t a0, int64_t a1) {
 }
 
 __global__ void k_pot_eval(PotArgs A, const double* __restrict__ rays, int64_t m,
-                           double* __restrict__ psi, int* __restrict__ err) {
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= m) return;
+                           const int* __restrict__ perm, double* __restrict__ psi,
+                           int* __restrict__ err) {
+  __shared__ double inv[kPotInv];
+  fill_inv(inv, A.p + 2);
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const int64_t r = perm[t];
   const double x = rays[2 * r], y = rays[2 * r + 1];
   const double scale = (double)(1ull << A.depth) / A.size;
   const double qmax = (double)((1u << A.depth) - 1u);
@@ -146,21 +168,42 @@ __global__ void k_pot_eval(PotArgs A, const double* __restrict__ rays, int64_t m
   // L2P of the integrated local expansion
   const double2 w = make_double2((x - cb.x) / rb, (y - cb.y) / rb);
   const double2* Bl = A.L + (int64_t)b * P1;
-  double2 acc = make_double2(Bl[A.p].x / P1, Bl[A.p].y / P1);
+  double2 acc = make_double2(Bl[A.p].x * inv[P1], Bl[A.p].y * inv[P1]);
   for (int l = A.p - 1; l >= 0; --l) {
     acc = cmul(acc, w);
-    acc.x += Bl[l].x / (l + 1);
-    acc.y += Bl[l].y / (l + 1);
+    acc.x += Bl[l].x * inv[l + 1];
+    acc.y += Bl[l].y * inv[l + 1];
   }
   acc = cmul(acc, w);
   double phi = A.c0[a] + rb * acc.x;
-  // P2P over U
-  for (int64_t e = A.U_off[a]; e < A.U_off[a + 1]; ++e) {
-    const int C = A.U_list[e];
-    for (int j = A.start[C]; j < A.start[C] + A.count[C]; ++j) {
-      const double dx = x - A.spos[j].x, dy = y - A.spos[j].y;
-      const double d2 = dx * dx + dy * dy;
-      if (d2 > 0.0) phi += A.smass[j] * 0.5 * log(d2);
+  // P2P over U (a star exactly at the ray contributes nothing)
+  if (A.um) {
+    double lsum = 0.0, prod = 1.0;
+    int n = 0;
+    for (int64_t e = A.U_off[a]; e < A.U_off[a + 1]; ++e) {
+      const int C = A.U_list[e];
+      for (int j = A.start[C]; j < A.start[C] + A.count[C]; ++j) {
+        const double dx = x - A.spos[j].x, dy = y - A.spos[j].y;
+        const double d2 = dx * dx + dy * dy;
+        if (!(d2 > 0.0)) continue;
+        prod *= d2;
+        if (++n == 8 || !(prod > 1e-200 && prod < 1e200)) {
+          lsum += log(prod);
+          prod = 1.0;
+          n = 0;
+        }
+      }
+    }
+    if (n > 0) lsum += log(prod);
+    phi += 0.5 * A.m0 * lsum;
+  } else {
+    for (int64_t e = A.U_off[a]; e < A.U_off[a + 1]; ++e) {
+      const int C = A.U_list[e];
+      for (int j = A.start[C]; j < A.start[C] + A.count[C]; ++j) {
+        const double dx = x - A.spos[j].x, dy = y - A.spos[j].y;
+        const double d2 = dx * dx + dy * dy;
+        if (d2 > 0.0) phi += A.smass[j] * 0.5 * log(d2);
+      }
     }
   }
   // M2P over W
@@ -172,7 +215,7 @@ __global__ void k_pot_eval(PotArgs A, const double* __restrict__ rays, int64_t m
     const double2* Ak = A.M + (int64_t)C * P1;
     const double2 it = cinv(t);
     phi += Ak[0].x * 0.5 * log(t.x * t.x + t.y * t.y) +
-           tail(Ak, A.p, make_double2(rC * it.x, rC * it.y));
+           tail(Ak, A.p, make_double2(rC * it.x, rC * it.y), inv);
   }
   psi[r] = phi + 0.5 * A.ks * (x * x + y * y) + 0.5 * A.g * (x * x - y * y);
 }
@@ -182,6 +225,9 @@ __global__ void k_pot_eval(PotArgs A, const double* __restrict__ rays, int64_t m
 void evaluate_potential(Plan& P, const double* rays, int64_t m, double* psi, cudaStream_t s) {
   if (m == 0) return;
   if (P.n_active == 0) fail(LENS_EDOMAIN, "plan has no active boxes");
+  // the rays in leaf order (fails with LENS_EDOMAIN for a ray outside the root)
+  RayBuckets RB;
+  bucket_rays(P, rays, m, 1, RB, s);
   wait_expansions(P, s);
   Scratch c0(&P.da, sizeof(double) * (size_t)P.n_active);
   Scratch err(&P.da, sizeof(int));
@@ -197,6 +243,8 @@ void evaluate_potential(Plan& P, const double* rays, int64_t m, double* psi, cud
   A.U_off = P.U_off; A.U_list = P.U_list; A.W_off = P.W_off; A.W_list = P.W_list;
   A.c0 = c0.as<double>();
   A.ks = P.kappa_s; A.g = P.gamma;
+  A.um = P.equal_mass ? 1 : 0;
+  A.m0 = P.mass0;
   k_pot_own<<<grid_for(P.n_active * 32, 256), 256, 0, s>>>(A, P.n_active);
   LENS_LAUNCHED("k_pot_own");
   for (size_t l = 1; l + 1 < P.active_level_off.size(); ++l) {
@@ -205,7 +253,7 @@ void evaluate_potential(Plan& P, const double* rays, int64_t m, double* psi, cud
     k_pot_down<<<grid_for(a1 - a0, 128), 128, 0, s>>>(A, a0, a1);
     LENS_LAUNCHED("k_pot_down");
   }
-  k_pot_eval<<<grid_for(m, 128), 128, 0, s>>>(A, rays, m, psi, err.as<int>());
+  k_pot_eval<<<grid_for(m, 128), 128, 0, s>>>(A, rays, m, RB.perm.as<int>(), psi, err.as<int>());
   LENS_LAUNCHED("k_pot_eval");
   int herr = 0;
   LENS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
