@@ -8,7 +8,11 @@
 //    y + dy and y - dy (added once into shared memory) against g(dx) over
 //    |dx| <= r(dy), folded as g(0) T[x] + sum_k g(k) (T[x+k] + T[x-k]); the
 //    normalisation is the same stack of segments over the all-ones map, a
-//    prefix sum of g per segment.  Block per 256 pixels of a row, float64;
+//    prefix sum of g per segment (one constant for the pixels at least R from
+//    every edge).  Block per 256 pixels of a row; the map and g are taken
+//    as float-float (pairs of float32, ~48 bits) and the sums run on the
+//    float32 pipe (GB300's float64 pipe is ~1/64 of it), the normalisation
+//    and the quotient in float64;
 //  * histogram: equal bins of the value or of log10(value), counts kept per
 //    block in shared memory, then one atomic per bin and block;
 //  * track: the map bilinear between pixel centres at source positions.
@@ -21,15 +25,24 @@ namespace {
 constexpr int kMaxSourceRadius = 1024;  // pixels
 constexpr int kSourceThreads = 256;
 
+// the map as float-float
+__global__ void k_map_ff(const double* __restrict__ map, int64_t n, float2* __restrict__ mf) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const ff v = ff_of(map[i]);
+  mf[i] = make_float2(v.hi, v.lo);
+}
+
 // tab: g[0..R] (g[k] = exp(-k^2 / 2 s^2)), G[0..R] (G[k] = g[0] + .. + g[k]),
 // then r[0..R] as ints (r[dy]: largest |dx| with dx^2 + dy^2 <= (trunc s)^2,
-// -1 if none).  Shared memory: g, then the folded row T (256 + 2 R values).
+// -1 if none).  dfull: the normalisation of a pixel at least R from every
+// edge.  Shared memory: g as float-float, then the folded row T (256 + 2 R).
 __global__ void __launch_bounds__(kSourceThreads)
-k_source_disk(const double* __restrict__ map, int npx, int npy, int R,
-              const double* __restrict__ tab, double* __restrict__ out) {
-  extern __shared__ double sm[];
-  double* g = sm;
-  double* T = sm + (R + 1);
+k_source_disk(const float2* __restrict__ mf, int npx, int npy, int R,
+              const double* __restrict__ tab, double dfull, double* __restrict__ out) {
+  extern __shared__ float2 smf[];
+  float2* gf = smf;
+  float2* T = smf + (R + 1);
   const double* G = tab + (R + 1);
   const int* rt = reinterpret_cast<const int*>(tab + 2 * (R + 1));
   const int t = threadIdx.x;
@@ -37,8 +50,15 @@ k_source_disk(const double* __restrict__ map, int npx, int npy, int R,
   const int py = blockIdx.x / blocks_x;
   const int x0 = (blockIdx.x - py * blocks_x) * kSourceThreads;
   const int px = x0 + t;
-  for (int k = t; k <= R; k += kSourceThreads) g[k] = tab[k];
-  double num = 0.0, den = 0.0;
+  for (int k = t; k <= R; k += kSourceThreads) {
+    const ff v = ff_of(tab[k]);
+    gf[k] = make_float2(v.hi, v.lo);
+  }
+  // every pixel of the block at least R from every edge: one normalisation
+  const bool interior = x0 >= R && x0 + kSourceThreads - 1 <= npx - 1 - R && py >= R &&
+                        py <= npy - 1 - R;
+  ff num{0.f, 0.f};
+  double den = 0.0;
   for (int dy = 0; dy <= R; ++dy) {
     const int r = rt[dy];
     const int ya = py + dy, yb = py - dy;
@@ -48,26 +68,30 @@ k_source_disk(const double* __restrict__ map, int npx, int npy, int R,
     const int nt = kSourceThreads + 2 * r;
     for (int i = t; i < nt; i += kSourceThreads) {
       const int x = x0 - r + i;
-      double v = 0.0;
+      ff v{0.f, 0.f};
       if (x >= 0 && x < npx) {
-        if (ina) v = map[(int64_t)ya * npx + x];
-        if (inb) v += map[(int64_t)yb * npx + x];
+        if (ina) { const float2 a = mf[(int64_t)ya * npx + x]; v = ff{a.x, a.y}; }
+        if (inb) { const float2 b = mf[(int64_t)yb * npx + x]; v = ff_add(v, ff{b.x, b.y}); }
       }
-      T[i] = v;
+      T[i] = make_float2(v.hi, v.lo);
     }
     __syncthreads();
     if (px < npx) {
       const int c = t + r;
-      double acc = g[0] * T[c];
-      for (int k = 1; k <= r; ++k) acc = fma(g[k], T[c + k] + T[c - k], acc);
-      const double gy = g[dy];
-      num = fma(gy, acc, num);
-      // in-map weight of this segment: columns px - min(r, px) .. px + min(r, npx-1-px)
-      const double seg = G[min(r, px)] + G[min(r, npx - 1 - px)] - g[0];
-      den = fma(gy * ((ina ? 1.0 : 0.0) + (inb ? 1.0 : 0.0)), seg, den);
+      ff acc = ff_mul(ff{gf[0].x, gf[0].y}, ff{T[c].x, T[c].y});
+      for (int k = 1; k <= r; ++k) {
+        const ff pair = ff_add(ff{T[c + k].x, T[c + k].y}, ff{T[c - k].x, T[c - k].y});
+        acc = ff_add(acc, ff_mul(ff{gf[k].x, gf[k].y}, pair));
+      }
+      num = ff_add(num, ff_mul(ff{gf[dy].x, gf[dy].y}, acc));
+      if (!interior) {
+        // in-map weight of this segment: columns px - min(r, px) .. px + min(r, npx-1-px)
+        const double seg = G[min(r, px)] + G[min(r, npx - 1 - px)] - tab[0];
+        den = fma(tab[dy] * ((ina ? 1.0 : 0.0) + (inb ? 1.0 : 0.0)), seg, den);
+      }
     }
   }
-  if (px < npx) out[(int64_t)py * npx + px] = num / den;
+  if (px < npx) out[(int64_t)py * npx + px] = ff_to_double(num) / (interior ? dfull : den);
 }
 
 __global__ void k_histogram(const double* __restrict__ v, int64_t n, double lo, double hi,
@@ -136,18 +160,29 @@ void map_source(const double* map, int npx, int npy, double sigma_px, double tru
     while (r < R && (double)(r + 1) * (r + 1) + (double)dy * dy <= cut2) ++r;
     rt[dy] = r;
   }
+  // the normalisation of an interior pixel, in the kernel's order
+  double dfull = 0.0;
+  for (int dy = 0; dy <= R; ++dy) {
+    if (rt[dy] < 0) continue;
+    const double seg = tab[n1 + (size_t)rt[dy]] + tab[n1 + (size_t)rt[dy]] - tab[0];
+    dfull = std::fma(tab[(size_t)dy] * (dy > 0 ? 2.0 : 1.0), seg, dfull);
+  }
   Scratch dt(&da, sizeof(double) * tab.size());
   LENS_CUDA(cudaMemcpyAsync(dt.p, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice,
                             s));
+  const int64_t npix = (int64_t)npx * npy;
+  Scratch mf(&da, sizeof(float2) * (size_t)npix);
+  k_map_ff<<<grid_for(npix, 256), 256, 0, s>>>(map, npix, mf.as<float2>());
+  LENS_LAUNCHED("k_map_ff");
   const int blocks_x = (npx + kSourceThreads - 1) / kSourceThreads;
   const int64_t blocks = (int64_t)blocks_x * npy;
   if (blocks > INT32_MAX) fail(LENS_EINVAL, "map too large");
-  const size_t smem = sizeof(double) * (n1 + kSourceThreads + 2 * (size_t)R);
+  const size_t smem = sizeof(float2) * (n1 + kSourceThreads + 2 * (size_t)R);
   if (smem > 48 * 1024)
     LENS_CUDA(cudaFuncSetAttribute(k_source_disk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
-  k_source_disk<<<(unsigned)blocks, kSourceThreads, smem, s>>>(map, npx, npy, R, dt.as<double>(),
-                                                               out);
+  k_source_disk<<<(unsigned)blocks, kSourceThreads, smem, s>>>(mf.as<float2>(), npx, npy, R,
+                                                               dt.as<double>(), dfull, out);
   LENS_LAUNCHED("k_source_disk");
   // the host table must outlive the copy
   LENS_CUDA(cudaStreamSynchronize(s));
