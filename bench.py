@@ -339,7 +339,10 @@ def next_rows(args, f, g, stars, masses, prec, target, mp, hbm_peak):
     image finding and the lensed Gaussian source on the whole deflected
     grid (float64 corners, (nx+1)(ny+1) x 16 B read), the lensing potential
     at 2^20 rays of the target region, the finite-source map and a
-    log-binned histogram of the map."""
+    log-binned histogram of the map, the map with one level of critical-cell
+    refinement (plan built once; beside the same map without it), and the map
+    through three lens planes (the stars split in thirds, the shear on the
+    nearest plane)."""
     import torch
 
     from paper_2211_00354_gb300 import lens
@@ -380,7 +383,34 @@ def next_rows(args, f, g, stars, masses, prec, target, mp, hbm_peak):
                       target[2] + (target[3] - target[2]) * u[:, 1]], dim=1).to(stars.device)
     t = timed(lambda: P.potential(xr), reps=3)
     out["potential"] = {"ms": t, "rays": 1 << 20, "rays_per_s": (1 << 20) / (t / 1e3)}
+    # critical-cell refinement: cells over the 64-pixel cap split 2 x 2 once
+    m2 = torch.empty_like(mp)
+    t0 = timed(lambda: P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=64, out=m2), reps=3)
+    t1 = timed(lambda: P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=64, out=m2, refine_levels=1),
+               reps=3)
+    _, st1 = P.ipm_map(g, f.box, f.npx, f.npy, bbox_cap=64, out=m2, refine_levels=1)
+    out["refined_map"] = {"ms": t1, "ms_unrefined": t0, "refine_levels": 1,
+                          "cells_refined": st1["cells_refined"],
+                          "cells_dropped": st1["cells_dropped"]}
     P.close()
+    # three lens planes
+    K = 3
+    part = torch.randperm(stars.shape[0], generator=gen).to(stars.device)
+    planes = []
+    for k in range(K):
+        sel = part[k::K]
+        planes.append((stars[sel].contiguous(), masses[sel].contiguous(), 0.0,
+                       f.gamma if k == 0 else 0.0))
+    beta = np.zeros((K, K))
+    beta[0, 1], beta[0, 2], beta[1, 2] = 0.2, 0.35, 0.2
+    t = timed(lambda: lens.multiplane_ipm_map(planes, beta, g, f.box, f.npx, f.npy, p=args.p,
+                                              leaf_size=args.leaf, prec=prec, bbox_cap=64,
+                                              out=m2), reps=1)
+    _, stm = lens.multiplane_ipm_map(planes, beta, g, f.box, f.npx, f.npy, p=args.p,
+                                     leaf_size=args.leaf, prec=prec, bbox_cap=64, out=m2)
+    out["multiplane_map"] = {"ms": t, "planes": K, "rays": stm["rays"],
+                             "rays_per_s": stm["rays"] / (t / 1e3), "chunks": stm["chunks"]}
+    del m2
     t = timed(lambda: lens.map_source(mp, 5.0), reps=3)
     out["map_source"] = {"ms": t, "sigma_px": 5.0, "npix": [f.npx, f.npy]}
     t = timed(lambda: lens.map_histogram(mp.reshape(-1), 1e-2, 1e3, 256, log_bins=True))
