@@ -35,30 +35,50 @@ constexpr int kFarPix = 0x7fffffff;
 
 // per block: min/max of x and y over its share of the points, and whether
 // any coordinate is not finite
+// the bounding box of m positions by order-preserving integer keys of the
+// float64 values (exact; min / max and the finiteness test on the integer
+// pipe -- float64 min / max run on GB300's slow float64 pipe), one partial
+// box per block
+__device__ __forceinline__ unsigned long long okey(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double unkey(unsigned long long k) {
+  return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+__device__ __forceinline__ bool finite_bits(double v) {
+  return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
 __global__ void k_mp_bounds(const double2* __restrict__ x, int64_t m, double* __restrict__ part,
                             int* __restrict__ bad) {
-  __shared__ double sh[4][256];
-  double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+  __shared__ unsigned long long sh[4][8];
+  unsigned long long x0 = ~0ull, x1 = 0ull, y0 = ~0ull, y1 = 0ull;
   int nf = 0;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
        r += (int64_t)gridDim.x * blockDim.x) {
     const double2 p = x[r];
-    if (!(isfinite(p.x) && isfinite(p.y))) { nf = 1; continue; }
-    x0 = fmin(x0, p.x); x1 = fmax(x1, p.x);
-    y0 = fmin(y0, p.y); y1 = fmax(y1, p.y);
+    if (!(finite_bits(p.x) && finite_bits(p.y))) { nf = 1; continue; }
+    const unsigned long long kx = okey(p.x), ky = okey(p.y);
+    x0 = min(x0, kx); x1 = max(x1, kx);
+    y0 = min(y0, ky); y1 = max(y1, ky);
   }
-  if (nf) atomicOr(bad, 1);
-  const int t = threadIdx.x;
-  sh[0][t] = x0; sh[1][t] = x1; sh[2][t] = y0; sh[3][t] = y1;
+  if (__any_sync(0xffffffffu, nf) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x0 = min(x0, __shfl_xor_sync(0xffffffffu, x0, o)); x1 = max(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+    y0 = min(y0, __shfl_xor_sync(0xffffffffu, y0, o)); y1 = max(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+  }
+  const int t = threadIdx.x, w = t >> 5;
+  if ((t & 31) == 0) { sh[0][w] = x0; sh[1][w] = x1; sh[2][w] = y0; sh[3][w] = y1; }
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (t < s) {
-      sh[0][t] = fmin(sh[0][t], sh[0][t + s]); sh[1][t] = fmax(sh[1][t], sh[1][t + s]);
-      sh[2][t] = fmin(sh[2][t], sh[2][t + s]); sh[3][t] = fmax(sh[3][t], sh[3][t + s]);
-    }
-    __syncthreads();
+  if (t < 4) {
+    unsigned long long v = sh[t][0];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) v = (t & 1) ? max(v, sh[t][q]) : min(v, sh[t][q]);
+    // an empty block keeps +inf / -inf, as the float64 form did
+    part[4 * blockIdx.x + t] = (t & 1) ? (v == 0ull ? -INFINITY : unkey(v))
+                                       : (v == ~0ull ? INFINITY : unkey(v));
   }
-  if (t < 4) part[4 * blockIdx.x + t] = sh[t][0];
 }
 
 struct MpStep {
