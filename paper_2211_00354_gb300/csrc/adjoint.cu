@@ -29,6 +29,7 @@ namespace lens {
 namespace {
 
 constexpr int kAdjTile = 128;  // rays per tile
+constexpr int kAdjU = 64;      // U-list leaves staged at a time by k_adj_p2p32
 
 __device__ __forceinline__ void atomic_add2(double2* p, double2 v) {
   atomicAdd(&p->x, v.x);
@@ -201,12 +202,32 @@ __global__ void __launch_bounds__(128) k_adj_p2p32(AdjArgs A) {
     sz[t] = make_float4(ox.hi, oy.hi, ox.lo, oy.lo);
     sc[t] = make_float2((float)-A.gy[2 * ridx], (float)-A.gy[2 * ridx + 1]);
   }
-  __syncthreads();
-  for (int64_t e = A.U_off[a]; e < A.U_off[a + 1]; ++e) {
-    const int C = A.U_list[e];
-    const int s0 = A.start[C], ns = A.count[C];
-    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
-      const int sj = s0 + j;
+  // the stars of the U-list leaves, flattened over the block's threads (a
+  // leaf's own count is often below the block size): up to kAdjU leaves at a
+  // time, their first star and inclusive star counts in shared memory
+  __shared__ int su_start[kAdjU], su_incl[kAdjU];
+  const int64_t u0 = A.U_off[a], nu = A.U_off[a + 1] - u0;
+  for (int64_t ub = 0; ub < nu; ub += kAdjU) {
+    const int nub = (int)min64(kAdjU, nu - ub);
+    __syncthreads();  // the previous group's readers are done (and the rays staged)
+    if (threadIdx.x < nub) {
+      const int C = A.U_list[u0 + ub + threadIdx.x];
+      su_start[threadIdx.x] = A.start[C];
+      su_incl[threadIdx.x] = A.count[C];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int i = 1; i < nub; ++i) su_incl[i] += su_incl[i - 1];
+    __syncthreads();
+    const int tot = su_incl[nub - 1];
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+      // the group's leaf holding flattened star q: the first with su_incl > q
+      int lo = 0, hi = nub - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (su_incl[mid] > q) hi = mid; else lo = mid + 1;
+      }
+      const int sj = su_start[lo] + q - (lo ? su_incl[lo - 1] : 0);
       const double2 zj = A.spos[sj];
       const ff sx = ff_of(zj.x - cB.x), sy = ff_of(zj.y - cB.y);
       fcomp F1{0.f, 0.f}, F2{0.f, 0.f}, G1{0.f, 0.f}, G2{0.f, 0.f};
@@ -232,7 +253,7 @@ __global__ void __launch_bounds__(128) k_adj_p2p32(AdjArgs A) {
 // L2P^T and M2P^T moments in float32: one warp per (leaf, tile), as
 // k_adj_leaf_moments.
 __global__ void __launch_bounds__(32) k_adj_leaf_moments32(AdjArgs A) {
-  extern __shared__ float2 acc32[];  // [(p+1)][32]
+  extern __shared__ float2 acc32[];  // [(p+1)][33]: lane partials, padded
   const int lane = threadIdx.x;
   const int64_t k = leaf_of_tile(A.tile_off, A.nleaf, blockIdx.x);
   const int B = A.leaves[k];
@@ -247,7 +268,7 @@ __global__ void __launch_bounds__(32) k_adj_leaf_moments32(AdjArgs A) {
   const double irB = 1.0 / rB;
   const int64_t nW = A.W_off[a + 1] - A.W_off[a];
   for (int64_t pass = 0; pass <= nW; ++pass) {
-    for (int l = 0; l <= p; ++l) acc32[l * 32 + lane] = make_float2(0.f, 0.f);
+    for (int l = 0; l <= p; ++l) acc32[l * 33 + lane] = make_float2(0.f, 0.f);
     int C = -1;
     double rC = 0;
     double2 cC = make_double2(0, 0);
@@ -271,21 +292,22 @@ __global__ void __launch_bounds__(32) k_adj_leaf_moments32(AdjArgs A) {
         pw = cmul(c, inv);
       }
       for (int l = 0; l <= p; ++l) {
-        acc32[l * 32 + lane] = acc32[l * 32 + lane] + pw;
+        acc32[l * 33 + lane] = acc32[l * 33 + lane] + pw;
         pw = cmul(pw, w);
       }
     }
     __syncwarp();
     double2* dst = pass == 0 ? A.Lh + (int64_t)B * (p + 1) : A.Mh + (int64_t)C * (p + 1);
-    for (int l = 0; l <= p; ++l) {
-      const float2 vf = acc32[l * 32 + lane];
-      double2 v = make_double2(vf.x, vf.y);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    // lane l sums order l's 32 lane partials in float64 (a float64 shuffle
+    // tree would run the adds on every lane of every order)
+    for (int l = lane; l <= p; l += 32) {
+      double vx = 0.0, vy = 0.0;
+      for (int q = 0; q < 32; ++q) {
+        const float2 vf = acc32[l * 33 + q];
+        vx += vf.x;
+        vy += vf.y;
       }
-      if (lane == 0 && (v.x != 0.0 || v.y != 0.0)) atomic_add2(dst + l, v);
+      if (vx != 0.0 || vy != 0.0) atomic_add2(dst + l, make_double2(vx, vy));
     }
     __syncwarp();
   }
@@ -482,7 +504,7 @@ void adjoint(Plan& P, const double* rays, int64_t m, const double* gy, double* g
   A.Phi = Phi.as<double2>(); A.Psi = Psi.as<double2>();
   if (RB.total > (int64_t)INT32_MAX) fail(LENS_EINVAL, "too many rays in one adjoint call");
   if (RB.total > 0 && P.prec == LENS_FP32_BULK) {
-    const size_t smem = sizeof(float2) * (size_t)P1 * 32;
+    const size_t smem = sizeof(float2) * (size_t)P1 * 33;
     k_adj_leaf_moments32<<<(unsigned)RB.total, 32, smem, s>>>(A);
     LENS_LAUNCHED("k_adj_leaf_moments32");
     k_adj_p2p32<<<(unsigned)RB.total, 128, 0, s>>>(A);
