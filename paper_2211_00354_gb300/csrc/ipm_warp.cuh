@@ -505,47 +505,50 @@ __device__ __forceinline__ void ipm_round(const IpmArgs& A, WarpCells& sh, int l
     base = __shfl_sync(0xffffffffu, base, 0);
     if (f64) A.queue[base + __popc(fm & ((1u << lane) - 1u))] = (int)c;
   }
-  // ---- B: pixels of small cells -------------------------------------------
-  const int tot1 = warp_counts(nsmall, sh.cum, lane);
-  {
-    // each lane marks its tasks with its index: one byte load finds a
-    // task's cell
-    const int st = sh.cum[lane] - nsmall;
-    for (int i = 0; i < nsmall; ++i) sh.own[st + i] = (unsigned char)lane;
-    __syncwarp();
-  }
-  for (int f0 = 0; f0 < tot1; f0 += 32) {
-    const int f = f0 + lane;
-    if (f < tot1) {
-      const int L = sh.own[f];
-      const int off = f - (L ? sh.cum[L - 1] : 0);
-      const int4 bx = sh.box[L];
-      const int2 ex = sh.ext[L];
-      const int wd = ex.x & 7, hg = ex.x >> 3;  // hg > 0: a whole-box cell of hg rows
-      // off < 16 and wd <= 4: off / wd without a division
-      const int r = wd == 3 ? (off * 21846) >> 16 : off >> (wd >> 1);
-      const int px = bx.z + off - r * wd, py = bx.w + r;
-      float qx[4], qy[4], sl[4];
-      unpack4(qx, sh.qx[L]);
-      unpack4(qy, sh.qy[L]);
-      unpack4(sl, sh.sl[L]);
-      const float a = pixel_area_f(qx, qy, sl, (float)(px - bx.x), (float)(py - bx.y));
-      if (a != 0.0f) {
-        const float fr = a * __int_as_float(ex.y);
-        atomicAdd(&A.map[(int64_t)py * npx + px], A.scale_f * fr);
-        led.nupd += 1;
-        if (hg) {
-          // inside the map: npx * npy < 2^31, the offset fits an int (the
-          // remainder's correction, not counted as a map increment)
-          atomicAdd(&A.map[(bx.w + hg - 1) * npx + bx.z + wd - 1], -A.scale_f * fr);
-        } else {
-          led.fin += fr;
-          led.fout -= fr;
+  // ---- B: pixels of small cells (skipped by a round without any) ----------
+  if (__any_sync(0xffffffffu, nsmall > 0)) {
+    const int tot1 = warp_counts(nsmall, sh.cum, lane);
+    {
+      // each lane marks its tasks with its index: one byte load finds a
+      // task's cell
+      const int st = sh.cum[lane] - nsmall;
+      for (int i = 0; i < nsmall; ++i) sh.own[st + i] = (unsigned char)lane;
+      __syncwarp();
+    }
+    for (int f0 = 0; f0 < tot1; f0 += 32) {
+      const int f = f0 + lane;
+      if (f < tot1) {
+        const int L = sh.own[f];
+        const int off = f - (L ? sh.cum[L - 1] : 0);
+        const int4 bx = sh.box[L];
+        const int2 ex = sh.ext[L];
+        const int wd = ex.x & 7, hg = ex.x >> 3;  // hg > 0: a whole-box cell of hg rows
+        // off < 16 and wd <= 4: off / wd without a division
+        const int r = wd == 3 ? (off * 21846) >> 16 : off >> (wd >> 1);
+        const int px = bx.z + off - r * wd, py = bx.w + r;
+        float qx[4], qy[4], sl[4];
+        unpack4(qx, sh.qx[L]);
+        unpack4(qy, sh.qy[L]);
+        unpack4(sl, sh.sl[L]);
+        const float a = pixel_area_f(qx, qy, sl, (float)(px - bx.x), (float)(py - bx.y));
+        if (a != 0.0f) {
+          const float fr = a * __int_as_float(ex.y);
+          atomicAdd(&A.map[(int64_t)py * npx + px], A.scale_f * fr);
+          led.nupd += 1;
+          if (hg) {
+            // inside the map: npx * npy < 2^31, the offset fits an int (the
+            // remainder's correction, not counted as a map increment)
+            atomicAdd(&A.map[(bx.w + hg - 1) * npx + bx.z + wd - 1], -A.scale_f * fr);
+          } else {
+            led.fin += fr;
+            led.fout -= fr;
+          }
         }
       }
     }
   }
-  // ---- C: rows of large cells ---------------------------------------------
+  // ---- C: rows of large cells (skipped by a round without any) -------------
+  if (!__any_sync(0xffffffffu, nrows > 0)) return;
   const int tot2 = warp_counts(nrows, sh.cum2, lane);
   for (int f0 = 0; f0 < tot2; f0 += 32) {
     const int f = f0 + lane;
