@@ -601,6 +601,34 @@ def config_line(args):
         line["config"]["parts"] = "forward (build + deflect + light curve) + backward (light-curve gradient + adjoint FMM)"
         n = args.steps
         line["phase_ms"] = {"forward": sum(split["fwd"][-n:]) / n, "backward": sum(split["bwd"][-n:]) / n}
+        # the adjoint FMM alone (lens_deflect_adjoint on this step's plan and
+        # rays, a random cotangent), against its near-field transpose: the
+        # forward's ray-star pairs (counted by a one-chunk map over the same
+        # grid) at ~14 float32 flops each (the complex 1/d and 1/d^2 per pair)
+        PA = lens.LensFMM(stars, masses, f.kappa_s, f.gamma, p=p, leaf_size=leaf,
+                          prec=lens.FP32_BULK, target_box=box)
+        _, st_a = PA.ipm_map(g, box, 1024, 1024)
+        assert st_a["chunks"] == 1
+        cot = torch.randn(rays.shape, dtype=torch.float64, device=dev,
+                          generator=torch.Generator(device=dev).manual_seed(args.seed + 5))
+        PA.adjoint(rays, cot)
+        torch.cuda.synchronize()
+        ea = torch.cuda.Event(enable_timing=True); eb = torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(3):
+            PA.adjoint(rays, cot)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        ms_adj = ea.elapsed_time(eb) / 3
+        PA.close()
+        atf = 14.0 * st_a["p2p_pairs"] / (ms_adj / 1e3) / 1e12
+        line["adjoint_roofline"] = {
+            "bound": "alu", "kernel": "lens_deflect_adjoint (P2P^T, L2P^T/M2P^T moments, "
+            "transposed translations)", "achieved": atf, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": atf / fp32_peak, "ms": ms_adj, "pairs": st_a["p2p_pairs"],
+            "work": "14 flops per ray-star pair of the near field (the transposed translations "
+                    "and moments not counted)"}
+        line["roofline"] = dict(line["adjoint_roofline"], traffic=None)
         # the float64 form of the same step (forward and adjoint in float64)
         for _ in range(2):
             step(lens.FP64, record=False)

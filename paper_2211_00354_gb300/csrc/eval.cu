@@ -411,19 +411,28 @@ __global__ void k_tiles_from_counts(const int64_t* __restrict__ counts, int64_t 
   tiles[k] = (counts[k] + tile - 1) / tile;
 }
 
-// (leaf, tile within the leaf) of every ray tile, from the tile offsets:
-// each block of the evaluation kernels finds its leaf with one load
-__global__ void k_tile_leaf(const int64_t* __restrict__ toff, int64_t nl, int2* __restrict__ out) {
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= nl) return;
-  const int64_t t0 = toff[k], t1 = toff[k + 1];
-  for (int64_t t = t0; t < t1; ++t) out[t] = make_int2((int)k, (int)(t - t0));
+// (leaf, tile within the leaf) of every ray tile, one thread per tile, so
+// that each block of the evaluation kernels finds its leaf with one load.
+// The offsets are an exclusive scan (toff[0] = 0, toff[nl] = total): the
+// tile's leaf is the last one whose offset is at or below it, found by
+// bisection with toff[lo] <= t < toff[hi] held throughout; a leaf of no
+// tiles shares its offset with the next and is passed over.
+__global__ void k_tile_leaf(const int64_t* __restrict__ toff, int64_t nl, int64_t total,
+                            int2* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int64_t lo = 0, hi = nl;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (toff[mid] <= t) lo = mid; else hi = mid;
+  }
+  out[t] = make_int2((int)lo, (int)(t - toff[lo]));
 }
 
 Scratch tile_leaves(Plan& P, const int64_t* toff, int64_t nl, int64_t total, cudaStream_t s) {
   if (total > (int64_t)INT32_MAX) fail(LENS_EINVAL, "too many ray tiles in one call");
   Scratch tl(&P.da, sizeof(int2) * (size_t)std::max<int64_t>(total, 1));
-  k_tile_leaf<<<grid_for(nl, 128), 128, 0, s>>>(toff, nl, tl.as<int2>());
+  k_tile_leaf<<<grid_for(total, 256), 256, 0, s>>>(toff, nl, total, tl.as<int2>());
   LENS_LAUNCHED("k_tile_leaf");
   return tl;
 }
