@@ -139,7 +139,7 @@ typedef struct {
   int64_t device_bytes;        /* plan-owned device memory */
   double ms_build;             /* device time of the build, tree to expansions */
   int64_t build_launches;      /* kernels the build launched */
-  double ms_tree;              /* of ms_build: tree, lists and near-field staging */
+  double ms_tree;              /* of ms_build: boxes and interaction lists */
   double ms_far_local;         /* device time of the far-field launch (M2L over the
                                   V lists and P2L over the X lists, all levels) */
 } lens_plan_info;

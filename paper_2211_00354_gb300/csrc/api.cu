@@ -226,33 +226,52 @@ lens_status lens_fmm_build(const double* stars_xy, const double* masses, int64_t
   LENS_CUDA(cudaEventCreate(&P.ev_start));
   LENS_CUDA(cudaEventCreate(&P.ev_tree));
   LENS_CUDA(cudaEventCreateWithFlags(&P.ev_boxes, cudaEventDisableTiming));
+  LENS_CUDA(cudaEventCreateWithFlags(&P.ev_up, cudaEventDisableTiming));
+  LENS_CUDA(cudaEventCreate(&P.ev_lists));
   LENS_CUDA(cudaEventCreate(&P.ev_fmm));
   LENS_CUDA(cudaEventCreate(&P.ev_far0));
   LENS_CUDA(cudaEventCreate(&P.ev_far1));
   LENS_CUDA(cudaEventRecord(P.ev_start, S(stream)));
   const long long l0 = launch_count();
-  // The tree on the caller's stream.  The upward pass (P2M, M2M) needs only
-  // the boxes, so it runs on the plan's high-priority stream while the
-  // caller's stream forms the active boxes, the interaction lists and the
-  // float32 near-field staging; the downward pass follows the lists.
+  // The boxes on the caller's stream.  The upward pass (P2M, M2M) needs only
+  // the boxes: it runs on the plan's low-priority stream, and the
+  // interaction lists on its high-priority stream, so that the lists (short
+  // launches and two read-backs) are not queued behind the float64 upward
+  // blocks.  The far field then waits for both, the float32 near-field
+  // staging for the lists only (on the caller's stream, beside the far field).
   fmm_tables(P, S(stream));
   tree_build_boxes(P, stars_xy, masses, S(stream));
   fmm_alloc(P);
   LENS_CUDA(cudaEventRecord(P.ev_boxes, S(stream)));
   int lo_prio = 0, hi_prio = 0;
   LENS_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+  LENS_CUDA(cudaStreamCreateWithPriority(&P.up_stream, cudaStreamNonBlocking, lo_prio));
   LENS_CUDA(cudaStreamCreateWithPriority(&P.fmm_stream, cudaStreamNonBlocking, hi_prio));
+  LENS_CUDA(cudaStreamWaitEvent(P.up_stream, P.ev_boxes, 0));
   LENS_CUDA(cudaStreamWaitEvent(P.fmm_stream, P.ev_boxes, 0));
-  fmm_p2m(P, P.fmm_stream);
-  fmm_m2m(P, P.fmm_stream);
-  tree_build_lists(P, S(stream));
+  fmm_p2m(P, P.up_stream);
+  fmm_m2m(P, P.up_stream);
+  LENS_CUDA(cudaEventRecord(P.ev_up, P.up_stream));
+  {
+    // the lists' allocations are ordered on the stream that uses them
+    struct Restore {
+      DeviceAlloc& da;
+      cudaStream_t s;
+      ~Restore() { da.stream = s; }
+    } restore{P.da, P.da.stream};
+    P.da.stream = P.fmm_stream;
+    tree_build_lists(P, P.fmm_stream);
+  }
+  LENS_CUDA(cudaEventRecord(P.ev_lists, P.fmm_stream));
+  LENS_CUDA(cudaStreamWaitEvent(P.fmm_stream, P.ev_up, 0));
+  fmm_downward(P, P.fmm_stream);
+  LENS_CUDA(cudaStreamWaitEvent(S(stream), P.ev_lists, 0));
   if (P.prec == LENS_FP32_BULK) {
     eval32_alloc(P);
     eval32_prepare_tree(P, S(stream));
   }
   LENS_CUDA(cudaEventRecord(P.ev_tree, S(stream)));
   LENS_CUDA(cudaStreamWaitEvent(P.fmm_stream, P.ev_tree, 0));
-  fmm_downward(P, P.fmm_stream);
   if (P.prec == LENS_FP32_BULK) eval32_prepare_expansions(P, P.fmm_stream);
   LENS_CUDA(cudaEventRecord(P.ev_fmm, P.fmm_stream));
   P.build_launches = launch_count() - l0;
@@ -282,7 +301,9 @@ void lens_plan_destroy(lens_plan* plan) {
   cudaStreamSynchronize(P.da.stream);
   P.ev_clear();
   if (P.fmm_stream) cudaStreamDestroy(P.fmm_stream);
-  for (cudaEvent_t e : {P.ev_start, P.ev_boxes, P.ev_tree, P.ev_fmm, P.ev_far0, P.ev_far1})
+  if (P.up_stream) cudaStreamDestroy(P.up_stream);
+  for (cudaEvent_t e : {P.ev_start, P.ev_boxes, P.ev_tree, P.ev_fmm, P.ev_far0, P.ev_far1,
+                        P.ev_up, P.ev_lists})
     if (e) cudaEventDestroy(e);
   delete plan;
 }
@@ -308,7 +329,7 @@ lens_status lens_plan_info_get(const lens_plan* plan, lens_plan_info* info) {
   if (P.ev_fmm) {
     LENS_CUDA(cudaEventSynchronize(P.ev_fmm));
     LENS_CUDA(cudaEventElapsedTime(&ms, P.ev_start, P.ev_fmm));
-    LENS_CUDA(cudaEventElapsedTime(&ms_tree, P.ev_start, P.ev_tree));
+    LENS_CUDA(cudaEventElapsedTime(&ms_tree, P.ev_start, P.ev_lists));
   }
   info->ms_build = ms;
   info->ms_tree = ms_tree;

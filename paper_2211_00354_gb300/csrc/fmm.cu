@@ -22,6 +22,7 @@
 // kernels are written to issue as few DFMAs as the series allow.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "cx.cuh"
@@ -437,18 +438,26 @@ void fmm_tables(Plan& P, cudaStream_t s) {
     auto w = cpow(0.5, 0.5, k);
     wp[(size_t)k] = make_double2(w.first, w.second);
   }
-  t.binom = P.dalloc_n<double>(bin.size());
-  t.m2m = P.dalloc_n<double2>(m2m.size());
-  t.l2l = P.dalloc_n<double2>(l2l.size());
-  t.upow = P.dalloc_n<double2>(up.size());
-  t.wpow = P.dalloc_n<double2>(wp.size());
-  LENS_CUDA(cudaMemcpyAsync(t.binom, bin.data(), bin.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  LENS_CUDA(cudaMemcpyAsync(t.m2m, m2m.data(), m2m.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
-  LENS_CUDA(cudaMemcpyAsync(t.l2l, l2l.data(), l2l.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
-  LENS_CUDA(cudaMemcpyAsync(t.upow, up.data(), up.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
-  LENS_CUDA(cudaMemcpyAsync(t.wpow, wp.data(), wp.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
-  // host vectors must stay alive until the copies have run
-  LENS_CUDA(cudaStreamSynchronize(s));
+  // one host block (kept in the plan until the copy has run: no wait here);
+  // bin holds (2p+2)(p+2) doubles, an even count, so the complex tables
+  // after it start on 16-byte boundaries
+  const size_t nd = bin.size() + 2 * (m2m.size() + l2l.size() + up.size() + wp.size());
+  P.tab_host.assign(nd, 0.0);
+  double* h = P.tab_host.data();
+  std::memcpy(h, bin.data(), bin.size() * sizeof(double));
+  size_t o = bin.size();
+  for (const auto* v : {&m2m, &l2l, &up, &wp}) {
+    std::memcpy(h + o, v->data(), v->size() * sizeof(double2));
+    o += 2 * v->size();
+  }
+  double* d = P.dalloc_n<double>(nd);
+  LENS_CUDA(cudaMemcpyAsync(d, h, nd * sizeof(double), cudaMemcpyHostToDevice, s));
+  o = bin.size();
+  t.binom = d;
+  t.m2m = reinterpret_cast<double2*>(d + o); o += 2 * m2m.size();
+  t.l2l = reinterpret_cast<double2*>(d + o); o += 2 * l2l.size();
+  t.upow = reinterpret_cast<double2*>(d + o); o += 2 * up.size();
+  t.wpow = reinterpret_cast<double2*>(d + o);
 }
 
 void fmm_alloc(Plan& P) {

@@ -181,13 +181,19 @@ struct Plan {
   double ms_build = 0;
   int64_t build_launches = 0;
 
-  // The expansions run on a high-priority stream of the plan: P2M and M2M
-  // once the boxes exist (ev_boxes), the downward pass and the float32 copies
-  // once the lists exist (ev_tree); ev_fmm marks their end.  Work that reads
-  // M or L waits on ev_fmm (wait_expansions); work that needs only the tree
-  // waits on ev_tree.
-  cudaStream_t fmm_stream = nullptr;
+  // Once the boxes exist (ev_boxes), P2M and M2M run on a low-priority
+  // stream of the plan (ev_up marks their end) while the interaction lists
+  // are formed on a high-priority one (ev_lists); the downward pass follows
+  // both on the high-priority stream, the float32 near-field staging follows
+  // the lists on the caller's stream (ev_tree), and the float32 copies of
+  // the expansions follow both (ev_fmm marks the end).  Work that reads M or
+  // L waits on ev_fmm (wait_expansions); work that needs only the tree waits
+  // on ev_tree.
+  cudaStream_t fmm_stream = nullptr, up_stream = nullptr;
   cudaEvent_t ev_start = nullptr, ev_boxes = nullptr, ev_tree = nullptr, ev_fmm = nullptr;
+  cudaEvent_t ev_up = nullptr, ev_lists = nullptr;
+  // host copies of the translation tables, alive until their copies have run
+  std::vector<double> tab_host;
   // around the far-field launch (M2L over V, P2L over X) on the plan's stream
   cudaEvent_t ev_far0 = nullptr, ev_far1 = nullptr;
   bool build_timed = false;
