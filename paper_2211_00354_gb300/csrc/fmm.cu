@@ -141,10 +141,21 @@ __global__ void __launch_bounds__(kM2MThreads)
 k_m2m(const int* __restrict__ parent, int64_t c0, int64_t ngroups, int p,
       const double* __restrict__ binom, int ldb, const double2* __restrict__ wpow,
       double2* __restrict__ M) {
-  extern __shared__ double2 H[];  // [parents per block][4][p+1]
+  extern __shared__ double2 H[];  // [parents per block][4][p+1], then the binomials
   const int P1 = p + 1;
   const int per = kM2MThreads / P1;  // parents per block (>= 1 for p <= 64)
   const int t = threadIdx.x, pb = t / P1, k = t - pb * P1;
+  // rows 0..p of the binomial table, triangular (row l from l (l+1) / 2), in
+  // shared memory: the row sums below then wait on no global load (a small
+  // level has too few blocks to keep the table in L1)
+  double* cb_tab = reinterpret_cast<double*>(H + (int64_t)per * 4 * P1);
+  for (int i = t; i < P1 * (P1 + 1) / 2; i += kM2MThreads) {
+    // i = l (l+1)/2 + kk, 0 <= kk <= l
+    int l = (int)((sqrtf(8.f * (float)i + 1.f) - 1.f) * 0.5f);
+    while (l * (l + 1) / 2 > i) --l;
+    while ((l + 1) * (l + 2) / 2 <= i) ++l;
+    cb_tab[i] = binom[(int64_t)l * ldb + (i - l * (l + 1) / 2)];
+  }
   const int64_t g = (int64_t)blockIdx.x * per + pb;
   const bool on = pb < per && g < ngroups;
   const int64_t c = c0 + 4 * g;     // first child of the group
@@ -166,8 +177,9 @@ k_m2m(const int* __restrict__ parent, int64_t c0, int64_t ngroups, int p,
   if (on) {
     const int l = k;
     double sx = 0.0, sy = 0.0;
+    const double* crow = cb_tab + l * (l + 1) / 2;
     for (int kk = 0; kk <= l; ++kk) {
-      const double cb = __ldg(binom + (int64_t)l * ldb + kk);
+      const double cb = crow[kk];
       const double2 h = Hp[((l - kk) & 3) * P1 + kk];
       sx = fma(cb, h.x, sx);
       sy = fma(cb, h.y, sy);
@@ -512,7 +524,7 @@ void fmm_m2m(Plan& P, cudaStream_t s) {
   const FmmTables& t = P.tab;
   const int P1 = P.p + 1;
   const int per = kM2MThreads / P1;
-  const size_t smem = sizeof(double2) * 4 * (size_t)P1 * per;
+  const size_t smem = sizeof(double2) * 4 * (size_t)P1 * per + sizeof(double) * P1 * (P1 + 1) / 2;
   for (int l = P.nlevels - 2; l >= 0; --l) {
     // level l+1 holds the children of the level-l splits, four per split
     const int64_t c0 = P.level_off[l + 1], ng = (P.level_off[l + 2] - c0) / 4;
