@@ -121,18 +121,31 @@ __device__ __forceinline__ int first_level(const uint64_t* k, int64_t i, int dep
   return lcp + 1;
 }
 
-// Pass 1 (write == false): per-level split counts.  Pass 2: write entries
-// (level << 32 | first star) at per-level cursors.
+// Pass 1 (write == false): per-level split counts, in total and per block
+// (bcnt, level-major: bcnt[l * blocks + block]).  Pass 2: write the entries
+// (level << 32 | first star) in star order within each level, which is the
+// order of (level, box code) that k_fill_boxes reads: boff is the exclusive
+// scan of bcnt (the level-major layout makes it the level's offset plus the
+// entries of earlier blocks), and inside a block the entries of a level are
+// ranked in thread order by warp ballots.  The grid is the same in both
+// passes (kSplitThreads threads a block over the n stars).
 // The keys need only be sorted by their level-dcap prefixes (the top 2 dcap
 // of their 2 depth bits): a box of level dcap with more than leaf stars sets
 // deep_flag (the caller then sorts fully, or, at dcap == depth, fails).
+constexpr int kSplitThreads = 256;
+
 template <bool WRITE>
-__global__ void k_splits(const uint64_t* __restrict__ k, int64_t n, int depth, int dcap, int leaf,
-                         unsigned long long* __restrict__ counts, int* __restrict__ deep_flag,
-                         unsigned long long* __restrict__ cursor, uint64_t* __restrict__ out) {
+__global__ void __launch_bounds__(kSplitThreads)
+k_splits(const uint64_t* __restrict__ k, int64_t n, int depth, int dcap, int leaf,
+         unsigned long long* __restrict__ counts, int* __restrict__ deep_flag,
+         int64_t* __restrict__ bcnt, const int64_t* __restrict__ boff,
+         uint64_t* __restrict__ out) {
+  constexpr int kW = kSplitThreads / 32;
   __shared__ unsigned int sc[kMaxDepth + 1];
-  __shared__ unsigned long long sbase[kMaxDepth + 1];
+  __shared__ unsigned int wc[kMaxDepth][kW];
+  __shared__ int lrange[2];
   for (int q = threadIdx.x; q <= kMaxDepth; q += blockDim.x) sc[q] = 0;
+  if (threadIdx.x == 0) { lrange[0] = kMaxDepth; lrange[1] = -1; }
   __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   uint64_t ki = 0, kl = 0;
@@ -157,21 +170,30 @@ __global__ void k_splits(const uint64_t* __restrict__ k, int64_t n, int depth, i
       }
     }
   }
-  for (int l = l0; l < l1; ++l) atomicAdd(&sc[l], 1u);
-  __syncthreads();
   if constexpr (!WRITE) {
-    for (int q = threadIdx.x; q < kMaxDepth; q += blockDim.x)
-      if (sc[q]) atomicAdd(&counts[q], (unsigned long long)sc[q]);
-  } else {
-    // one global reservation per level and block, then block-local slots
+    for (int l = l0; l < l1; ++l) atomicAdd(&sc[l], 1u);
+    __syncthreads();
     for (int q = threadIdx.x; q < kMaxDepth; q += blockDim.x) {
-      sbase[q] = sc[q] ? atomicAdd(&cursor[q], (unsigned long long)sc[q]) : 0ull;
-      sc[q] = 0;
+      if (sc[q]) atomicAdd(&counts[q], (unsigned long long)sc[q]);
+      bcnt[(int64_t)q * gridDim.x + blockIdx.x] = sc[q];
+    }
+  } else {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (l1 > l0) { atomicMin(&lrange[0], l0); atomicMax(&lrange[1], l1 - 1); }
+    __syncthreads();
+    const int la = lrange[0], lb = lrange[1];  // block-uniform
+    for (int l = la; l <= lb; ++l) {
+      const unsigned m = __ballot_sync(0xffffffffu, l >= l0 && l < l1);
+      if (lane == 0) wc[l][w] = __popc(m);
     }
     __syncthreads();
-    for (int l = l0; l < l1; ++l) {
-      const unsigned int r = atomicAdd(&sc[l], 1u);
-      out[sbase[l] + r] = ((uint64_t)l << 32) | (uint64_t)i;
+    for (int l = la; l <= lb; ++l) {
+      const unsigned m = __ballot_sync(0xffffffffu, l >= l0 && l < l1);
+      if (l >= l0 && l < l1) {
+        int64_t pos = boff[(int64_t)l * gridDim.x + blockIdx.x] + __popc(m & ((1u << lane) - 1u));
+        for (int q = 0; q < w; ++q) pos += wc[l][q];
+        out[pos] = ((uint64_t)l << 32) | (uint64_t)i;
+      }
     }
   }
 }
@@ -466,12 +488,14 @@ void tree_build_boxes(Plan& P, const double* stars, const double* masses, cudaSt
   Scratch dcnt(&P.da, sizeof(unsigned long long) * (kMaxDepth + 2) + sizeof(int) * 4);
   unsigned long long* counts = dcnt.as<unsigned long long>();
   int* deep = reinterpret_cast<int*>(counts + kMaxDepth + 2);
+  const unsigned nblk = grid_for(n, kSplitThreads);
+  Scratch bcnt(&P.da, sizeof(int64_t) * kMaxDepth * (size_t)nblk);
   unsigned long long hc[kMaxDepth + 2];
   int hdeep[4];
   for (;;) {
     LENS_CUDA(cudaMemsetAsync(dcnt.p, 0, dcnt.bytes, s));
-    k_splits<false><<<grid_for(n, 256), 256, 0, s>>>(P.skey, n, depth, dcap, P.leaf, counts, deep,
-                                                     nullptr, nullptr);
+    k_splits<false><<<nblk, kSplitThreads, 0, s>>>(P.skey, n, depth, dcap, P.leaf, counts, deep,
+                                                   bcnt.as<int64_t>(), nullptr, nullptr);
     LENS_LAUNCHED("k_splits<count>");
     LENS_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
     LENS_CUDA(cudaMemcpyAsync(hdeep, deep, sizeof(hdeep), cudaMemcpyDeviceToHost, s));
@@ -523,18 +547,11 @@ void tree_build_boxes(Plan& P, const double* stars, const double* masses, cudaSt
   LENS_LAUNCHED("k_root");
   if (nsplit > 0) {
     Scratch dspl(&P.da, sizeof(uint64_t) * nsplit);
-    Scratch dcur(&P.da, sizeof(unsigned long long) * (kMaxDepth + 2));
-    std::vector<unsigned long long> hcur(kMaxDepth + 2);
-    for (int l = 0; l < kMaxDepth + 2; ++l) hcur[l] = (unsigned long long)soff.off[l];
-    LENS_CUDA(cudaMemcpyAsync(dcur.p, hcur.data(), sizeof(unsigned long long) * hcur.size(),
-                              cudaMemcpyHostToDevice, s));
-    k_splits<true><<<grid_for(n, 256), 256, 0, s>>>(P.skey, n, depth, dcap, P.leaf, nullptr, nullptr,
-                                                    dcur.as<unsigned long long>(),
-                                                    dspl.as<uint64_t>());
+    Scratch bpos(&P.da, sizeof(int64_t) * kMaxDepth * (size_t)nblk);
+    exclusive_scan_i64(bcnt.as<int64_t>(), bpos.as<int64_t>(), (int64_t)kMaxDepth * nblk, P.da, s);
+    k_splits<true><<<nblk, kSplitThreads, 0, s>>>(P.skey, n, depth, dcap, P.leaf, nullptr, nullptr,
+                                                  nullptr, bpos.as<int64_t>(), dspl.as<uint64_t>());
     LENS_LAUNCHED("k_splits<write>");
-    int bits = 32;
-    while ((1ll << (bits - 32)) <= depth) ++bits;
-    radix_sort_u64(dspl.as<uint64_t>(), nullptr, nsplit, bits, P.da, s);
     k_fill_boxes<<<grid_for(nsplit, 256), 256, 0, s>>>(
         dspl.as<uint64_t>(), nsplit, soff, boff, P.skey, n, depth, P.box_start, P.box_count,
         P.box_child, P.box_parent, P.box_level, P.box_ix, P.box_iy, P.box_code);
