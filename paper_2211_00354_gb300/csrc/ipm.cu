@@ -127,70 +127,6 @@ void event_pair_end(std::pair<cudaEvent_t, cudaEvent_t>& e, cudaStream_t s) {
   LENS_CUDA(cudaEventRecord(e.second, s));
 }
 
-// map (+)= map32 + row-wise prefix sum of the difference array (float64),
-// one warp per map row: the warp walks the row 32 columns at a time (four
-// such groups loaded ahead), a shuffle scan gives each column its prefix
-// within the group and a running total carries it across groups, so every
-// load and store is coalesced.  With `clear` the float32 accumulators are
-// zeroed behind the read, so the next cells start from zero (a flush
-// between chunks).
-constexpr int kFinishThreads = 256;
-constexpr int kFinishAhead = 4;
-
-__global__ void __launch_bounds__(kFinishThreads)
-k_map_finish(float* __restrict__ m32, float* __restrict__ D, int npx, int npy, int64_t ldd,
-             double* __restrict__ out, bool accumulate, bool clear) {
-  constexpr int kWarps = kFinishThreads / 32;
-  const int lane = threadIdx.x & 31;
-  const int64_t step = (int64_t)gridDim.x * kWarps;
-  for (int64_t row = blockIdx.x * (int64_t)kWarps + (threadIdx.x >> 5); row < npy; row += step) {
-    float* d = D + row * ldd;
-    float* m = m32 + row * (int64_t)npx;
-    double* o = out + row * (int64_t)npx;
-    double carry = 0.0;
-    for (int c0 = 0; c0 < npx; c0 += 32 * kFinishAhead) {
-      float dv[kFinishAhead], mv[kFinishAhead];
-      double ov[kFinishAhead];
-#pragma unroll
-      for (int j = 0; j < kFinishAhead; ++j) {
-        const int c = c0 + 32 * j + lane;
-        const bool in = c < npx;
-        dv[j] = in ? d[c] : 0.f;
-        mv[j] = in ? m[c] : 0.f;
-        ov[j] = in && accumulate ? o[c] : 0.0;
-      }
-#pragma unroll
-      for (int j = 0; j < kFinishAhead; ++j) {
-        const int c = c0 + 32 * j + lane;
-        double incl = (double)dv[j];
-#pragma unroll
-        for (int k = 1; k < 32; k <<= 1) {
-          const double v = __shfl_up_sync(0xffffffffu, incl, k);
-          if (lane >= k) incl += v;
-        }
-        const double base = carry + incl;
-        carry += __shfl_sync(0xffffffffu, incl, 31);
-        if (c < npx) {
-          const double v = (double)mv[j] + base;
-          o[c] = accumulate ? ov[j] + v : v;
-          if (clear) { m[c] = 0.f; d[c] = 0.f; }
-        }
-      }
-    }
-    // column npx of the difference array only ever receives run ends
-    if (clear && lane == 0) d[npx] = 0.f;
-  }
-}
-
-void ipm_finish_map(float* map32, float* rowdiff, int npx, int npy, double* map, bool accumulate,
-                    bool clear, cudaStream_t s) {
-  constexpr int kWarps = kFinishThreads / 32;
-  const unsigned blocks = (unsigned)std::min<int64_t>((npy + kWarps - 1) / kWarps, 152 * 8);
-  k_map_finish<<<blocks, kFinishThreads, 0, s>>>(map32, rowdiff, npx, npy, (int64_t)npx + 1, map,
-                                                 accumulate, clear);
-  LENS_LAUNCHED("k_map_finish");
-}
-
 // thresholds and the float32 map increment of a launch (from ip and wcell)
 void ipm_prepare(IpmArgs& A) {
   A.thr_area = (float)(1e-13 * A.ip.a_cell / A.ip.s_star);

@@ -346,8 +346,10 @@ Scratch eval32_fused(Plan& P, const GridRows& g, const int64_t* rect, PixCorner*
 void evaluate_grid_fused(Plan& P, const GridRows& g, PixCorner* edge, const IpmParams& ip,
                          float* map32, float* rowdiff, double* stats_dev, int* queue, int* qcount,
                          int* rq, int* rqcount, cudaStream_t s);
-// map (float64 output) = map32 + row-wise prefix sums of rowdiff, or += with
-// `accumulate`; `clear` zeroes map32 and rowdiff behind the read
+// map = map32 + row-wise prefix sums of rowdiff (mapfinish.cu): `clear` (a
+// flush between chunks) keeps the sum in map's slots as float-float pairs
+// and zeroes map32 and rowdiff; otherwise float64 is written, the pairs
+// added first with `accumulate`
 void ipm_finish_map(float* map32, float* rowdiff, int npx, int npy, double* map, bool accumulate,
                     bool clear, cudaStream_t s);
 // map consumers (mapops.cu): Gaussian finite source, histogram, track

@@ -67,6 +67,23 @@ def test_affine_lens_map_is_inverse_determinant():
     assert ledger_ok(st)
 
 
+def test_flushed_map_of_an_expanding_affine_lens():
+    # kappa_s = -3, gamma = 0 and no stars: y = 4 x, so every cell maps to a
+    # square 4 h = 0.084 on a side, 8.4 pixels of 0.01 (the large-cell path:
+    # row bands, crossed pixels and the difference array), and every pixel
+    # of the window is covered with magnification 1/16.  A 40 x 40 map
+    # flushes its float32 accumulators into the float-float running map every
+    # 64 x 1600 cells, three times over the 571^2 grid, in chunks of 20 rows.
+    ks, g = -3.0, 0.0
+    grid = synth.Grid(x0=-6.0, y0=-6.0, h=0.021, nx=571, ny=571)
+    with lens.LensFMM(T([[0.0, 0.0]]), T([0.0]), ks, g, p=4, leaf_size=4, prec=lens.FP32_BULK,
+                      target_box=(-6, 6, -6, 6)) as P:
+        mp, st = P.ipm_map(grid, (-0.2, 0.2, -0.2, 0.2), 40, 40, max_cells_per_chunk=20 * 571)
+    assert st["chunks"] == 29
+    np.testing.assert_allclose(mp.cpu().numpy(), 1 / 16, rtol=2e-6)
+    assert ledger_ok(st)
+
+
 def test_point_lens_magnification():
     box = (-2.0, 2.0, -2.0, 2.0)
     h = 0.0125
