@@ -239,8 +239,7 @@ lens_status lens_fmm_build(const double* stars_xy, const double* masses, int64_t
   // launches and two read-backs) are not queued behind the float64 upward
   // blocks.  The far field then waits for both, the float32 near-field
   // staging for the lists only (on the caller's stream, beside the far field).
-  fmm_tables(P, S(stream));
-  tree_build_boxes(P, stars_xy, masses, S(stream));
+  tree_build_boxes(P, stars_xy, masses, S(stream));  // and the translation tables
   fmm_alloc(P);
   LENS_CUDA(cudaEventRecord(P.ev_boxes, S(stream)));
   int lo_prio = 0, hi_prio = 0;

@@ -434,6 +434,8 @@ void tree_build_boxes(Plan& P, const double* stars, const double* masses, cudaSt
     Scratch dpart(&P.da, sizeof(double) * kBoundsParts * nbb);
     k_bounds<<<nbb, 256, 0, s>>>(stars, masses, n, dpart.as<double>());
     LENS_LAUNCHED("k_bounds");
+    // the translation tables are formed on the host while the bounds run
+    fmm_tables(P, s);
     LENS_CUDA(cudaMemcpyAsync(part.data(), dpart.p, sizeof(double) * kBoundsParts * nbb,
                               cudaMemcpyDeviceToHost, s));
     LENS_CUDA(cudaStreamSynchronize(s));
