@@ -222,6 +222,27 @@ def test_evaluation_on_another_stream_waits_for_the_build():
             assert P.info()["ms_build"] > 0
 
 
+def test_plans_on_the_torch_allocator_match_the_default_pool():
+    # the build allocates on three streams (the caller's, and the plan's two
+    # for the upward pass and the lists); through torch's caching allocator
+    # the plan must give the same bits as with the library's own pool
+    f = synth.config_uniform(seed=7, n=30000, kappa_star=0.45, kappa_s=0.0, gamma=0.45)
+    g = synth.Grid(x0=-15.0, y0=-15.0, h=0.05, nx=600, ny=600)
+    box = (g.x0, g.x0 + g.nx * g.h, g.y0, g.y0 + g.ny * g.h)
+    x = T(synth.random_rays(8, 40000, (-15, -15), (15, 15)))
+    out = []
+    for torch_alloc in (False, True):
+        with lens.LensFMM(T(f.stars), T(f.masses), f.kappa_s, f.gamma, p=16, leaf_size=8,
+                          prec=lens.FP32_BULK, target_box=box, use_torch_allocator=torch_alloc) as P:
+            y = P.deflect(x)
+            mp, st = P.ipm_map(g, (-4.0, 4.0, -4.0, 4.0), 200, 200)
+            out.append((y.cpu().numpy(), mp.cpu().numpy(), st["area_in_map"]))
+    np.testing.assert_array_equal(out[1][0], out[0][0])
+    # the map's float32 atomics add in a schedule-dependent order
+    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-5, atol=1e-6 * np.abs(out[0][1]).max())
+    assert abs(out[1][2] - out[0][2]) <= 1e-6 * abs(out[0][2])
+
+
 def test_tiny_fields():
     for n, leaf in ((1, 16), (5, 16), (40, 1), (17, 16)):
         f = synth.config_uniform(seed=n, n=n, kappa_star=0.3, kappa_s=0.0, gamma=0.1)
