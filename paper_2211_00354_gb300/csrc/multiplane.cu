@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "lens_internal.h"
+#include "okey.cuh"
 
 namespace lens {
 namespace {
@@ -36,19 +37,8 @@ constexpr int kFarPix = 0x7fffffff;
 // per block: min/max of x and y over its share of the points, and whether
 // any coordinate is not finite
 // the bounding box of m positions by order-preserving integer keys of the
-// float64 values (exact; min / max and the finiteness test on the integer
-// pipe -- float64 min / max run on GB300's slow float64 pipe), one partial
-// box per block
-__device__ __forceinline__ unsigned long long okey(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double unkey(unsigned long long k) {
-  return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
-}
-__device__ __forceinline__ bool finite_bits(double v) {
-  return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
-}
+// float64 values (okey.cuh: exact, on the integer pipe), one partial box per
+// block
 
 __global__ void k_mp_bounds(const double2* __restrict__ x, int64_t m, double* __restrict__ part,
                             int* __restrict__ bad) {

@@ -1,13 +1,15 @@
 // sort.cu -- LSD radix sort of 64-bit keys (+ optional 32-bit values) and
-// device-wide exclusive scans.  Used for the Morton-order quadtree build
-// (Appendix A, step 1) and for the ordered split-node list.
+// device-wide exclusive scans.  The sort puts the stars in Morton order for
+// the quadtree build (Appendix A, step 1); the scans size the build's lists.
 //
 // Each 8-bit pass is reduce-then-scan: (1) per-tile digit histograms plus
 // the digit totals (atomics), (2) one block per digit scans its row of the
 // digit-major histogram matrix and adds the keys of smaller digits, (3) a
-// stable scatter in which every warp ranks its keys with __match_any_sync and
-// the block combines the per-warp counts.  No kernel waits on another block, so
-// nothing can spin: there is no decoupled look-back and no device-side wait.
+// stable scatter in which every warp ranks its keys with __match_any_sync,
+// the block combines the per-warp counts, stages its tile in shared memory
+// in digit order and writes each digit's keys out as one contiguous run.
+// No kernel waits on another block, so nothing can spin: there is no
+// decoupled look-back and no device-side wait.
 #include "cx.cuh"
 #include "lens_internal.h"
 
@@ -83,6 +85,11 @@ k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ v
                 uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
                 int shift, int nblocks, const uint32_t* __restrict__ hist) {
   __shared__ uint32_t wcnt[kSortWarps][256];
+  __shared__ uint32_t wsum[kSortWarps];
+  __shared__ uint32_t dstart[256];       // per digit: its start in the tile
+  __shared__ int64_t dofs[256];          // per digit: global start - start in the tile
+  __shared__ uint64_t skey[kSortTile];   // the tile in digit order
+  __shared__ uint32_t sval[kSortTile];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int q = threadIdx.x; q < kSortWarps * 256; q += kSortThreads) (&wcnt[0][0])[q] = 0;
   __syncthreads();
@@ -108,26 +115,49 @@ k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ v
     rank[k] = b0 + before;
   }
   __syncthreads();
-  // exclusive prefix of the per-warp counts, digit by digit
   {
-    const int d = threadIdx.x;  // 256 threads, one digit each
+    // per digit (one thread each): exclusive prefix of the per-warp counts,
+    // then the digit's start in the tile (a scan over the 256 digits' totals)
+    const int d = threadIdx.x;
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
-      uint32_t c = wcnt[w][d];
+      const uint32_t c = wcnt[w][d];
       wcnt[w][d] = run;
       run += c;
     }
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t start = incl - run;
+    for (int q = 0; q < warp; ++q) start += wsum[q];
+    dstart[d] = start;
+    dofs[d] = (int64_t)hist[(int64_t)d * nblocks + blockIdx.x] - (int64_t)start;
   }
   __syncthreads();
+  // every key's place in the tile: its digit's start, the earlier warps' keys
+  // of that digit, its rank in the warp (so the scatter stays stable)
 #pragma unroll
   for (int k = 0; k < kIPT; ++k) {
     const int64_t i = base + k * 32 + lane;
     if (i >= n) continue;
     const uint32_t d = (uint32_t)((key[k] >> shift) & 0xff);
-    const int64_t pos = (int64_t)hist[(int64_t)d * nblocks + blockIdx.x] + wcnt[warp][d] + rank[k];
-    kout[pos] = key[k];
-    if (vout) vout[pos] = val[k];
+    const int p = (int)(dstart[d] + wcnt[warp][d] + rank[k]);
+    skey[p] = key[k];
+    sval[p] = val[k];
+  }
+  __syncthreads();
+  const int nloc = (int)min64(kSortTile, n - (int64_t)blockIdx.x * kSortTile);
+  for (int t = threadIdx.x; t < nloc; t += kSortThreads) {
+    const uint64_t kk = skey[t];
+    const int64_t pos = dofs[(kk >> shift) & 0xff] + t;
+    kout[pos] = kk;
+    if (vout) vout[pos] = sval[t];
   }
 }
 

@@ -28,6 +28,7 @@
 
 #include "cx.cuh"
 #include "lens_internal.h"
+#include "okey.cuh"
 
 namespace lens {
 
@@ -41,36 +42,63 @@ struct LevelOffsets {
 // per block: x min, x max, y min, y max, non-finite count, mass min, mass max
 constexpr int kBoundsParts = 7;
 
-__global__ void k_bounds(const double* __restrict__ stars, const double* __restrict__ m,
-                         int64_t n, double* __restrict__ part) {
-  __shared__ double sh[kBoundsParts][256];
-  double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY, bad = 0;
-  double mmin = INFINITY, mmax = -INFINITY;
+// Per block: the bounds of its stars (grid-stride) by order-preserving
+// integer keys (okey.cuh: exact, on the integer pipe), reduced by warp
+// shuffles and across the block's warps.
+constexpr int kBoundsThreads = 256;
+
+__global__ void __launch_bounds__(kBoundsThreads)
+k_bounds(const double* __restrict__ stars, const double* __restrict__ m, int64_t n,
+         double* __restrict__ part) {
+  constexpr int kW = kBoundsThreads / 32;
+  __shared__ unsigned long long sh[6][kW];
+  __shared__ unsigned int shb[kW];
+  // keys of x min, x max, y min, y max, mass min, mass max
+  unsigned long long k[6] = {~0ull, 0ull, ~0ull, 0ull, ~0ull, 0ull};
+  unsigned int bad = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double x = stars[2 * i], y = stars[2 * i + 1], w = m[i];
-    if (!isfinite(x) || !isfinite(y) || !isfinite(w)) { bad += 1; continue; }
-    xmin = fmin(xmin, x); xmax = fmax(xmax, x);
-    ymin = fmin(ymin, y); ymax = fmax(ymax, y);
-    mmin = fmin(mmin, w); mmax = fmax(mmax, w);
+    if (!(finite_bits(x) && finite_bits(y) && finite_bits(w))) { ++bad; continue; }
+    const unsigned long long kx = okey(x), ky = okey(y), kw = okey(w);
+    k[0] = min(k[0], kx); k[1] = max(k[1], kx);
+    k[2] = min(k[2], ky); k[3] = max(k[3], ky);
+    k[4] = min(k[4], kw); k[5] = max(k[5], kw);
   }
-  sh[0][threadIdx.x] = xmin; sh[1][threadIdx.x] = xmax;
-  sh[2][threadIdx.x] = ymin; sh[3][threadIdx.x] = ymax; sh[4][threadIdx.x] = bad;
-  sh[5][threadIdx.x] = mmin; sh[6][threadIdx.x] = mmax;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      sh[0][threadIdx.x] = fmin(sh[0][threadIdx.x], sh[0][threadIdx.x + o]);
-      sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + o]);
-      sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + o]);
-      sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + o]);
-      sh[4][threadIdx.x] += sh[4][threadIdx.x + o];
-      sh[5][threadIdx.x] = fmin(sh[5][threadIdx.x], sh[5][threadIdx.x + o]);
-      sh[6][threadIdx.x] = fmax(sh[6][threadIdx.x], sh[6][threadIdx.x + o]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, k[q], o);
+      k[q] = (q & 1) ? max(k[q], v) : min(k[q], v);
     }
-    __syncthreads();
   }
-  if (threadIdx.x < kBoundsParts) part[blockIdx.x * kBoundsParts + threadIdx.x] = sh[threadIdx.x][0];
+  bad = __reduce_add_sync(0xffffffffu, bad);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sh[q][w] = k[q];
+    shb[w] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x < kBoundsParts) {
+    const int t = threadIdx.x;
+    double v;
+    if (t == 4) {
+      unsigned int s = 0;
+      for (int q = 0; q < kW; ++q) s += shb[q];
+      v = (double)s;
+    } else {
+      // slots 0..3 and 5, 6: the key row t (t < 4) or t - 1
+      const int q = t < 4 ? t : t - 1;
+      unsigned long long r = sh[q][0];
+      for (int j = 1; j < kW; ++j) r = (q & 1) ? max(r, sh[q][j]) : min(r, sh[q][j]);
+      // no finite star in this block: the empty bounds
+      const bool none = (q & 1) ? r == 0ull : r == ~0ull;
+      v = none ? ((q & 1) ? -INFINITY : INFINITY) : unkey(r);
+    }
+    part[blockIdx.x * kBoundsParts + t] = v;
+  }
 }
 
 __global__ void k_keys(const double* __restrict__ stars, int64_t n, double lo_x, double lo_y,
@@ -432,7 +460,7 @@ void tree_build_boxes(Plan& P, const double* stars, const double* masses, cudaSt
   std::vector<double> part(kBoundsParts * (size_t)nbb);
   {
     Scratch dpart(&P.da, sizeof(double) * kBoundsParts * nbb);
-    k_bounds<<<nbb, 256, 0, s>>>(stars, masses, n, dpart.as<double>());
+    k_bounds<<<nbb, kBoundsThreads, 0, s>>>(stars, masses, n, dpart.as<double>());
     LENS_LAUNCHED("k_bounds");
     // the translation tables are formed on the host while the bounds run
     fmm_tables(P, s);
