@@ -312,7 +312,7 @@ __device__ __forceinline__ void grid_offset(const E32Args& A, const LeafGrid& lg
 }
 
 template <bool JAC, bool GRID, bool PIX, bool UM = false>
-__global__ void __launch_bounds__(kT, 6) k_eval32(E32Args A) {
+__global__ void __launch_bounds__(kT, 7) k_eval32(E32Args A) {
   __shared__ E32Smem sm;
   const int tid = threadIdx.x;
   const int p = A.p;
