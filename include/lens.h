@@ -202,15 +202,18 @@ lens_status lens_deflect_grid(lens_plan* plan, const lens_grid* grid,
 
 /* FMM-IPM magnification map (Sec. 2.4 steps 2-4): the grid is split into row
  * chunks of at most max_cells_per_chunk cells (0 = sized from free device
- * memory; never more than 64 cells per map pixel, after which the float32
- * accumulators are flushed into the float64 map); each chunk's corner rays
+ * memory; never more than 64 cells per map pixel or 2^30 cells, after which
+ * the float32 accumulators are flushed into a running float-float sum); each
+ * chunk's corner rays
  * are deflected and each cell's mapped
  * quadrilateral is apportioned over the pixels it overlaps (signed-area
  * fraction, Sec. 2.3), accumulating
  *     map[pix] = sum_cells h^2 * a_pix / A_P / S*     (S* = pixel area).
  * Cells whose pixel bounding box spans more than bbox_cap_px pixels on a side
  * are dropped and booked in the ledger (bbox_cap_px = 0: no cap).
- *   map_out: dev npy x npx (overwritten); stats: host or NULL.
+ *   map_out: dev npy x npx (overwritten; between chunks it holds the running
+ *   sum as float pairs, so its contents are the map only once the call has
+ *   returned LENS_OK); stats: host or NULL.
  * Synchronises `stream` at the end. */
 lens_status lens_ipm_map(lens_plan* plan, const lens_grid* grid,
                          const lens_box* box, int npx, int npy,
